@@ -1,0 +1,278 @@
+/*
+ * nbody_oracle.c -- the reference ("oracle") for the direct-sum N-body method
+ * with velocity-Verlet integration studied in arXiv:2112.15079.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously correct
+ * CPU statement of what the CUDA library computes.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark load it.  It shares no
+ * code, header, constant or helper with the CUDA library, and the CUDA
+ * library never calls it.
+ *
+ * Arithmetic: IEEE binary64 throughout.  Build with -O2 -ffp-contract=off
+ * and without -ffast-math, so every expression rounds exactly as written.
+ * An optional -fopenmp build parallelises only the outer loop over target
+ * bodies p; each p owns its accumulator and visits j in ascending order, so
+ * that build is bitwise identical to the single-threaded one.
+ *
+ * Notation (paper Section 2): bodies p, j = 0..n-1, position r_p = (x,y,z),
+ * mass m_j, gravitational constant G, step size dt.  "Eq. 1" is the
+ * direct-sum acceleration, "Eq. 3"/"Eq. 4" the velocity-Verlet position and
+ * velocity updates.  The paper uses no softening; the pair j == p is left out
+ * by its index, as the sum in Eq. 1 states.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Eq. 1: acceleration of body p,
+ *   a_p = sum_{j != p} G m_j (r_j - r_p) / |r_j - r_p|^3,
+ * summed over j in ascending order.  rows: the target bodies to evaluate
+ * (n_rows of them, out arrays indexed like rows); rows == NULL means all n. */
+static void accel_rows(int64_t n, double G, const double *x, const double *y,
+                       const double *z, const double *m, int64_t n_rows,
+                       const int64_t *rows, double *ax, double *ay,
+                       double *az) {
+  int64_t k;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (k = 0; k < n_rows; k++) {
+    const int64_t p = rows ? rows[k] : k;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      if (j == p) continue;
+      const double dx = x[j] - x[p];
+      const double dy = y[j] - y[p];
+      const double dz = z[j] - z[p];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double s = 1.0 / (r2 * sqrt(r2)); /* |d|^-3 */
+      const double f = G * m[j] * s;
+      sx += f * dx;
+      sy += f * dy;
+      sz += f * dz;
+    }
+    ax[k] = sx;
+    ay[k] = sy;
+    az[k] = sz;
+  }
+}
+
+/* Eq. 1 for every body. */
+void oracle_accel(int64_t n, double G, const double *x, const double *y,
+                  const double *z, const double *m, double *ax, double *ay,
+                  double *az) {
+  accel_rows(n, G, x, y, z, m, n, NULL, ax, ay, az);
+}
+
+/* Eq. 1 for the listed target bodies only (sampled rows at large n). */
+void oracle_accel_rows(int64_t n, double G, const double *x, const double *y,
+                       const double *z, const double *m, int64_t n_rows,
+                       const int64_t *rows, double *ax, double *ay,
+                       double *az) {
+  accel_rows(n, G, x, y, z, m, n_rows, rows, ax, ay, az);
+}
+
+/* Eqs. 3-4, n_steps velocity-Verlet steps of size dt, in place.
+ * On entry (ax,ay,az) must hold a_i = Eq. 1 evaluated at the entry
+ * positions; on return it holds the acceleration at the returned positions.
+ * Per step:
+ *   Eq. 3: r_{i+1} = r_i + v_i dt + (1/2) a_i dt^2
+ *   Eq. 1: a_{i+1} = A(r_{i+1})
+ *   Eq. 4: v_{i+1} = v_i + (1/2) (a_i + a_{i+1}) dt
+ * Returns 0, or -1 if scratch could not be allocated. */
+int oracle_verlet(int64_t n, double G, double dt, int64_t n_steps, double *x,
+                  double *y, double *z, double *vx, double *vy, double *vz,
+                  const double *m, double *ax, double *ay, double *az) {
+  double *nx = (double *)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
+  if (!nx) return -1;
+  double *ny = nx + n, *nz = nx + 2 * n;
+  const double h = 0.5 * dt * dt;
+  for (int64_t step = 0; step < n_steps; step++) {
+    for (int64_t p = 0; p < n; p++) { /* Eq. 3 */
+      x[p] = x[p] + vx[p] * dt + h * ax[p];
+      y[p] = y[p] + vy[p] * dt + h * ay[p];
+      z[p] = z[p] + vz[p] * dt + h * az[p];
+    }
+    oracle_accel(n, G, x, y, z, m, nx, ny, nz); /* Eq. 1 */
+    for (int64_t p = 0; p < n; p++) { /* Eq. 4 */
+      vx[p] = vx[p] + 0.5 * (ax[p] + nx[p]) * dt;
+      vy[p] = vy[p] + 0.5 * (ay[p] + ny[p]) * dt;
+      vz[p] = vz[p] + 0.5 * (az[p] + nz[p]) * dt;
+      ax[p] = nx[p];
+      ay[p] = ny[p];
+      az[p] = nz[p];
+    }
+  }
+  free(nx);
+  return 0;
+}
+
+/* Neumaier's compensated summation: running (sum, compensation). */
+static void neumaier_add(double *sum, double *comp, double v) {
+  const double t = *sum + v;
+  if (fabs(*sum) >= fabs(v))
+    *comp += (*sum - t) + v;
+  else
+    *comp += (v - t) + *sum;
+  *sum = t;
+}
+
+/* Total energy, the accuracy criterion of Section 2 and Section 4:
+ *   E_kin = sum_p (1/2) m_p |v_p|^2
+ *   E_pot = - sum_{p < j} G m_p m_j / |r_j - r_p|
+ * Both sums use Neumaier summation, pairs visited p ascending then j > p
+ * ascending. */
+void oracle_energy(int64_t n, double G, const double *x, const double *y,
+                   const double *z, const double *vx, const double *vy,
+                   const double *vz, const double *m, double *e_kin,
+                   double *e_pot) {
+  double ks = 0.0, kc = 0.0, ps = 0.0, pc = 0.0;
+  for (int64_t p = 0; p < n; p++) {
+    const double v2 = vx[p] * vx[p] + vy[p] * vy[p] + vz[p] * vz[p];
+    neumaier_add(&ks, &kc, 0.5 * m[p] * v2);
+  }
+  for (int64_t p = 0; p < n; p++) {
+    for (int64_t j = p + 1; j < n; j++) {
+      const double dx = x[j] - x[p];
+      const double dy = y[j] - y[p];
+      const double dz = z[j] - z[p];
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      neumaier_add(&ps, &pc, -(G * m[p] * m[j] / r));
+    }
+  }
+  *e_kin = ks + kc;
+  *e_pot = ps + pc;
+}
+
+/* Vector-Jacobian product of Eq. 1, accumulated into (rx,ry,rz) and gm.
+ * With d = r_j - r_q and the pair kernel f(d) = d / |d|^3, the Jacobian of f
+ * is the symmetric 3x3 matrix
+ *   K(d) = I / |d|^3 - 3 d d^T / |d|^5,        K(-d) = K(d).
+ * dA_p/dr_q = G m_q K(r_q - r_p) for q != p and -G sum_j m_j K(r_j - r_p)
+ * for q == p, so for an adjoint vector w on the accelerations
+ *   (J^T w)_q  = G sum_{j != q} K(r_j - r_q) (m_q w_j - m_j w_q),
+ *   (dA/dm)^T w at q = G sum_{p != q} w_p . (r_q - r_p) / |r_q - r_p|^3.
+ * K is formed explicitly per pair, j ascending. */
+void oracle_vjp(int64_t n, double G, const double *x, const double *y,
+                const double *z, const double *m, const double *wx,
+                const double *wy, const double *wz, double *rx, double *ry,
+                double *rz, double *gm) {
+  int64_t q;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (q = 0; q < n; q++) {
+    double sx = 0.0, sy = 0.0, sz = 0.0, sm = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      if (j == q) continue;
+      const double d[3] = {x[j] - x[q], y[j] - y[q], z[j] - z[q]};
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const double r = sqrt(r2);
+      const double i3 = 1.0 / (r2 * r); /* |d|^-3 */
+      const double i5 = i3 / r2;        /* |d|^-5 */
+      double K[3][3];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+          K[a][b] = (a == b ? i3 : 0.0) - 3.0 * d[a] * d[b] * i5;
+      const double u[3] = {m[q] * wx[j] - m[j] * wx[q],
+                           m[q] * wy[j] - m[j] * wy[q],
+                           m[q] * wz[j] - m[j] * wz[q]};
+      sx += G * (K[0][0] * u[0] + K[0][1] * u[1] + K[0][2] * u[2]);
+      sy += G * (K[1][0] * u[0] + K[1][1] * u[1] + K[1][2] * u[2]);
+      sz += G * (K[2][0] * u[0] + K[2][1] * u[1] + K[2][2] * u[2]);
+      /* w_j . (r_q - r_j) |r_q - r_j|^-3 = -(w_j . d) i3 */
+      sm += -G * (wx[j] * d[0] + wy[j] * d[1] + wz[j] * d[2]) * i3;
+    }
+    rx[q] += sx;
+    ry[q] += sy;
+    rz[q] += sz;
+    gm[q] += sm;
+  }
+}
+
+/* Gradient of a loss L(r_T, v_T) with respect to (r_0, v_0, m) through T
+ * velocity-Verlet steps (Eqs. 1, 3, 4), by the discrete adjoint of exactly
+ * that recurrence.  Reverse sweep, adjoints rho = dL/dr, nu = dL/dv,
+ * alpha = dL/da:
+ *   start rho = dL/dr_T, nu = dL/dv_T, alpha = 0;
+ *   for i = T-1 .. 0:
+ *     alpha += dt/2 nu                 (Eq. 4 of step i feeds a_{i+1})
+ *     rho += J(r_{i+1})^T alpha;  gm += (dA/dm)(r_{i+1})^T alpha
+ *     (rho, nu, alpha) <- (rho, nu + dt rho, dt/2 nu + dt^2/2 rho)
+ *                                      (Eq. 3 and Eq. 4 of step i)
+ *   finally rho += J(r_0)^T alpha;  gm += (dA/dm)(r_0)^T alpha.
+ * The forward trajectory r_0..r_T is stored whole (no checkpointing).
+ * dLdv_T may be NULL (zero).  Outputs are 3n (x block, y block, z block),
+ * 3n and n doubles.  Returns 0, or -1 if memory could not be allocated. */
+int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
+                const double *y0, const double *z0, const double *vx0,
+                const double *vy0, const double *vz0, const double *m,
+                const double *dLdr_T, const double *dLdv_T, double *dLdr0,
+                double *dLdv0, double *dLdm) {
+  const size_t N = (size_t)n;
+  double *traj = (double *)malloc(sizeof(double) * 3 * N * (size_t)(T + 1));
+  double *work = (double *)malloc(sizeof(double) * 9 * N + 8);
+  if (!traj || !work) {
+    free(traj);
+    free(work);
+    return -1;
+  }
+  double *x = work, *y = work + N, *z = work + 2 * N;
+  double *vx = work + 3 * N, *vy = work + 4 * N, *vz = work + 5 * N;
+  double *ax = work + 6 * N, *ay = work + 7 * N, *az = work + 8 * N;
+  memcpy(x, x0, sizeof(double) * N);
+  memcpy(y, y0, sizeof(double) * N);
+  memcpy(z, z0, sizeof(double) * N);
+  memcpy(vx, vx0, sizeof(double) * N);
+  memcpy(vy, vy0, sizeof(double) * N);
+  memcpy(vz, vz0, sizeof(double) * N);
+  oracle_accel(n, G, x, y, z, m, ax, ay, az);
+  for (int64_t i = 0; i <= T; i++) {
+    double *r = traj + 3 * N * (size_t)i;
+    memcpy(r, x, sizeof(double) * N);
+    memcpy(r + N, y, sizeof(double) * N);
+    memcpy(r + 2 * N, z, sizeof(double) * N);
+    if (i < T &&
+        oracle_verlet(n, G, dt, 1, x, y, z, vx, vy, vz, m, ax, ay, az) != 0) {
+      free(traj);
+      free(work);
+      return -1;
+    }
+  }
+  /* reuse work as (nu, alpha, nu_next) */
+  double *nu = work, *al = work + 3 * N, *tmp = work + 6 * N;
+  double *rho = dLdr0;
+  memcpy(rho, dLdr_T, sizeof(double) * 3 * N);
+  if (dLdv_T)
+    memcpy(nu, dLdv_T, sizeof(double) * 3 * N);
+  else
+    memset(nu, 0, sizeof(double) * 3 * N);
+  memset(al, 0, sizeof(double) * 3 * N);
+  memset(dLdm, 0, sizeof(double) * N);
+  for (int64_t i = T - 1; i >= 0; i--) {
+    for (size_t k = 0; k < 3 * N; k++) al[k] += 0.5 * dt * nu[k];
+    const double *r = traj + 3 * N * (size_t)(i + 1);
+    oracle_vjp(n, G, r, r + N, r + 2 * N, m, al, al + N, al + 2 * N, rho,
+               rho + N, rho + 2 * N, dLdm);
+    for (size_t k = 0; k < 3 * N; k++) {
+      tmp[k] = nu[k] + dt * rho[k];
+      al[k] = 0.5 * dt * nu[k] + 0.5 * dt * dt * rho[k];
+    }
+    memcpy(nu, tmp, sizeof(double) * 3 * N);
+  }
+  oracle_vjp(n, G, traj, traj + N, traj + 2 * N, m, al, al + N, al + 2 * N,
+             rho, rho + N, rho + 2 * N, dLdm);
+  memcpy(dLdv0, nu, sizeof(double) * 3 * N);
+  free(traj);
+  free(work);
+  return 0;
+}
+
+/* 1 when built with OpenMP, else 0; and the thread count it would use. */
+int oracle_openmp_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 0;
+#endif
+}

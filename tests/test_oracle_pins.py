@@ -1,0 +1,381 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: exact
+hand-derived values (tests/golden), closed forms of special configurations,
+conservation laws and symmetries of Eqs. 1, 3, 4, convergence orders, and
+finite differences of the oracle's own forward map for the adjoint.  These
+run on the CPU (no GPU marker).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_15079_gb300 import inputs
+
+EPS = np.finfo(np.float64).eps
+
+
+def _read_records(path):
+    out = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                out.append(line.split())
+    return out
+
+
+def _perm(r, k):
+    """Exact axis permutation (x,y,z) -> rows rolled by k."""
+    return np.roll(r, k, axis=0)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 1: hand cases, closed forms, symmetry
+# ---------------------------------------------------------------------------
+
+def test_three_body_hand_cases(golden_dir):
+    cfg = _read_records(os.path.join(golden_dir, "three_body_hand_config.txt"))
+    exp = _read_records(os.path.join(golden_dir, "three_body_hand.txt"))
+    cases = sorted({c[0] for c in cfg})
+    comp = {"x": 0, "y": 1, "z": 2}
+    for case in cases:
+        rows = [c for c in cfg if c[0] == case]
+        m = np.array([float(Fraction(c[2])) for c in rows])
+        r = np.array([[float(Fraction(c[3 + k])) for c in rows] for k in range(3)])
+        want = np.zeros((3, len(rows)))
+        for e in exp:
+            if e[0] == case:
+                want[comp[e[2]], int(e[1])] = float(Fraction(e[3]))
+        for k in range(3):  # every component path
+            got = oracle.accel(1.0, _perm(r, k), m)
+            np.testing.assert_allclose(got, _perm(want, k), rtol=0, atol=4 * EPS * np.abs(want).max())
+
+
+def test_equal_distance_closed_form():
+    """Bodies with all pairwise distances equal to L (equilateral triangle,
+    regular tetrahedron): Eq. 1 reduces to a_p = -(G M / L^3)(r_p - r_cm)
+    for any masses, M the total mass."""
+    G = 0.37
+    tri = np.array([[1.0, -0.5, -0.5], [0.0, math.sqrt(3) / 2, -math.sqrt(3) / 2], [0.0, 0.0, 0.0]]) * 2.3
+    tet = np.array([[1.0, 1.0, -1.0, -1.0], [1.0, -1.0, 1.0, -1.0], [1.0, -1.0, -1.0, 1.0]]) * 0.7 + 3.0
+    for r, m in ((tri, np.array([1.0, 2.5, 0.3])), (tet, np.array([0.2, 1.0, 3.0, 0.01]))):
+        L = np.linalg.norm(r[:, 0] - r[:, 1])
+        M = m.sum()
+        rcm = (r * m).sum(axis=1, keepdims=True) / M
+        want = -(G * M / L**3) * (r - rcm)
+        got = oracle.accel(G, r, m)
+        np.testing.assert_allclose(got, want, rtol=0, atol=64 * EPS * np.abs(want).max())
+
+
+@pytest.mark.parametrize("n_ring", [3, 7, 64, 1000])
+def test_ngon_ring_closed_form(n_ring):
+    """Regular n-gon of equal masses m at radius R around a central mass Mc:
+    every ring body is pulled toward the centre with
+      |a| = G Mc / R^2 + (G m / R^2) sum_{k=1}^{n-1} 1 / (4 sin(pi k / n)),
+    the tangential parts cancel, and the centre feels no force."""
+    G, R, m, Mc = 2.9591220828e-4, 1.7, 3e-6, 1.0
+    th = 2 * np.pi * np.arange(n_ring) / n_ring
+    r = np.concatenate([np.zeros((3, 1)), np.stack([R * np.cos(th), R * np.sin(th), 0 * th])], axis=1)
+    mass = np.concatenate([[Mc], np.full(n_ring, m)])
+    k = np.arange(1, n_ring)
+    radial = G * Mc / R**2 + G * m / R**2 * np.sum(1.0 / (4.0 * np.sin(np.pi * k / n_ring)))
+    for p in range(3):
+        a = _perm(oracle.accel(G, _perm(r, p), mass), -p)
+        ring = a[:, 1:]
+        inward = -(ring[0] * np.cos(th) + ring[1] * np.sin(th))
+        tangential = -ring[0] * np.sin(th) + ring[1] * np.cos(th)
+        np.testing.assert_allclose(inward, radial, rtol=1e-13)
+        assert np.abs(tangential).max() <= 1e-12 * radial
+        assert np.abs(ring[2]).max() == 0.0
+        assert np.abs(a[:, 0]).max() <= 1e-12 * G * m * n_ring / R**2
+
+
+def test_momentum_conservation_antisymmetry():
+    """Pairwise antisymmetry of Eq. 1: sum_p m_p a_p = 0 up to rounding."""
+    s = inputs.solar_system(400, seed=11)
+    a = oracle.accel(s.G, s.r, s.m)
+    ma = a * s.m
+    total = np.abs(ma.sum(axis=1))
+    scale = np.abs(ma).sum(axis=1)
+    assert np.all(total <= 64 * EPS * scale)
+
+
+def test_accel_rows_matches_full():
+    s = inputs.solar_system(500, seed=3)
+    rows = np.array([0, 1, 30, 131, 250, 499])
+    full = oracle.accel(s.G, s.r, s.m)
+    part = oracle.accel_rows(s.G, s.r, s.m, rows)
+    assert np.array_equal(full[:, rows], part)
+
+
+def test_openmp_build_bitwise_identical():
+    s = inputs.solar_system(1500, seed=5)
+    a1 = oracle.accel(s.G, s.r, s.m, openmp=False)
+    a2 = oracle.accel(s.G, s.r, s.m, openmp=True)
+    assert np.array_equal(a1, a2)
+    out1 = oracle.verlet(s.G, s.dt, 3, s.r, s.v, s.m, openmp=False)
+    out2 = oracle.verlet(s.G, s.dt, 3, s.r, s.v, s.m, openmp=True)
+    for x, y in zip(out1, out2):
+        assert np.array_equal(x, y)
+
+
+# ---------------------------------------------------------------------------
+# Eqs. 3-4: hand steps, Kepler closed forms, convergence order, reversibility
+# ---------------------------------------------------------------------------
+
+def test_verlet_two_body_hand(golden_dir):
+    recs = _read_records(os.path.join(golden_dir, "verlet_two_body_hand.txt"))
+    r = np.array([[0.0, 2.0], [0.0, 0.0], [0.0, 0.0]])
+    v = np.zeros((3, 2))
+    m = np.array([1.0, 1.0])
+    for k in range(3):
+        rr, vv, aa = _perm(r, k), _perm(v, k), None
+        states = {}
+        for step in (1, 2):
+            rr, vv, aa = oracle.verlet(1.0, 1.0, 1, rr, vv, m, aa)
+            states[step] = (_perm(rr, -k), _perm(vv, -k), _perm(aa, -k))
+        for st, body, q, val in recs:
+            rq, vq, aq = states[int(st)]
+            got = {"x": rq, "v": vq, "a": aq}[q][0, int(body)]
+            want = float(Fraction(val))
+            assert abs(got - want) <= 8 * EPS * max(1.0, abs(want)), (st, body, q, got, want)
+        for st in (1, 2):  # y and z stay exactly zero
+            for arr in states[st]:
+                assert np.all(arr[1:] == 0.0)
+
+
+def _two_body(m1, m2, a_sep, e, G):
+    """Barycentric two-body state at periapsis of an orbit with semi-major
+    axis a_sep and eccentricity e (vis-viva speed)."""
+    M = m1 + m2
+    d = a_sep * (1 - e)
+    vrel = math.sqrt(G * M * (1 + e) / (a_sep * (1 - e)))
+    r = np.array([[-m2 / M * d, m1 / M * d], [0.0, 0.0], [0.0, 0.0]])
+    v = np.array([[0.0, 0.0], [-m2 / M * vrel, m1 / M * vrel], [0.0, 0.0]])
+    return r, v, np.array([m1, m2])
+
+
+def test_kepler_energy_closed_form():
+    """E = -G m1 m2 / (2a) for a bound two-body orbit (any eccentricity)."""
+    G = 2.9591220828e-4
+    for e in (0.0, 0.3, 0.7):
+        r, v, m = _two_body(1.0, 3e-3, 1.3, e, G)
+        ek, ep = oracle.energy(G, r, v, m)
+        want = -G * m[0] * m[1] / (2 * 1.3)
+        assert abs((ek + ep) - want) <= 1e-13 * abs(want)
+        assert abs(ep - (-G * m[0] * m[1] / (1.3 * (1 - e)))) <= 1e-14 * abs(ep)
+
+
+def test_three_body_potential_hand():
+    """Collinear hand case: E_pot = -(1*2/1 + 1*3/3 + 2*3/2) = -6 (G = 1)."""
+    r = np.array([[0.0, 1.0, 3.0], [0.0] * 3, [0.0] * 3])
+    ek, ep = oracle.energy(1.0, r, np.ones((3, 3)), np.array([1.0, 2.0, 3.0]))
+    assert ep == -6.0
+    assert ek == 0.5 * 3 * (1 + 2 + 3)
+
+
+def _period_from_run(G, r, v, m, dt, n_steps):
+    """Time at which the relative separation vector first completes 2 pi."""
+    rr, vv, aa = r, v, None
+    prev = 0.0
+    for i in range(1, n_steps + 1):
+        rr, vv, aa = oracle.verlet(G, dt, 1, rr, vv, m, aa)
+        d = rr[:, 1] - rr[:, 0]
+        ang = math.atan2(d[1], d[0]) % (2 * math.pi)
+        if i > 10 and ang < prev:  # wrapped through 2 pi
+            frac = (2 * math.pi - prev) / (2 * math.pi - prev + ang)
+            return (i - 1 + frac) * dt
+        prev = ang
+    raise AssertionError("no full revolution")
+
+
+def test_kepler_period_second_order():
+    """Circular orbit: the measured period tends to 2 pi sqrt(a^3 / G M) and its
+    error falls as dt^2 (Verlet is second order, Section 2)."""
+    G, a = 2.9591220828e-4, 1.0
+    r, v, m = _two_body(1.0, 1e-3, a, 0.0, G)
+    P = 2 * math.pi * math.sqrt(a**3 / (G * m.sum()))
+    errs = []
+    for dt in (4.0, 2.0, 1.0):
+        Pn = _period_from_run(G, r, v, m, dt, int(1.2 * P / dt))
+        errs.append(abs(Pn - P))
+    assert errs[-1] < 1e-3 * P
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.0 < e1 / e2 < 5.0, errs
+
+
+def test_kepler_energy_error_second_order():
+    """Eccentric orbit: the largest energy error over one period shrinks as dt^2."""
+    G, a, e = 2.9591220828e-4, 1.0, 0.5
+    r, v, m = _two_body(1.0, 1e-3, a, e, G)
+    P = 2 * math.pi * math.sqrt(a**3 / (G * m.sum()))
+    E0 = sum(oracle.energy(G, r, v, m))
+    errs = []
+    for dt in (2.0, 1.0, 0.5):
+        rr, vv, aa = r, v, None
+        worst = 0.0
+        for _ in range(int(P / dt)):
+            rr, vv, aa = oracle.verlet(G, dt, 1, rr, vv, m, aa)
+            worst = max(worst, abs(sum(oracle.energy(G, rr, vv, m)) - E0) / abs(E0))
+        errs.append(worst)
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.0 < e1 / e2 < 5.0, errs
+
+
+def test_circular_orbit_rigid_rotation_triangle():
+    """Lagrange equilateral triangle spun at w^2 = G M / L^3 rotates rigidly;
+    Verlet keeps the side lengths to O(dt^2)."""
+    G = 1.0
+    L = 1.0
+    r = np.array([[1.0, -0.5, -0.5], [0.0, math.sqrt(3) / 2, -math.sqrt(3) / 2], [0.0, 0.0, 0.0]]) / math.sqrt(3)
+    m = np.array([1.0, 1.0, 1.0])
+    w = math.sqrt(G * m.sum() / L**3)
+    v = np.stack([-w * r[1], w * r[0], 0 * r[0]])
+    devs = []
+    for dt in (0.02, 0.01):
+        rr, vv, _ = oracle.verlet(G, dt, int(2 * math.pi / w / dt), r, v, m)
+        sides = [np.linalg.norm(rr[:, i] - rr[:, j]) for i, j in ((0, 1), (1, 2), (0, 2))]
+        devs.append(max(abs(s - L) for s in sides))
+    assert devs[0] < 1e-3
+    assert 3.0 < devs[0] / devs[1] < 5.0, devs
+
+
+def test_time_reversibility():
+    """Verlet is time-symmetric: n steps with dt then n steps with -dt from
+    (r_n, v_n, a_n) return to (r_0, v_0)."""
+    s = inputs.solar_system(31, seed=21)
+    r, v, a = oracle.verlet(s.G, s.dt, 400, s.r, s.v, s.m)
+    rb, vb, _ = oracle.verlet(s.G, -s.dt, 400, r, v, s.m, a)
+    assert np.abs(rb - s.r).max() <= 1e-12 * np.abs(s.r).max()
+    assert np.abs(vb - s.v).max() <= 1e-12 * np.abs(s.v).max()
+
+
+def test_energy_bounded_no_secular_drift():
+    """31-body system, 3650 steps at dt = 0.1 day: the total energy error stays
+    small and does not grow secularly (symplectic Verlet, Section 4)."""
+    s = inputs.solar_system(31)
+    E0 = sum(oracle.energy(s.G, s.r, s.v, s.m))
+    r, v, a = s.r, s.v, None
+    errs = []
+    for _ in range(73):
+        r, v, a = oracle.verlet(s.G, s.dt, 50, r, v, s.m, a)
+        errs.append((sum(oracle.energy(s.G, r, v, s.m)) - E0) / abs(E0))
+    errs = np.abs(np.array(errs))
+    # The error oscillates with the orbits (peak ~6e-6 on this seed), far inside
+    # the paper's +-0.02 % for the Earth's orbit at dt = 0.1 day (Section 4).
+    assert errs.max() < 1e-5
+    assert errs[-18:].max() < 4 * errs[:18].max() + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (vector-Jacobian product of Eq. 1 and the reverse Verlet sweep)
+# ---------------------------------------------------------------------------
+
+def _separated_cloud(n, seed, box=10.0, min_sep=0.5):
+    rng = np.random.default_rng(seed)
+    pts = []
+    while len(pts) < n:
+        c = rng.uniform(-box / 2, box / 2, 3)
+        if all(np.linalg.norm(c - q) > min_sep for q in pts):
+            pts.append(c)
+    return np.array(pts).T.copy(), rng.uniform(0.1, 2.0, n)
+
+
+def test_vjp_positions_vs_central_difference():
+    """<J^T w, u> against the central difference of Eq. 1 along u; bodies
+    at least 0.5 apart so the O(h^2) truncation stays near 1e-12."""
+    rng = np.random.default_rng(1)
+    r, m = _separated_cloud(40, seed=8)
+    G = 0.8
+    for _ in range(3):
+        w = rng.normal(size=r.shape)
+        u = rng.normal(size=r.shape)
+        rho, _ = oracle.vjp(G, r, m, w)
+        h = 1e-5
+        fd = (oracle.accel(G, r + h * u, m) - oracle.accel(G, r - h * u, m)) / (2 * h)
+        lhs = np.sum(rho * u)
+        rhs = np.sum(w * fd)
+        assert abs(lhs - rhs) <= 1e-7 * np.sum(np.abs(w * fd))
+
+
+def test_vjp_masses_exact_linearity():
+    """Eq. 1 is linear in the masses, so the central difference is exact up to
+    rounding: <w, dA/dm . dm> = <(dA/dm)^T w, dm>."""
+    rng = np.random.default_rng(2)
+    s = inputs.solar_system(40, seed=9)
+    w = rng.normal(size=(3, s.n))
+    dm = rng.uniform(0.5, 1.5, size=s.n) * s.m
+    _, gm = oracle.vjp(s.G, s.r, s.m, w)
+    fd = oracle.accel(s.G, s.r, s.m + dm) - oracle.accel(s.G, s.r, s.m)
+    lhs = np.sum(gm * dm)
+    rhs = np.sum(w * fd)
+    assert abs(lhs - rhs) <= 1e-10 * np.sum(np.abs(w * fd))
+
+
+def test_vjp_pair_closed_form():
+    """Two bodies: (J^T w) and (dA/dm)^T w written out for a single pair."""
+    G = 1.3
+    r = np.array([[0.0, 3.0], [0.0, 4.0], [0.0, 0.0]])  # d = (3,4,0), |d| = 5
+    m = np.array([2.0, 0.5])
+    w = np.array([[1.0, -2.0], [0.5, 1.0], [0.25, 3.0]])
+    rho, gm = oracle.vjp(G, r, m, w)
+    d = np.array([3.0, 4.0, 0.0])
+    K = np.eye(3) / 125.0 - 3.0 * np.outer(d, d) / 3125.0
+    want0 = G * K @ (m[0] * w[:, 1] - m[1] * w[:, 0])
+    want1 = G * K @ (m[1] * w[:, 0] - m[0] * w[:, 1])
+    np.testing.assert_allclose(rho[:, 0], want0, rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(rho[:, 1], want1, rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(gm, [G * w[:, 1] @ (-d) / 125.0, G * w[:, 0] @ d / 125.0], rtol=1e-14)
+
+
+def test_grad_zero_steps_is_identity():
+    s = inputs.solar_system(31, seed=4)
+    rng = np.random.default_rng(3)
+    gr, gv = rng.normal(size=(3, s.n)), rng.normal(size=(3, s.n))
+    dr, dv, dm = oracle.grad(s.G, s.dt, 0, s.r, s.v, s.m, gr, gv)
+    assert np.array_equal(dr, gr) and np.array_equal(dv, gv) and np.all(dm == 0)
+
+
+@pytest.mark.parametrize("T", [1, 2, 25])
+def test_grad_vs_central_difference(T):
+    """dL/d(r0, v0, m) from the reverse sweep against central differences of
+    the oracle's forward map along random directions; L = sum |r_k(T) - t_k|^2
+    over a few bodies plus a velocity term."""
+    s = inputs.solar_system(31, seed=6)
+    G, dt = s.G, 5.0  # a large step makes every term of the sweep matter
+    rng = np.random.default_rng(T)
+    idx = np.array([3, 7, 20])
+    tgt = s.r[:, idx] + 0.01
+    cv = 10.0
+
+    def loss(r, v):
+        return float(np.sum((r[:, idx] - tgt) ** 2) + cv * np.sum(v[:, idx] ** 2))
+
+    rT, vT, _ = oracle.verlet(G, dt, T, s.r, s.v, s.m)
+    gr = np.zeros((3, s.n))
+    gv = np.zeros((3, s.n))
+    gr[:, idx] = 2 * (rT[:, idx] - tgt)
+    gv[:, idx] = 2 * cv * vT[:, idx]
+    dr, dv, dm = oracle.grad(G, dt, T, s.r, s.v, s.m, gr, gv)
+    for trial in range(3):
+        ur = rng.normal(size=(3, s.n))
+        uv = rng.normal(size=(3, s.n)) * 1e-2
+        um = rng.normal(size=s.n) * s.m
+        fd = oracle.fd_grad_dir(loss, G, dt, T, s.r, s.v, s.m, ur, uv, um, h=1e-6)
+        an = np.sum(dr * ur) + np.sum(dv * uv) + np.sum(dm * um)
+        assert abs(an - fd) <= 2e-6 * max(abs(fd), 1e-300) + 1e-12, (trial, an, fd)
+
+
+def test_grad_openmp_identical():
+    s = inputs.solar_system(131, seed=2)
+    rng = np.random.default_rng(0)
+    gr = rng.normal(size=(3, s.n))
+    a = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=False)
+    b = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
