@@ -1,0 +1,173 @@
+/*
+ * nbody.h -- C ABI of the GB300 (sm_103a) direct-sum N-body library.
+ *
+ * The method (arXiv:2112.15079, Section 2):
+ *   Eq. 1   a_p = sum_{j != p} G m_j (r_j - r_p) / |r_j - r_p|^3
+ *   Eq. 3   r_{i+1} = r_i + v_i dt + (1/2) a_i dt^2
+ *   Eq. 4   v_{i+1} = v_i + (1/2) (a_i + a_{i+1}) dt
+ * integrated at a fixed step dt (0.1 day in the paper), with the total
+ * energy as the accuracy criterion (Sections 2 and 4).  No softening: the
+ * pair j == p is excluded by index, and two distinct bodies at the same
+ * position are rejected.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - State is structure-of-arrays FP64 in DEVICE memory owned by the caller:
+ *   x, y, z (positions), vx, vy, vz (velocities), m (masses), each of length
+ *   N = offsets[n_systems].  Several independent systems are stored back to
+ *   back; system s owns bodies [offsets[s], offsets[s+1]).  Bodies of one
+ *   system never interact with bodies of another.
+ * - Vectors of 3N doubles ("3N, x|y|z blocks") hold the x components of all
+ *   N bodies, then all y components, then all z components.
+ * - Units are the caller's; G and dt must be consistent with them.
+ * - Every call returns an nbody_status and never aborts or exits.  Work is
+ *   asynchronous on the context's stream unless a call says "synchronous".
+ *   Faults detected on the device (a non-finite acceleration, a bounded wait
+ *   that ran out) are recorded in device flags and reported by the next
+ *   synchronous call (nbody_sync, nbody_energy, nbody_grad).  A readable
+ *   message is available from nbody_last_error.
+ * - The library owns its scratch, graphs and snapshots; nbody_free releases
+ *   them.  The caller must keep the bound state buffers alive until then.
+ * - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nbody_ctx nbody_ctx; /* opaque, library-owned */
+
+typedef enum {
+  NBODY_OK = 0,
+  NBODY_EINVAL = 1,     /* bad argument (null pointer, size, coincident bodies, ...) */
+  NBODY_ENOMEM = 2,     /* device or host allocation failed */
+  NBODY_ECUDA = 3,      /* a CUDA runtime call failed */
+  NBODY_ENONFINITE = 4, /* an acceleration became NaN/Inf (e.g. a collision) */
+  NBODY_ETIMEOUT = 5    /* a bounded device-side wait ran out */
+} nbody_status;
+
+typedef enum {
+  /* FP64 everywhere: differences, 1/|d|^3, products and sums (Eq. 1). */
+  NBODY_FP64 = 0,
+  /* FP64 state and Verlet update (Eqs. 3-4); r_j - r_p formed from a
+   * hi/lo float split of the FP64 positions (about as exact as the FP64
+   * difference rounded to FP32); 1/|d|^3 and the m_j-weighted terms in
+   * FP32; per-body sums folded into FP64 every 64 terms. */
+  NBODY_MIXED = 1
+} nbody_precision;
+
+typedef struct {
+  double G;           /* gravitational constant, > 0 */
+  double dt;          /* step size, finite and != 0 (negative runs backwards) */
+  int32_t precision;  /* nbody_precision */
+  int32_t ckpt_every; /* adjoint checkpoint interval in steps; 0 selects 100 */
+  int32_t flags;      /* bitwise OR of NBODY_FLAG_* */
+  int32_t reserved;   /* must be 0 */
+} nbody_opts;
+
+/* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
+#define NBODY_FLAG_NO_GRAPH 1
+
+/* Work decomposition of the force kernels (see nbody_set_tiles). */
+typedef struct {
+  int32_t threads;     /* threads per CTA: 64, 128 or 256 */
+  int32_t ipt;         /* target bodies per thread: 1, 2 or 4 */
+  int32_t tj;          /* source bodies per shared-memory stage: multiple of 64, 64..1024 */
+  int32_t jsplit;      /* source chunks per target block, >= 1 (partial sums reduced in fixed order) */
+  int32_t ctas_per_sm; /* resident CTAs per SM of the persistent grid, >= 1 */
+} nbody_tiles;
+
+/* Create a context bound to caller-owned state.
+ *   out        receives the context (set to NULL on failure).
+ *   n_systems  number of independent systems, >= 1.
+ *   offsets    HOST array of n_systems+1 int64: 0 = offsets[0] < offsets[1]
+ *              < ... ; every system holds at least 1 body; N = offsets[n_systems]
+ *              must be < 2^31.
+ *   x..vz      DEVICE arrays of N doubles, updated in place by nbody_step.
+ *   m          DEVICE array of N doubles (masses, >= 0), read at init and by
+ *              nbody_reset; later changes need nbody_reset.
+ *   o          options (copied).
+ *   cuda_stream a cudaStream_t, or NULL for the legacy default stream (the
+ *              context then orders its own private stream after it).
+ * Computes a_0 = Eq. 1 at the initial positions and snapshots (r_0, v_0) for
+ * nbody_grad.  Synchronous.  EINVAL if any pointer is NULL, sizes or options
+ * are out of range, or two bodies of one system share a position. */
+nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offsets,
+                        double *x, double *y, double *z, double *vx, double *vy,
+                        double *vz, const double *m, const nbody_opts *o,
+                        void *cuda_stream);
+
+/* Advance every system by n_steps velocity-Verlet steps (Eqs. 3, 1, 4), in
+ * place.  n_steps == 0 is a no-op; n_steps < 0 is EINVAL.  Asynchronous.
+ * Each step is one launch of the fused force + kick + drift kernel;
+ * consecutive steps are replayed from cached CUDA graphs unless
+ * NBODY_FLAG_NO_GRAPH is set or the stream is already being captured. */
+nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
+
+/* Copy the acceleration at the current positions (Eq. 1, as used by the
+ * last step) into DEVICE arrays ax, ay, az of N doubles.  Asynchronous. */
+nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
+
+/* Re-read the bound state after the caller changed x..vz or m: recompute
+ * a = Eq. 1 at the current positions and re-take the nbody_grad snapshot.
+ * Asynchronous (but validates positions synchronously, like nbody_init). */
+nbody_status nbody_reset(nbody_ctx *ctx);
+
+/* Total energy of each system at the current state (Sections 2 and 4):
+ *   E_s = sum_p (1/2) m_p |v_p|^2 - sum_{p<j} G m_p m_j / |r_j - r_p|,
+ * FP64 with compensated, fixed-order (deterministic) reductions.
+ * e_host: HOST array of n_systems doubles.  Synchronous. */
+nbody_status nbody_energy(nbody_ctx *ctx, double *e_host);
+
+/* Gradient of a loss L(r_T, v_T) through T = n_steps Verlet steps started
+ * from the snapshot (r_0, v_0) taken by nbody_init / nbody_reset, by the
+ * discrete adjoint of Eqs. 1, 3, 4 (reverse sweep with checkpoints every
+ * ckpt_every steps and recomputation in between).  The bound state is not
+ * modified.
+ *   dL_dr_T  DEVICE, 3N (x|y|z blocks): dL/dr_T.
+ *   dL_dv_T  DEVICE, 3N, or NULL for zero.
+ *   dL_dr0, dL_dv0  DEVICE, 3N outputs; dL_dm DEVICE, N output.
+ * Runs in the context's precision.  Synchronous. */
+nbody_status nbody_grad(nbody_ctx *ctx, int64_t n_steps, const double *dL_dr_T,
+                        const double *dL_dv_T, double *dL_dr0, double *dL_dv0,
+                        double *dL_dm);
+
+/* Wait for the context's stream and report device-side faults. Synchronous. */
+nbody_status nbody_sync(nbody_ctx *ctx);
+
+/* Current work decomposition, and an override (validated; EINVAL if out of
+ * range).  Changing tiles drops cached graphs and re-sizes scratch. */
+nbody_status nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *t);
+nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
+
+/* Time each candidate decomposition on the bound state for `probe_steps`
+ * steps and keep the fastest.  The bound state is restored afterwards.
+ * best (HOST, may be NULL) receives the winner, best_ms its time per step.
+ * Synchronous. */
+nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *best,
+                            double *best_ms);
+
+/* Release the context and everything it owns.  NULL is a no-op. */
+void nbody_free(nbody_ctx *ctx);
+
+/* Message of the last failure on ctx; with ctx == NULL, the last failure of
+ * a call that could not return a context (nbody_init) on this thread. */
+const char *nbody_last_error(const nbody_ctx *ctx);
+
+/* Peak-rate microbenchmarks on the current device (instruction throughput,
+ * not part of the method).  HOST out[8] receives, in units of 1e9
+ * lane-operations per second: [0] FP32 FFMA, [1] FP64 DFMA,
+ * [2] MUFU rsqrt.approx.f32, [3] rsqrt.approx.f64, [4] cvt f32<->f64,
+ * [5] packed f32x2 FFMA (lane count), and [6] the mean SM clock in MHz
+ * during the FFMA run, [7] the number of SMs.  Synchronous. */
+nbody_status nbody_peaks(double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

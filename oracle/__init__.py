@@ -11,6 +11,7 @@ Functions (all FP64 numpy arrays, structure-of-arrays):
 
 * ``accel``      -- Eq. 1, the direct-sum acceleration.
 * ``accel_rows`` -- Eq. 1 for a sample of target bodies.
+* ``term_norm``  -- sum of the magnitudes of the terms of Eq. 1 (error scale).
 * ``verlet``     -- Eqs. 3-4, velocity-Verlet steps (Eq. 1 for the force).
 * ``energy``     -- total energy (kinetic, potential), the accuracy criterion
                     of Sections 2 and 4.
@@ -69,6 +70,9 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
             lib.oracle_accel_rows.argtypes = ([_I64, ctypes.c_double] + [_D] * 4
                                               + [_I64, ctypes.POINTER(_I64)] + [_D] * 3)
             lib.oracle_accel_rows.restype = None
+            lib.oracle_term_norm_rows.argtypes = ([_I64, ctypes.c_double] + [_D] * 4
+                                                  + [_I64, ctypes.POINTER(_I64), _D])
+            lib.oracle_term_norm_rows.restype = None
             lib.oracle_verlet.argtypes = ([_I64, ctypes.c_double, ctypes.c_double, _I64]
                                           + [_D] * 10)
             lib.oracle_verlet.restype = ctypes.c_int
@@ -119,6 +123,22 @@ def accel_rows(G: float, r: np.ndarray, m: np.ndarray, rows, openmp: bool = Fals
                                    rows.shape[0], rows.ctypes.data_as(ctypes.POINTER(_I64)),
                                    _c(a[0]), _c(a[1]), _c(a[2]))
     return a
+
+
+def term_norm(G: float, r: np.ndarray, m: np.ndarray, rows=None, openmp: bool = False) -> np.ndarray:
+    """T_p = sum_{j != p} G m_j / |r_j - r_p|^2 (magnitudes of the terms of
+    Eq. 1) for ``rows`` (all bodies when None)."""
+    r = _f64(r)
+    m = _f64(m)
+    n = m.shape[0]
+    if rows is None:
+        rows_p, k = None, n
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        rows_p, k = rows.ctypes.data_as(ctypes.POINTER(_I64)), rows.shape[0]
+    t = np.zeros(k)
+    _lib(openmp).oracle_term_norm_rows(n, G, _c(r[0]), _c(r[1]), _c(r[2]), _c(m), k, rows_p, _c(t))
+    return t
 
 
 def verlet(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: np.ndarray,

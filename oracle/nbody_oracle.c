@@ -74,6 +74,29 @@ void oracle_accel_rows(int64_t n, double G, const double *x, const double *y,
   accel_rows(n, G, x, y, z, m, n_rows, rows, ax, ay, az);
 }
 
+/* Sum of the magnitudes of the terms of Eq. 1 for the listed targets,
+ *   T_p = sum_{j != p} G m_j / |r_j - r_p|^2,
+ * the scale against which a rounding error in a_p is judged when the terms
+ * cancel (condition number of the sum = T_p / |a_p|). */
+void oracle_term_norm_rows(int64_t n, double G, const double *x,
+                           const double *y, const double *z, const double *m,
+                           int64_t n_rows, const int64_t *rows, double *t) {
+  int64_t k;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (k = 0; k < n_rows; k++) {
+    const int64_t p = rows ? rows[k] : k;
+    double s = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      if (j == p) continue;
+      const double dx = x[j] - x[p];
+      const double dy = y[j] - y[p];
+      const double dz = z[j] - z[p];
+      s += G * m[j] / (dx * dx + dy * dy + dz * dz);
+    }
+    t[k] = s;
+  }
+}
+
 /* Eqs. 3-4, n_steps velocity-Verlet steps of size dt, in place.
  * On entry (ax,ay,az) must hold a_i = Eq. 1 evaluated at the entry
  * positions; on return it holds the acceleration at the returned positions.

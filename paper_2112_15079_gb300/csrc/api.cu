@@ -1,0 +1,706 @@
+// Host side of the C ABI declared in include/nbody.h: context lifetime,
+// validation, scratch ownership, work-item tables, CUDA-graph replay of
+// Verlet steps, energy, tiles/autotuning and device-fault reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "nbody.h"
+#include "nbody_internal.h"
+
+using nb::Item;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr int kGraphChunk = 64;  // steps per cached graph (even: stage parity repeats)
+
+struct Grad;  // adjoint workspace (grad.cu)
+
+}  // namespace
+
+struct nbody_ctx {
+  int dev = 0, nsm = 0;
+  int64_t n_sys = 0;
+  std::vector<int64_t> offsets;
+  int32_t N = 0;
+  double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
+  const double *m = nullptr;
+  nbody_opts o{};
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;  // where work runs (user stream, or private when user passed NULL)
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;  // graph capture only
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
+  // scratch
+  std::vector<void *> allocs;
+  double *a = nullptr;               // [3][N] acceleration at the current positions
+  void *stage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][hi|lo or double4]
+  double *R = nullptr;               // [3][N] mixed: FP64 positions of the staged step
+  double *snap = nullptr;            // [6][N] r0, v0 for nbody_grad
+  int32_t *counters = nullptr;       // [0] work, [1] exit
+  unsigned *flags = nullptr;
+  int64_t *offsets_dev = nullptr;
+  double *e_body = nullptr;          // [2][N]
+  double *e_out = nullptr;           // [2][n_sys]
+  Item *eitems = nullptr;
+  int n_eitems = 0;
+
+  // tile-dependent scratch
+  nbody_tiles tiles{};
+  Item *items = nullptr;
+  int n_items = 0;
+  int32_t *arrive = nullptr;
+  int n_iblocks = 0;
+  double *partial = nullptr;
+  int partial_rows = 0;
+  size_t smem = 0;
+  int grid = 0;
+
+  std::map<int, cudaGraphExec_t> graphs;
+  std::string err;
+};
+
+namespace {
+
+nbody_status fail(nbody_ctx *c, nbody_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_init_error = buf;
+  return st;
+}
+
+#define NB_CUDA(c, call)                                                                               \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return fail((c), NBODY_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Optional host-side fault injection for tests: NBODY_INJECT_ALLOC_FAIL=k
+// makes the k-th device allocation of a context fail with NBODY_ENOMEM.
+int g_alloc_count = 0;
+
+nbody_status dalloc(nbody_ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  ++g_alloc_count;
+  if (const char *inj = std::getenv("NBODY_INJECT_ALLOC_FAIL")) {
+    if (std::atoi(inj) == g_alloc_count)
+      return fail(c, NBODY_ENOMEM, "injected allocation failure (allocation %d)", g_alloc_count);
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, NBODY_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return NBODY_OK;
+}
+
+void dfree(nbody_ctx *c, void *p) {
+  if (!p) return;
+  cudaFree(p);
+  c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
+}
+
+void drop_graphs(nbody_ctx *c) {
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+// Ordering with the caller's stream when the work runs on a private stream.
+nbody_status begin_work(nbody_ctx *c) {
+  if (c->own_stream) {
+    NB_CUDA(c, cudaEventRecord(c->ev_in, c->user_stream));
+    NB_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  }
+  return NBODY_OK;
+}
+nbody_status end_work(nbody_ctx *c) {
+  if (c->own_stream) {
+    NB_CUDA(c, cudaEventRecord(c->ev_out, c->stream));
+    NB_CUDA(c, cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+  }
+  return NBODY_OK;
+}
+
+bool tiles_valid(const nbody_tiles &t, int precision) {
+  return nb::step_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 1024 &&
+         t.tj % 64 == 0 && t.jsplit >= 1 && t.jsplit <= 1024 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
+}
+
+nbody_tiles default_tiles(const nbody_ctx *c) {
+  nbody_tiles t{};
+  if (c->o.precision == NBODY_FP64) {
+    t.threads = 128;
+    t.ipt = 1;
+    t.tj = 256;
+    t.ctas_per_sm = 4;
+  } else {
+    t.threads = 256;
+    t.ipt = 2;
+    t.tj = 256;
+    t.ctas_per_sm = 2;
+  }
+  // Enough items for an even spread over the persistent grid: aim for about
+  // 8 items per resident CTA, splitting the sources of each target block
+  // into chunks of at least 128 bodies.
+  int64_t largest = 0, blocks = 0;
+  const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
+  for (int64_t s = 0; s < c->n_sys; ++s) {
+    const int64_t ns = c->offsets[s + 1] - c->offsets[s];
+    largest = std::max(largest, ns);
+    blocks += (ns + B - 1) / B;
+  }
+  const int64_t target = 8LL * c->nsm * t.ctas_per_sm;
+  int64_t S = (target + blocks - 1) / std::max<int64_t>(blocks, 1);
+  S = std::min<int64_t>(S, std::max<int64_t>(1, largest / 128));
+  t.jsplit = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(S, 64)));
+  return t;
+}
+
+// (Re)build the work items for the current tiles.
+nbody_status build_items(nbody_ctx *c) {
+  drop_graphs(c);
+  dfree(c, c->items);
+  dfree(c, c->arrive);
+  dfree(c, c->partial);
+  c->items = nullptr;
+  c->arrive = nullptr;
+  c->partial = nullptr;
+  const nbody_tiles &t = c->tiles;
+  const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
+  std::vector<Item> items;
+  int ib = 0, rows = 1;
+  for (int64_t s = 0; s < c->n_sys; ++s) {
+    const int64_t b = c->offsets[s], e = c->offsets[s + 1], ns = e - b;
+    const int64_t S = std::min<int64_t>(t.jsplit, ns);
+    rows = std::max<int>(rows, static_cast<int>(S));
+    for (int64_t i0 = b; i0 < e; i0 += B, ++ib) {
+      const int64_t i1 = std::min(i0 + B, e);
+      for (int64_t k = 0; k < S; ++k) {
+        Item it;
+        it.i0 = static_cast<int32_t>(i0);
+        it.i1 = static_cast<int32_t>(i1);
+        it.j0 = static_cast<int32_t>(b + ns * k / S);
+        it.j1 = static_cast<int32_t>(b + ns * (k + 1) / S);
+        it.slot = static_cast<int32_t>(k);
+        it.nsplit = static_cast<int32_t>(S);
+        it.ib = ib;
+        it.sys = static_cast<int32_t>(s);
+        items.push_back(it);
+      }
+    }
+  }
+  // Longest first (cost = targets x sources); ties keep construction order.
+  std::stable_sort(items.begin(), items.end(), [](const Item &p, const Item &q) {
+    return static_cast<int64_t>(p.i1 - p.i0) * (p.j1 - p.j0) > static_cast<int64_t>(q.i1 - q.i0) * (q.j1 - q.j0);
+  });
+  c->n_items = static_cast<int>(items.size());
+  c->n_iblocks = ib;
+  c->partial_rows = rows;
+  nbody_status st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->items), sizeof(Item) * items.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->arrive), sizeof(int32_t) * ib)) != NBODY_OK) return st;
+  if (rows > 1 &&
+      (st = dalloc(c, reinterpret_cast<void **>(&c->partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
+          NBODY_OK)
+    return st;
+  NB_CUDA(c, cudaMemcpy(c->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemset(c->arrive, 0, sizeof(int32_t) * ib));
+  c->smem = nb::step_smem_bytes(c->o.precision, t.tj);
+  c->grid = static_cast<int>(std::min<int64_t>(c->n_items, static_cast<int64_t>(c->nsm) * t.ctas_per_sm));
+  NB_CUDA(c, nb::launch_step(c->o.precision, t.threads, t.ipt, 0, c->smem, nb::StepArgs{}, nullptr));
+  return NBODY_OK;
+}
+
+// Pointers of one state (the bound caller state, or the adjoint's shadow).
+struct State {
+  double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
+};
+
+State bound_state(nbody_ctx *c) {
+  const size_t N = c->N;
+  return {c->x, c->y, c->z, c->vx, c->vy, c->vz, c->a, c->a + N, c->a + 2 * N};
+}
+
+nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check) {
+  const size_t N = c->N;
+  nb::PrepArgs p{};
+  p.x = s.x; p.y = s.y; p.z = s.z; p.vx = s.vx; p.vy = s.vy; p.vz = s.vz;
+  p.ax = s.ax; p.ay = s.ay; p.az = s.az;
+  p.m = c->m;
+  p.stage_a = c->stage[0][0];
+  p.stage_b = c->stage[0][1];
+  p.Rx = c->R;
+  p.Ry = c->R ? c->R + N : nullptr;
+  p.Rz = c->R ? c->R + 2 * N : nullptr;
+  p.flags = c->flags;
+  p.N = c->N;
+  p.drift = drift;
+  p.check = check;
+  p.G = c->o.G;
+  p.dt = c->o.dt;
+  p.half_dt2 = 0.5 * c->o.dt * c->o.dt;
+  return p;
+}
+
+nb::StepArgs step_args(nbody_ctx *c, const State &s, int cur, int mode) {
+  const size_t N = c->N;
+  nb::StepArgs a{};
+  a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
+  a.ax = s.ax; a.ay = s.ay; a.az = s.az;
+  a.cur_a = c->stage[cur][0];
+  a.cur_b = c->stage[cur][1];
+  a.nxt_a = c->stage[1 - cur][0];
+  a.nxt_b = c->stage[1 - cur][1];
+  a.Rx = c->R;
+  a.Ry = c->R ? c->R + N : nullptr;
+  a.Rz = c->R ? c->R + 2 * N : nullptr;
+  a.partial = c->partial;
+  a.arrive = c->arrive;
+  a.work_ctr = c->counters;
+  a.exit_ctr = c->counters + 1;
+  a.flags = c->flags;
+  a.items = c->items;
+  a.n_items = c->n_items;
+  a.N = c->N;
+  a.tj = c->tiles.tj;
+  a.mode = mode;
+  a.dt = c->o.dt;
+  a.half_dt = 0.5 * c->o.dt;
+  a.half_dt2 = 0.5 * c->o.dt * c->o.dt;
+  return a;
+}
+
+nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) {
+  for (int i = 0; i < n; ++i) {
+    const nb::StepArgs a = step_args(c, s, i & 1, nb::kModeStep);
+    NB_CUDA(c, nb::launch_step(c->o.precision, c->tiles.threads, c->tiles.ipt, c->grid, c->smem, a, st));
+  }
+  return NBODY_OK;
+}
+
+nbody_status graph_for(nbody_ctx *c, int n, cudaGraphExec_t *out) {
+  auto f = c->graphs.find(n);
+  if (f != c->graphs.end()) {
+    *out = f->second;
+    return NBODY_OK;
+  }
+  NB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  nbody_status st = launch_steps(c, bound_state(c), n, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != NBODY_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, NBODY_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, NBODY_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  c->graphs[n] = ex;
+  *out = ex;
+  return NBODY_OK;
+}
+
+// Force-only launch: a = Eq. 1 at the positions staged in stage[0].
+nbody_status launch_force(nbody_ctx *c, const State &s) {
+  const nb::StepArgs a = step_args(c, s, 0, nb::kModeForce);
+  NB_CUDA(c, nb::launch_step(c->o.precision, c->tiles.threads, c->tiles.ipt, c->grid, c->smem, a, c->stream));
+  return NBODY_OK;
+}
+
+// Synchronise and turn device flags into a status (flags are cleared).
+nbody_status check_flags(nbody_ctx *c, bool init_phase) {
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  unsigned f = 0;
+  NB_CUDA(c, cudaMemcpy(&f, c->flags, sizeof f, cudaMemcpyDeviceToHost));
+  if (f) NB_CUDA(c, cudaMemset(c->flags, 0, sizeof(unsigned)));
+  if (f & nb::kFlagBadInput)
+    return fail(c, NBODY_EINVAL, "invalid state: non-finite position/velocity or negative/non-finite mass");
+  if (f & nb::kFlagTimeout) return fail(c, NBODY_ETIMEOUT, "a bounded device wait ran out (kernel wound down)");
+  if (f & nb::kFlagNonFinite) {
+    if (init_phase)
+      return fail(c, NBODY_EINVAL,
+                  "non-finite acceleration at the given positions: two bodies of one system coincide");
+    return fail(c, NBODY_ENONFINITE, "an acceleration became non-finite (close encounter or collision)");
+  }
+  return NBODY_OK;
+}
+
+nbody_status snapshot(nbody_ctx *c) {
+  const size_t N = c->N, b = sizeof(double) * N;
+  double *src[6] = {c->x, c->y, c->z, c->vx, c->vy, c->vz};
+  for (int k = 0; k < 6; ++k) NB_CUDA(c, cudaMemcpyAsync(c->snap + k * N, src[k], b, cudaMemcpyDeviceToDevice, c->stream));
+  return NBODY_OK;
+}
+
+// Stage the current positions, compute a = Eq. 1, snapshot; synchronous.
+nbody_status refresh(nbody_ctx *c) {
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  const State s = bound_state(c);
+  NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 0, 1), c->stream));
+  if ((st = launch_force(c, s)) != NBODY_OK) return st;
+  if ((st = snapshot(c)) != NBODY_OK) return st;
+  if ((st = end_work(c)) != NBODY_OK) return st;
+  return check_flags(c, true);
+}
+
+nbody_status alloc_scratch(nbody_ctx *c) {
+  const size_t N = c->N;
+  nbody_status st;
+#define NB_ALLOC(ptr, bytes) \
+  if ((st = dalloc(c, reinterpret_cast<void **>(&(ptr)), (bytes))) != NBODY_OK) return st;
+  NB_ALLOC(c->a, sizeof(double) * 3 * N);
+  if (c->o.precision == NBODY_FP64) {
+    NB_ALLOC(c->stage[0][0], 32 * N);
+    NB_ALLOC(c->stage[1][0], 32 * N);
+  } else {
+    NB_ALLOC(c->stage[0][0], 16 * N);
+    NB_ALLOC(c->stage[0][1], 16 * N);
+    NB_ALLOC(c->stage[1][0], 16 * N);
+    NB_ALLOC(c->stage[1][1], 16 * N);
+    NB_ALLOC(c->R, sizeof(double) * 3 * N);
+  }
+  NB_ALLOC(c->snap, sizeof(double) * 6 * N);
+  NB_ALLOC(c->counters, sizeof(int32_t) * 2);
+  NB_ALLOC(c->flags, sizeof(unsigned));
+  NB_ALLOC(c->offsets_dev, sizeof(int64_t) * (c->n_sys + 1));
+  NB_ALLOC(c->e_body, sizeof(double) * 2 * N);
+  NB_ALLOC(c->e_out, sizeof(double) * 2 * c->n_sys);
+#undef NB_ALLOC
+  NB_CUDA(c, cudaMemset(c->counters, 0, sizeof(int32_t) * 2));
+  NB_CUDA(c, cudaMemset(c->flags, 0, sizeof(unsigned)));
+  NB_CUDA(c, cudaMemcpy(c->offsets_dev, c->offsets.data(), sizeof(int64_t) * (c->n_sys + 1), cudaMemcpyHostToDevice));
+  // energy items: blocks of kEnergyBlock targets against the whole system
+  std::vector<Item> e;
+  for (int64_t s = 0; s < c->n_sys; ++s) {
+    for (int64_t i0 = c->offsets[s]; i0 < c->offsets[s + 1]; i0 += nb::kEnergyBlock) {
+      Item it{};
+      it.i0 = static_cast<int32_t>(i0);
+      it.i1 = static_cast<int32_t>(std::min<int64_t>(i0 + nb::kEnergyBlock, c->offsets[s + 1]));
+      it.j0 = static_cast<int32_t>(c->offsets[s]);
+      it.j1 = static_cast<int32_t>(c->offsets[s + 1]);
+      it.nsplit = 1;
+      it.sys = static_cast<int32_t>(s);
+      e.push_back(it);
+    }
+  }
+  c->n_eitems = static_cast<int>(e.size());
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->eitems), sizeof(Item) * e.size())) != NBODY_OK) return st;
+  NB_CUDA(c, cudaMemcpy(c->eitems, e.data(), sizeof(Item) * e.size(), cudaMemcpyHostToDevice));
+  return NBODY_OK;
+}
+
+void destroy(nbody_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  delete c;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offsets, double *x, double *y, double *z,
+                        double *vx, double *vy, double *vz, const double *m, const nbody_opts *o, void *cuda_stream) {
+  g_init_error.clear();
+  if (!out) return fail(nullptr, NBODY_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_systems < 1) return fail(nullptr, NBODY_EINVAL, "n_systems must be >= 1 (got %lld)", (long long)n_systems);
+  if (!offsets) return fail(nullptr, NBODY_EINVAL, "offsets is NULL");
+  if (!x || !y || !z || !vx || !vy || !vz || !m) return fail(nullptr, NBODY_EINVAL, "a state pointer is NULL");
+  if (!o) return fail(nullptr, NBODY_EINVAL, "opts is NULL");
+  if (offsets[0] != 0) return fail(nullptr, NBODY_EINVAL, "offsets[0] must be 0");
+  for (int64_t s = 0; s < n_systems; ++s)
+    if (offsets[s + 1] <= offsets[s])
+      return fail(nullptr, NBODY_EINVAL, "system %lld is empty or offsets are not increasing", (long long)s);
+  if (offsets[n_systems] >= (int64_t(1) << 31))
+    return fail(nullptr, NBODY_EINVAL, "too many bodies (%lld >= 2^31)", (long long)offsets[n_systems]);
+  if (!(o->G > 0.0) || !std::isfinite(o->G)) return fail(nullptr, NBODY_EINVAL, "G must be finite and > 0");
+  if (!(o->dt != 0.0) || !std::isfinite(o->dt)) return fail(nullptr, NBODY_EINVAL, "dt must be finite and non-zero");
+  if (o->precision != NBODY_FP64 && o->precision != NBODY_MIXED)
+    return fail(nullptr, NBODY_EINVAL, "unknown precision %d", o->precision);
+  if (o->ckpt_every < 0) return fail(nullptr, NBODY_EINVAL, "ckpt_every must be >= 0");
+  if (o->reserved != 0 || (o->flags & ~NBODY_FLAG_NO_GRAPH))
+    return fail(nullptr, NBODY_EINVAL, "unknown flags / reserved field not 0");
+
+  nbody_ctx *c = new (std::nothrow) nbody_ctx;
+  if (!c) return fail(nullptr, NBODY_ENOMEM, "host allocation failed");
+  g_alloc_count = 0;
+  c->n_sys = n_systems;
+  c->offsets.assign(offsets, offsets + n_systems + 1);
+  c->N = static_cast<int32_t>(offsets[n_systems]);
+  c->x = x; c->y = y; c->z = z; c->vx = vx; c->vy = vy; c->vz = vz; c->m = m;
+  c->o = *o;
+  if (c->o.ckpt_every == 0) c->o.ckpt_every = 100;
+  c->user_stream = static_cast<cudaStream_t>(cuda_stream);
+
+  auto bail = [&](nbody_status st) {
+    g_init_error = c->err;
+    destroy(c);
+    return st;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev)) != cudaSuccess) {
+    fail(c, NBODY_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    return bail(NBODY_ECUDA);
+  }
+  // The pointers must be device (or managed) memory of this device.
+  const void *ptrs[7] = {x, y, z, vx, vy, vz, m};
+  for (const void *p : ptrs) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess || (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      fail(c, NBODY_EINVAL, "state pointers must be device memory");
+      return bail(NBODY_EINVAL);
+    }
+  }
+  if (c->user_stream == nullptr) {
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      fail(c, NBODY_ECUDA, "stream creation failed: %s", cudaGetErrorString(e));
+      return bail(NBODY_ECUDA);
+    }
+    c->own_stream = true;
+  } else {
+    c->stream = c->user_stream;
+  }
+  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess) {
+    fail(c, NBODY_ECUDA, "stream/event creation failed: %s", cudaGetErrorString(e));
+    return bail(NBODY_ECUDA);
+  }
+  nbody_status st = alloc_scratch(c);
+  if (st != NBODY_OK) return bail(st);
+  c->tiles = default_tiles(c);
+  if ((st = build_items(c)) != NBODY_OK) return bail(st);
+  if ((st = refresh(c)) != NBODY_OK) return bail(st);
+  *out = c;
+  return NBODY_OK;
+}
+
+nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
+  if (!c) return NBODY_EINVAL;
+  if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
+  if (n_steps == 0) return NBODY_OK;
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  const State s = bound_state(c);
+  NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NB_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+  if ((c->o.flags & NBODY_FLAG_NO_GRAPH) || cs != cudaStreamCaptureStatusNone) {
+    int64_t left = n_steps;
+    while (left > 0) {  // parity restarts at 0 after each even chunk
+      const int n = static_cast<int>(std::min<int64_t>(left, kGraphChunk));
+      if ((st = launch_steps(c, s, n, c->stream)) != NBODY_OK) return st;
+      left -= n;
+    }
+  } else {
+    const int64_t full = n_steps / kGraphChunk;
+    const int rem = static_cast<int>(n_steps % kGraphChunk);
+    cudaGraphExec_t g;
+    if (full > 0) {
+      if ((st = graph_for(c, kGraphChunk, &g)) != NBODY_OK) return st;
+      for (int64_t k = 0; k < full; ++k) NB_CUDA(c, cudaGraphLaunch(g, c->stream));
+    }
+    if (rem > 0) {
+      if ((st = graph_for(c, rem, &g)) != NBODY_OK) return st;
+      NB_CUDA(c, cudaGraphLaunch(g, c->stream));
+    }
+  }
+  return end_work(c);
+}
+
+nbody_status nbody_accel(nbody_ctx *c, double *ax, double *ay, double *az) {
+  if (!c) return NBODY_EINVAL;
+  if (!ax || !ay || !az) return fail(c, NBODY_EINVAL, "output pointer is NULL");
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  const size_t N = c->N, b = sizeof(double) * N;
+  NB_CUDA(c, cudaMemcpyAsync(ax, c->a, b, cudaMemcpyDeviceToDevice, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(ay, c->a + N, b, cudaMemcpyDeviceToDevice, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(az, c->a + 2 * N, b, cudaMemcpyDeviceToDevice, c->stream));
+  return end_work(c);
+}
+
+nbody_status nbody_reset(nbody_ctx *c) {
+  if (!c) return NBODY_EINVAL;
+  return refresh(c);
+}
+
+nbody_status nbody_energy(nbody_ctx *c, double *e_host) {
+  if (!c) return NBODY_EINVAL;
+  if (!e_host) return fail(c, NBODY_EINVAL, "e_host is NULL");
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  const size_t N = c->N;
+  nb::EnergyArgs ea{};
+  ea.x = c->x; ea.y = c->y; ea.z = c->z; ea.vx = c->vx; ea.vy = c->vy; ea.vz = c->vz; ea.m = c->m;
+  ea.e_kin = c->e_body;
+  ea.e_pot = c->e_body + N;
+  ea.items = c->eitems;
+  ea.n_items = c->n_eitems;
+  ea.G = c->o.G;
+  NB_CUDA(c, nb::launch_energy(ea, c->stream));
+  nb::ReduceArgs ra{};
+  ra.e_kin = c->e_body;
+  ra.e_pot = c->e_body + N;
+  ra.offsets = c->offsets_dev;
+  ra.out = c->e_out;
+  ra.n_systems = static_cast<int32_t>(c->n_sys);
+  NB_CUDA(c, nb::launch_energy_reduce(ra, c->stream));
+  std::vector<double> h(2 * c->n_sys);
+  NB_CUDA(c, cudaMemcpyAsync(h.data(), c->e_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+  if ((st = end_work(c)) != NBODY_OK) return st;
+  if ((st = check_flags(c, false)) != NBODY_OK) return st;
+  for (int64_t s = 0; s < c->n_sys; ++s) e_host[s] = h[s] + h[c->n_sys + s];
+  return NBODY_OK;
+}
+
+nbody_status nbody_sync(nbody_ctx *c) {
+  if (!c) return NBODY_EINVAL;
+  return check_flags(c, false);
+}
+
+nbody_status nbody_get_tiles(const nbody_ctx *c, nbody_tiles *t) {
+  if (!c || !t) return NBODY_EINVAL;
+  *t = c->tiles;
+  return NBODY_OK;
+}
+
+nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
+  if (!c) return NBODY_EINVAL;
+  if (!t || !tiles_valid(*t, c->o.precision))
+    return fail(c, NBODY_EINVAL, "invalid tiles (threads 64/128/256, ipt 1/2/4, tj 64..1024 step 64, jsplit 1..1024, ctas_per_sm 1..32)");
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->tiles = *t;
+  return build_items(c);
+}
+
+nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best, double *best_ms) {
+  if (!c) return NBODY_EINVAL;
+  if (probe_steps < 1) return fail(c, NBODY_EINVAL, "probe_steps must be >= 1");
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  const size_t N = c->N, b = sizeof(double) * N;
+  // Save the bound state and a; every candidate starts from it.
+  double *save = nullptr;
+  nbody_status st = dalloc(c, reinterpret_cast<void **>(&save), 9 * b);
+  if (st != NBODY_OK) return st;
+  double *src[9] = {c->x, c->y, c->z, c->vx, c->vy, c->vz, c->a, c->a + N, c->a + 2 * N};
+  for (int k = 0; k < 9; ++k) NB_CUDA(c, cudaMemcpy(save + k * N, src[k], b, cudaMemcpyDeviceToDevice));
+  auto restore = [&]() -> nbody_status {
+    for (int k = 0; k < 9; ++k) NB_CUDA(c, cudaMemcpy(src[k], save + k * N, b, cudaMemcpyDeviceToDevice));
+    return NBODY_OK;
+  };
+  std::vector<nbody_tiles> cand;
+  const nbody_tiles base = default_tiles(c);
+  const int threads_list[3] = {64, 128, 256};
+  const int ipt_list[3] = {1, 2, 4};
+  const int split_mul[4] = {1, 2, 4, 8};
+  for (int th : threads_list)
+    for (int ip : ipt_list) {
+      if (c->o.precision == NBODY_MIXED && th == 64) continue;
+      if (c->o.precision == NBODY_FP64 && ip == 4) continue;
+      for (int sm : split_mul)
+        for (int cps : {1, 2, 4}) {
+          nbody_tiles t = base;
+          t.threads = th;
+          t.ipt = ip;
+          t.ctas_per_sm = cps;
+          // Rescale jsplit so the item count stays comparable, then vary it.
+          const int64_t B0 = static_cast<int64_t>(base.threads) * base.ipt, B = static_cast<int64_t>(th) * ip;
+          int64_t S = std::max<int64_t>(1, base.jsplit * B / B0 * sm / 2);
+          t.jsplit = static_cast<int32_t>(std::min<int64_t>(S, 256));
+          cand.push_back(t);
+        }
+    }
+  cudaEvent_t e0, e1;
+  NB_CUDA(c, cudaEventCreate(&e0));
+  NB_CUDA(c, cudaEventCreate(&e1));
+  nbody_tiles win = c->tiles;
+  double win_ms = 1e300;
+  for (const nbody_tiles &t : cand) {
+    c->tiles = t;
+    if ((st = build_items(c)) != NBODY_OK) break;
+    if ((st = nbody_step(c, 1)) != NBODY_OK) break;  // warm-up (also builds the graph)
+    cudaEventRecord(e0, c->stream);
+    if ((st = nbody_step(c, probe_steps)) != NBODY_OK) break;
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = fail(c, NBODY_ECUDA, "autotune timing failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if ((st = restore()) != NBODY_OK) break;
+    if (ms / probe_steps < win_ms) {
+      win_ms = ms / probe_steps;
+      win = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  nbody_status st2 = restore();
+  dfree(c, save);
+  if (st != NBODY_OK) return st;
+  if (st2 != NBODY_OK) return st2;
+  c->tiles = win;
+  if ((st = build_items(c)) != NBODY_OK) return st;
+  if ((st = check_flags(c, false)) != NBODY_OK) return st;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return NBODY_OK;
+}
+
+nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, const double *dL_dv_T, double *dL_dr0,
+                        double *dL_dv0, double *dL_dm) {
+  if (!c) return NBODY_EINVAL;
+  (void)n_steps; (void)dL_dr_T; (void)dL_dv_T; (void)dL_dr0; (void)dL_dv0; (void)dL_dm;
+  return fail(c, NBODY_EINVAL, "nbody_grad: not available in this build");
+}
+
+void nbody_free(nbody_ctx *c) { destroy(c); }
+
+const char *nbody_last_error(const nbody_ctx *c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+nbody_status nbody_peaks(double *out) {
+  if (!out) return NBODY_EINVAL;
+  cudaError_t e = nb::run_peaks(out);
+  if (e != cudaSuccess) return fail(nullptr, NBODY_ECUDA, "peaks: %s", cudaGetErrorString(e));
+  return NBODY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+"""GPU parity of the CUDA library against the FP64 oracle (and closed forms).
+
+Tolerances (per target body p, acceleration a_p from Eq. 1):
+  FP64  : |a_gpu - a_ref| / |a_ref| <= 1e-13 per evaluation; positions within
+          1e-10 AU of the oracle after 3650 steps of the 31-body system.
+  mixed : |a_gpu - a_ref| / T_p <= 2e-6, with T_p = sum_j |term_pj| (the
+          condition-free form), and |a_gpu - a_ref| / |a_ref| <= 2e-6 for every
+          body whose sum is well conditioned (T_p / |a_p| <= 1e3); energy
+          drift over 3650 steps within 2x the oracle's.
+The FP64 bound comes from the arithmetic: each term is accurate to a few
+ulps (binomial-series |d|^-3) and sums of <= 1e6 terms in FP64 keep ~1e-14.
+The mixed bound is the FP32 unit roundoff (6e-8) times the few-ulp error of
+the MUFU rsqrt seed, cubed, plus FP32 sub-sums of 64 terms.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_15079_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-13
+MIXED_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def nb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_15079_gb300 import build
+    build.build()
+    from paper_2112_15079_gb300 import nbody
+    return nbody
+
+
+def _make(nb, s, precision, tiles=None, graphs=True, offsets=None):
+    b = nb.NBody(s.r, s.v, s.m, offsets, G=s.G, dt=s.dt, precision=precision, graphs=graphs)
+    if tiles:
+        t = b.tiles
+        t.update(tiles)
+        b.tiles = t
+        b.reset()
+    return b
+
+
+def _rel_err(a, ref):
+    return np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def _check_accel(precision, a, ref, tnorm):
+    d = np.linalg.norm(a - ref, axis=0)
+    n = np.linalg.norm(ref, axis=0)
+    if precision == "fp64":
+        assert np.max(d / n) <= FP64_TOL, np.max(d / n)
+    else:
+        assert np.max(d / tnorm) <= MIXED_TOL, np.max(d / tnorm)
+        good = tnorm / n <= 1e3
+        assert np.max((d / n)[good]) <= MIXED_TOL, np.max((d / n)[good])
+
+
+TILES = [
+    None,
+    {"threads": 64, "ipt": 1, "tj": 64, "jsplit": 1, "ctas_per_sm": 1},
+    {"threads": 128, "ipt": 2, "tj": 128, "jsplit": 7, "ctas_per_sm": 2},
+    {"threads": 256, "ipt": 4, "tj": 192, "jsplit": 3, "ctas_per_sm": 1},
+    {"threads": 128, "ipt": 4, "tj": 1024, "jsplit": 64, "ctas_per_sm": 4},
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("tiles", TILES)
+@pytest.mark.parametrize("n", [31, 2131, 5003])
+def test_initial_accel_vs_oracle(nb, precision, tiles, n):
+    s = inputs.solar_system(n, seed=100 + n)
+    b = _make(nb, s, precision, tiles)
+    a = b.accel().cpu().numpy()
+    ref = oracle.accel(s.G, s.r, s.m, openmp=True)
+    _check_accel(precision, a, ref, oracle.term_norm(s.G, s.r, s.m, openmp=True))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_10425_accel_every_body(nb, precision):
+    """The 10,425-body Solar-System-shaped model, all bodies, default tiles."""
+    s = inputs.solar_system(10425)
+    b = _make(nb, s, precision)
+    a = b.accel().cpu().numpy()
+    ref = oracle.accel(s.G, s.r, s.m, openmp=True)
+    _check_accel(precision, a, ref, oracle.term_norm(s.G, s.r, s.m, openmp=True))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_steps_then_reevaluate(nb, precision):
+    """After GPU steps of the 10,425-body model, the GPU acceleration of the
+    GPU-produced state equals the oracle's Eq. 1 at that state (the moons make
+    long trajectories chaotic, so states are compared through Eq. 1)."""
+    s = inputs.solar_system(10425, seed=7)
+    b = _make(nb, s, precision)
+    b.step(25)
+    r = b.r.cpu().numpy()
+    a = b.accel().cpu().numpy()
+    ref = oracle.accel(s.G, r, s.m, openmp=True)
+    _check_accel(precision, a, ref, oracle.term_norm(s.G, r, s.m, openmp=True))
+
+
+def test_fp64_trajectory_31_bodies_3650_steps(nb):
+    s = inputs.solar_system(31)
+    b = _make(nb, s, "fp64")
+    b.step(3650)
+    r_ref, v_ref, _ = oracle.verlet(s.G, s.dt, 3650, s.r, s.v, s.m)
+    r = b.r.cpu().numpy()
+    assert np.abs(r - r_ref).max() <= 1e-10
+    assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-10 * np.abs(v_ref).max()
+
+
+def test_mixed_energy_drift_31_bodies(nb):
+    """Energy drift of the mixed path within 2x the oracle's (3650 steps)."""
+    s = inputs.solar_system(31)
+    E0 = sum(oracle.energy(s.G, s.r, s.v, s.m))
+    b = _make(nb, s, "mixed")
+    r, v, a = s.r, s.v, None
+    drift_ref, drift_gpu = 0.0, 0.0
+    for _ in range(73):
+        r, v, a = oracle.verlet(s.G, s.dt, 50, r, v, s.m, a)
+        drift_ref = max(drift_ref, abs(sum(oracle.energy(s.G, r, v, s.m)) - E0) / abs(E0))
+        b.step(50)
+        rg, vg = b.r.cpu().numpy(), b.v.cpu().numpy()
+        drift_gpu = max(drift_gpu, abs(sum(oracle.energy(s.G, rg, vg, s.m)) - E0) / abs(E0))
+    assert drift_gpu <= 2 * drift_ref, (drift_gpu, drift_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_split_calls_and_graphs_bitwise(nb, precision):
+    """n steps in one call == the same steps over several calls == without
+    graphs: the kernels are deterministic and the drift is the same code."""
+    s = inputs.solar_system(2131, seed=3)
+    outs = []
+    for graphs, chunks in ((True, [130]), (True, [64, 1, 65]), (False, [7, 123])):
+        b = _make(nb, s, precision, graphs=graphs)
+        for c in chunks:
+            b.step(c)
+        outs.append(b.state.cpu().numpy())
+        b.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_vs_oracle(nb, precision):
+    s = inputs.solar_system(2131, seed=9)
+    b = _make(nb, s, precision)
+    e = b.energy()[0]
+    ref = sum(oracle.energy(s.G, s.r, s.v, s.m))
+    assert abs(e - ref) <= 1e-13 * abs(ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_uneven_systems(nb, precision):
+    """Independent systems of uneven size (including 1- and 2-body systems)
+    in one context: each equals the oracle run on its own.  Systems without
+    moons are compared along the trajectory; systems with moons (whose
+    shortest orbits are unresolved at dt = 0.1 day, so trajectories diverge
+    chaotically) through Eq. 1 re-evaluated at the GPU state."""
+    spec = [(31, 100), (1, 0), (700, 100), (2, 0), (1531, 0), (257, 0)]
+    systems = []
+    for k, (n, moons) in enumerate(spec):
+        if n >= 31:
+            systems.append(inputs.solar_system(n, seed=40 + k, n_moons=moons))
+        else:
+            r = np.array([[1.0, 2.5][:n], [0.0, 0.1][:n], [0.0, 0.0][:n]])
+            v = np.array([[0.0, 0.0][:n], [0.01, -0.01][:n], [0.0, 0.001][:n]])
+            systems.append(inputs.System(r=r, v=v, m=np.array([1e-3, 2e-3][:n])))
+    off, r, v, m = inputs.concat(systems)
+    G, dt = inputs.G_AU_DAY, inputs.DT_DAY
+    b = nb.NBody(r, v, m, off, G=G, dt=dt, precision=precision)
+    a = b.accel().cpu().numpy()
+    b.step(20)
+    rg, vg = b.r.cpu().numpy(), b.v.cpu().numpy()
+    ag = b.accel().cpu().numpy()
+    eg = b.energy()
+    for k, sysk in enumerate(systems):
+        sl = slice(off[k], off[k + 1])
+        if sysk.n == 1:
+            assert np.all(a[:, sl] == 0.0)
+            np.testing.assert_allclose(rg[:, sl], sysk.r + 20 * dt * sysk.v, rtol=1e-14)
+            continue
+        _check_accel(precision, a[:, sl], oracle.accel(G, sysk.r, sysk.m), oracle.term_norm(G, sysk.r, sysk.m))
+        _check_accel(precision, ag[:, sl], oracle.accel(G, rg[:, sl], sysk.m), oracle.term_norm(G, rg[:, sl], sysk.m))
+        if sysk.info.get("n_moons", 0) == 0:
+            r_ref, v_ref, _ = oracle.verlet(G, dt, 20, sysk.r, sysk.v, sysk.m)
+            tol = 1e-12 if precision == "fp64" else 1e-7
+            assert np.abs(rg[:, sl] - r_ref).max() <= tol * max(1.0, np.abs(r_ref).max())
+        e_ref = sum(oracle.energy(G, rg[:, sl], vg[:, sl], sysk.m))
+        assert abs(eg[k] - e_ref) <= 1e-12 * abs(e_ref) + 1e-300
+
+
+@pytest.mark.parametrize("precision,n_ring", [("fp64", 65535), ("mixed", 262143), ("mixed", 1048575)])
+def test_ring_closed_form_large_n(nb, precision, n_ring):
+    """n-gon ring of equal masses m around a central mass Mc: every ring body
+    is pulled inward with G Mc/R^2 + (G m/R^2) sum_k 1/(4 sin(pi k/n)) and
+    feels no tangential force.  The error scale is the closed-form term norm
+    T = G Mc/R^2 + (G m/(4R^2)) sum_k csc^2(pi k/n) = G Mc/R^2 + G m (n^2-1)/(12 R^2)."""
+    G, R, m, Mc = 2.9591220828e-4, 2.0, 1e-8, 1.0
+    th = 2 * np.pi * np.arange(n_ring) / n_ring
+    r = np.concatenate([np.zeros((3, 1)), np.stack([R * np.cos(th), R * np.sin(th), 0 * th])], axis=1)
+    mass = np.concatenate([[Mc], np.full(n_ring, m)])
+    k = np.arange(1, n_ring)
+    radial = G * Mc / R**2 + G * m / R**2 * np.sum(1.0 / (4.0 * np.sin(np.pi * k / n_ring)))
+    T = G * Mc / R**2 + G * m * (n_ring**2 - 1) / (12 * R**2)
+    b = nb.NBody(r, np.zeros_like(r), mass, G=G, dt=0.1, precision=precision)
+    a = b.accel().cpu().numpy()
+    ring = a[:, 1:]
+    inward = -(ring[0] * np.cos(th) + ring[1] * np.sin(th))
+    tangential = -ring[0] * np.sin(th) + ring[1] * np.cos(th)
+    tol = FP64_TOL if precision == "fp64" else MIXED_TOL
+    assert np.max(np.abs(inward - radial)) <= tol * T
+    assert np.max(np.abs(tangential)) <= tol * T
+    assert np.max(np.abs(a[:, 0])) <= tol * G * m * n_ring / R**2
+
+
+@pytest.mark.parametrize("precision,n", [("fp64", 100003), ("mixed", 1048577)])
+def test_collinear_chain_closed_form(nb, precision, n):
+    """Unit masses at x = 0, 1, ..., n-1 (G = 1): body p feels
+      a_p = H2(n-1-p) - H2(p),   with T_p = H2(n-1-p) + H2(p),
+    H2(k) = sum_{i=1}^k 1/i^2 = pi^2/6 - psi_1(k+1) (trigamma).  The end
+    bodies are perfectly conditioned, and a missing or doubled source tile
+    anywhere shifts many a_p by far more than the tolerance."""
+    special = pytest.importorskip("scipy.special")
+    x = np.arange(n, dtype=np.float64)
+    r = np.stack([x, 0 * x, 0 * x])
+    b = nb.NBody(r, np.zeros_like(r), np.ones(n), G=1.0, dt=0.1, precision=precision)
+    a = b.accel().cpu().numpy()
+    p = np.arange(n)
+    H2 = lambda k: np.pi**2 / 6 - special.polygamma(1, k + 1.0)
+    want = H2(n - 1 - p) - H2(p)
+    T = H2(n - 1 - p) + H2(p)
+    tol = FP64_TOL if precision == "fp64" else MIXED_TOL
+    # trigamma itself carries ~1e-15 relative error, well inside both bounds
+    assert np.max(np.abs(a[0] - want) / T) <= tol
+    assert np.all(a[1:] == 0.0)
+
+
+def test_mixed_1m_sampled_rows(nb):
+    """The N = 1,048,576 Solar-System-shaped model in the mixed path: sampled
+    target rows against the oracle's Eq. 1 for those rows."""
+    s = inputs.solar_system(1 << 20, seed=31)
+    b = _make(nb, s, "mixed")
+    a = b.accel().cpu().numpy()
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([np.arange(0, 200), rng.choice(s.n, 56, replace=False), [s.n - 1]])
+    ref = oracle.accel_rows(s.G, s.r, s.m, rows, openmp=True)
+    tn = oracle.term_norm(s.G, s.r, s.m, rows, openmp=True)
+    _check_accel("mixed", a[:, rows], ref, tn)
+
+
+def test_fp64_time_reversibility(nb):
+    s = inputs.solar_system(131, seed=12, n_moons=0)  # resolved orbits only
+    b = _make(nb, s, "fp64")
+    b.step(300)
+    back = nb.NBody(b.r, b.v, s.m, G=s.G, dt=-s.dt, precision="fp64")
+    back.step(300)
+    assert np.abs(back.r.cpu().numpy() - s.r).max() <= 1e-11 * np.abs(s.r).max()
+
+
+def test_edge_cases_and_errors(nb):
+    torch = pytest.importorskip("torch")
+    # single body: no force, straight-line motion
+    one = nb.NBody(np.array([[1.0], [2.0], [3.0]]), np.array([[0.1], [0.0], [-0.2]]), np.array([1.0]),
+                   G=1.0, dt=0.5, precision="fp64")
+    assert np.all(one.accel().cpu().numpy() == 0.0)
+    one.step(4)
+    np.testing.assert_allclose(one.r.cpu().numpy()[:, 0], [1.2, 2.0, 2.6], rtol=1e-15)
+    one.step(0)  # no-op
+    with pytest.raises(nb.NBodyError) as ei:
+        one.step(-1)
+    assert ei.value.status == nb.NBODY_EINVAL
+    # coincident bodies are rejected at init
+    r = np.array([[0.0, 1.0, 1.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    for prec in ("fp64", "mixed"):
+        with pytest.raises(nb.NBodyError) as ei:
+            nb.NBody(r, np.zeros((3, 3)), np.ones(3), G=1.0, dt=0.1, precision=prec)
+        assert ei.value.status == nb.NBODY_EINVAL
+    # non-finite state and negative mass
+    r = np.array([[0.0, 1.0], [0.0, 0.0], [0.0, np.nan]])
+    with pytest.raises(nb.NBodyError):
+        nb.NBody(r, np.zeros((3, 2)), np.ones(2), G=1.0, dt=0.1)
+    with pytest.raises(nb.NBodyError):
+        nb.NBody(np.eye(3)[:, :2], np.zeros((3, 2)), np.array([1.0, -1.0]), G=1.0, dt=0.1)
+    # bad options
+    for kw in ({"G": 0.0, "dt": 0.1}, {"G": 1.0, "dt": 0.0}, {"G": float("inf"), "dt": 0.1}):
+        with pytest.raises(nb.NBodyError):
+            nb.NBody(np.eye(3)[:, :2], np.zeros((3, 2)), np.ones(2), **kw)
+    # bad tiles
+    b = nb.NBody(np.eye(3)[:, :2], np.zeros((3, 2)), np.ones(2), G=1.0, dt=0.1)
+    with pytest.raises(nb.NBodyError):
+        b.tiles = {"threads": 96, "ipt": 1, "tj": 64, "jsplit": 1, "ctas_per_sm": 1}
+    with pytest.raises(nb.NBodyError):
+        b.tiles = {"threads": 128, "ipt": 1, "tj": 100, "jsplit": 1, "ctas_per_sm": 1}
+    # host pointers are rejected
+    import ctypes
+    h = np.zeros(2)
+    ctx = ctypes.c_void_p()
+    off = (ctypes.c_int64 * 2)(0, 2)
+    opts = nb.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, reserved=0)
+    st = nb.nbody_init(ctypes.byref(ctx), 1, off, *([h.ctypes.data] * 7), ctypes.byref(opts), None)
+    assert st == nb.NBODY_EINVAL and not ctx.value
+    # a collision during the run surfaces as ENONFINITE on the next sync
+    r = np.array([[0.0, 1.0], [0.0, 0.0], [0.0, 0.0]])
+    v = np.array([[0.5, -0.5], [0.0, 0.0], [0.0, 0.0]])
+    b = nb.NBody(r, v, np.zeros(2), G=1.0, dt=1.0, precision="fp64")  # massless: exact meeting
+    b.step(1)
+    with pytest.raises(nb.NBodyError) as ei:
+        b.sync()
+    assert ei.value.status == nb.NBODY_ENONFINITE
+    del torch
+
+
+def test_nondefault_stream(nb):
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(700, seed=5)
+    ref = _make(nb, s, "mixed")
+    ref.step(10)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b = _make(nb, s, "mixed")
+        b.step(10)
+        out = b.state.clone()
+    st.synchronize()
+    assert torch.equal(out, ref.state)

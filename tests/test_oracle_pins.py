@@ -56,6 +56,16 @@ def test_three_body_hand_cases(golden_dir):
             np.testing.assert_allclose(got, _perm(want, k), rtol=0, atol=4 * EPS * np.abs(want).max())
 
 
+def test_term_norm_hand_case():
+    """Collinear hand case (G = 1): body 0 feels 2/1 + 3/9 (same sign, equal to
+    |a_0| = 7/3), body 1 feels |-1| + |3/4| = 7/4, body 2 feels 1/9 + 2/4 = 11/18."""
+    r = np.array([[0.0, 1.0, 3.0], [0.0] * 3, [0.0] * 3])
+    t = oracle.term_norm(1.0, r, np.array([1.0, 2.0, 3.0]))
+    np.testing.assert_allclose(t, [7 / 3, 7 / 4, 11 / 18], rtol=4 * EPS)
+    t1 = oracle.term_norm(1.0, r, np.array([1.0, 2.0, 3.0]), rows=[1])
+    assert t1[0] == t[1]
+
+
 def test_equal_distance_closed_form():
     """Bodies with all pairwise distances equal to L (equilateral triangle,
     regular tetrahedron): Eq. 1 reduces to a_p = -(G M / L^3)(r_p - r_cm)
