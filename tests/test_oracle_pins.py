@@ -105,6 +105,43 @@ def test_ngon_ring_closed_form(n_ring):
         assert np.abs(a[:, 0]).max() <= 1e-12 * G * m * n_ring / R**2
 
 
+def test_collinear_chain_closed_form():
+    """Unit masses at x = 0..n-1 (G = 1): a_p = H2(n-1-p) - H2(p) with
+    H2(k) = sum_{i<=k} 1/i^2 = pi^2/6 - psi_1(k+1).  Every term of the end body
+    has the same sign, so a plain running sum would drift by ~n ulp/4
+    (~5e-13 here); Eq. 1's exact sum needs ~1 ulp."""
+    special = pytest.importorskip("scipy.special")
+    n = 20000
+    x = np.arange(n, dtype=np.float64)
+    a = oracle.accel(1.0, np.stack([x, 0 * x, 0 * x]), np.ones(n), openmp=True)
+    p = np.arange(n)
+    H2 = lambda k: np.pi**2 / 6 - special.polygamma(1, k + 1.0)
+    want = H2(n - 1 - p) - H2(p)
+    T = H2(n - 1 - p) + H2(p)
+    assert np.max(np.abs(a[0] - want) / T) <= 2e-15
+    assert np.all(a[1:] == 0.0)
+
+
+def test_many_subulp_terms_half_ring():
+    """Target at the origin, a unit mass at distance 1 listed first, then n
+    tiny masses m on a half-circle of radius R at angles
+    theta_k = -pi/2 + (k + 1/2) pi / n (G = 1).  Closed form:
+      a_x = 1 + (m / R^2) / sin(pi / (2n)),   a_y = 0.
+    Each tiny term is below half an ulp of the running sum, so a plain
+    ascending sum drops all of them (6e-13 relative here); the exact sum of
+    Eq. 1 keeps them."""
+    n, R = 20000, 2.0
+    m = 5e-17 * R * R
+    th = -np.pi / 2 + (np.arange(n) + 0.5) * np.pi / n
+    x = np.concatenate([[0.0, 1.0], R * np.cos(th)])
+    y = np.concatenate([[0.0, 0.0], R * np.sin(th)])
+    mass = np.concatenate([[1.0, 1.0], np.full(n, m)])
+    a = oracle.accel_rows(1.0, np.stack([x, y, 0 * x]), mass, [0])
+    want = 1.0 + (m / R**2) / np.sin(np.pi / (2 * n))
+    assert abs(a[0, 0] - want) <= 2 * EPS * want
+    assert abs(a[1, 0]) <= 1e-30
+
+
 def test_momentum_conservation_antisymmetry():
     """Pairwise antisymmetry of Eq. 1: sum_p m_p a_p = 0 up to rounding."""
     s = inputs.solar_system(400, seed=11)
