@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--inner", type=int, default=100, help="Verlet steps per benchmark step (mixed)")
     ap.add_argument("--inner-fp64", type=int, default=10, help="Verlet steps per benchmark step (FP64)")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--only", choices=["mixed", "fp64"], default=None, help="time one precision only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -280,7 +281,7 @@ def run_ours(args):
     results = {}
     tiles = {}
     for prec, inner in (("mixed", args.inner), ("fp64", args.inner_fp64)):
-        if prec == "fp64" and args.no_fp64:
+        if (prec == "fp64" and args.no_fp64) or (args.only and prec != args.only):
             continue
         with torch.cuda.stream(stream):
             b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, device=device)
@@ -311,6 +312,19 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(s, args.cpu_seconds)
+    peaks = None
+    if rank == 0 and not args.only:
+        p = nbody.peaks()  # measured instruction rates (1e9 lane-ops/s) on this GPU
+        peaks = {"fp32_tflops": 2 * p["ffma"] * 1e-3, "fp64_tflops": 2 * p["dfma"] * 1e-3,
+                 "mufu_rsqrt_f32_gops": p["rsqrt_f32"], "mufu_rsqrt_f64_gops": p["rsqrt_f64"],
+                 "cvt_f32_f64_gops": p["cvt_f32_f64"], "ffma2_tflops": 2 * p["ffma2_lanes"] * 1e-3,
+                 "sm_mhz_during_ffma": p["sm_mhz"]}
+    if rank == 0 and args.only and args.only not in results:
+        return 0
+    if rank == 0 and args.only == "fp64":
+        print(json.dumps({"metric": METRIC, "value": results["fp64"]["value"], "unit": UNIT,
+                          "ms_per_step": results["fp64"]["ms_per_step"], "precision": "fp64"}), flush=True)
+        return 0
     if rank == 0:
         m = results["mixed"]
         khash = kernel_hash()
@@ -338,6 +352,10 @@ def run_ours(args):
             "gpu_launches": args.steps * (1 + args.inner),
             "clocks": results.get("clocks"),
         }
+        if peaks:
+            line["roofline"]["peak_measured_tflops"] = peaks["fp32_tflops"]
+            line["roofline"]["frac_of_measured"] = m["achieved_tflops"] / peaks["fp32_tflops"]
+            line["measured_peaks"] = peaks
         if "fp64" in results:
             f = results["fp64"]
             line["fp64"] = {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"],
@@ -349,6 +367,9 @@ def run_ours(args):
                                          "traffic": NCU_TRAFFIC.get((khash, "fp64")),
                                          "peak_note": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x 2070 MHz"},
                             "mixed_speedup": m["value"] / f["value"]}
+            if peaks:
+                line["fp64"]["roofline"]["peak_measured_tflops"] = peaks["fp64_tflops"]
+                line["fp64"]["roofline"]["frac_of_measured"] = f["achieved_tflops"] / peaks["fp64_tflops"]
             line["gpu_launches"] += args.steps * (1 + f["inner"])
         if "e2e" in results:
             line["e2e"] = results["e2e"]

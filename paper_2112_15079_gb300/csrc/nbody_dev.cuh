@@ -165,6 +165,23 @@ __device__ __forceinline__ float lo_part(double x, float hi) {
   return __double2float_rn(x - static_cast<double>(hi));
 }
 
+// Knuth's TwoSum: (hi, lo) += v with the rounding error of hi + v kept in lo.
+// Used once per source tile, so long sums do not drop terms below half an
+// ulp of a dominant term (a moon next to its planet among ~1e6 asteroids).
+__device__ __forceinline__ void two_sum_acc(double &hi, double &lo, double v) {
+  const double s = hi + v;
+  const double bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
 __device__ __forceinline__ bool finite3(double a, double b, double c) {
   return isfinite(a) && isfinite(b) && isfinite(c);
 }

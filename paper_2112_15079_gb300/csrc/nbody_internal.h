@@ -90,7 +90,7 @@ cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);
 
 constexpr int kStages = 2;          // shared-memory pipeline depth of the force kernels
-constexpr int kFoldEvery = 64;      // mixed path: FP32 partial sums folded into FP64 every 64 sources
+constexpr int kFoldEvery = 64;      // mixed path: FP32 sub-sums of 64 sources folded into a float pair
 constexpr int kEnergyBlock = 256;
 
 }  // namespace nb

@@ -37,8 +37,17 @@ struct Prec<1> {  // mixed
   static constexpr int kBytesPerSource = 32;  // float4 hi (x,y,z,mu) + float4 lo (x,y,z,0)
 };
 
+// Minimum resident CTAs per SM the register allocation must allow: the
+// mixed kernel is latency-bound on the FP32 pipe and wants ~32 warps/SM
+// (<= 64 registers); the FP64 kernel saturates GB300's narrow FP64 pipe
+// with few warps, so it trades occupancy for registers.
 template <int PREC, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
+struct MinBlocks {  // mixed: 32 / 24 / 16 warps per SM for IPT 1 / 2 / 4 (64 / 85 / 128 registers)
+  static constexpr int value = PREC == 1 ? ((IPT == 1 ? 1024 : IPT == 2 ? 768 : 512) / THREADS) : 1;
+};
+
+template <int PREC, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value)) step_kernel(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ int s_item;
@@ -74,12 +83,21 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
       valid[k] = p < it.i1;
       pidx[k] = valid[k] ? p : it.i1 - 1;  // duplicate a real target, result discarded
     }
-    double accx[IPT], accy[IPT], accz[IPT];
+    // FP64 path: (acc, cmp) is a hi/lo pair fed once per tile with the tile's
+    // FP64 sub-sum through TwoSum.  Both paths leave the item's sums in acc.
+    double accx[IPT], accy[IPT], accz[IPT], cmpx[IPT], cmpy[IPT], cmpz[IPT];
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) accx[k] = accy[k] = accz[k] = 0.0;
+    for (int k = 0; k < IPT; ++k) accx[k] = accy[k] = accz[k] = cmpx[k] = cmpy[k] = cmpz[k] = 0.0;
 
     double px[IPT], py[IPT], pz[IPT];                               // FP64 path
     float hx[IPT], hy[IPT], hz[IPT], lx[IPT], ly[IPT], lz[IPT];     // mixed path
+    // mixed path: per-target sums as unevaluated float pairs (hi + lo), fed
+    // one FP32 sub-sum of kFoldEvery sources at a time through TwoSum and
+    // converted to FP64 once per item, so the source loop issues no FP64
+    // instruction (GB300 runs FP64 and f32<->f64 conversions at 1/64 rate).
+    float shx[IPT], shy[IPT], shz[IPT], slx[IPT], sly[IPT], slz[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) shx[k] = shy[k] = shz[k] = slx[k] = sly[k] = slz[k] = 0.f;
     if (PREC == 0) {
       const double4_32a *cur = static_cast<const double4_32a *>(a.cur_a);
 #pragma unroll
@@ -132,6 +150,9 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
 
       if (PREC == 0) {
         const double4_32a *src = reinterpret_cast<const double4_32a *>(stage_ptr(s));
+        double tx[IPT], ty[IPT], tz[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) tx[k] = ty[k] = tz[k] = 0.0;
         if (!diag) {
           int jj = 0;
           for (; jj + 4 <= cnt; jj += 4) {
@@ -139,13 +160,13 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
             for (int u = 0; u < 4; ++u) {
               const double4_32a sj = src[jj + u];
 #pragma unroll
-              for (int k = 0; k < IPT; ++k) interact_fp64<false>(sj, px[k], py[k], pz[k], false, accx[k], accy[k], accz[k]);
+              for (int k = 0; k < IPT; ++k) interact_fp64<false>(sj, px[k], py[k], pz[k], false, tx[k], ty[k], tz[k]);
             }
           }
           for (; jj < cnt; ++jj) {
             const double4_32a sj = src[jj];
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) interact_fp64<false>(sj, px[k], py[k], pz[k], false, accx[k], accy[k], accz[k]);
+            for (int k = 0; k < IPT; ++k) interact_fp64<false>(sj, px[k], py[k], pz[k], false, tx[k], ty[k], tz[k]);
           }
         } else {
           for (int jj = 0; jj < cnt; ++jj) {
@@ -153,8 +174,14 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
             const int jg = jt0 + jj;
 #pragma unroll
             for (int k = 0; k < IPT; ++k)
-              interact_fp64<true>(sj, px[k], py[k], pz[k], jg == pidx[k], accx[k], accy[k], accz[k]);
+              interact_fp64<true>(sj, px[k], py[k], pz[k], jg == pidx[k], tx[k], ty[k], tz[k]);
           }
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+          two_sum_acc(accx[k], cmpx[k], tx[k]);
+          two_sum_acc(accy[k], cmpy[k], ty[k]);
+          two_sum_acc(accz[k], cmpz[k], tz[k]);
         }
       } else {
         const float4 *sh = reinterpret_cast<const float4 *>(stage_ptr(s));
@@ -185,10 +212,10 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
             }
           }
 #pragma unroll
-          for (int k = 0; k < IPT; ++k) {  // fold the FP32 sub-sum into FP64
-            accx[k] += static_cast<double>(fx[k]);
-            accy[k] += static_cast<double>(fy[k]);
-            accz[k] += static_cast<double>(fz[k]);
+          for (int k = 0; k < IPT; ++k) {  // fold the sub-sum into the two-float accumulator
+            two_sum_acc(shx[k], slx[k], fx[k]);
+            two_sum_acc(shy[k], sly[k], fy[k]);
+            two_sum_acc(shz[k], slz[k], fz[k]);
           }
         }
       }
@@ -214,6 +241,19 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
     if (aborted) {
       if (tid == 0) atomicOr(a.flags, kFlagTimeout);
       break;
+    }
+
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {  // collapse the hi/lo pairs
+      if (PREC == 0) {
+        accx[k] += cmpx[k];
+        accy[k] += cmpy[k];
+        accz[k] += cmpz[k];
+      } else {
+        accx[k] = static_cast<double>(shx[k]) + static_cast<double>(slx[k]);
+        accy[k] = static_cast<double>(shy[k]) + static_cast<double>(sly[k]);
+        accz[k] = static_cast<double>(shz[k]) + static_cast<double>(slz[k]);
+      }
     }
 
     // ---- split-source reduction ---------------------------------------
@@ -244,16 +284,16 @@ __global__ void __launch_bounds__(THREADS) step_kernel(const StepArgs a) {
       if (!last) continue;  // s_flag bit 1 is clear here; the next fetch re-syncs
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
-        double sx = 0.0, sy = 0.0, sz = 0.0;
+        double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
         for (int c = 0; c < it.nsplit; ++c) {
           const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
-          sx += __ldcg(row + pidx[k]);
-          sy += __ldcg(row + N + pidx[k]);
-          sz += __ldcg(row + 2 * N + pidx[k]);
+          two_sum_acc(sx, ex, __ldcg(row + pidx[k]));
+          two_sum_acc(sy, ey, __ldcg(row + N + pidx[k]));
+          two_sum_acc(sz, ez, __ldcg(row + 2 * N + pidx[k]));
         }
-        accx[k] = sx;
-        accy[k] = sy;
-        accz[k] = sz;
+        accx[k] = sx + ex;
+        accy[k] = sy + ey;
+        accz[k] = sz + ez;
       }
       __syncthreads();
       if (tid == 0) s_flag &= ~2;

@@ -241,6 +241,28 @@ def test_collinear_chain_closed_form(nb, precision, n):
     assert np.all(a[1:] == 0.0)
 
 
+def test_fp64_many_subulp_terms(nb):
+    """A unit mass at distance 1 listed first, then n tiny masses on a
+    half-circle of radius R: a_x = 1 + (m/R^2)/sin(pi/(2n)) exactly.  Each
+    tiny term is below half an ulp of the running sum; a plain FP64 running
+    sum over one chunk would miss them all (~3e-12 relative at n = 1e5)."""
+    n, R = 100000, 2.0
+    m = 5e-17 * R * R
+    th = -np.pi / 2 + (np.arange(n) + 0.5) * np.pi / n
+    x = np.concatenate([[0.0, 1.0], R * np.cos(th)])
+    y = np.concatenate([[0.0, 0.0], R * np.sin(th)])
+    mass = np.concatenate([[1.0, 1.0], np.full(n, m)])
+    b = nb.NBody(np.stack([x, y, 0 * x]), np.zeros((3, n + 2)), mass, G=1.0, dt=0.1, precision="fp64")
+    for tiles in (None, {"threads": 128, "ipt": 1, "tj": 256, "jsplit": 1, "ctas_per_sm": 2}):
+        if tiles:
+            b.tiles = tiles
+            b.reset()
+        a = b.accel()[:, 0].cpu().numpy()
+        want = 1.0 + (m / R**2) / np.sin(np.pi / (2 * n))
+        assert abs(a[0] - want) <= 1e-15 * want, (tiles, a[0] - want)
+        assert abs(a[1]) <= 1e-20
+
+
 def test_mixed_1m_sampled_rows(nb):
     """The N = 1,048,576 Solar-System-shaped model in the mixed path: sampled
     target rows against the oracle's Eq. 1 for those rows."""
