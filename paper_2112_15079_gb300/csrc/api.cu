@@ -157,7 +157,7 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
     t.threads = 256;
     t.ipt = 2;
     t.tj = 256;
-    t.ctas_per_sm = 2;
+    t.ctas_per_sm = 3;  // 80 registers x 256 threads: 3 CTAs (24 warps) per SM
   }
   // Enough items for an even spread over the persistent grid: aim for about
   // 8 items per resident CTA, splitting the sources of each target block
@@ -635,7 +635,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
       if (c->o.precision == NBODY_MIXED && th == 64) continue;
       if (c->o.precision == NBODY_FP64 && ip == 4) continue;
       for (int sm : split_mul)
-        for (int cps : {1, 2, 4}) {
+        for (int cps : {1, 2, 3, 4}) {
           nbody_tiles t = base;
           t.threads = th;
           t.ipt = ip;

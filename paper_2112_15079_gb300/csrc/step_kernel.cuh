@@ -257,15 +257,25 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     }
 
     // ---- split-source reduction ---------------------------------------
+    // Partials: FP64 path -> 3 doubles per target and slot, summed by FP64
+    // TwoSum; mixed path -> 3 float pairs (hi, lo) in the same 24 bytes,
+    // summed by FP32 TwoSum (GB300's FP64 pipe is 64x narrower, and a few
+    // last-arriving CTAs doing FP64 sums over many slots become the tail).
     if (it.nsplit > 1) {
       const size_t N = static_cast<size_t>(a.N);
       double *prow = a.partial + static_cast<size_t>(it.slot) * 3 * N;
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
-        if (valid[k]) {
+        if (!valid[k]) continue;
+        if (PREC == 0) {
           __stcg(prow + pidx[k], accx[k]);
           __stcg(prow + N + pidx[k], accy[k]);
           __stcg(prow + 2 * N + pidx[k], accz[k]);
+        } else {
+          float2 *frow = reinterpret_cast<float2 *>(prow);
+          __stcg(frow + pidx[k], make_float2(shx[k], slx[k]));
+          __stcg(frow + N + pidx[k], make_float2(shy[k], sly[k]));
+          __stcg(frow + 2 * N + pidx[k], make_float2(shz[k], slz[k]));
         }
       }
       __threadfence();
@@ -284,16 +294,35 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
       if (!last) continue;  // s_flag bit 1 is clear here; the next fetch re-syncs
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
-        double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-        for (int c = 0; c < it.nsplit; ++c) {
-          const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
-          two_sum_acc(sx, ex, __ldcg(row + pidx[k]));
-          two_sum_acc(sy, ey, __ldcg(row + N + pidx[k]));
-          two_sum_acc(sz, ez, __ldcg(row + 2 * N + pidx[k]));
+        if (PREC == 0) {
+          double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+          for (int c = 0; c < it.nsplit; ++c) {
+            const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
+            two_sum_acc(sx, ex, __ldcg(row + pidx[k]));
+            two_sum_acc(sy, ey, __ldcg(row + N + pidx[k]));
+            two_sum_acc(sz, ez, __ldcg(row + 2 * N + pidx[k]));
+          }
+          accx[k] = sx + ex;
+          accy[k] = sy + ey;
+          accz[k] = sz + ez;
+        } else {
+          float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+          for (int c = 0; c < it.nsplit; ++c) {
+            const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
+            const float2 vx = __ldcg(row + pidx[k]);
+            const float2 vy = __ldcg(row + N + pidx[k]);
+            const float2 vz = __ldcg(row + 2 * N + pidx[k]);
+            two_sum_acc(sx, ex, vx.x);
+            two_sum_acc(sy, ey, vy.x);
+            two_sum_acc(sz, ez, vz.x);
+            ex += vx.y;
+            ey += vy.y;
+            ez += vz.y;
+          }
+          accx[k] = static_cast<double>(sx) + static_cast<double>(ex);
+          accy[k] = static_cast<double>(sy) + static_cast<double>(ey);
+          accz[k] = static_cast<double>(sz) + static_cast<double>(ez);
         }
-        accx[k] = sx + ex;
-        accy[k] = sy + ey;
-        accz[k] = sz + ez;
       }
       __syncthreads();
       if (tid == 0) s_flag &= ~2;

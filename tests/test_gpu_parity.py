@@ -195,12 +195,17 @@ def test_batched_uneven_systems(nb, precision):
         assert abs(eg[k] - e_ref) <= 1e-12 * abs(e_ref) + 1e-300
 
 
-@pytest.mark.parametrize("precision,n_ring", [("fp64", 65535), ("mixed", 262143), ("mixed", 1048575)])
+@pytest.mark.parametrize("precision,n_ring", [("fp64", 4095), ("mixed", 262143), ("mixed", 1048575)])
 def test_ring_closed_form_large_n(nb, precision, n_ring):
     """n-gon ring of equal masses m around a central mass Mc: every ring body
     is pulled inward with G Mc/R^2 + (G m/R^2) sum_k 1/(4 sin(pi k/n)) and
     feels no tangential force.  The error scale is the closed-form term norm
-    T = G Mc/R^2 + (G m/(4R^2)) sum_k csc^2(pi k/n) = G Mc/R^2 + G m (n^2-1)/(12 R^2)."""
+    T = G Mc/R^2 + (G m/(4R^2)) sum_k csc^2(pi k/n) = G Mc/R^2 + G m (n^2-1)/(12 R^2).
+    The closed form holds for the exact polygon; rounding R cos, R sin to
+    FP64 moves neighbours (2 pi R/n apart) by ~eps R, which shifts a_p by
+    ~4 G m eps R (n / 2 pi R)^3 -- below 1e-13 T only for n of a few
+    thousand, so the FP64 case uses n = 4095 (FP64 at large n is pinned by the
+    integer-position chain below)."""
     G, R, m, Mc = 2.9591220828e-4, 2.0, 1e-8, 1.0
     th = 2 * np.pi * np.arange(n_ring) / n_ring
     r = np.concatenate([np.zeros((3, 1)), np.stack([R * np.cos(th), R * np.sin(th), 0 * th])], axis=1)
