@@ -151,11 +151,42 @@ nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
 nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *best,
                             double *best_ms);
 
+/* Largest system nbody_accel_static accepts. */
+#define NBODY_STATIC_MAX_BODIES 65536
+
+/* Eq. 1 accelerations of ONE system, FP64, without allocating device memory.
+ * (The paper has no counterpart: this is a deployment variant of the force
+ * kernel.)  Some callers cannot allocate: a host that reserves all device
+ * memory at start-up and forbids allocation afterwards (a real-time loop, a
+ * service with a fixed memory budget), or a component running while another
+ * allocator owns the device memory, where one more cudaMalloc may fail or
+ * stall.  This call uses no context and calls no cudaMalloc/cudaFree: its
+ * scratch (staged sources, work items, counters, fault flags) lives in one
+ * fixed-size __device__ array inside the library, about 2.1 MB, which every
+ * GPU that loads the library holds until the process exits.
+ *   n        bodies, 1 <= n <= NBODY_STATIC_MAX_BODIES, else NBODY_EINVAL.
+ *   G        gravitational constant, > 0.
+ *   x, y, z, m   DEVICE arrays of n doubles (positions, masses >= 0).
+ *   ax, ay, az   DEVICE arrays of n doubles, written with a_p.
+ *   cuda_stream  stream to run on (NULL: legacy default stream).
+ * Synchronous: returns after the results are written.  EINVAL for coincident
+ * bodies or non-finite input.  Messages: nbody_last_error(NULL).
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's
+ * contents; each call re-stages its inputs and clears its counters, but calls
+ * that overlap on the GPU (other streams or host threads) race on the array
+ * and must be serialised by the caller.  Results match nbody_init +
+ * nbody_accel in FP64 to rounding (the source order of the sum differs). */
+nbody_status nbody_accel_static(int64_t n, double G, const double *x, const double *y, const double *z,
+                                const double *m, double *ax, double *ay, double *az, void *cuda_stream);
+
 /* Release the context and everything it owns.  NULL is a no-op. */
 void nbody_free(nbody_ctx *ctx);
 
 /* Message of the last failure on ctx; with ctx == NULL, the last failure of
- * a call that could not return a context (nbody_init) on this thread. */
+ * a call that has no context (nbody_init, nbody_accel_static, nbody_peaks)
+ * on this thread. */
 const char *nbody_last_error(const nbody_ctx *ctx);
 
 /* Peak-rate microbenchmarks on the current device (instruction throughput,

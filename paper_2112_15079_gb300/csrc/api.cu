@@ -28,6 +28,10 @@ struct Grad;  // adjoint workspace (grad.cu)
 
 }  // namespace
 
+namespace nb {
+void set_last_error(const char *msg) { g_init_error = msg; }
+}  // namespace nb
+
 struct nbody_ctx {
   int dev = 0, nsm = 0;
   int64_t n_sys = 0;

@@ -88,6 +88,7 @@ size_t step_smem_bytes(int precision, int tj);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);
+void set_last_error(const char *msg);  // message returned by nbody_last_error(NULL) on this thread
 
 constexpr int kStages = 2;          // shared-memory pipeline depth of the force kernels
 constexpr int kFoldEvery = 64;      // mixed path: FP32 sub-sums of 64 sources folded into a float pair

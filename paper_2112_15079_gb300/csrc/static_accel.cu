@@ -1,0 +1,147 @@
+// nbody_accel_static: Eq. 1 accelerations of one system without allocating
+// device memory.  Some callers cannot allocate: hosts that reserve all device
+// memory up front and forbid allocation afterwards (real-time or embedded
+// loops, services with a fixed memory budget), and components that run while
+// another allocator owns the device memory, where an extra cudaMalloc may fail
+// or stall.  This entry point therefore keeps its scratch (the staged
+// sources, the work items, the work counters and the fault flags) in one
+// file-scope __device__ array of fixed size instead of asking for memory.
+//
+// The array is shared by every call on a device and keeps the previous
+// call's contents; each call re-stages what it reads and clears the counters
+// and flags that must start at zero.  Calls whose work overlaps on the GPU
+// (concurrent streams, or several host threads) race on the array and give
+// wrong results: serialise them.  Every GPU that loads this library holds the
+// array (kStaticScratchBytes) until the process exits.
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "nbody.h"
+#include "nbody_internal.h"
+
+namespace {
+
+using nb::Item;
+
+constexpr int64_t kMaxBodies = NBODY_STATIC_MAX_BODIES;
+constexpr int kThreads = 128;  // targets per work item (IPT 1)
+constexpr int kTj = 256;       // sources per shared-memory stage
+constexpr int kMaxItems = static_cast<int>((kMaxBodies + kThreads - 1) / kThreads);
+
+// Layout of the static scratch (byte offsets, each 256-byte aligned).
+constexpr size_t kOffStage = 0;                                     // double4 (x, y, z, G m) [kMaxBodies]
+constexpr size_t kOffItems = kOffStage + 32 * kMaxBodies;           // Item [kMaxItems]
+constexpr size_t kOffCounters = kOffItems + ((sizeof(Item) * kMaxItems + 255) / 256) * 256;  // int32 [2]
+constexpr size_t kOffFlags = kOffCounters + 256;                    // unsigned
+constexpr size_t kStaticScratchBytes = kOffFlags + 256;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device addresses of g_static_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+// Failure messages go where nbody_last_error(NULL) reads them.
+nbody_status fail(nbody_status st, const char *msg) {
+  nb::set_last_error(msg);
+  return st;
+}
+
+// One target block of kThreads bodies per item, all n sources (no split).
+__global__ void static_items_kernel(int32_t n, Item *items) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb_items = (n + kThreads - 1) / kThreads;
+  if (b >= nb_items) return;
+  Item it;
+  it.i0 = b * kThreads;
+  it.i1 = min(it.i0 + kThreads, n);
+  it.j0 = 0;
+  it.j1 = n;
+  it.slot = 0;
+  it.nsplit = 1;
+  it.ib = b;
+  it.sys = 0;
+  items[b] = it;
+}
+
+}  // namespace
+
+extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x, const double *y, const double *z,
+                                           const double *m, double *ax, double *ay, double *az, void *cuda_stream) {
+  nb::set_last_error("");
+  if (n < 1 || n > kMaxBodies) return fail(NBODY_EINVAL, "n must be in [1, NBODY_STATIC_MAX_BODIES]");
+  if (!x || !y || !z || !m || !ax || !ay || !az) return fail(NBODY_EINVAL, "a pointer is NULL");
+  if (!(G > 0.0)) return fail(NBODY_EINVAL, "G must be > 0");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail(NBODY_ECUDA, "no usable CUDA device");
+  void *base = nullptr;
+  {
+    // First call on this device: find the device address of the array (the
+    // host-side symbol is only a stand-in and must never reach a kernel).
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess || !p) return fail(NBODY_ECUDA, "cudaGetSymbolAddress failed for the static scratch");
+      g_addr[dev] = p;
+    }
+    base = g_addr[dev];
+  }
+  unsigned char *s = static_cast<unsigned char *>(base);
+  void *stage = s + kOffStage;
+  Item *items = reinterpret_cast<Item *>(s + kOffItems);
+  int32_t *counters = reinterpret_cast<int32_t *>(s + kOffCounters);
+  unsigned *flags = reinterpret_cast<unsigned *>(s + kOffFlags);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int N = static_cast<int>(n);
+  const int n_items = (N + kThreads - 1) / kThreads;
+
+  // Counters and flags start at zero on every call.
+  if (cudaMemsetAsync(counters, 0, 256 + 256, st) != cudaSuccess) return fail(NBODY_ECUDA, "cudaMemsetAsync failed");
+  static_items_kernel<<<(n_items + 127) / 128, 128, 0, st>>>(N, items);
+  if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA, "item launch failed");
+
+  nb::PrepArgs p{};
+  // The staging kernel validates positions and masses; it also reads
+  // velocities for that check, which this entry point does not take, so the
+  // positions stand in for them.
+  p.x = x; p.y = y; p.z = z; p.vx = x; p.vy = y; p.vz = z;
+  p.m = m;
+  p.stage_a = stage;
+  p.flags = flags;
+  p.N = N;
+  p.drift = 0;
+  p.check = 1;
+  p.G = G;
+  if (nb::launch_prep(0, p, st) != cudaSuccess) return fail(NBODY_ECUDA, "staging launch failed");
+
+  nb::StepArgs a{};
+  a.ax = ax; a.ay = ay; a.az = az;
+  a.cur_a = stage;
+  a.work_ctr = counters;
+  a.exit_ctr = counters + 1;
+  a.flags = flags;
+  a.items = items;
+  a.n_items = n_items;
+  a.N = N;
+  a.tj = kTj;
+  a.mode = nb::kModeForce;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = n_items < 4 * nsm ? n_items : 4 * nsm;
+  if (nb::launch_step(0, kThreads, 1, grid, nb::step_smem_bytes(0, kTj), a, st) != cudaSuccess)
+    return fail(NBODY_ECUDA, "force launch failed");
+
+  unsigned f = 0;
+  if (cudaMemcpyAsync(&f, flags, sizeof f, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(NBODY_ECUDA, "synchronisation failed");
+  if (f & nb::kFlagBadInput) return fail(NBODY_EINVAL, "non-finite position or negative/non-finite mass");
+  if (f & nb::kFlagTimeout) return fail(NBODY_ETIMEOUT, "a bounded device wait ran out");
+  if (f & nb::kFlagNonFinite) return fail(NBODY_EINVAL, "non-finite acceleration: two bodies coincide");
+  return NBODY_OK;
+}

@@ -60,6 +60,7 @@ _SIGS = {
     "nbody_free": (None, [_P]),
     "nbody_last_error": (ctypes.c_char_p, [_P]),
     "nbody_peaks": (_S, [ctypes.POINTER(ctypes.c_double)]),
+    "nbody_accel_static": (_S, [ctypes.c_int64, ctypes.c_double] + [_P] * 8),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -88,6 +89,24 @@ def peaks() -> dict:
     check(nbody_peaks(out))
     keys = ["ffma", "dfma", "rsqrt_f32", "rsqrt_f64", "cvt_f32_f64", "ffma2_lanes", "sm_mhz", "sms"]
     return dict(zip(keys, list(out)))
+
+
+NBODY_STATIC_MAX_BODIES = 65536
+
+
+def accel_static(r, m, G: float, stream=None):
+    """Eq. 1 accelerations [3, n] (FP64) of one system through
+    ``nbody_accel_static``, which allocates no device memory itself (its
+    scratch is a fixed array inside the library).  r: [3, n] and m: [n] CUDA
+    float64 tensors; the result tensor is allocated here, by torch."""
+    torch = _torch()
+    n = int(m.shape[0])
+    r = r.contiguous()
+    out = torch.empty((3, n), dtype=torch.float64, device=r.device)
+    s = stream if stream is not None else torch.cuda.current_stream(r.device)
+    check(nbody_accel_static(n, float(G), r[0].data_ptr(), r[1].data_ptr(), r[2].data_ptr(), m.data_ptr(),
+                             out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), _P(s.cuda_stream or None)))
+    return out
 
 
 def _torch():
