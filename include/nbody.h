@@ -72,13 +72,17 @@ typedef struct {
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
 #define NBODY_FLAG_NO_GRAPH 1
 
-/* Work decomposition of the force kernels (see nbody_set_tiles). */
+/* Work decomposition of the force kernels (see nbody_set_tiles).  The work
+ * of a step -- every target block (threads * ipt bodies of one system) times
+ * the sources of its system -- is cut into SMs * ctas_per_sm * jsplit equal
+ * shares, one per CTA; a block cut across shares gets partial sums that are
+ * reduced in a fixed order. */
 typedef struct {
   int32_t threads;     /* threads per CTA: 64, 128 or 256 */
   int32_t ipt;         /* target bodies per thread: 1, 2 or 4 */
   int32_t tj;          /* source bodies per shared-memory stage: multiple of 64, 64..1024 */
-  int32_t jsplit;      /* source chunks per target block, >= 1 (partial sums reduced in fixed order) */
-  int32_t ctas_per_sm; /* resident CTAs per SM of the persistent grid, >= 1 */
+  int32_t jsplit;      /* waves of CTAs, >= 1 (1: every CTA resident at once) */
+  int32_t ctas_per_sm; /* CTAs per SM per wave, >= 1 (capped at what fits) */
 } nbody_tiles;
 
 /* Create a context bound to caller-owned state.

@@ -49,10 +49,12 @@ struct nbody_ctx {
   // scratch
   std::vector<void *> allocs;
   double *a = nullptr;               // [3][N] acceleration at the current positions
-  void *stage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][hi|lo or double4]
+  void *stage[2] = {nullptr, nullptr};  // ping-pong staged sources (layout per precision)
+  int64_t n_stage = 0;               // stage entries (mixed: systems padded to even length)
+  std::vector<int64_t> soff;         // stage offset of each system
+  int32_t *qidx = nullptr;           // [N] stage index of each body (mixed)
   double *R = nullptr;               // [3][N] mixed: FP64 positions of the staged step
   double *snap = nullptr;            // [6][N] r0, v0 for nbody_grad
-  int32_t *counters = nullptr;       // [0] work, [1] exit
   unsigned *flags = nullptr;
   int64_t *offsets_dev = nullptr;
   double *e_body = nullptr;          // [2][N]
@@ -60,12 +62,13 @@ struct nbody_ctx {
   Item *eitems = nullptr;
   int n_eitems = 0;
 
-  // tile-dependent scratch
+  // tile-dependent scratch (stream-K work tables)
   nbody_tiles tiles{};
-  Item *items = nullptr;
-  int n_items = 0;
+  nb::Blk *blks = nullptr;
+  int n_blks = 0;
+  nb::Seg *segs = nullptr;
+  int32_t *seg_off = nullptr;
   int32_t *arrive = nullptr;
-  int n_iblocks = 0;
   double *partial = nullptr;
   int partial_rows = 0;
   size_t smem = 0;
@@ -147,11 +150,12 @@ nbody_status end_work(nbody_ctx *c) {
 
 bool tiles_valid(const nbody_tiles &t, int precision) {
   return nb::step_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 1024 &&
-         t.tj % 64 == 0 && t.jsplit >= 1 && t.jsplit <= 1024 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
+         t.tj % 64 == 0 && t.jsplit >= 1 && t.jsplit <= 64 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
   nbody_tiles t{};
+  t.jsplit = 1;  // one wave of CTAs
   if (c->o.precision == NBODY_FP64) {
     t.threads = 128;
     t.ipt = 1;
@@ -159,79 +163,96 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
     t.ctas_per_sm = 4;
   } else {
     t.threads = 256;
-    t.ipt = 2;
-    t.tj = 256;
-    t.ctas_per_sm = 3;  // 80 registers x 256 threads: 3 CTAs (24 warps) per SM
+    t.ipt = 1;
+    t.tj = 512;
+    t.ctas_per_sm = 4;  // 64 registers x 256 threads: 4 CTAs (32 warps) per SM
   }
-  // Enough items for an even spread over the persistent grid: aim for about
-  // 8 items per resident CTA, splitting the sources of each target block
-  // into chunks of at least 128 bodies.
-  int64_t largest = 0, blocks = 0;
-  const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
-  for (int64_t s = 0; s < c->n_sys; ++s) {
-    const int64_t ns = c->offsets[s + 1] - c->offsets[s];
-    largest = std::max(largest, ns);
-    blocks += (ns + B - 1) / B;
-  }
-  const int64_t target = 8LL * c->nsm * t.ctas_per_sm;
-  int64_t S = (target + blocks - 1) / std::max<int64_t>(blocks, 1);
-  S = std::min<int64_t>(S, std::max<int64_t>(1, largest / 128));
-  t.jsplit = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(S, 64)));
   return t;
 }
 
-// (Re)build the work items for the current tiles.
+// (Re)build the stream-K work tables for the current tiles: target blocks of
+// threads*ipt bodies per system, the line of (block, source) work cut into
+// `grid` equal shares (in units of 2 sources for the mixed pair layout, 1
+// for FP64), and per block the number of shares it is cut into.
 nbody_status build_items(nbody_ctx *c) {
   drop_graphs(c);
-  dfree(c, c->items);
+  dfree(c, c->blks);
+  dfree(c, c->segs);
+  dfree(c, c->seg_off);
   dfree(c, c->arrive);
   dfree(c, c->partial);
-  c->items = nullptr;
+  c->blks = nullptr;
+  c->segs = nullptr;
+  c->seg_off = nullptr;
   c->arrive = nullptr;
   c->partial = nullptr;
   const nbody_tiles &t = c->tiles;
   const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
-  std::vector<Item> items;
-  int ib = 0, rows = 1;
+  const int64_t unit = c->o.precision == NBODY_MIXED ? 2 : 1;
+  std::vector<nb::Blk> blks;
+  std::vector<int64_t> bj0, bunits, bstart;  // per block: first source (stage), length in units, line start
+  int64_t W = 0;
   for (int64_t s = 0; s < c->n_sys; ++s) {
     const int64_t b = c->offsets[s], e = c->offsets[s + 1], ns = e - b;
-    const int64_t S = std::min<int64_t>(t.jsplit, ns);
-    rows = std::max<int>(rows, static_cast<int>(S));
-    for (int64_t i0 = b; i0 < e; i0 += B, ++ib) {
-      const int64_t i1 = std::min(i0 + B, e);
-      for (int64_t k = 0; k < S; ++k) {
-        Item it;
-        it.i0 = static_cast<int32_t>(i0);
-        it.i1 = static_cast<int32_t>(i1);
-        it.j0 = static_cast<int32_t>(b + ns * k / S);
-        it.j1 = static_cast<int32_t>(b + ns * (k + 1) / S);
-        it.slot = static_cast<int32_t>(k);
-        it.nsplit = static_cast<int32_t>(S);
-        it.ib = ib;
-        it.sys = static_cast<int32_t>(s);
-        items.push_back(it);
-      }
+    const int64_t len = (ns + unit - 1) / unit;  // units of this system's (padded) source range
+    for (int64_t i0 = b; i0 < e; i0 += B) {
+      nb::Blk k;
+      k.i0 = static_cast<int32_t>(i0);
+      k.i1 = static_cast<int32_t>(std::min(i0 + B, e));
+      k.q0 = static_cast<int32_t>(c->soff[s] + (i0 - b));
+      k.nsplit = 0;
+      blks.push_back(k);
+      bj0.push_back(c->soff[s]);
+      bunits.push_back(len);
+      bstart.push_back(W);
+      W += len;
     }
   }
-  // Longest first (cost = targets x sources); ties keep construction order.
-  std::stable_sort(items.begin(), items.end(), [](const Item &p, const Item &q) {
-    return static_cast<int64_t>(p.i1 - p.i0) * (p.j1 - p.j0) > static_cast<int64_t>(q.i1 - q.i0) * (q.j1 - q.j0);
-  });
-  c->n_items = static_cast<int>(items.size());
-  c->n_iblocks = ib;
+  // Resident CTAs: never more than fit at once (a share per CTA, one wave).
+  c->smem = nb::step_smem_bytes(c->o.precision, t.tj);
+  NB_CUDA(c, nb::launch_step(c->o.precision, t.threads, t.ipt, 0, c->smem, nb::StepArgs{}, nullptr));
+  const int occ = nb::step_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->smem);
+  if (occ < 1) return fail(c, NBODY_EINVAL, "tiles do not fit on an SM (threads %d, ipt %d, tj %d)", t.threads, t.ipt, t.tj);
+  const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(W, static_cast<int64_t>(c->nsm) * cps * t.jsplit));
+  std::vector<nb::Seg> segs;
+  std::vector<int32_t> seg_off(G + 1, 0);
+  size_t b = 0;
+  for (int64_t g = 0; g < G; ++g) {
+    const int64_t lo = W * g / G, hi = W * (g + 1) / G;
+    seg_off[g] = static_cast<int32_t>(segs.size());
+    while (b < blks.size() && bstart[b] + bunits[b] <= lo) ++b;
+    for (size_t k = b; k < blks.size() && bstart[k] < hi; ++k) {
+      const int64_t u0 = std::max(lo, bstart[k]) - bstart[k];
+      const int64_t u1 = std::min(hi, bstart[k] + bunits[k]) - bstart[k];
+      if (u1 <= u0) continue;
+      nb::Seg sg;
+      sg.blk = static_cast<int32_t>(k);
+      sg.s0 = static_cast<int32_t>(bj0[k] + u0 * unit);
+      sg.s1 = static_cast<int32_t>(bj0[k] + u1 * unit);
+      sg.slot = blks[k].nsplit++;
+      segs.push_back(sg);
+    }
+  }
+  seg_off[G] = static_cast<int32_t>(segs.size());
+  int rows = 1;
+  for (const nb::Blk &k : blks) rows = std::max(rows, static_cast<int>(k.nsplit));
+  c->n_blks = static_cast<int>(blks.size());
   c->partial_rows = rows;
+  c->grid = static_cast<int>(G);
   nbody_status st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->items), sizeof(Item) * items.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->arrive), sizeof(int32_t) * ib)) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->arrive), sizeof(int32_t) * blks.size())) != NBODY_OK) return st;
   if (rows > 1 &&
       (st = dalloc(c, reinterpret_cast<void **>(&c->partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
           NBODY_OK)
     return st;
-  NB_CUDA(c, cudaMemcpy(c->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemset(c->arrive, 0, sizeof(int32_t) * ib));
-  c->smem = nb::step_smem_bytes(c->o.precision, t.tj);
-  c->grid = static_cast<int>(std::min<int64_t>(c->n_items, static_cast<int64_t>(c->nsm) * t.ctas_per_sm));
-  NB_CUDA(c, nb::launch_step(c->o.precision, t.threads, t.ipt, 0, c->smem, nb::StepArgs{}, nullptr));
+  NB_CUDA(c, cudaMemcpy(c->blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemcpy(c->segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemcpy(c->seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemset(c->arrive, 0, sizeof(int32_t) * blks.size()));
   return NBODY_OK;
 }
 
@@ -251,8 +272,8 @@ nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check) {
   p.x = s.x; p.y = s.y; p.z = s.z; p.vx = s.vx; p.vy = s.vy; p.vz = s.vz;
   p.ax = s.ax; p.ay = s.ay; p.az = s.az;
   p.m = c->m;
-  p.stage_a = c->stage[0][0];
-  p.stage_b = c->stage[0][1];
+  p.stage = c->stage[0];
+  p.qidx = c->qidx;
   p.Rx = c->R;
   p.Ry = c->R ? c->R + N : nullptr;
   p.Rz = c->R ? c->R + 2 * N : nullptr;
@@ -271,20 +292,17 @@ nb::StepArgs step_args(nbody_ctx *c, const State &s, int cur, int mode) {
   nb::StepArgs a{};
   a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
   a.ax = s.ax; a.ay = s.ay; a.az = s.az;
-  a.cur_a = c->stage[cur][0];
-  a.cur_b = c->stage[cur][1];
-  a.nxt_a = c->stage[1 - cur][0];
-  a.nxt_b = c->stage[1 - cur][1];
+  a.cur = c->stage[cur];
+  a.nxt = c->stage[1 - cur];
   a.Rx = c->R;
   a.Ry = c->R ? c->R + N : nullptr;
   a.Rz = c->R ? c->R + 2 * N : nullptr;
   a.partial = c->partial;
   a.arrive = c->arrive;
-  a.work_ctr = c->counters;
-  a.exit_ctr = c->counters + 1;
   a.flags = c->flags;
-  a.items = c->items;
-  a.n_items = c->n_items;
+  a.blks = c->blks;
+  a.segs = c->segs;
+  a.seg_off = c->seg_off;
   a.N = c->N;
   a.tj = c->tiles.tj;
   a.mode = mode;
@@ -373,27 +391,35 @@ nbody_status refresh(nbody_ctx *c) {
 nbody_status alloc_scratch(nbody_ctx *c) {
   const size_t N = c->N;
   nbody_status st;
+  // Stage layout: FP64 in body order; mixed in pair blocks with every system
+  // padded to an even number of entries.
+  c->soff.assign(c->n_sys + 1, 0);
+  for (int64_t s = 0; s < c->n_sys; ++s) {
+    const int64_t ns = c->offsets[s + 1] - c->offsets[s];
+    c->soff[s + 1] = c->soff[s] + (c->o.precision == NBODY_MIXED ? (ns + 1) / 2 * 2 : ns);
+  }
+  c->n_stage = c->soff[c->n_sys];
 #define NB_ALLOC(ptr, bytes) \
   if ((st = dalloc(c, reinterpret_cast<void **>(&(ptr)), (bytes))) != NBODY_OK) return st;
   NB_ALLOC(c->a, sizeof(double) * 3 * N);
-  if (c->o.precision == NBODY_FP64) {
-    NB_ALLOC(c->stage[0][0], 32 * N);
-    NB_ALLOC(c->stage[1][0], 32 * N);
-  } else {
-    NB_ALLOC(c->stage[0][0], 16 * N);
-    NB_ALLOC(c->stage[0][1], 16 * N);
-    NB_ALLOC(c->stage[1][0], 16 * N);
-    NB_ALLOC(c->stage[1][1], 16 * N);
+  NB_ALLOC(c->stage[0], 32 * static_cast<size_t>(c->n_stage));
+  NB_ALLOC(c->stage[1], 32 * static_cast<size_t>(c->n_stage));
+  if (c->o.precision == NBODY_MIXED) {
     NB_ALLOC(c->R, sizeof(double) * 3 * N);
+    NB_ALLOC(c->qidx, sizeof(int32_t) * N);
+    std::vector<int32_t> q(N);
+    for (int64_t s = 0; s < c->n_sys; ++s)
+      for (int64_t p = c->offsets[s]; p < c->offsets[s + 1]; ++p)
+        q[p] = static_cast<int32_t>(c->soff[s] + (p - c->offsets[s]));
+    NB_CUDA(c, cudaMemcpy(c->qidx, q.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+    for (int b = 0; b < 2; ++b) NB_CUDA(c, nb::launch_pad_fill(c->stage[b], c->n_stage / 2, c->stream));
   }
   NB_ALLOC(c->snap, sizeof(double) * 6 * N);
-  NB_ALLOC(c->counters, sizeof(int32_t) * 2);
   NB_ALLOC(c->flags, sizeof(unsigned));
   NB_ALLOC(c->offsets_dev, sizeof(int64_t) * (c->n_sys + 1));
   NB_ALLOC(c->e_body, sizeof(double) * 2 * N);
   NB_ALLOC(c->e_out, sizeof(double) * 2 * c->n_sys);
 #undef NB_ALLOC
-  NB_CUDA(c, cudaMemset(c->counters, 0, sizeof(int32_t) * 2));
   NB_CUDA(c, cudaMemset(c->flags, 0, sizeof(unsigned)));
   NB_CUDA(c, cudaMemcpy(c->offsets_dev, c->offsets.data(), sizeof(int64_t) * (c->n_sys + 1), cudaMemcpyHostToDevice));
   // energy items: blocks of kEnergyBlock targets against the whole system
@@ -608,7 +634,7 @@ nbody_status nbody_get_tiles(const nbody_ctx *c, nbody_tiles *t) {
 nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
   if (!c) return NBODY_EINVAL;
   if (!t || !tiles_valid(*t, c->o.precision))
-    return fail(c, NBODY_EINVAL, "invalid tiles (threads 64/128/256, ipt 1/2/4, tj 64..1024 step 64, jsplit 1..1024, ctas_per_sm 1..32)");
+    return fail(c, NBODY_EINVAL, "invalid tiles (threads 64/128/256, ipt 1/2/4, tj 64..1024 step 64, jsplit 1..64, ctas_per_sm 1..32)");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tiles = *t;
   return build_items(c);
@@ -630,27 +656,21 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
     return NBODY_OK;
   };
   std::vector<nbody_tiles> cand;
-  const nbody_tiles base = default_tiles(c);
-  const int threads_list[3] = {64, 128, 256};
-  const int ipt_list[3] = {1, 2, 4};
-  const int split_mul[4] = {1, 2, 4, 8};
-  for (int th : threads_list)
-    for (int ip : ipt_list) {
-      if (c->o.precision == NBODY_MIXED && th == 64) continue;
-      if (c->o.precision == NBODY_FP64 && ip == 4) continue;
-      for (int sm : split_mul)
-        for (int cps : {1, 2, 3, 4}) {
-          nbody_tiles t = base;
-          t.threads = th;
-          t.ipt = ip;
-          t.ctas_per_sm = cps;
-          // Rescale jsplit so the item count stays comparable, then vary it.
-          const int64_t B0 = static_cast<int64_t>(base.threads) * base.ipt, B = static_cast<int64_t>(th) * ip;
-          int64_t S = std::max<int64_t>(1, base.jsplit * B / B0 * sm / 2);
-          t.jsplit = static_cast<int32_t>(std::min<int64_t>(S, 256));
-          cand.push_back(t);
-        }
-    }
+  const bool mixed = c->o.precision == NBODY_MIXED;
+  for (int th : {64, 128, 256})
+    for (int ip : {1, 2})
+      for (int tj : {256, 512, 1024})
+        for (int cps : {1, 2, 3, 4})
+          for (int waves : {1, 2}) {
+            if (mixed ? (th == 64 || cps == 1) : (tj != 256 || cps == 3)) continue;
+            nbody_tiles t;
+            t.threads = th;
+            t.ipt = ip;
+            t.tj = tj;
+            t.ctas_per_sm = cps;
+            t.jsplit = waves;
+            cand.push_back(t);
+          }
   cudaEvent_t e0, e1;
   NB_CUDA(c, cudaEventCreate(&e0));
   NB_CUDA(c, cudaEventCreate(&e1));

@@ -3,13 +3,29 @@
 
 namespace nb {
 
-cudaError_t launch_step_fp64(int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s);
-cudaError_t launch_step_mixed(int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s);
+cudaError_t run_step_fp64(int op, int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s,
+                          int *occ);
+cudaError_t run_step_mixed(int op, int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s,
+                           int *occ);
 
+// grid == 0: only raise the dynamic shared-memory limit (see step_launch.cuh).
 cudaError_t launch_step(int precision, int threads, int ipt, int grid, size_t smem, const StepArgs &a,
                         cudaStream_t s) {
-  return precision == 0 ? launch_step_fp64(threads, ipt, grid, smem, a, s)
-                        : launch_step_mixed(threads, ipt, grid, smem, a, s);
+  const int op = grid == 0 ? 1 : 0;
+  return precision == 0 ? run_step_fp64(op, threads, ipt, grid, smem, a, s, nullptr)
+                        : run_step_mixed(op, threads, ipt, grid, smem, a, s, nullptr);
+}
+
+int step_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem) {
+  int occ = 0;
+  const StepArgs a{};
+  cudaError_t e = precision == 0 ? run_step_fp64(2, threads, ipt, 0, smem, a, nullptr, &occ)
+                                 : run_step_mixed(2, threads, ipt, 0, smem, a, nullptr, &occ);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
 }
 
 bool step_config_supported(int precision, int threads, int ipt) {
@@ -24,8 +40,10 @@ size_t step_smem_bytes(int precision, int tj) {
 
 // ---------------------------------------------------------------------------
 // Stage the sources of the next force launch: r (drift == 0) or the Eq. 3
-// drift of (r, v, a) (drift == 1), with mu = G m.  FP64: double4_32a (x,y,z,mu).
-// Mixed: FP64 positions R plus float4 hi (x,y,z,mu) and lo (x,y,z,0).
+// drift of (r, v, a) (drift == 1), with mu = G m.
+//   FP64: double4 (x, y, z, mu) at index p.
+//   Mixed: FP64 positions R[p], and hi = fl32(r), lo = fl32(r - hi), mu into
+//   the pair block of stage entry q = qidx[p] (layout in step_kernel.cuh).
 // ---------------------------------------------------------------------------
 template <int PREC>
 __global__ void prep_kernel(const PrepArgs a) {
@@ -44,14 +62,22 @@ __global__ void prep_kernel(const PrepArgs a) {
   }
   const double mu = a.G * m;
   if (PREC == 0) {
-    static_cast<double4_32a *>(a.stage_a)[p] = make_double4_32a(rx, ry, rz, mu);
+    static_cast<double4_32a *>(a.stage)[p] = make_double4_32a(rx, ry, rz, mu);
   } else {
     a.Rx[p] = rx;
     a.Ry[p] = ry;
     a.Rz[p] = rz;
+    const int q = a.qidx[p];
+    float *w = static_cast<float *>(a.stage) + static_cast<size_t>(q >> 1) * 16 + (q & 1);
     const float hx = hi_part(rx), hy = hi_part(ry), hz = hi_part(rz);
-    static_cast<float4 *>(a.stage_a)[p] = make_float4(hx, hy, hz, static_cast<float>(mu));
-    static_cast<float4 *>(a.stage_b)[p] = make_float4(lo_part(rx, hx), lo_part(ry, hy), lo_part(rz, hz), 0.f);
+    w[0] = hx;
+    w[2] = hy;
+    w[4] = hz;
+    w[6] = static_cast<float>(mu);
+    w[8] = lo_part(rx, hx);
+    w[10] = lo_part(ry, hy);
+    w[12] = lo_part(rz, hz);
+    w[14] = 0.f;
   }
 }
 
@@ -62,6 +88,23 @@ cudaError_t launch_prep(int precision, const PrepArgs &a, cudaStream_t s) {
     prep_kernel<0><<<grid, 256, 0, s>>>(a);
   else
     prep_kernel<1><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Padding sources of the mixed layout: hi = (kPadCoord, kPadCoord,
+// kPadCoord), mu = 0, lo = 0.  Against any real target r2 ~ 3e30 stays
+// finite in FP32, q = r2^{-1/2} is tiny and mu = 0 makes the term exactly 0.
+__global__ void pad_fill_kernel(float *stage, int64_t n_pairs) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_pairs * 16) return;
+  const int f = static_cast<int>(i & 15);
+  stage[i] = f < 6 ? kPadCoord : 0.f;
+}
+
+cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s) {
+  if (n_pairs <= 0) return cudaSuccess;
+  const int64_t n = n_pairs * 16;
+  pad_fill_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(static_cast<float *>(stage), n_pairs);
   return cudaGetLastError();
 }
 

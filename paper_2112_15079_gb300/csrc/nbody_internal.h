@@ -14,48 +14,64 @@ enum : unsigned {
   kFlagBadInput = 4u,   // negative mass or non-finite state at staging time
 };
 
-// One unit of force work: targets [i0, i1) of one system against the
-// sources [j0, j1) of the same system.  The sources of a target block are
-// split into `nsplit` chunks; `slot` is this chunk's index (partial-sum row)
-// and `ib` the global index of the target block (arrival counter).
+// Work description shared by the energy kernel: targets [i0, i1) against
+// sources [j0, j1) of the same system.
 struct Item {
   int32_t i0, i1, j0, j1;
   int32_t slot, nsplit, ib, sys;
 };
 static_assert(sizeof(Item) == 32, "Item layout");
 
+// Force kernels: a target block of one system (threads * ipt consecutive
+// bodies [i0, i1); q0 = stage index of body i0) whose source range is cut
+// into `nsplit` contiguous segments processed by different CTAs.
+struct Blk {
+  int32_t i0, i1, q0, nsplit;
+};
+static_assert(sizeof(Blk) == 16, "Blk layout");
+
+// One segment: sources [s0, s1) (stage indices) of block `blk`; `slot` is the
+// segment's rank within the block (partial-sum row, reduction order).
+struct Seg {
+  int32_t blk, s0, s1, slot;
+};
+static_assert(sizeof(Seg) == 16, "Seg layout");
+
 enum Mode : int32_t {
   kModeForce = 0,  // write a = Eq. 1 only
   kModeStep = 1,   // Eq. 4 kick with the new a, then Eq. 3 drift into the next stage
 };
 
-// Arguments of one force launch (passed by value).
+// Arguments of one force launch (passed by value).  CTA c processes the
+// segments segs[seg_off[c] .. seg_off[c+1]) in order (an equal share of the
+// whole work, stream-K style).
 struct StepArgs {
   // state (caller-owned or the adjoint's shadow copy)
   double *x, *y, *z, *vx, *vy, *vz;
   double *ax, *ay, *az;  // a at the previous step in, a at this step out
   // staged sources of this step and the stage the epilogue fills for the next
-  const void *cur_a, *cur_b;  // FP64: double4 (x,y,z,Gm); mixed: float4 hi, float4 lo
-  void *nxt_a, *nxt_b;
+  const void *cur;  // FP64: double4 (x,y,z,Gm) per body; mixed: pair blocks (see kernels)
+  void *nxt;
   double *Rx, *Ry, *Rz;  // mixed only: FP64 positions of the current step (updated in place)
-  double *partial;       // [jsplit][3][N] partial sums
-  int32_t *arrive;       // [n_iblocks] arrival counters (self-resetting)
-  int32_t *work_ctr;     // persistent-grid work counter (self-resetting)
-  int32_t *exit_ctr;
+  double *partial;       // [max nsplit][3][N] partial sums
+  int32_t *arrive;       // [n_blocks] arrival counters (self-resetting)
   unsigned *flags;
-  const Item *items;
-  int32_t n_items;
+  const Blk *blks;
+  const Seg *segs;
+  const int32_t *seg_off;  // [gridDim.x + 1]
   int32_t N;
   int32_t tj;
   int32_t mode;
   double dt, half_dt, half_dt2;
 };
 
-// Staging / pre-drift over all N bodies: stage r (mode 0) or drift(r, v, a)
-// (mode 1) into the stage buffers, with mu = G m.
+// Staging / pre-drift over all N bodies: stage r (drift == 0) or
+// drift(r, v, a) (drift == 1), with mu = G m, at stage index qidx[p]
+// (mixed; FP64 stages in body order).
 struct PrepArgs {
   const double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az, *m;
-  void *stage_a, *stage_b;
+  void *stage;
+  const int32_t *qidx;
   double *Rx, *Ry, *Rz;
   unsigned *flags;
   int32_t N;
@@ -81,6 +97,9 @@ struct ReduceArgs {
 
 // Launchers (return the launch's cudaError_t).
 cudaError_t launch_prep(int precision, const PrepArgs &a, cudaStream_t s);
+// Mixed stages: fill n_pairs pair blocks with inert padding sources.
+cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s);
+int step_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 cudaError_t launch_step(int precision, int threads, int ipt, int grid, size_t smem,
                         const StepArgs &a, cudaStream_t s);
 bool step_config_supported(int precision, int threads, int ipt);
@@ -91,7 +110,8 @@ cudaError_t run_peaks(double *out);
 void set_last_error(const char *msg);  // message returned by nbody_last_error(NULL) on this thread
 
 constexpr int kStages = 2;          // shared-memory pipeline depth of the force kernels
-constexpr int kFoldEvery = 64;      // mixed path: FP32 sub-sums of 64 sources folded into a float pair
+constexpr int kFoldPairs = 64;      // mixed path: packed sub-sums of 64 source pairs folded into a float pair
+constexpr float kPadCoord = 1e15f;  // mixed padding source: far away and massless (term exactly 0)
 constexpr int kEnergyBlock = 256;
 
 }  // namespace nb

@@ -4,12 +4,12 @@
 // loops, services with a fixed memory budget), and components that run while
 // another allocator owns the device memory, where an extra cudaMalloc may fail
 // or stall.  This entry point therefore keeps its scratch (the staged
-// sources, the work items, the work counters and the fault flags) in one
+// sources, the work tables and the fault flags) in one
 // file-scope __device__ array of fixed size instead of asking for memory.
 //
 // The array is shared by every call on a device and keeps the previous
-// call's contents; each call re-stages what it reads and clears the counters
-// and flags that must start at zero.  Calls whose work overlaps on the GPU
+// call's contents; each call rewrites the staged sources and work tables it
+// reads and clears the fault flags, which must start at zero.  Calls whose work overlaps on the GPU
 // (concurrent streams, or several host threads) race on the array and give
 // wrong results: serialise them.  Every GPU that loads this library holds the
 // array (kStaticScratchBytes) until the process exits.
@@ -23,18 +23,19 @@
 
 namespace {
 
-using nb::Item;
-
 constexpr int64_t kMaxBodies = NBODY_STATIC_MAX_BODIES;
-constexpr int kThreads = 128;  // targets per work item (IPT 1)
+constexpr int kThreads = 128;  // targets per block (IPT 1)
 constexpr int kTj = 256;       // sources per shared-memory stage
-constexpr int kMaxItems = static_cast<int>((kMaxBodies + kThreads - 1) / kThreads);
+constexpr int kMaxBlocks = static_cast<int>((kMaxBodies + kThreads - 1) / kThreads);
+
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Layout of the static scratch (byte offsets, each 256-byte aligned).
-constexpr size_t kOffStage = 0;                                     // double4 (x, y, z, G m) [kMaxBodies]
-constexpr size_t kOffItems = kOffStage + 32 * kMaxBodies;           // Item [kMaxItems]
-constexpr size_t kOffCounters = kOffItems + ((sizeof(Item) * kMaxItems + 255) / 256) * 256;  // int32 [2]
-constexpr size_t kOffFlags = kOffCounters + 256;                    // unsigned
+constexpr size_t kOffStage = 0;                                             // double4 (x, y, z, G m) [kMaxBodies]
+constexpr size_t kOffBlks = kOffStage + 32 * kMaxBodies;                    // Blk [kMaxBlocks]
+constexpr size_t kOffSegs = kOffBlks + align256(sizeof(nb::Blk) * kMaxBlocks);  // Seg [kMaxBlocks]
+constexpr size_t kOffSegOff = kOffSegs + align256(sizeof(nb::Seg) * kMaxBlocks);  // int32 [kMaxBlocks + 1]
+constexpr size_t kOffFlags = kOffSegOff + align256(sizeof(int32_t) * (kMaxBlocks + 1));  // unsigned
 constexpr size_t kStaticScratchBytes = kOffFlags + 256;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -50,21 +51,26 @@ nbody_status fail(nbody_status st, const char *msg) {
   return st;
 }
 
-// One target block of kThreads bodies per item, all n sources (no split).
-__global__ void static_items_kernel(int32_t n, Item *items) {
+// One block of kThreads targets per CTA, each against all n sources (no
+// split): block b is CTA b's only segment.
+__global__ void static_tables_kernel(int32_t n, nb::Blk *blks, nb::Seg *segs, int32_t *seg_off) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nb_items = (n + kThreads - 1) / kThreads;
-  if (b >= nb_items) return;
-  Item it;
-  it.i0 = b * kThreads;
-  it.i1 = min(it.i0 + kThreads, n);
-  it.j0 = 0;
-  it.j1 = n;
-  it.slot = 0;
-  it.nsplit = 1;
-  it.ib = b;
-  it.sys = 0;
-  items[b] = it;
+  const int n_blocks = (n + kThreads - 1) / kThreads;
+  if (b > n_blocks) return;
+  seg_off[b] = b;
+  if (b == n_blocks) return;
+  nb::Blk k;
+  k.i0 = b * kThreads;
+  k.i1 = min(k.i0 + kThreads, n);
+  k.q0 = k.i0;
+  k.nsplit = 1;
+  blks[b] = k;
+  nb::Seg sg;
+  sg.blk = b;
+  sg.s0 = 0;
+  sg.s1 = n;
+  sg.slot = 0;
+  segs[b] = sg;
 }
 
 }  // namespace
@@ -93,17 +99,18 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   }
   unsigned char *s = static_cast<unsigned char *>(base);
   void *stage = s + kOffStage;
-  Item *items = reinterpret_cast<Item *>(s + kOffItems);
-  int32_t *counters = reinterpret_cast<int32_t *>(s + kOffCounters);
+  nb::Blk *blks = reinterpret_cast<nb::Blk *>(s + kOffBlks);
+  nb::Seg *segs = reinterpret_cast<nb::Seg *>(s + kOffSegs);
+  int32_t *seg_off = reinterpret_cast<int32_t *>(s + kOffSegOff);
   unsigned *flags = reinterpret_cast<unsigned *>(s + kOffFlags);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int N = static_cast<int>(n);
-  const int n_items = (N + kThreads - 1) / kThreads;
+  const int n_blocks = (N + kThreads - 1) / kThreads;
 
-  // Counters and flags start at zero on every call.
-  if (cudaMemsetAsync(counters, 0, 256 + 256, st) != cudaSuccess) return fail(NBODY_ECUDA, "cudaMemsetAsync failed");
-  static_items_kernel<<<(n_items + 127) / 128, 128, 0, st>>>(N, items);
-  if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA, "item launch failed");
+  // The fault flags start at zero on every call; the tables are rewritten.
+  if (cudaMemsetAsync(flags, 0, sizeof(unsigned), st) != cudaSuccess) return fail(NBODY_ECUDA, "cudaMemsetAsync failed");
+  static_tables_kernel<<<(n_blocks + 1 + 127) / 128, 128, 0, st>>>(N, blks, segs, seg_off);
+  if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA, "table launch failed");
 
   nb::PrepArgs p{};
   // The staging kernel validates positions and masses; it also reads
@@ -111,7 +118,7 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   // positions stand in for them.
   p.x = x; p.y = y; p.z = z; p.vx = x; p.vy = y; p.vz = z;
   p.m = m;
-  p.stage_a = stage;
+  p.stage = stage;
   p.flags = flags;
   p.N = N;
   p.drift = 0;
@@ -121,19 +128,15 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
 
   nb::StepArgs a{};
   a.ax = ax; a.ay = ay; a.az = az;
-  a.cur_a = stage;
-  a.work_ctr = counters;
-  a.exit_ctr = counters + 1;
+  a.cur = stage;
   a.flags = flags;
-  a.items = items;
-  a.n_items = n_items;
+  a.blks = blks;
+  a.segs = segs;
+  a.seg_off = seg_off;
   a.N = N;
   a.tj = kTj;
   a.mode = nb::kModeForce;
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = n_items < 4 * nsm ? n_items : 4 * nsm;
-  if (nb::launch_step(0, kThreads, 1, grid, nb::step_smem_bytes(0, kTj), a, st) != cudaSuccess)
+  if (nb::launch_step(0, kThreads, 1, n_blocks, nb::step_smem_bytes(0, kTj), a, st) != cudaSuccess)
     return fail(NBODY_ECUDA, "force launch failed");
 
   unsigned f = 0;

@@ -2,7 +2,8 @@
 #include "step_launch.cuh"
 
 namespace nb {
-cudaError_t launch_step_fp64(int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s) {
-  return launch_prec<0>(threads, ipt, grid, smem, a, s);
+cudaError_t run_step_fp64(int op, int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s,
+                          int *occ) {
+  return run_prec<0>(op, threads, ipt, grid, smem, a, s, occ);
 }
 }  // namespace nb

@@ -1,20 +1,29 @@
 // Fused Eq. 1 force + Eq. 4 kick + Eq. 3 drift, one launch per Verlet step.
 //
-// Work decomposition: a persistent grid (ctas_per_sm CTAs per SM) pulls
-// Items from an atomic counter.  Items are sorted by cost (largest first),
-// so the pull order is a longest-processing-time list schedule, which also
-// balances uneven systems of a batched run.  An Item is a block of
-// THREADS*IPT targets of one system against one chunk of that system's
-// sources.  Targets live in registers (IPT per thread, strided by THREADS
-// for coalesced access); sources stream through a kStages-deep shared-memory
-// ring filled by 1-D bulk copies (cp.async.bulk, completion on mbarriers),
-// issued by one thread, `tj` sources per stage.
+// Work decomposition (stream-K style): the force work of a step is the list
+// of target blocks (THREADS*IPT consecutive bodies of one system) times the
+// sources of their system, laid end to end.  The host cuts that line into
+// gridDim.x equal shares; CTA c walks the segments of share c in order.  A
+// block whose sources are cut across several CTAs gets one FP64 (FP64 path)
+// or float-pair (mixed path) partial sum per segment; the CTA that finishes
+// the block's last segment sums the partials in segment order (fixed order,
+// so results do not depend on scheduling) and runs the epilogue.  No CTA ever
+// waits for another, and every CTA has the same amount of work, so a step
+// has no tail of idle SMs beyond the epilogues.
 //
-// Split sources: when a target block has nsplit > 1 chunks, each chunk's CTA
-// writes FP64 partial sums, then bumps the block's arrival counter; the CTA
-// that arrives last sums the partials in slot order 0..nsplit-1 (fixed
-// order, so results do not depend on scheduling) and runs the epilogue.
-// Nothing ever spins on another CTA.
+// Sources stream through a kStages-deep shared-memory ring filled by 1-D bulk
+// copies (cp.async.bulk, completion on mbarriers) issued by one thread, `tj`
+// sources per stage.  Targets live in registers (IPT per thread, strided by
+// THREADS so their loads coalesce).
+//
+// FP64 path: sources as double4 (x, y, z, G m), one per body.
+// Mixed path: sources as pair blocks of 64 bytes holding two consecutive
+// stage entries field by field,
+//     [xh0 xh1 yh0 yh1 | zh0 zh1 mu0 mu1 | xl0 xl1 yl0 yl1 | zl0 zl1 0 0],
+// so one 16-byte shared load yields two packed f32x2 operands; the pair
+// arithmetic then runs two sources per packed instruction (add/mul/fma
+// .f32x2), halving the issued FP32 instructions.  Systems are padded to an
+// even length with inert sources (far away, massless: their term is 0).
 //
 // Epilogue (kModeStep), per target p, FP64: Eq. 4 kick with the previous
 // and the new acceleration, the caller's position array receives r_i, and
@@ -25,24 +34,75 @@
 
 namespace nb {
 
-template <int PREC>
-struct Prec;
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (.f32x2, sm_100 and later): two floats in one 64-bit
+// register pair.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;
 
-template <>
-struct Prec<0> {  // FP64
-  static constexpr int kBytesPerSource = 32;  // double4_32a (x, y, z, mu)
-};
-template <>
-struct Prec<1> {  // mixed
-  static constexpr int kBytesPerSource = 32;  // float4 hi (x,y,z,mu) + float4 lo (x,y,z,0)
-};
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Mixed pair-block layout: float offset of field f of stage entry q.
+enum PairField { kXh = 0, kYh = 2, kZh = 4, kMu = 6, kXl = 8, kYl = 10, kZl = 12 };
+__device__ __forceinline__ size_t pair_off(int q) { return static_cast<size_t>(q >> 1) * 16 + (q & 1); }
+
+// Eq. 1 for one target (negated hi/lo coordinates duplicated in both halves)
+// against a pair of sources, accumulating both terms into one packed pair.
+// d = (hi_j - hi_p) + (lo_j - lo_p) per component: the hi difference is exact
+// for close pairs (Sterbenz), so close pairs keep the FP64 difference to
+// about one FP32 ulp.  MASK: replace r2 by 1 where the source is the target.
+template <bool MASK>
+__device__ __forceinline__ void interact_pair(const ulonglong2 &v0, const ulonglong2 &v1, const ulonglong2 &v2,
+                                              const ulonglong2 &v3, f2 nxh, f2 nyh, f2 nzh, f2 nxl, f2 nyl,
+                                              f2 nzl, bool self_a, bool self_b, f2 &ax, f2 &ay, f2 &az) {
+  // v0 = (xh, yh), v1 = (zh, mu), v2 = (xl, yl), v3 = (zl, -)
+  const f2 dx = add2(add2(v0.x, nxh), add2(v2.x, nxl));
+  const f2 dy = add2(add2(v0.y, nyh), add2(v2.y, nyl));
+  const f2 dz = add2(add2(v1.x, nzh), add2(v3.x, nzl));
+  f2 r2 = mul2(dx, dx);
+  r2 = fma2(dy, dy, r2);
+  r2 = fma2(dz, dz, r2);
+  float ra, rb;
+  upk(r2, ra, rb);
+  if (MASK) {
+    ra = self_a ? 1.0f : ra;
+    rb = self_b ? 1.0f : rb;
+  }
+  const f2 q = pk(rsqrt_approx(ra), rsqrt_approx(rb));
+  const f2 f = mul2(mul2(v1.y, q), mul2(q, q));
+  ax = fma2(f, dx, ax);
+  ay = fma2(f, dy, ay);
+  az = fma2(f, dz, az);
+}
 
 // Minimum resident CTAs per SM the register allocation must allow: the
-// mixed kernel is latency-bound on the FP32 pipe and wants ~32 warps/SM
-// (<= 64 registers); the FP64 kernel saturates GB300's narrow FP64 pipe
-// with few warps, so it trades occupancy for registers.
+// mixed kernel wants 32 / 24 / 16 warps per SM for IPT 1 / 2 / 4 (64 / 85 /
+// 128 registers); the FP64 kernel saturates GB300's narrow FP64 pipe with
+// few warps and trades occupancy for registers.
 template <int PREC, int THREADS, int IPT>
-struct MinBlocks {  // mixed: 32 / 24 / 16 warps per SM for IPT 1 / 2 / 4 (64 / 85 / 128 registers)
+struct MinBlocks {
   static constexpr int value = PREC == 1 ? ((IPT == 1 ? 1024 : IPT == 2 ? 768 : 512) / THREADS) : 1;
 };
 
@@ -50,13 +110,11 @@ template <int PREC, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value)) step_kernel(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ int s_item;
   __shared__ int s_flag;  // bit 0: abort (a wait ran out); bit 1: this CTA reduces the block
 
   const int tid = threadIdx.x;
-  const int tj = a.tj;
-  // Stage s holds tj sources: FP64 -> double4_32a[tj]; mixed -> float4 hi[tj], float4 lo[tj].
-  auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * tj * Prec<PREC>::kBytesPerSource; };
+  const int tj = a.tj;  // sources per stage; both layouts take 32 bytes per source
+  auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * tj * 32; };
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
@@ -66,87 +124,77 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
   __syncthreads();
 
   uint32_t phase = 0;  // bit s: parity of the next completion of stage s
+  bool aborted = false;
+  const int seg_end = a.seg_off[blockIdx.x + 1];
 
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(a.work_ctr, 1);
-    __syncthreads();
-    const int item_idx = s_item;
-    if (item_idx >= a.n_items) break;
-    const Item it = a.items[item_idx];
+  for (int si = a.seg_off[blockIdx.x]; si < seg_end && !aborted; ++si) {
+    const Seg sg = a.segs[si];
+    const Blk bk = a.blks[sg.blk];
+    const int q_end = bk.q0 + (bk.i1 - bk.i0);  // stage indices of the block's targets: [q0, q_end)
 
     // ---- targets into registers ---------------------------------------
-    int pidx[IPT];
+    int pidx[IPT], tq[IPT];
     bool valid[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-      const int p = it.i0 + tid + k * THREADS;
-      valid[k] = p < it.i1;
-      pidx[k] = valid[k] ? p : it.i1 - 1;  // duplicate a real target, result discarded
+      const int p = bk.i0 + tid + k * THREADS;
+      valid[k] = p < bk.i1;
+      pidx[k] = valid[k] ? p : bk.i1 - 1;  // duplicate a real target, result discarded
+      tq[k] = bk.q0 + (pidx[k] - bk.i0);
     }
     // FP64 path: (acc, cmp) is a hi/lo pair fed once per tile with the tile's
-    // FP64 sub-sum through TwoSum.  Both paths leave the item's sums in acc.
+    // FP64 sub-sum through TwoSum.  Both paths leave the segment's sums in acc.
     double accx[IPT], accy[IPT], accz[IPT], cmpx[IPT], cmpy[IPT], cmpz[IPT];
-#pragma unroll
-    for (int k = 0; k < IPT; ++k) accx[k] = accy[k] = accz[k] = cmpx[k] = cmpy[k] = cmpz[k] = 0.0;
-
-    double px[IPT], py[IPT], pz[IPT];                               // FP64 path
-    float hx[IPT], hy[IPT], hz[IPT], lx[IPT], ly[IPT], lz[IPT];     // mixed path
-    // mixed path: per-target sums as unevaluated float pairs (hi + lo), fed
-    // one FP32 sub-sum of kFoldEvery sources at a time through TwoSum and
-    // converted to FP64 once per item, so the source loop issues no FP64
-    // instruction (GB300 runs FP64 and f32<->f64 conversions at 1/64 rate).
+    double px[IPT], py[IPT], pz[IPT];
+    // Mixed path: packed partial sums (even / odd sources) and the running
+    // sums as unevaluated float pairs (hi + lo), fed one packed sub-sum of
+    // kFoldPairs source pairs at a time through TwoSum and converted to FP64
+    // once per segment, so the source loop issues no FP64 instruction
+    // (GB300 runs FP64 and f32<->f64 conversions at 1/64 of the FP32 rate).
+    f2 nxh[IPT], nyh[IPT], nzh[IPT], nxl[IPT], nyl[IPT], nzl[IPT], pax[IPT], pay[IPT], paz[IPT];
     float shx[IPT], shy[IPT], shz[IPT], slx[IPT], sly[IPT], slz[IPT];
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) shx[k] = shy[k] = shz[k] = slx[k] = sly[k] = slz[k] = 0.f;
-    if (PREC == 0) {
-      const double4_32a *cur = static_cast<const double4_32a *>(a.cur_a);
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        const double4_32a r = cur[pidx[k]];
-        px[k] = r.x; py[k] = r.y; pz[k] = r.z;
-      }
-    } else {
-      const float4 *hi = static_cast<const float4 *>(a.cur_a);
-      const float4 *lo = static_cast<const float4 *>(a.cur_b);
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        const float4 h = hi[pidx[k]];
-        const float4 l = lo[pidx[k]];
-        hx[k] = h.x; hy[k] = h.y; hz[k] = h.z;
-        lx[k] = l.x; ly[k] = l.y; lz[k] = l.z;
+    for (int k = 0; k < IPT; ++k) {
+      accx[k] = accy[k] = accz[k] = cmpx[k] = cmpy[k] = cmpz[k] = 0.0;
+      shx[k] = shy[k] = shz[k] = slx[k] = sly[k] = slz[k] = 0.f;
+      pax[k] = pay[k] = paz[k] = 0ull;
+      if (PREC == 0) {
+        const double4_32a r = static_cast<const double4_32a *>(a.cur)[tq[k]];
+        px[k] = r.x;
+        py[k] = r.y;
+        pz[k] = r.z;
+      } else {
+        const float *e = static_cast<const float *>(a.cur) + pair_off(tq[k]);
+        nxh[k] = pk(-e[kXh], -e[kXh]);
+        nyh[k] = pk(-e[kYh], -e[kYh]);
+        nzh[k] = pk(-e[kZh], -e[kZh]);
+        nxl[k] = pk(-e[kXl], -e[kXl]);
+        nyl[k] = pk(-e[kYl], -e[kYl]);
+        nzl[k] = pk(-e[kZl], -e[kZl]);
       }
     }
 
-    // ---- source loop -----------------------------------------------------
-    const int nsrc = it.j1 - it.j0;
-    const int ntiles = (nsrc + tj - 1) / tj;
+    // ---- source loop over [s0, s1) in tiles of tj ---------------------
+    const int ntiles = (sg.s1 - sg.s0 + tj - 1) / tj;
     auto issue = [&](int t) {  // tid 0 only
       const int s = t % kStages;
-      const int j = it.j0 + t * tj;
-      const int cnt = min(tj, it.j1 - j);
-      unsigned char *dst = stage_ptr(s);
-      if (PREC == 0) {
-        mbar_arrive_expect_tx(&bar[s], static_cast<uint32_t>(cnt) * 32u);
-        bulk_g2s(dst, static_cast<const double4_32a *>(a.cur_a) + j, static_cast<uint32_t>(cnt) * 32u, &bar[s]);
-      } else {
-        mbar_arrive_expect_tx(&bar[s], static_cast<uint32_t>(cnt) * 32u);
-        bulk_g2s(dst, static_cast<const float4 *>(a.cur_a) + j, static_cast<uint32_t>(cnt) * 16u, &bar[s]);
-        bulk_g2s(dst + static_cast<size_t>(tj) * 16, static_cast<const float4 *>(a.cur_b) + j,
-                 static_cast<uint32_t>(cnt) * 16u, &bar[s]);
-      }
+      const int j = sg.s0 + t * tj;
+      const uint32_t bytes = static_cast<uint32_t>(min(tj, sg.s1 - j)) * 32u;
+      mbar_arrive_expect_tx(&bar[s], bytes);
+      bulk_g2s(stage_ptr(s), static_cast<const unsigned char *>(a.cur) + static_cast<size_t>(j) * 32, bytes,
+               &bar[s]);
     };
     if (tid == 0) {
       for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
     }
 
-    bool aborted = false;
     for (int t = 0; t < ntiles; ++t) {
       const int s = t % kStages;
       if (!mbar_wait(&bar[s], (phase >> s) & 1u)) atomicOr(&s_flag, 1);
       phase ^= 1u << s;
-      const int jt0 = it.j0 + t * tj;
-      const int cnt = min(tj, it.j1 - jt0);
-      const bool diag = jt0 < it.i1 && jt0 + cnt > it.i0;  // tile may contain a target itself
+      const int jt0 = sg.s0 + t * tj;
+      const int cnt = min(tj, sg.s1 - jt0);
+      const bool diag = jt0 < q_end && jt0 + cnt > bk.q0;  // tile may contain a target itself
 
       if (PREC == 0) {
         const double4_32a *src = reinterpret_cast<const double4_32a *>(stage_ptr(s));
@@ -174,7 +222,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
             const int jg = jt0 + jj;
 #pragma unroll
             for (int k = 0; k < IPT; ++k)
-              interact_fp64<true>(sj, px[k], py[k], pz[k], jg == pidx[k], tx[k], ty[k], tz[k]);
+              interact_fp64<true>(sj, px[k], py[k], pz[k], jg == tq[k], tx[k], ty[k], tz[k]);
           }
         }
 #pragma unroll
@@ -184,38 +232,41 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
           two_sum_acc(accz[k], cmpz[k], tz[k]);
         }
       } else {
-        const float4 *sh = reinterpret_cast<const float4 *>(stage_ptr(s));
-        const float4 *sl = sh + tj;
-        for (int base = 0; base < cnt; base += kFoldEvery) {
-          const int lim = min(kFoldEvery, cnt - base);
-          float fx[IPT], fy[IPT], fz[IPT];
-#pragma unroll
-          for (int k = 0; k < IPT; ++k) fx[k] = fy[k] = fz[k] = 0.f;
-          if (!diag && lim == kFoldEvery) {
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(stage_ptr(s));  // 4 per pair block
+        const int npairs = cnt >> 1;
+        for (int g0 = 0; g0 < npairs; g0 += kFoldPairs) {
+          const int lim = min(kFoldPairs, npairs - g0);
+          if (!diag && lim == kFoldPairs) {
 #pragma unroll 4
-            for (int jj = 0; jj < kFoldEvery; ++jj) {
-              const float4 hj = sh[base + jj];
-              const float4 lj = sl[base + jj];
+            for (int b = 0; b < kFoldPairs; ++b) {
+              const ulonglong2 *pb = src + 4 * (g0 + b);
+              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
 #pragma unroll
               for (int k = 0; k < IPT; ++k)
-                interact_mixed<false>(hj, lj, hx[k], hy[k], hz[k], lx[k], ly[k], lz[k], false, fx[k], fy[k], fz[k]);
+                interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
+                                     pax[k], pay[k], paz[k]);
             }
           } else {
-            for (int jj = 0; jj < lim; ++jj) {
-              const float4 hj = sh[base + jj];
-              const float4 lj = sl[base + jj];
-              const int jg = jt0 + base + jj;
+            for (int b = 0; b < lim; ++b) {
+              const ulonglong2 *pb = src + 4 * (g0 + b);
+              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
+              const int qa = jt0 + 2 * (g0 + b);
 #pragma unroll
               for (int k = 0; k < IPT; ++k)
-                interact_mixed<true>(hj, lj, hx[k], hy[k], hz[k], lx[k], ly[k], lz[k], jg == pidx[k], fx[k], fy[k],
-                                     fz[k]);
+                interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], qa == tq[k],
+                                    qa + 1 == tq[k], pax[k], pay[k], paz[k]);
             }
           }
 #pragma unroll
-          for (int k = 0; k < IPT; ++k) {  // fold the sub-sum into the two-float accumulator
-            two_sum_acc(shx[k], slx[k], fx[k]);
-            two_sum_acc(shy[k], sly[k], fy[k]);
-            two_sum_acc(shz[k], slz[k], fz[k]);
+          for (int k = 0; k < IPT; ++k) {  // fold the packed sub-sums into the float pairs
+            float e, o;
+            upk(pax[k], e, o);
+            two_sum_acc(shx[k], slx[k], e + o);
+            upk(pay[k], e, o);
+            two_sum_acc(shy[k], sly[k], e + o);
+            upk(paz[k], e, o);
+            two_sum_acc(shz[k], slz[k], e + o);
+            pax[k] = pay[k] = paz[k] = 0ull;
           }
         }
       }
@@ -244,26 +295,22 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     }
 
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) {  // collapse the hi/lo pairs
+    for (int k = 0; k < IPT; ++k) {  // collapse the hi/lo pairs of the FP64 path
       if (PREC == 0) {
         accx[k] += cmpx[k];
         accy[k] += cmpy[k];
         accz[k] += cmpz[k];
-      } else {
-        accx[k] = static_cast<double>(shx[k]) + static_cast<double>(slx[k]);
-        accy[k] = static_cast<double>(shy[k]) + static_cast<double>(sly[k]);
-        accz[k] = static_cast<double>(shz[k]) + static_cast<double>(slz[k]);
       }
     }
 
-    // ---- split-source reduction ---------------------------------------
-    // Partials: FP64 path -> 3 doubles per target and slot, summed by FP64
+    // ---- split-block reduction ---------------------------------------
+    // Partials: FP64 path -> 3 doubles per target and segment, summed by FP64
     // TwoSum; mixed path -> 3 float pairs (hi, lo) in the same 24 bytes,
-    // summed by FP32 TwoSum (GB300's FP64 pipe is 64x narrower, and a few
-    // last-arriving CTAs doing FP64 sums over many slots become the tail).
-    if (it.nsplit > 1) {
+    // summed by FP32 TwoSum (GB300's FP64 pipe is 64x narrower, and a CTA
+    // doing FP64 sums over many segments would hold back the step).
+    if (bk.nsplit > 1) {
       const size_t N = static_cast<size_t>(a.N);
-      double *prow = a.partial + static_cast<size_t>(it.slot) * 3 * N;
+      double *prow = a.partial + static_cast<size_t>(sg.slot) * 3 * N;
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
         if (!valid[k]) continue;
@@ -281,22 +328,23 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
       __threadfence();
       __syncthreads();
       if (tid == 0) {
-        const int old = atomicAdd(a.arrive + it.ib, 1);
-        const bool last = old == it.nsplit - 1;
-        if (last) {
-          atomicExch(a.arrive + it.ib, 0);
+        const int old = atomicAdd(a.arrive + sg.blk, 1);
+        if (old == bk.nsplit - 1) {
+          atomicExch(a.arrive + sg.blk, 0);
           __threadfence();
           atomicOr(&s_flag, 2);
         }
       }
       __syncthreads();
       const bool last = (s_flag & 2) != 0;
-      if (!last) continue;  // s_flag bit 1 is clear here; the next fetch re-syncs
+      __syncthreads();  // every thread has read s_flag before it is cleared
+      if (!last) continue;
+      if (tid == 0) atomicAnd(&s_flag, ~2);
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
         if (PREC == 0) {
           double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-          for (int c = 0; c < it.nsplit; ++c) {
+          for (int c = 0; c < bk.nsplit; ++c) {
             const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
             two_sum_acc(sx, ex, __ldcg(row + pidx[k]));
             two_sum_acc(sy, ey, __ldcg(row + N + pidx[k]));
@@ -307,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
           accz[k] = sz + ez;
         } else {
           float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-          for (int c = 0; c < it.nsplit; ++c) {
+          for (int c = 0; c < bk.nsplit; ++c) {
             const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
             const float2 vx = __ldcg(row + pidx[k]);
             const float2 vy = __ldcg(row + N + pidx[k]);
@@ -319,13 +367,22 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
             ey += vy.y;
             ez += vz.y;
           }
-          accx[k] = static_cast<double>(sx) + static_cast<double>(ex);
-          accy[k] = static_cast<double>(sy) + static_cast<double>(ey);
-          accz[k] = static_cast<double>(sz) + static_cast<double>(ez);
+          shx[k] = sx;
+          slx[k] = ex;
+          shy[k] = sy;
+          sly[k] = ey;
+          shz[k] = sz;
+          slz[k] = ez;
         }
       }
-      __syncthreads();
-      if (tid == 0) s_flag &= ~2;
+    }
+    if (PREC == 1) {
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        accx[k] = static_cast<double>(shx[k]) + static_cast<double>(slx[k]);
+        accy[k] = static_cast<double>(shy[k]) + static_cast<double>(sly[k]);
+        accz[k] = static_cast<double>(shz[k]) + static_cast<double>(slz[k]);
+      }
     }
 
     // ---- epilogue --------------------------------------------------------
@@ -341,40 +398,45 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         const double vz = kick(a.vz[p], a.az[p], anz, a.half_dt);
         double rx, ry, rz;
         if (PREC == 0) {
-          const double4_32a r = static_cast<const double4_32a *>(a.cur_a)[p];
-          rx = r.x; ry = r.y; rz = r.z;
-          const double4_32a rn = make_double4_32a(drift(rx, vx, anx, a.dt, a.half_dt2), drift(ry, vy, any, a.dt, a.half_dt2),
-                                          drift(rz, vz, anz, a.dt, a.half_dt2), r.w);
-          static_cast<double4_32a *>(a.nxt_a)[p] = rn;
+          const double4_32a r = static_cast<const double4_32a *>(a.cur)[tq[k]];
+          rx = r.x;
+          ry = r.y;
+          rz = r.z;
+          static_cast<double4_32a *>(a.nxt)[tq[k]] =
+              make_double4_32a(drift(rx, vx, anx, a.dt, a.half_dt2), drift(ry, vy, any, a.dt, a.half_dt2),
+                               drift(rz, vz, anz, a.dt, a.half_dt2), r.w);
         } else {
-          rx = a.Rx[p]; ry = a.Ry[p]; rz = a.Rz[p];
+          rx = a.Rx[p];
+          ry = a.Ry[p];
+          rz = a.Rz[p];
           const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
           const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
           const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
-          a.Rx[p] = nx; a.Ry[p] = ny; a.Rz[p] = nz;
+          a.Rx[p] = nx;
+          a.Ry[p] = ny;
+          a.Rz[p] = nz;
+          const size_t o = pair_off(tq[k]);
+          const float *e = static_cast<const float *>(a.cur) + o;
+          float *w = static_cast<float *>(a.nxt) + o;
           const float hxn = hi_part(nx), hyn = hi_part(ny), hzn = hi_part(nz);
-          const float mu = static_cast<const float4 *>(a.cur_a)[p].w;
-          static_cast<float4 *>(a.nxt_a)[p] = make_float4(hxn, hyn, hzn, mu);
-          static_cast<float4 *>(a.nxt_b)[p] = make_float4(lo_part(nx, hxn), lo_part(ny, hyn), lo_part(nz, hzn), 0.f);
+          w[kXh] = hxn;
+          w[kYh] = hyn;
+          w[kZh] = hzn;
+          w[kMu] = e[kMu];
+          w[kXl] = lo_part(nx, hxn);
+          w[kYl] = lo_part(ny, hyn);
+          w[kZl] = lo_part(nz, hzn);
         }
-        a.x[p] = rx; a.y[p] = ry; a.z[p] = rz;
-        a.vx[p] = vx; a.vy[p] = vy; a.vz[p] = vz;
+        a.x[p] = rx;
+        a.y[p] = ry;
+        a.z[p] = rz;
+        a.vx[p] = vx;
+        a.vy[p] = vy;
+        a.vz[p] = vz;
       }
-      a.ax[p] = anx; a.ay[p] = any; a.az[p] = anz;
-    }
-    // The next iteration's fetch is preceded by __syncthreads() inside the
-    // loop head, so s_item is not overwritten while still being read.
-    __syncthreads();
-  }
-
-  // ---- persistent-grid bookkeeping: the last CTA out resets the counters --
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const int done = atomicAdd(a.exit_ctr, 1);
-    if (done == static_cast<int>(gridDim.x) - 1) {
-      atomicExch(a.work_ctr, 0);
-      atomicExch(a.exit_ctr, 0);
+      a.ax[p] = anx;
+      a.ay[p] = any;
+      a.az[p] = anz;
     }
   }
 }
