@@ -174,6 +174,19 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
       }
     }
 
+    // Mixed path: the source pairs that may hold one of this warp's own
+    // targets (for each k, the warp's 32 consecutive targets span <= 17
+    // pairs).  Only those pairs take the masked path, so a CTA whose share
+    // contains a block's diagonal costs no more than any other share.
+    int mlo[IPT], mhi[IPT];
+    if (PREC == 1) {
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        mlo[k] = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
+        mhi[k] = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
+      }
+    }
+
     // ---- source loop over [s0, s1) in tiles of tj ---------------------
     const int ntiles = (sg.s1 - sg.s0 + tj - 1) / tj;
     auto issue = [&](int t) {  // tid 0 only
@@ -236,7 +249,11 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         const int npairs = cnt >> 1;
         for (int g0 = 0; g0 < npairs; g0 += kFoldPairs) {
           const int lim = min(kFoldPairs, npairs - g0);
-          if (!diag && lim == kFoldPairs) {
+          const int P0 = (jt0 >> 1) + g0;  // stage pair index of the group's first pair
+          bool need_mask = false;
+#pragma unroll
+          for (int k = 0; k < IPT; ++k) need_mask |= mlo[k] < P0 + lim && mhi[k] >= P0;
+          if (!need_mask && lim == kFoldPairs) {
 #pragma unroll 4
             for (int b = 0; b < kFoldPairs; ++b) {
               const ulonglong2 *pb = src + 4 * (g0 + b);
@@ -250,11 +267,21 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
             for (int b = 0; b < lim; ++b) {
               const ulonglong2 *pb = src + 4 * (g0 + b);
               const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
-              const int qa = jt0 + 2 * (g0 + b);
+              const int P = P0 + b;
+              bool in_mask = false;  // warp-uniform
 #pragma unroll
-              for (int k = 0; k < IPT; ++k)
-                interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], qa == tq[k],
-                                    qa + 1 == tq[k], pax[k], pay[k], paz[k]);
+              for (int k = 0; k < IPT; ++k) in_mask |= P >= mlo[k] && P <= mhi[k];
+              if (!in_mask) {
+#pragma unroll
+                for (int k = 0; k < IPT; ++k)
+                  interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
+                                       pax[k], pay[k], paz[k]);
+              } else {
+#pragma unroll
+                for (int k = 0; k < IPT; ++k)
+                  interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k],
+                                      2 * P == tq[k], 2 * P + 1 == tq[k], pax[k], pay[k], paz[k]);
+              }
             }
           }
 #pragma unroll
