@@ -165,8 +165,8 @@ nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *be
  * service with a fixed memory budget), or a component running while another
  * allocator owns the device memory, where one more cudaMalloc may fail or
  * stall.  This call uses no context and calls no cudaMalloc/cudaFree: its
- * scratch (staged sources, work items, counters, fault flags) lives in one
- * fixed-size __device__ array inside the library, about 2.1 MB, which every
+ * scratch (staged sources, partial sums, work tables, fault flags) lives in one
+ * fixed-size __device__ array inside the library, about 3.7 MB, which every
  * GPU that loads the library holds until the process exits.
  *   n        bodies, 1 <= n <= NBODY_STATIC_MAX_BODIES, else NBODY_EINVAL.
  *   G        gravitational constant, > 0.

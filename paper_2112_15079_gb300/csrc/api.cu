@@ -68,7 +68,7 @@ struct nbody_ctx {
   int n_blks = 0;
   nb::Seg *segs = nullptr;
   int32_t *seg_off = nullptr;
-  int32_t *arrive = nullptr;
+  uint16_t *nsl = nullptr;           // [N] partial rows of each body
   double *partial = nullptr;
   int partial_rows = 0;
   size_t smem = 0;
@@ -149,94 +149,113 @@ nbody_status end_work(nbody_ctx *c) {
 }
 
 bool tiles_valid(const nbody_tiles &t, int precision) {
-  return nb::step_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 1024 &&
+  return nb::force_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 1024 &&
          t.tj % 64 == 0 && t.jsplit >= 1 && t.jsplit <= 64 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
   nbody_tiles t{};
   t.jsplit = 1;  // one wave of CTAs
+  t.ctas_per_sm = 1;
   if (c->o.precision == NBODY_FP64) {
-    t.threads = 128;
-    t.ipt = 1;
-    t.tj = 256;
-    t.ctas_per_sm = 4;
-  } else {
     t.threads = 256;
     t.ipt = 1;
+    t.tj = 256;
+  } else {
+    t.threads = 1024;  // one CTA holds every warp of its SM (64 registers)
+    t.ipt = 1;
     t.tj = 512;
-    t.ctas_per_sm = 4;  // 64 registers x 256 threads: 4 CTAs (32 warps) per SM
   }
   return t;
 }
 
-// (Re)build the stream-K work tables for the current tiles: target blocks of
-// threads*ipt bodies per system, the line of (block, source) work cut into
-// `grid` equal shares (in units of 2 sources for the mixed pair layout, 1
-// for FP64), and per block the number of shares it is cut into.
+// (Re)build the stream-K work tables for the current tiles.  Each system is
+// cut into target blocks of balanced size (at most threads*ipt bodies).  The
+// work line lists, block by block, the sources of the block's system in
+// units of 2 sources (mixed pair layout) or 1 (FP64), each unit weighted by
+// the warps the block keeps busy; it is cut into `grid` equal shares.
 nbody_status build_items(nbody_ctx *c) {
   drop_graphs(c);
   dfree(c, c->blks);
   dfree(c, c->segs);
   dfree(c, c->seg_off);
-  dfree(c, c->arrive);
+  dfree(c, c->nsl);
   dfree(c, c->partial);
   c->blks = nullptr;
   c->segs = nullptr;
   c->seg_off = nullptr;
-  c->arrive = nullptr;
+  c->nsl = nullptr;
   c->partial = nullptr;
   const nbody_tiles &t = c->tiles;
   const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
   const int64_t unit = c->o.precision == NBODY_MIXED ? 2 : 1;
   std::vector<nb::Blk> blks;
-  std::vector<int64_t> bj0, bunits, bstart;  // per block: first source (stage), length in units, line start
+  std::vector<int64_t> bj0, bunits, bw, bstart;  // per block: first source, units, weight, line start
   int64_t W = 0;
   for (int64_t s = 0; s < c->n_sys; ++s) {
     const int64_t b = c->offsets[s], e = c->offsets[s + 1], ns = e - b;
     const int64_t len = (ns + unit - 1) / unit;  // units of this system's (padded) source range
-    for (int64_t i0 = b; i0 < e; i0 += B) {
-      nb::Blk k;
-      k.i0 = static_cast<int32_t>(i0);
-      k.i1 = static_cast<int32_t>(std::min(i0 + B, e));
-      k.q0 = static_cast<int32_t>(c->soff[s] + (i0 - b));
-      k.nsplit = 0;
-      blks.push_back(k);
+    const int64_t nb_s = (ns + B - 1) / B;
+    for (int64_t k = 0; k < nb_s; ++k) {
+      const int64_t i0 = b + ns * k / nb_s, i1 = b + ns * (k + 1) / nb_s;
+      nb::Blk blk;
+      blk.i0 = static_cast<int32_t>(i0);
+      blk.i1 = static_cast<int32_t>(i1);
+      blk.q0 = static_cast<int32_t>(c->soff[s] + (i0 - b));
+      blk.nsplit = 0;
+      blks.push_back(blk);
+      // warps with at least one target: thread t holds targets t + k*threads
+      const int64_t busy = std::min<int64_t>(t.threads, i1 - i0);
+      const int64_t w = (busy + 31) / 32;
       bj0.push_back(c->soff[s]);
       bunits.push_back(len);
+      bw.push_back(w);
       bstart.push_back(W);
-      W += len;
+      W += len * w;
     }
   }
   // Resident CTAs: never more than fit at once (a share per CTA, one wave).
-  c->smem = nb::step_smem_bytes(c->o.precision, t.tj);
-  NB_CUDA(c, nb::launch_step(c->o.precision, t.threads, t.ipt, 0, c->smem, nb::StepArgs{}, nullptr));
-  const int occ = nb::step_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->smem);
+  c->smem = nb::force_smem_bytes(c->o.precision, t.tj);
+  NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, c->smem));
+  const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->smem);
   if (occ < 1) return fail(c, NBODY_EINVAL, "tiles do not fit on an SM (threads %d, ipt %d, tj %d)", t.threads, t.ipt, t.tj);
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
-  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(W, static_cast<int64_t>(c->nsm) * cps * t.jsplit));
+  int64_t units_total = 0;
+  for (int64_t u : bunits) units_total += u;
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total, static_cast<int64_t>(c->nsm) * cps * t.jsplit));
+  // Unit boundary of line position x inside block k (the same rounding for
+  // both neighbours of a cut, so segments tile each block exactly).
+  auto cut = [&](size_t k, int64_t x) {
+    const int64_t off = std::min(std::max<int64_t>(x - bstart[k], 0), bunits[k] * bw[k]);
+    return (off + bw[k] / 2) / bw[k];
+  };
   std::vector<nb::Seg> segs;
   std::vector<int32_t> seg_off(G + 1, 0);
   size_t b = 0;
   for (int64_t g = 0; g < G; ++g) {
     const int64_t lo = W * g / G, hi = W * (g + 1) / G;
     seg_off[g] = static_cast<int32_t>(segs.size());
-    while (b < blks.size() && bstart[b] + bunits[b] <= lo) ++b;
+    while (b < blks.size() && bstart[b] + bunits[b] * bw[b] <= lo) ++b;
     for (size_t k = b; k < blks.size() && bstart[k] < hi; ++k) {
-      const int64_t u0 = std::max(lo, bstart[k]) - bstart[k];
-      const int64_t u1 = std::min(hi, bstart[k] + bunits[k]) - bstart[k];
+      const int64_t u0 = cut(k, lo), u1 = cut(k, hi);
       if (u1 <= u0) continue;
       nb::Seg sg;
       sg.blk = static_cast<int32_t>(k);
       sg.s0 = static_cast<int32_t>(bj0[k] + u0 * unit);
-      sg.s1 = static_cast<int32_t>(bj0[k] + u1 * unit);
+      sg.s1 = static_cast<int32_t>(bj0[k] + std::min(u1 * unit, bunits[k] * unit));
       sg.slot = blks[k].nsplit++;
       segs.push_back(sg);
     }
   }
   seg_off[G] = static_cast<int32_t>(segs.size());
+  // Per body: how many partial rows its block has.
+  std::vector<uint16_t> nsl(c->N);
   int rows = 1;
-  for (const nb::Blk &k : blks) rows = std::max(rows, static_cast<int>(k.nsplit));
+  for (const nb::Blk &k : blks) {
+    rows = std::max(rows, static_cast<int>(k.nsplit));
+    for (int32_t p = k.i0; p < k.i1; ++p) nsl[p] = static_cast<uint16_t>(k.nsplit);
+  }
+  if (rows > 65535) return fail(c, NBODY_EINVAL, "too many source splits (%d)", rows);
   c->n_blks = static_cast<int>(blks.size());
   c->partial_rows = rows;
   c->grid = static_cast<int>(G);
@@ -244,15 +263,14 @@ nbody_status build_items(nbody_ctx *c) {
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->arrive), sizeof(int32_t) * blks.size())) != NBODY_OK) return st;
-  if (rows > 1 &&
-      (st = dalloc(c, reinterpret_cast<void **>(&c->partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
-          NBODY_OK)
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
+      NBODY_OK)
     return st;
   NB_CUDA(c, cudaMemcpy(c->blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
   NB_CUDA(c, cudaMemcpy(c->segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
   NB_CUDA(c, cudaMemcpy(c->seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemset(c->arrive, 0, sizeof(int32_t) * blks.size()));
+  NB_CUDA(c, cudaMemcpy(c->nsl, nsl.data(), sizeof(uint16_t) * nsl.size(), cudaMemcpyHostToDevice));
   return NBODY_OK;
 }
 
@@ -287,9 +305,22 @@ nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check) {
   return p;
 }
 
-nb::StepArgs step_args(nbody_ctx *c, const State &s, int cur, int mode) {
+nb::ForceArgs force_args(nbody_ctx *c, int cur) {
+  nb::ForceArgs a{};
+  a.cur = c->stage[cur];
+  a.partial = c->partial;
+  a.flags = c->flags;
+  a.blks = c->blks;
+  a.segs = c->segs;
+  a.seg_off = c->seg_off;
+  a.N = c->N;
+  a.tj = c->tiles.tj;
+  return a;
+}
+
+nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, int cur, int mode) {
   const size_t N = c->N;
-  nb::StepArgs a{};
+  nb::VerletArgs a{};
   a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
   a.ax = s.ax; a.ay = s.ay; a.az = s.az;
   a.cur = c->stage[cur];
@@ -298,13 +329,10 @@ nb::StepArgs step_args(nbody_ctx *c, const State &s, int cur, int mode) {
   a.Ry = c->R ? c->R + N : nullptr;
   a.Rz = c->R ? c->R + 2 * N : nullptr;
   a.partial = c->partial;
-  a.arrive = c->arrive;
+  a.nsl = c->nsl;
+  a.qidx = c->qidx;
   a.flags = c->flags;
-  a.blks = c->blks;
-  a.segs = c->segs;
-  a.seg_off = c->seg_off;
   a.N = c->N;
-  a.tj = c->tiles.tj;
   a.mode = mode;
   a.dt = c->o.dt;
   a.half_dt = 0.5 * c->o.dt;
@@ -312,10 +340,19 @@ nb::StepArgs step_args(nbody_ctx *c, const State &s, int cur, int mode) {
   return a;
 }
 
+// One Verlet step (or, kModeForce, only a = Eq. 1) from stage `cur`: the
+// force kernel, then the per-body Verlet kernel, chained.
+nbody_status launch_one_step(nbody_ctx *c, const State &s, int cur, int mode, cudaStream_t st) {
+  NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->grid, c->smem, force_args(c, cur), st,
+                              true));
+  NB_CUDA(c, nb::launch_verlet(c->o.precision, verlet_args(c, s, cur, mode), st, true));
+  return NBODY_OK;
+}
+
 nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) {
   for (int i = 0; i < n; ++i) {
-    const nb::StepArgs a = step_args(c, s, i & 1, nb::kModeStep);
-    NB_CUDA(c, nb::launch_step(c->o.precision, c->tiles.threads, c->tiles.ipt, c->grid, c->smem, a, st));
+    nbody_status r = launch_one_step(c, s, i & 1, nb::kModeStep, st);
+    if (r != NBODY_OK) return r;
   }
   return NBODY_OK;
 }
@@ -345,11 +382,7 @@ nbody_status graph_for(nbody_ctx *c, int n, cudaGraphExec_t *out) {
 }
 
 // Force-only launch: a = Eq. 1 at the positions staged in stage[0].
-nbody_status launch_force(nbody_ctx *c, const State &s) {
-  const nb::StepArgs a = step_args(c, s, 0, nb::kModeForce);
-  NB_CUDA(c, nb::launch_step(c->o.precision, c->tiles.threads, c->tiles.ipt, c->grid, c->smem, a, c->stream));
-  return NBODY_OK;
-}
+nbody_status launch_force(nbody_ctx *c, const State &s) { return launch_one_step(c, s, 0, nb::kModeForce, c->stream); }
 
 // Synchronise and turn device flags into a status (flags are cleared).
 nbody_status check_flags(nbody_ctx *c, bool init_phase) {
@@ -657,12 +690,14 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   };
   std::vector<nbody_tiles> cand;
   const bool mixed = c->o.precision == NBODY_MIXED;
-  for (int th : {64, 128, 256})
+  for (int th : {64, 128, 256, 512, 1024})
     for (int ip : {1, 2})
       for (int tj : {256, 512, 1024})
-        for (int cps : {1, 2, 3, 4})
+        for (int cps : {1, 2, 4})
           for (int waves : {1, 2}) {
-            if (mixed ? (th == 64 || cps == 1) : (tj != 256 || cps == 3)) continue;
+            if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
+            if (!mixed && (tj != 256 || waves != 1)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
+            if (th * cps > 1024 || (mixed && th * cps < 512)) continue;
             nbody_tiles t;
             t.threads = th;
             t.ipt = ip;

@@ -3,39 +3,151 @@
 
 namespace nb {
 
-cudaError_t run_step_fp64(int op, int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s,
-                          int *occ);
-cudaError_t run_step_mixed(int op, int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s,
-                           int *occ);
+bool force_fp64_supported(int threads, int ipt);
+bool force_mixed_supported(int threads, int ipt);
+cudaError_t run_force_fp64(int op, int threads, int ipt, int grid, size_t smem, const ForceArgs &a, cudaStream_t s,
+                           bool chained, int *occ);
+cudaError_t run_force_mixed(int op, int threads, int ipt, int grid, size_t smem, const ForceArgs &a, cudaStream_t s,
+                            bool chained, int *occ);
 
-// grid == 0: only raise the dynamic shared-memory limit (see step_launch.cuh).
-cudaError_t launch_step(int precision, int threads, int ipt, int grid, size_t smem, const StepArgs &a,
-                        cudaStream_t s) {
-  const int op = grid == 0 ? 1 : 0;
-  return precision == 0 ? run_step_fp64(op, threads, ipt, grid, smem, a, s, nullptr)
-                        : run_step_mixed(op, threads, ipt, grid, smem, a, s, nullptr);
+static cudaError_t run_force(int precision, int op, int threads, int ipt, int grid, size_t smem, const ForceArgs &a,
+                             cudaStream_t s, bool chained, int *occ) {
+  return precision == 0 ? run_force_fp64(op, threads, ipt, grid, smem, a, s, chained, occ)
+                        : run_force_mixed(op, threads, ipt, grid, smem, a, s, chained, occ);
 }
 
-int step_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem) {
+cudaError_t launch_force(int precision, int threads, int ipt, int grid, size_t smem, const ForceArgs &a,
+                         cudaStream_t s, bool chained) {
+  return run_force(precision, 0, threads, ipt, grid, smem, a, s, chained, nullptr);
+}
+
+cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem) {
+  return run_force(precision, 1, threads, ipt, 0, smem, ForceArgs{}, nullptr, false, nullptr);
+}
+
+int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem) {
   int occ = 0;
-  const StepArgs a{};
-  cudaError_t e = precision == 0 ? run_step_fp64(2, threads, ipt, 0, smem, a, nullptr, &occ)
-                                 : run_step_mixed(2, threads, ipt, 0, smem, a, nullptr, &occ);
-  if (e != cudaSuccess) {
+  if (run_force(precision, 2, threads, ipt, 0, smem, ForceArgs{}, nullptr, false, &occ) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return occ;
 }
 
-bool step_config_supported(int precision, int threads, int ipt) {
-  (void)precision;
-  return (threads == 64 || threads == 128 || threads == 256) && (ipt == 1 || ipt == 2 || ipt == 4);
+bool force_config_supported(int precision, int threads, int ipt) {
+  return precision == 0 ? force_fp64_supported(threads, ipt) : force_mixed_supported(threads, ipt);
 }
 
-size_t step_smem_bytes(int precision, int tj) {
+size_t force_smem_bytes(int precision, int tj) {
   (void)precision;  // both layouts take 32 bytes per staged source
   return static_cast<size_t>(kStages) * tj * 32;
+}
+
+// ---------------------------------------------------------------------------
+// Completes a step, one thread per body p: a_new = sum of the body's force
+// partials in row order (TwoSum: FP64 for the FP64 path, float pairs for the
+// mixed path, converted to FP64 once); then, for kModeStep,
+//   Eq. 4  v_{i+1} = v_i + dt/2 (a_i + a_{i+1}),
+//   the caller's position receives r_{i+1} (the staged positions),
+//   Eq. 3  r_{i+2} = r_{i+1} + v_{i+1} dt + dt^2/2 a_{i+1} -> next stage.
+// All FP64 arithmetic of a step happens here, spread over every SM.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(256) verlet_kernel(const VerletArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  grid_dependency_launch();
+  grid_dependency_wait();  // the force partials of this step are complete
+  if (p >= a.N) return;
+  const size_t N = static_cast<size_t>(a.N);
+  const int rows = a.nsl[p];
+  double anx, any, anz;
+  if (PREC == 0) {
+    double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    for (int c = 0; c < rows; ++c) {
+      const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
+      two_sum_acc(sx, ex, row[p]);
+      two_sum_acc(sy, ey, row[N + p]);
+      two_sum_acc(sz, ez, row[2 * N + p]);
+    }
+    anx = sx + ex;
+    any = sy + ey;
+    anz = sz + ez;
+  } else {
+    float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    for (int c = 0; c < rows; ++c) {
+      const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
+      const float2 vx = row[p], vy = row[N + p], vz = row[2 * N + p];
+      two_sum_acc(sx, ex, vx.x);
+      two_sum_acc(sy, ey, vy.x);
+      two_sum_acc(sz, ez, vz.x);
+      ex += vx.y;
+      ey += vy.y;
+      ez += vz.y;
+    }
+    anx = static_cast<double>(sx) + static_cast<double>(ex);
+    any = static_cast<double>(sy) + static_cast<double>(ey);
+    anz = static_cast<double>(sz) + static_cast<double>(ez);
+  }
+  if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
+  if (a.mode == kModeStep) {
+    const double vx = kick(a.vx[p], a.ax[p], anx, a.half_dt);
+    const double vy = kick(a.vy[p], a.ay[p], any, a.half_dt);
+    const double vz = kick(a.vz[p], a.az[p], anz, a.half_dt);
+    double rx, ry, rz;
+    if (PREC == 0) {
+      const double4_32a r = static_cast<const double4_32a *>(a.cur)[p];
+      rx = r.x;
+      ry = r.y;
+      rz = r.z;
+      static_cast<double4_32a *>(a.nxt)[p] =
+          make_double4_32a(drift(rx, vx, anx, a.dt, a.half_dt2), drift(ry, vy, any, a.dt, a.half_dt2),
+                           drift(rz, vz, anz, a.dt, a.half_dt2), r.w);
+    } else {
+      rx = a.Rx[p];
+      ry = a.Ry[p];
+      rz = a.Rz[p];
+      const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
+      const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
+      const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
+      a.Rx[p] = nx;
+      a.Ry[p] = ny;
+      a.Rz[p] = nz;
+      const size_t o = pair_off(a.qidx[p]);
+      const float *e = static_cast<const float *>(a.cur) + o;
+      float *w = static_cast<float *>(a.nxt) + o;
+      const float hxn = hi_part(nx), hyn = hi_part(ny), hzn = hi_part(nz);
+      w[kXh] = hxn;
+      w[kYh] = hyn;
+      w[kZh] = hzn;
+      w[kMu] = e[kMu];
+      w[kXl] = lo_part(nx, hxn);
+      w[kYl] = lo_part(ny, hyn);
+      w[kZl] = lo_part(nz, hzn);
+    }
+    a.x[p] = rx;
+    a.y[p] = ry;
+    a.z[p] = rz;
+    a.vx[p] = vx;
+    a.vy[p] = vy;
+    a.vz[p] = vz;
+  }
+  a.ax[p] = anx;
+  a.ay[p] = any;
+  a.az[p] = anz;
+}
+
+cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {
+  if (a.N <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((a.N + 255) / 256);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return precision == 0 ? cudaLaunchKernelEx(&cfg, verlet_kernel<0>, a) : cudaLaunchKernelEx(&cfg, verlet_kernel<1>, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -68,15 +180,15 @@ __global__ void prep_kernel(const PrepArgs a) {
     a.Ry[p] = ry;
     a.Rz[p] = rz;
     const int q = a.qidx[p];
-    float *w = static_cast<float *>(a.stage) + static_cast<size_t>(q >> 1) * 16 + (q & 1);
+    float *w = static_cast<float *>(a.stage) + pair_off(q);
     const float hx = hi_part(rx), hy = hi_part(ry), hz = hi_part(rz);
-    w[0] = hx;
-    w[2] = hy;
-    w[4] = hz;
-    w[6] = static_cast<float>(mu);
-    w[8] = lo_part(rx, hx);
-    w[10] = lo_part(ry, hy);
-    w[12] = lo_part(rz, hz);
+    w[kXh] = hx;
+    w[kYh] = hy;
+    w[kZh] = hz;
+    w[kMu] = static_cast<float>(mu);
+    w[kXl] = lo_part(rx, hx);
+    w[kYl] = lo_part(ry, hy);
+    w[kZl] = lo_part(rz, hz);
     w[14] = 0.f;
   }
 }

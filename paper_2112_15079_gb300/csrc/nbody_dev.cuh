@@ -65,6 +65,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start
+// launching, and wait until the previous kernel has completed and its
+// writes are visible (no-ops when the launch was not chained).
+__device__ __forceinline__ void grid_dependency_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Mixed-path stage layout: pair blocks of two stage entries, 16 floats
+//   [xh0 xh1 yh0 yh1 | zh0 zh1 mu0 mu1 | xl0 xl1 yl0 yl1 | zl0 zl1 0 0];
+// float offset of field f of entry q is pair_off(q) + f.
+enum PairField { kXh = 0, kYh = 2, kZh = 4, kMu = 6, kXl = 8, kYl = 10, kZl = 12 };
+__device__ __forceinline__ size_t pair_off(int q) { return static_cast<size_t>(q >> 1) * 16 + (q & 1); }
+
 // ---------------------------------------------------------------------------
 // Reciprocal square-root seeds (MUFU) and their refinement
 // ---------------------------------------------------------------------------

@@ -22,45 +22,55 @@ struct Item {
 };
 static_assert(sizeof(Item) == 32, "Item layout");
 
-// Force kernels: a target block of one system (threads * ipt consecutive
-// bodies [i0, i1); q0 = stage index of body i0) whose source range is cut
-// into `nsplit` contiguous segments processed by different CTAs.
+// Force kernels: a target block of one system (at most threads * ipt
+// consecutive bodies [i0, i1); q0 = stage index of body i0) whose source
+// range is cut into `nsplit` contiguous segments processed by different CTAs.
 struct Blk {
   int32_t i0, i1, q0, nsplit;
 };
 static_assert(sizeof(Blk) == 16, "Blk layout");
 
 // One segment: sources [s0, s1) (stage indices) of block `blk`; `slot` is the
-// segment's rank within the block (partial-sum row, reduction order).
+// segment's rank within the block: the partial-sum row it writes, and its
+// place in the fixed summation order.
 struct Seg {
   int32_t blk, s0, s1, slot;
 };
 static_assert(sizeof(Seg) == 16, "Seg layout");
 
-enum Mode : int32_t {
-  kModeForce = 0,  // write a = Eq. 1 only
-  kModeStep = 1,   // Eq. 4 kick with the new a, then Eq. 3 drift into the next stage
-};
-
-// Arguments of one force launch (passed by value).  CTA c processes the
+// Arguments of one force launch (Eq. 1 partial sums).  CTA c processes the
 // segments segs[seg_off[c] .. seg_off[c+1]) in order (an equal share of the
 // whole work, stream-K style).
-struct StepArgs {
-  // state (caller-owned or the adjoint's shadow copy)
-  double *x, *y, *z, *vx, *vy, *vz;
-  double *ax, *ay, *az;  // a at the previous step in, a at this step out
-  // staged sources of this step and the stage the epilogue fills for the next
-  const void *cur;  // FP64: double4 (x,y,z,Gm) per body; mixed: pair blocks (see kernels)
-  void *nxt;
-  double *Rx, *Ry, *Rz;  // mixed only: FP64 positions of the current step (updated in place)
-  double *partial;       // [max nsplit][3][N] partial sums
-  int32_t *arrive;       // [n_blocks] arrival counters (self-resetting)
+struct ForceArgs {
+  const void *cur;  // staged sources: FP64 double4 (x,y,z,Gm) per body; mixed pair blocks
+  double *partial;  // [rows][3][N]: doubles (FP64) or float pairs (mixed), 24 B per row and body
   unsigned *flags;
   const Blk *blks;
   const Seg *segs;
   const int32_t *seg_off;  // [gridDim.x + 1]
   int32_t N;
   int32_t tj;
+};
+
+enum Mode : int32_t {
+  kModeForce = 0,  // write a = Eq. 1 only
+  kModeStep = 1,   // Eq. 4 kick with the new a, then Eq. 3 drift into the next stage
+};
+
+// Arguments of the per-body Verlet kernel that completes a step: sums the
+// force partials of body p (rows 0..nsl[p]-1, in order), then applies Eq. 4
+// and Eq. 3 and stages r_{i+1} for the next force launch.
+struct VerletArgs {
+  double *x, *y, *z, *vx, *vy, *vz;  // state (caller-owned or the adjoint's shadow copy)
+  double *ax, *ay, *az;              // a at the previous step in, a at this step out
+  const void *cur;                   // staged sources of this step (mixed: mu is copied from here)
+  void *nxt;                         // stage of the next step
+  double *Rx, *Ry, *Rz;              // mixed only: FP64 positions of the current step (in place)
+  const double *partial;
+  const uint16_t *nsl;  // [N] partial rows of body p
+  const int32_t *qidx;  // [N] stage index of body p (mixed); NULL: p
+  unsigned *flags;
+  int32_t N;
   int32_t mode;
   double dt, half_dt, half_dt2;
 };
@@ -95,15 +105,19 @@ struct ReduceArgs {
   int32_t n_systems;
 };
 
-// Launchers (return the launch's cudaError_t).
+// Launchers (return the launch's cudaError_t).  `chained`: launch with
+// programmatic stream serialization, so the kernel may start while the
+// previous one in the stream finishes (each kernel waits for its inputs).
 cudaError_t launch_prep(int precision, const PrepArgs &a, cudaStream_t s);
 // Mixed stages: fill n_pairs pair blocks with inert padding sources.
 cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s);
-int step_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
-cudaError_t launch_step(int precision, int threads, int ipt, int grid, size_t smem,
-                        const StepArgs &a, cudaStream_t s);
-bool step_config_supported(int precision, int threads, int ipt);
-size_t step_smem_bytes(int precision, int tj);
+cudaError_t launch_force(int precision, int threads, int ipt, int grid, size_t smem, const ForceArgs &a,
+                         cudaStream_t s, bool chained);
+cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained);
+cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem);  // raise the dynamic smem limit
+int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
+bool force_config_supported(int precision, int threads, int ipt);
+size_t force_smem_bytes(int precision, int tj);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);

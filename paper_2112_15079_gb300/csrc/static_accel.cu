@@ -4,7 +4,7 @@
 // loops, services with a fixed memory budget), and components that run while
 // another allocator owns the device memory, where an extra cudaMalloc may fail
 // or stall.  This entry point therefore keeps its scratch (the staged
-// sources, the work tables and the fault flags) in one
+// sources, the partial sums, the work tables and the fault flags) in one
 // file-scope __device__ array of fixed size instead of asking for memory.
 //
 // The array is shared by every call on a device and keeps the previous
@@ -31,9 +31,11 @@ constexpr int kMaxBlocks = static_cast<int>((kMaxBodies + kThreads - 1) / kThrea
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Layout of the static scratch (byte offsets, each 256-byte aligned).
-constexpr size_t kOffStage = 0;                                             // double4 (x, y, z, G m) [kMaxBodies]
-constexpr size_t kOffBlks = kOffStage + 32 * kMaxBodies;                    // Blk [kMaxBlocks]
-constexpr size_t kOffSegs = kOffBlks + align256(sizeof(nb::Blk) * kMaxBlocks);  // Seg [kMaxBlocks]
+constexpr size_t kOffStage = 0;                                                  // double4 (x, y, z, G m) [max]
+constexpr size_t kOffPartial = kOffStage + 32 * kMaxBodies;                      // double [3][max]
+constexpr size_t kOffNsl = kOffPartial + 24 * kMaxBodies;                        // uint16 [max]
+constexpr size_t kOffBlks = kOffNsl + align256(2 * kMaxBodies);                  // Blk [kMaxBlocks]
+constexpr size_t kOffSegs = kOffBlks + align256(sizeof(nb::Blk) * kMaxBlocks);   // Seg [kMaxBlocks]
 constexpr size_t kOffSegOff = kOffSegs + align256(sizeof(nb::Seg) * kMaxBlocks);  // int32 [kMaxBlocks + 1]
 constexpr size_t kOffFlags = kOffSegOff + align256(sizeof(int32_t) * (kMaxBlocks + 1));  // unsigned
 constexpr size_t kStaticScratchBytes = kOffFlags + 256;
@@ -52,25 +54,26 @@ nbody_status fail(nbody_status st, const char *msg) {
 }
 
 // One block of kThreads targets per CTA, each against all n sources (no
-// split): block b is CTA b's only segment.
-__global__ void static_tables_kernel(int32_t n, nb::Blk *blks, nb::Seg *segs, int32_t *seg_off) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// split): block b is CTA b's only segment and every body has one partial row.
+__global__ void static_tables_kernel(int32_t n, nb::Blk *blks, nb::Seg *segs, int32_t *seg_off, uint16_t *nsl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) nsl[i] = 1;
   const int n_blocks = (n + kThreads - 1) / kThreads;
-  if (b > n_blocks) return;
-  seg_off[b] = b;
-  if (b == n_blocks) return;
+  if (i > n_blocks) return;
+  seg_off[i] = i;
+  if (i == n_blocks) return;
   nb::Blk k;
-  k.i0 = b * kThreads;
+  k.i0 = i * kThreads;
   k.i1 = min(k.i0 + kThreads, n);
   k.q0 = k.i0;
   k.nsplit = 1;
-  blks[b] = k;
+  blks[i] = k;
   nb::Seg sg;
-  sg.blk = b;
+  sg.blk = i;
   sg.s0 = 0;
   sg.s1 = n;
   sg.slot = 0;
-  segs[b] = sg;
+  segs[i] = sg;
 }
 
 }  // namespace
@@ -99,6 +102,8 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   }
   unsigned char *s = static_cast<unsigned char *>(base);
   void *stage = s + kOffStage;
+  double *partial = reinterpret_cast<double *>(s + kOffPartial);
+  uint16_t *nsl = reinterpret_cast<uint16_t *>(s + kOffNsl);
   nb::Blk *blks = reinterpret_cast<nb::Blk *>(s + kOffBlks);
   nb::Seg *segs = reinterpret_cast<nb::Seg *>(s + kOffSegs);
   int32_t *seg_off = reinterpret_cast<int32_t *>(s + kOffSegOff);
@@ -109,7 +114,8 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
 
   // The fault flags start at zero on every call; the tables are rewritten.
   if (cudaMemsetAsync(flags, 0, sizeof(unsigned), st) != cudaSuccess) return fail(NBODY_ECUDA, "cudaMemsetAsync failed");
-  static_tables_kernel<<<(n_blocks + 1 + 127) / 128, 128, 0, st>>>(N, blks, segs, seg_off);
+  const int span = N > n_blocks + 1 ? N : n_blocks + 1;
+  static_tables_kernel<<<(span + 127) / 128, 128, 0, st>>>(N, blks, segs, seg_off, nsl);
   if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA, "table launch failed");
 
   nb::PrepArgs p{};
@@ -126,18 +132,25 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   p.G = G;
   if (nb::launch_prep(0, p, st) != cudaSuccess) return fail(NBODY_ECUDA, "staging launch failed");
 
-  nb::StepArgs a{};
-  a.ax = ax; a.ay = ay; a.az = az;
-  a.cur = stage;
-  a.flags = flags;
-  a.blks = blks;
-  a.segs = segs;
-  a.seg_off = seg_off;
-  a.N = N;
-  a.tj = kTj;
-  a.mode = nb::kModeForce;
-  if (nb::launch_step(0, kThreads, 1, n_blocks, nb::step_smem_bytes(0, kTj), a, st) != cudaSuccess)
+  nb::ForceArgs fa{};
+  fa.cur = stage;
+  fa.partial = partial;
+  fa.flags = flags;
+  fa.blks = blks;
+  fa.segs = segs;
+  fa.seg_off = seg_off;
+  fa.N = N;
+  fa.tj = kTj;
+  if (nb::launch_force(0, kThreads, 1, n_blocks, nb::force_smem_bytes(0, kTj), fa, st, false) != cudaSuccess)
     return fail(NBODY_ECUDA, "force launch failed");
+  nb::VerletArgs va{};
+  va.ax = ax; va.ay = ay; va.az = az;
+  va.partial = partial;
+  va.nsl = nsl;
+  va.flags = flags;
+  va.N = N;
+  va.mode = nb::kModeForce;
+  if (nb::launch_verlet(0, va, st, false) != cudaSuccess) return fail(NBODY_ECUDA, "sum launch failed");
 
   unsigned f = 0;
   if (cudaMemcpyAsync(&f, flags, sizeof f, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -1,20 +1,25 @@
-// Fused Eq. 1 force + Eq. 4 kick + Eq. 3 drift, one launch per Verlet step.
+// Eq. 1 force kernel (one launch per Verlet step, followed by the per-body
+// Verlet kernel in kernels_misc.cu that sums its partials and applies
+// Eqs. 4 and 3).
 //
 // Work decomposition (stream-K style): the force work of a step is the list
-// of target blocks (THREADS*IPT consecutive bodies of one system) times the
-// sources of their system, laid end to end.  The host cuts that line into
-// gridDim.x equal shares; CTA c walks the segments of share c in order.  A
-// block whose sources are cut across several CTAs gets one FP64 (FP64 path)
-// or float-pair (mixed path) partial sum per segment; the CTA that finishes
-// the block's last segment sums the partials in segment order (fixed order,
-// so results do not depend on scheduling) and runs the epilogue.  No CTA ever
-// waits for another, and every CTA has the same amount of work, so a step
-// has no tail of idle SMs beyond the epilogues.
+// of target blocks (at most THREADS*IPT consecutive bodies of one system,
+// sizes balanced within a system) times the sources of their system, laid
+// end to end and weighted by the warps a block keeps busy.  The host cuts
+// that line into gridDim.x equal shares; CTA c walks the segments of share c
+// in order and writes, per segment, one partial sum per target: FP64 for the
+// FP64 path, a float pair (hi, lo) for the mixed path, in row `slot` of the
+// partial array.  The Verlet kernel adds a body's rows in slot order (fixed
+// order, so results do not depend on scheduling).  No CTA ever waits for
+// another.  The intended grid is one CTA of up to 1024 threads per SM: all
+// warps of an SM then belong to one CTA, meet at every tile, and finish
+// their share together, so no SM idles while a neighbouring CTA still runs.
 //
 // Sources stream through a kStages-deep shared-memory ring filled by 1-D bulk
 // copies (cp.async.bulk, completion on mbarriers) issued by one thread, `tj`
 // sources per stage.  Targets live in registers (IPT per thread, strided by
-// THREADS so their loads coalesce).
+// THREADS so their loads coalesce); warps without a valid target skip the
+// arithmetic.
 //
 // FP64 path: sources as double4 (x, y, z, G m), one per body.
 // Mixed path: sources as pair blocks of 64 bytes holding two consecutive
@@ -25,9 +30,9 @@
 // .f32x2), halving the issued FP32 instructions.  Systems are padded to an
 // even length with inert sources (far away, massless: their term is 0).
 //
-// Epilogue (kModeStep), per target p, FP64: Eq. 4 kick with the previous
-// and the new acceleration, the caller's position array receives r_i, and
-// the Eq. 3 drift r_{i+1} is staged for the next launch (ping-pong stages).
+// Launch chaining: griddepcontrol.wait before the first read of data the
+// previous kernel wrote (staged sources), griddepcontrol.launch_dependents
+// once this CTA has started, so the Verlet kernel's launch overlaps our tail.
 #pragma once
 
 #include "nbody_dev.cuh"
@@ -64,10 +69,6 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
   return r;
 }
 
-// Mixed pair-block layout: float offset of field f of stage entry q.
-enum PairField { kXh = 0, kYh = 2, kZh = 4, kMu = 6, kXl = 8, kYl = 10, kZl = 12 };
-__device__ __forceinline__ size_t pair_off(int q) { return static_cast<size_t>(q >> 1) * 16 + (q & 1); }
-
 // Eq. 1 for one target (negated hi/lo coordinates duplicated in both halves)
 // against a pair of sources, accumulating both terms into one packed pair.
 // d = (hi_j - hi_p) + (lo_j - lo_p) per component: the hi difference is exact
@@ -97,20 +98,20 @@ __device__ __forceinline__ void interact_pair(const ulonglong2 &v0, const ulongl
   az = fma2(f, dz, az);
 }
 
-// Minimum resident CTAs per SM the register allocation must allow: the
-// mixed kernel wants 32 / 24 / 16 warps per SM for IPT 1 / 2 / 4 (64 / 85 /
-// 128 registers); the FP64 kernel saturates GB300's narrow FP64 pipe with
-// few warps and trades occupancy for registers.
+// Register budget: the mixed kernel wants a full SM of warps (64 registers
+// at 1024 threads per SM for IPT 1, 80 for IPT 2 at 768); the FP64 kernel
+// saturates GB300's narrow FP64 pipe with few warps and takes what it needs.
 template <int PREC, int THREADS, int IPT>
 struct MinBlocks {
-  static constexpr int value = PREC == 1 ? ((IPT == 1 ? 1024 : IPT == 2 ? 768 : 512) / THREADS) : 1;
+  static constexpr int raw = PREC == 1 ? ((IPT == 1 ? 1024 : IPT == 2 ? 768 : 512) / THREADS) : 1;
+  static constexpr int value = raw < 1 ? 1 : raw;
 };
 
 template <int PREC, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value)) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value)) force_kernel(const ForceArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ int s_flag;  // bit 0: abort (a wait ran out); bit 1: this CTA reduces the block
+  __shared__ int s_flag;  // bit 0: abort (a wait ran out)
 
   const int tid = threadIdx.x;
   const int tj = a.tj;  // sources per stage; both layouts take 32 bytes per source
@@ -121,13 +122,16 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     mbar_init_fence();
     s_flag = 0;
   }
+  const int seg_begin = a.seg_off[blockIdx.x], seg_end = a.seg_off[blockIdx.x + 1];
+  grid_dependency_launch();  // the Verlet kernel may start launching
+  grid_dependency_wait();    // staged sources of this step are complete
   __syncthreads();
 
   uint32_t phase = 0;  // bit s: parity of the next completion of stage s
   bool aborted = false;
-  const int seg_end = a.seg_off[blockIdx.x + 1];
+  const size_t N = static_cast<size_t>(a.N);
 
-  for (int si = a.seg_off[blockIdx.x]; si < seg_end && !aborted; ++si) {
+  for (int si = seg_begin; si < seg_end && !aborted; ++si) {
     const Seg sg = a.segs[si];
     const Blk bk = a.blks[sg.blk];
     const int q_end = bk.q0 + (bk.i1 - bk.i0);  // stage indices of the block's targets: [q0, q_end)
@@ -135,22 +139,25 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     // ---- targets into registers ---------------------------------------
     int pidx[IPT], tq[IPT];
     bool valid[IPT];
+    bool any_valid = false;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       const int p = bk.i0 + tid + k * THREADS;
       valid[k] = p < bk.i1;
+      any_valid |= valid[k];
       pidx[k] = valid[k] ? p : bk.i1 - 1;  // duplicate a real target, result discarded
       tq[k] = bk.q0 + (pidx[k] - bk.i0);
     }
+    const bool warp_busy = __any_sync(0xffffffffu, any_valid);  // warp-uniform
     // FP64 path: (acc, cmp) is a hi/lo pair fed once per tile with the tile's
-    // FP64 sub-sum through TwoSum.  Both paths leave the segment's sums in acc.
+    // FP64 sub-sum through TwoSum.
     double accx[IPT], accy[IPT], accz[IPT], cmpx[IPT], cmpy[IPT], cmpz[IPT];
     double px[IPT], py[IPT], pz[IPT];
     // Mixed path: packed partial sums (even / odd sources) and the running
     // sums as unevaluated float pairs (hi + lo), fed one packed sub-sum of
-    // kFoldPairs source pairs at a time through TwoSum and converted to FP64
-    // once per segment, so the source loop issues no FP64 instruction
-    // (GB300 runs FP64 and f32<->f64 conversions at 1/64 of the FP32 rate).
+    // kFoldPairs source pairs at a time through TwoSum, so the source loop
+    // issues no FP64 instruction (GB300 runs FP64 and f32<->f64 conversions
+    // at 1/64 of the FP32 rate).
     f2 nxh[IPT], nyh[IPT], nzh[IPT], nxl[IPT], nyl[IPT], nzl[IPT], pax[IPT], pay[IPT], paz[IPT];
     float shx[IPT], shy[IPT], shz[IPT], slx[IPT], sly[IPT], slz[IPT];
 #pragma unroll
@@ -173,18 +180,14 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         nzl[k] = pk(-e[kZl], -e[kZl]);
       }
     }
-
     // Mixed path: the source pairs that may hold one of this warp's own
     // targets (for each k, the warp's 32 consecutive targets span <= 17
-    // pairs).  Only those pairs take the masked path, so a CTA whose share
-    // contains a block's diagonal costs no more than any other share.
+    // pairs).  Only those pairs take the masked path.
     int mlo[IPT], mhi[IPT];
-    if (PREC == 1) {
 #pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        mlo[k] = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
-        mhi[k] = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
-      }
+    for (int k = 0; k < IPT; ++k) {
+      mlo[k] = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
+      mhi[k] = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
     }
 
     // ---- source loop over [s0, s1) in tiles of tj ---------------------
@@ -207,9 +210,9 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
       phase ^= 1u << s;
       const int jt0 = sg.s0 + t * tj;
       const int cnt = min(tj, sg.s1 - jt0);
-      const bool diag = jt0 < q_end && jt0 + cnt > bk.q0;  // tile may contain a target itself
 
-      if (PREC == 0) {
+      if (warp_busy && PREC == 0) {
+        const bool diag = jt0 < q_end && jt0 + cnt > bk.q0;  // tile may contain a target itself
         const double4_32a *src = reinterpret_cast<const double4_32a *>(stage_ptr(s));
         double tx[IPT], ty[IPT], tz[IPT];
 #pragma unroll
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
           two_sum_acc(accy[k], cmpy[k], ty[k]);
           two_sum_acc(accz[k], cmpz[k], tz[k]);
         }
-      } else {
+      } else if (warp_busy) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(stage_ptr(s));  // 4 per pair block
         const int npairs = cnt >> 1;
         for (int g0 = 0; g0 < npairs; g0 += kFoldPairs) {
@@ -321,149 +324,21 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
       break;
     }
 
-#pragma unroll
-    for (int k = 0; k < IPT; ++k) {  // collapse the hi/lo pairs of the FP64 path
-      if (PREC == 0) {
-        accx[k] += cmpx[k];
-        accy[k] += cmpy[k];
-        accz[k] += cmpz[k];
-      }
-    }
-
-    // ---- split-block reduction ---------------------------------------
-    // Partials: FP64 path -> 3 doubles per target and segment, summed by FP64
-    // TwoSum; mixed path -> 3 float pairs (hi, lo) in the same 24 bytes,
-    // summed by FP32 TwoSum (GB300's FP64 pipe is 64x narrower, and a CTA
-    // doing FP64 sums over many segments would hold back the step).
-    if (bk.nsplit > 1) {
-      const size_t N = static_cast<size_t>(a.N);
-      double *prow = a.partial + static_cast<size_t>(sg.slot) * 3 * N;
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        if (!valid[k]) continue;
-        if (PREC == 0) {
-          __stcg(prow + pidx[k], accx[k]);
-          __stcg(prow + N + pidx[k], accy[k]);
-          __stcg(prow + 2 * N + pidx[k], accz[k]);
-        } else {
-          float2 *frow = reinterpret_cast<float2 *>(prow);
-          __stcg(frow + pidx[k], make_float2(shx[k], slx[k]));
-          __stcg(frow + N + pidx[k], make_float2(shy[k], sly[k]));
-          __stcg(frow + 2 * N + pidx[k], make_float2(shz[k], slz[k]));
-        }
-      }
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) {
-        const int old = atomicAdd(a.arrive + sg.blk, 1);
-        if (old == bk.nsplit - 1) {
-          atomicExch(a.arrive + sg.blk, 0);
-          __threadfence();
-          atomicOr(&s_flag, 2);
-        }
-      }
-      __syncthreads();
-      const bool last = (s_flag & 2) != 0;
-      __syncthreads();  // every thread has read s_flag before it is cleared
-      if (!last) continue;
-      if (tid == 0) atomicAnd(&s_flag, ~2);
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        if (PREC == 0) {
-          double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-          for (int c = 0; c < bk.nsplit; ++c) {
-            const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
-            two_sum_acc(sx, ex, __ldcg(row + pidx[k]));
-            two_sum_acc(sy, ey, __ldcg(row + N + pidx[k]));
-            two_sum_acc(sz, ez, __ldcg(row + 2 * N + pidx[k]));
-          }
-          accx[k] = sx + ex;
-          accy[k] = sy + ey;
-          accz[k] = sz + ez;
-        } else {
-          float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-          for (int c = 0; c < bk.nsplit; ++c) {
-            const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
-            const float2 vx = __ldcg(row + pidx[k]);
-            const float2 vy = __ldcg(row + N + pidx[k]);
-            const float2 vz = __ldcg(row + 2 * N + pidx[k]);
-            two_sum_acc(sx, ex, vx.x);
-            two_sum_acc(sy, ey, vy.x);
-            two_sum_acc(sz, ez, vz.x);
-            ex += vx.y;
-            ey += vy.y;
-            ez += vz.y;
-          }
-          shx[k] = sx;
-          slx[k] = ex;
-          shy[k] = sy;
-          sly[k] = ey;
-          shz[k] = sz;
-          slz[k] = ez;
-        }
-      }
-    }
-    if (PREC == 1) {
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        accx[k] = static_cast<double>(shx[k]) + static_cast<double>(slx[k]);
-        accy[k] = static_cast<double>(shy[k]) + static_cast<double>(sly[k]);
-        accz[k] = static_cast<double>(shz[k]) + static_cast<double>(slz[k]);
-      }
-    }
-
-    // ---- epilogue --------------------------------------------------------
+    // ---- this segment's partial sums, row `slot` ---------------------
+    double *prow = a.partial + static_cast<size_t>(sg.slot) * 3 * N;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       if (!valid[k]) continue;
-      const int p = pidx[k];
-      const double anx = accx[k], any = accy[k], anz = accz[k];
-      if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
-      if (a.mode == kModeStep) {
-        const double vx = kick(a.vx[p], a.ax[p], anx, a.half_dt);
-        const double vy = kick(a.vy[p], a.ay[p], any, a.half_dt);
-        const double vz = kick(a.vz[p], a.az[p], anz, a.half_dt);
-        double rx, ry, rz;
-        if (PREC == 0) {
-          const double4_32a r = static_cast<const double4_32a *>(a.cur)[tq[k]];
-          rx = r.x;
-          ry = r.y;
-          rz = r.z;
-          static_cast<double4_32a *>(a.nxt)[tq[k]] =
-              make_double4_32a(drift(rx, vx, anx, a.dt, a.half_dt2), drift(ry, vy, any, a.dt, a.half_dt2),
-                               drift(rz, vz, anz, a.dt, a.half_dt2), r.w);
-        } else {
-          rx = a.Rx[p];
-          ry = a.Ry[p];
-          rz = a.Rz[p];
-          const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
-          const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
-          const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
-          a.Rx[p] = nx;
-          a.Ry[p] = ny;
-          a.Rz[p] = nz;
-          const size_t o = pair_off(tq[k]);
-          const float *e = static_cast<const float *>(a.cur) + o;
-          float *w = static_cast<float *>(a.nxt) + o;
-          const float hxn = hi_part(nx), hyn = hi_part(ny), hzn = hi_part(nz);
-          w[kXh] = hxn;
-          w[kYh] = hyn;
-          w[kZh] = hzn;
-          w[kMu] = e[kMu];
-          w[kXl] = lo_part(nx, hxn);
-          w[kYl] = lo_part(ny, hyn);
-          w[kZl] = lo_part(nz, hzn);
-        }
-        a.x[p] = rx;
-        a.y[p] = ry;
-        a.z[p] = rz;
-        a.vx[p] = vx;
-        a.vy[p] = vy;
-        a.vz[p] = vz;
+      if (PREC == 0) {
+        prow[pidx[k]] = accx[k] + cmpx[k];
+        prow[N + pidx[k]] = accy[k] + cmpy[k];
+        prow[2 * N + pidx[k]] = accz[k] + cmpz[k];
+      } else {
+        float2 *frow = reinterpret_cast<float2 *>(prow);
+        frow[pidx[k]] = make_float2(shx[k], slx[k]);
+        frow[N + pidx[k]] = make_float2(shy[k], sly[k]);
+        frow[2 * N + pidx[k]] = make_float2(shz[k], slz[k]);
       }
-      a.ax[p] = anx;
-      a.ay[p] = any;
-      a.az[p] = anz;
     }
   }
 }

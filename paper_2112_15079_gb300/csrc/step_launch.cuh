@@ -1,4 +1,4 @@
-// Instantiation + dispatch of step_kernel for one precision (included by
+// Instantiation + dispatch of force_kernel for one precision (included by
 // step_fp64.cu / step_mixed.cu so the two precisions compile in parallel).
 #pragma once
 
@@ -6,37 +6,30 @@
 
 namespace nb {
 
-enum StepOp { kLaunch = 0, kSetSmem = 1, kOccupancy = 2 };
+enum ForceOp { kLaunch = 0, kSetSmem = 1, kOccupancy = 2 };
 
-// kLaunch: launch on `grid` CTAs.  kSetSmem: raise the kernel's dynamic
-// shared-memory limit to `smem` (needed above 48 KB; done outside any stream
-// capture).  kOccupancy: resident CTAs per SM at `smem` bytes, in *occ.
+// kLaunch: launch on `grid` CTAs (chained: programmatic stream
+// serialization).  kSetSmem: raise the kernel's dynamic shared-memory limit
+// to `smem` (needed above 48 KB; done outside any stream capture).
+// kOccupancy: resident CTAs per SM at `smem` bytes, in *occ.
 template <int PREC, int THREADS, int IPT>
-static cudaError_t run_one(int op, int grid, size_t smem, const StepArgs &a, cudaStream_t s, int *occ) {
-  auto k = step_kernel<PREC, THREADS, IPT>;
+static cudaError_t run_one(int op, int grid, size_t smem, const ForceArgs &a, cudaStream_t s, bool chained,
+                           int *occ) {
+  auto k = force_kernel<PREC, THREADS, IPT>;
   if (op == kSetSmem)
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (op == kOccupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, THREADS, smem);
-  k<<<grid, THREADS, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int PREC>
-static cudaError_t run_prec(int op, int threads, int ipt, int grid, size_t smem, const StepArgs &a, cudaStream_t s,
-                            int *occ) {
-#define NB_CASE(T, I) \
-  if (threads == T && ipt == I) return run_one<PREC, T, I>(op, grid, smem, a, s, occ);
-  NB_CASE(64, 1)
-  NB_CASE(64, 2)
-  NB_CASE(64, 4)
-  NB_CASE(128, 1)
-  NB_CASE(128, 2)
-  NB_CASE(128, 4)
-  NB_CASE(256, 1)
-  NB_CASE(256, 2)
-  NB_CASE(256, 4)
-#undef NB_CASE
-  return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 }  // namespace nb

@@ -60,17 +60,20 @@ def _check_accel(precision, a, ref, tnorm):
         assert np.max((d / n)[good]) <= MIXED_TOL, np.max((d / n)[good])
 
 
-TILES = [
-    None,
-    {"threads": 64, "ipt": 1, "tj": 64, "jsplit": 1, "ctas_per_sm": 1},
-    {"threads": 128, "ipt": 2, "tj": 128, "jsplit": 7, "ctas_per_sm": 2},
-    {"threads": 256, "ipt": 4, "tj": 192, "jsplit": 3, "ctas_per_sm": 1},
-    {"threads": 128, "ipt": 4, "tj": 1024, "jsplit": 64, "ctas_per_sm": 4},
-]
+def _t(threads, ipt, tj, jsplit, cps):
+    return {"threads": threads, "ipt": ipt, "tj": tj, "jsplit": jsplit, "ctas_per_sm": cps}
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("tiles", TILES)
+# Work decompositions exercised per precision (None: the library's default).
+TILES = {
+    "fp64": [None, _t(64, 1, 64, 1, 1), _t(128, 2, 128, 2, 2), _t(256, 1, 192, 1, 3), _t(512, 1, 1024, 1, 1)],
+    "mixed": [None, _t(128, 1, 64, 1, 1), _t(256, 2, 128, 2, 2), _t(512, 1, 192, 1, 2), _t(1024, 1, 1024, 1, 1),
+              _t(512, 2, 512, 3, 1)],
+}
+CASES = [(p, t) for p in ("fp64", "mixed") for t in TILES[p]]
+
+
+@pytest.mark.parametrize("precision,tiles", CASES)
 @pytest.mark.parametrize("n", [31, 2131, 5003])
 def test_initial_accel_vs_oracle(nb, precision, tiles, n):
     s = inputs.solar_system(n, seed=100 + n)
