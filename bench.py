@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiles", default=None,
+                    help='JSON work decomposition for both precisions, e.g. {"threads":1024,"ipt":1,"tj":512,'
+                         '"jsplit":1,"ctas_per_sm":1}; skips the autotuner')
+    ap.add_argument("--tiles-fp64", default=None, help="JSON work decomposition for the FP64 path only")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -285,8 +289,12 @@ def run_ours(args):
             continue
         with torch.cuda.stream(stream):
             b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, device=device)
-            if not args.no_autotune:
-                b.autotune(probe_steps=4 if prec == "mixed" else 2)
+            forced = args.tiles_fp64 if (prec == "fp64" and args.tiles_fp64) else args.tiles
+            if forced:
+                b.tiles = json.loads(forced)
+                b.reset()
+            elif not args.no_autotune:
+                b.autotune(probe_steps=8 if prec == "mixed" else 2)
             tiles[prec] = b.tiles
             for _ in range(args.warmup):
                 b.step(inner)

@@ -78,9 +78,10 @@ typedef struct {
  * shares, one per CTA; a block cut across shares gets partial sums that are
  * reduced in a fixed order. */
 typedef struct {
-  int32_t threads;     /* threads per CTA: 64, 128 or 256 */
-  int32_t ipt;         /* target bodies per thread: 1, 2 or 4 */
-  int32_t tj;          /* source bodies per shared-memory stage: multiple of 64, 64..1024 */
+  int32_t threads;     /* threads per CTA; (threads, ipt) pairs built: FP64 (64|128|256|512, 1),
+                        * (128|256, 2); mixed (128|256|512|1024, 1), (256|512, 2) */
+  int32_t ipt;         /* target bodies per thread */
+  int32_t tj;          /* source bodies per shared-memory stage: multiple of 64, 64..2048 */
   int32_t jsplit;      /* waves of CTAs, >= 1 (1: every CTA resident at once) */
   int32_t ctas_per_sm; /* CTAs per SM per wave, >= 1 (capped at what fits) */
 } nbody_tiles;

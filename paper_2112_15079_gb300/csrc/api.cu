@@ -149,22 +149,22 @@ nbody_status end_work(nbody_ctx *c) {
 }
 
 bool tiles_valid(const nbody_tiles &t, int precision) {
-  return nb::force_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 1024 &&
+  return nb::force_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 2048 &&
          t.tj % 64 == 0 && t.jsplit >= 1 && t.jsplit <= 64 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
   nbody_tiles t{};
   t.jsplit = 1;  // one wave of CTAs
-  t.ctas_per_sm = 1;
+  t.tj = 1024;
   if (c->o.precision == NBODY_FP64) {
+    t.threads = 256;  // 8 warps keep GB300's 2-lane FP64 pipe ~90% busy
+    t.ipt = 1;
+    t.ctas_per_sm = 1;
+  } else {
     t.threads = 256;
     t.ipt = 1;
-    t.tj = 256;
-  } else {
-    t.threads = 1024;  // one CTA holds every warp of its SM (64 registers)
-    t.ipt = 1;
-    t.tj = 512;
+    t.ctas_per_sm = 4;  // 64 registers: 4 CTAs (32 warps) per SM
   }
   return t;
 }
@@ -667,7 +667,7 @@ nbody_status nbody_get_tiles(const nbody_ctx *c, nbody_tiles *t) {
 nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
   if (!c) return NBODY_EINVAL;
   if (!t || !tiles_valid(*t, c->o.precision))
-    return fail(c, NBODY_EINVAL, "invalid tiles (threads 64/128/256, ipt 1/2/4, tj 64..1024 step 64, jsplit 1..64, ctas_per_sm 1..32)");
+    return fail(c, NBODY_EINVAL, "invalid tiles (see nbody.h: supported threads/ipt pairs, tj 64..2048 step 64, jsplit 1..64, ctas_per_sm 1..32)");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tiles = *t;
   return build_items(c);
@@ -692,11 +692,11 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   const bool mixed = c->o.precision == NBODY_MIXED;
   for (int th : {64, 128, 256, 512, 1024})
     for (int ip : {1, 2})
-      for (int tj : {256, 512, 1024})
-        for (int cps : {1, 2, 4})
+      for (int tj : {512, 1024, 2048})
+        for (int cps : {1, 2, 3, 4})
           for (int waves : {1, 2}) {
             if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
-            if (!mixed && (tj != 256 || waves != 1)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
+            if (!mixed && (tj != 1024 || waves != 1)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
             if (th * cps > 1024 || (mixed && th * cps < 512)) continue;
             nbody_tiles t;
             t.threads = th;

@@ -50,39 +50,68 @@ size_t force_smem_bytes(int precision, int tj) {
 //   Eq. 4  v_{i+1} = v_i + dt/2 (a_i + a_{i+1}),
 //   the caller's position receives r_{i+1} (the staged positions),
 //   Eq. 3  r_{i+2} = r_{i+1} + v_{i+1} dt + dt^2/2 a_{i+1} -> next stage.
-// All FP64 arithmetic of a step happens here, spread over every SM.
+// All FP64 arithmetic of a step happens here, spread over every SM.  Sums
+// are formed in row order whatever the batching, so results are fixed.
 // ---------------------------------------------------------------------------
+// Rows are read kRowBatch at a time before they are summed, so the loads of
+// a batch are in flight together instead of one L2 round trip per row.
+constexpr int kRowBatch = 4;
+constexpr int kVerletBlock = 64;  // small CTAs: a step's bodies spread over every SM
+
 template <int PREC>
-__global__ void __launch_bounds__(256) verlet_kernel(const VerletArgs a) {
+__global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  grid_dependency_launch();
   grid_dependency_wait();  // the force partials of this step are complete
-  if (p >= a.N) return;
+  if (p >= a.N) {
+    grid_dependency_launch();
+    return;
+  }
   const size_t N = static_cast<size_t>(a.N);
   const int rows = a.nsl[p];
   double anx, any, anz;
   if (PREC == 0) {
     double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    for (int c = 0; c < rows; ++c) {
-      const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
-      two_sum_acc(sx, ex, row[p]);
-      two_sum_acc(sy, ey, row[N + p]);
-      two_sum_acc(sz, ez, row[2 * N + p]);
+    for (int c0 = 0; c0 < rows; c0 += kRowBatch) {
+      double vx[kRowBatch], vy[kRowBatch], vz[kRowBatch];
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        const double *row = a.partial + static_cast<size_t>(c0 + u) * 3 * N;
+        const bool in = c0 + u < rows;
+        vx[u] = in ? __ldg(row + p) : 0.0;
+        vy[u] = in ? __ldg(row + N + p) : 0.0;
+        vz[u] = in ? __ldg(row + 2 * N + p) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        two_sum_acc(sx, ex, vx[u]);
+        two_sum_acc(sy, ey, vy[u]);
+        two_sum_acc(sz, ez, vz[u]);
+      }
     }
     anx = sx + ex;
     any = sy + ey;
     anz = sz + ez;
   } else {
     float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-    for (int c = 0; c < rows; ++c) {
-      const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
-      const float2 vx = row[p], vy = row[N + p], vz = row[2 * N + p];
-      two_sum_acc(sx, ex, vx.x);
-      two_sum_acc(sy, ey, vy.x);
-      two_sum_acc(sz, ez, vz.x);
-      ex += vx.y;
-      ey += vy.y;
-      ez += vz.y;
+    for (int c0 = 0; c0 < rows; c0 += kRowBatch) {
+      float2 vx[kRowBatch], vy[kRowBatch], vz[kRowBatch];
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c0 + u) * 3 * N);
+        const bool in = c0 + u < rows;
+        vx[u] = in ? __ldg(row + p) : make_float2(0.f, 0.f);
+        vy[u] = in ? __ldg(row + N + p) : make_float2(0.f, 0.f);
+        vz[u] = in ? __ldg(row + 2 * N + p) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        two_sum_acc(sx, ex, vx[u].x);
+        two_sum_acc(sy, ey, vy[u].x);
+        two_sum_acc(sz, ez, vz[u].x);
+        ex += vx[u].y;
+        ey += vy[u].y;
+        ez += vz[u].y;
+      }
     }
     anx = static_cast<double>(sx) + static_cast<double>(ex);
     any = static_cast<double>(sy) + static_cast<double>(ey);
@@ -134,13 +163,16 @@ __global__ void __launch_bounds__(256) verlet_kernel(const VerletArgs a) {
   a.ax[p] = anx;
   a.ay[p] = any;
   a.az[p] = anz;
+  // Only now may the next force launch be placed: its CTAs then land on an
+  // idle GPU, one share per slot, as the equal-share decomposition assumes.
+  grid_dependency_launch();
 }
 
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {
   if (a.N <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((a.N + 255) / 256);
-  cfg.blockDim = dim3(256);
+  cfg.gridDim = dim3((a.N + kVerletBlock - 1) / kVerletBlock);
+  cfg.blockDim = dim3(kVerletBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
