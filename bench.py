@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tiles", default=None,
                     help='JSON work decomposition for both precisions, e.g. {"threads":1024,"ipt":1,"tj":512,'
-                         '"jsplit":1,"ctas_per_sm":1}; skips the autotuner')
+                         '"jsplit":4,"ctas_per_sm":1}; skips the autotuner')
     ap.add_argument("--tiles-fp64", default=None, help="JSON work decomposition for the FP64 path only")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()

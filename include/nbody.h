@@ -73,17 +73,20 @@ typedef struct {
 #define NBODY_FLAG_NO_GRAPH 1
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work
- * of a step -- every target block (threads * ipt bodies of one system) times
- * the sources of its system -- is cut into SMs * ctas_per_sm * jsplit equal
- * shares, one per CTA; a block cut across shares gets partial sums that are
- * reduced in a fixed order. */
+ * of a step -- every target block (at most threads * ipt bodies of one
+ * system) times the sources of its system -- is laid out as one line.  Three
+ * quarters of it are cut into SMs * ctas_per_sm equal static shares, one per
+ * CTA; the last quarter into ctas_per_sm * SMs * jsplit small chunks that
+ * CTAs pull as they finish (jsplit = 0: all static).  Each piece writes fixed
+ * partial-sum rows, added in a fixed order, so results do not depend on the
+ * schedule. */
 typedef struct {
   int32_t threads;     /* threads per CTA; (threads, ipt) pairs built: FP64 (64|128|256|512, 1),
                         * (128|256, 2); mixed (128|256|512|1024, 1), (256|512, 2) */
   int32_t ipt;         /* target bodies per thread */
   int32_t tj;          /* source bodies per shared-memory stage: multiple of 64, 64..2048 */
-  int32_t jsplit;      /* waves of CTAs, >= 1 (1: every CTA resident at once) */
-  int32_t ctas_per_sm; /* CTAs per SM per wave, >= 1 (capped at what fits) */
+  int32_t jsplit;      /* dynamic chunks per CTA, 0..64 */
+  int32_t ctas_per_sm; /* CTAs per SM, >= 1 (capped at what fits) */
 } nbody_tiles;
 
 /* Create a context bound to caller-owned state.

@@ -68,6 +68,8 @@ struct nbody_ctx {
   int n_blks = 0;
   nb::Seg *segs = nullptr;
   int32_t *seg_off = nullptr;
+  int32_t *dyn_ctr = nullptr;        // [2] dynamic-chunk counter of the force kernel (self-resetting)
+  int n_dyn = 0;
   uint16_t *nsl = nullptr;           // [N] partial rows of each body
   double *partial = nullptr;
   int partial_rows = 0;
@@ -150,12 +152,12 @@ nbody_status end_work(nbody_ctx *c) {
 
 bool tiles_valid(const nbody_tiles &t, int precision) {
   return nb::force_config_supported(precision, t.threads, t.ipt) && t.tj >= 64 && t.tj <= 2048 &&
-         t.tj % 64 == 0 && t.jsplit >= 1 && t.jsplit <= 64 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
+         t.tj % 64 == 0 && t.jsplit >= 0 && t.jsplit <= 64 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
   nbody_tiles t{};
-  t.jsplit = 1;  // one wave of CTAs
+  t.jsplit = 4;  // a quarter of the work in 4 small chunks per CTA, pulled dynamically
   t.tj = 1024;
   if (c->o.precision == NBODY_FP64) {
     t.threads = 256;  // 8 warps keep GB300's 2-lane FP64 pipe ~90% busy
@@ -214,7 +216,7 @@ nbody_status build_items(nbody_ctx *c) {
       W += len * w;
     }
   }
-  // Resident CTAs: never more than fit at once (a share per CTA, one wave).
+  // Resident CTAs: never more than fit at once (one static share per CTA).
   c->smem = nb::force_smem_bytes(c->o.precision, t.tj);
   NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, c->smem));
   const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->smem);
@@ -222,7 +224,15 @@ nbody_status build_items(nbody_ctx *c) {
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
   int64_t units_total = 0;
   for (int64_t u : bunits) units_total += u;
-  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total, static_cast<int64_t>(c->nsm) * cps * t.jsplit));
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total, static_cast<int64_t>(c->nsm) * cps));
+  // Pieces: G static shares of the first (1 - f) of the line, then
+  // D = G * jsplit dynamic chunks of the rest (f = 1/4 when jsplit > 0).
+  const int64_t D = std::min<int64_t>(static_cast<int64_t>(t.jsplit) * G, std::max<int64_t>(units_total - G, 0));
+  const int64_t Ws = D > 0 ? W - W / 4 : W;
+  std::vector<int64_t> cuts;  // piece boundaries on the line
+  for (int64_t g = 0; g <= G; ++g) cuts.push_back(Ws * g / G);
+  for (int64_t d = 1; d <= D; ++d) cuts.push_back(Ws + (W - Ws) * d / D);
+  const int64_t P = static_cast<int64_t>(cuts.size()) - 1;
   // Unit boundary of line position x inside block k (the same rounding for
   // both neighbours of a cut, so segments tile each block exactly).
   auto cut = [&](size_t k, int64_t x) {
@@ -230,10 +240,10 @@ nbody_status build_items(nbody_ctx *c) {
     return (off + bw[k] / 2) / bw[k];
   };
   std::vector<nb::Seg> segs;
-  std::vector<int32_t> seg_off(G + 1, 0);
+  std::vector<int32_t> seg_off(P + 1, 0);
   size_t b = 0;
-  for (int64_t g = 0; g < G; ++g) {
-    const int64_t lo = W * g / G, hi = W * (g + 1) / G;
+  for (int64_t g = 0; g < P; ++g) {
+    const int64_t lo = cuts[g], hi = cuts[g + 1];
     seg_off[g] = static_cast<int32_t>(segs.size());
     while (b < blks.size() && bstart[b] + bunits[b] * bw[b] <= lo) ++b;
     for (size_t k = b; k < blks.size() && bstart[k] < hi; ++k) {
@@ -247,7 +257,8 @@ nbody_status build_items(nbody_ctx *c) {
       segs.push_back(sg);
     }
   }
-  seg_off[G] = static_cast<int32_t>(segs.size());
+  seg_off[P] = static_cast<int32_t>(segs.size());
+  c->n_dyn = static_cast<int>(D);
   // Per body: how many partial rows its block has.
   std::vector<uint16_t> nsl(c->N);
   int rows = 1;
@@ -264,6 +275,10 @@ nbody_status build_items(nbody_ctx *c) {
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK) return st;
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
+  if (!c->dyn_ctr) {
+    if ((st = dalloc(c, reinterpret_cast<void **>(&c->dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
+    NB_CUDA(c, cudaMemset(c->dyn_ctr, 0, sizeof(int32_t) * 2));
+  }
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
       NBODY_OK)
     return st;
@@ -313,6 +328,8 @@ nb::ForceArgs force_args(nbody_ctx *c, int cur) {
   a.blks = c->blks;
   a.segs = c->segs;
   a.seg_off = c->seg_off;
+  a.dyn_ctr = c->dyn_ctr;
+  a.n_dyn = c->n_dyn;
   a.N = c->N;
   a.tj = c->tiles.tj;
   return a;
@@ -667,7 +684,7 @@ nbody_status nbody_get_tiles(const nbody_ctx *c, nbody_tiles *t) {
 nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
   if (!c) return NBODY_EINVAL;
   if (!t || !tiles_valid(*t, c->o.precision))
-    return fail(c, NBODY_EINVAL, "invalid tiles (see nbody.h: supported threads/ipt pairs, tj 64..2048 step 64, jsplit 1..64, ctas_per_sm 1..32)");
+    return fail(c, NBODY_EINVAL, "invalid tiles (see nbody.h: supported threads/ipt pairs, tj 64..2048 step 64, jsplit 0..64, ctas_per_sm 1..32)");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tiles = *t;
   return build_items(c);
@@ -694,9 +711,9 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
     for (int ip : {1, 2})
       for (int tj : {512, 1024, 2048})
         for (int cps : {1, 2, 3, 4})
-          for (int waves : {1, 2}) {
+          for (int waves : {0, 4, 8}) {
             if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
-            if (!mixed && (tj != 1024 || waves != 1)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
+            if (!mixed && (tj != 1024 || waves != 4)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
             if (th * cps > 1024 || (mixed && th * cps < 512)) continue;
             nbody_tiles t;
             t.threads = th;

@@ -61,31 +61,60 @@ constexpr int kVerletBlock = 64;  // small CTAs: a step's bodies spread over eve
 template <int PREC>
 __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < a.N;
+  const int pp = live ? p : 0;
+  const size_t N = static_cast<size_t>(a.N);
+  // Before the wait: everything this step's force kernel does not write (it
+  // writes only the partial rows), so these loads overlap its tail.
+  const int rows = a.nsl[pp];
+  const bool step = a.mode == kModeStep;
+  double vx = 0.0, vy = 0.0, vz = 0.0, aox = 0.0, aoy = 0.0, aoz = 0.0, rx = 0.0, ry = 0.0, rz = 0.0, mu = 0.0;
+  float muf = 0.f;
+  size_t o = 0;
+  if (step) {
+    vx = a.vx[pp];
+    vy = a.vy[pp];
+    vz = a.vz[pp];
+    aox = a.ax[pp];
+    aoy = a.ay[pp];
+    aoz = a.az[pp];
+    if (PREC == 0) {
+      const double4_32a r = static_cast<const double4_32a *>(a.cur)[pp];
+      rx = r.x;
+      ry = r.y;
+      rz = r.z;
+      mu = r.w;
+    } else {
+      rx = a.Rx[pp];
+      ry = a.Ry[pp];
+      rz = a.Rz[pp];
+      o = pair_off(a.qidx[pp]);
+      muf = static_cast<const float *>(a.cur)[o + kMu];
+    }
+  }
   grid_dependency_wait();  // the force partials of this step are complete
-  if (p >= a.N) {
+  if (!live) {
     grid_dependency_launch();
     return;
   }
-  const size_t N = static_cast<size_t>(a.N);
-  const int rows = a.nsl[p];
   double anx, any, anz;
   if (PREC == 0) {
     double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
     for (int c0 = 0; c0 < rows; c0 += kRowBatch) {
-      double vx[kRowBatch], vy[kRowBatch], vz[kRowBatch];
+      double px[kRowBatch], py[kRowBatch], pz[kRowBatch];
 #pragma unroll
       for (int u = 0; u < kRowBatch; ++u) {
         const double *row = a.partial + static_cast<size_t>(c0 + u) * 3 * N;
         const bool in = c0 + u < rows;
-        vx[u] = in ? __ldg(row + p) : 0.0;
-        vy[u] = in ? __ldg(row + N + p) : 0.0;
-        vz[u] = in ? __ldg(row + 2 * N + p) : 0.0;
+        px[u] = in ? __ldg(row + p) : 0.0;
+        py[u] = in ? __ldg(row + N + p) : 0.0;
+        pz[u] = in ? __ldg(row + 2 * N + p) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < kRowBatch; ++u) {
-        two_sum_acc(sx, ex, vx[u]);
-        two_sum_acc(sy, ey, vy[u]);
-        two_sum_acc(sz, ez, vz[u]);
+        two_sum_acc(sx, ex, px[u]);
+        two_sum_acc(sy, ey, py[u]);
+        two_sum_acc(sz, ez, pz[u]);
       }
     }
     anx = sx + ex;
@@ -94,23 +123,23 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
   } else {
     float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
     for (int c0 = 0; c0 < rows; c0 += kRowBatch) {
-      float2 vx[kRowBatch], vy[kRowBatch], vz[kRowBatch];
+      float2 px[kRowBatch], py[kRowBatch], pz[kRowBatch];
 #pragma unroll
       for (int u = 0; u < kRowBatch; ++u) {
         const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c0 + u) * 3 * N);
         const bool in = c0 + u < rows;
-        vx[u] = in ? __ldg(row + p) : make_float2(0.f, 0.f);
-        vy[u] = in ? __ldg(row + N + p) : make_float2(0.f, 0.f);
-        vz[u] = in ? __ldg(row + 2 * N + p) : make_float2(0.f, 0.f);
+        px[u] = in ? __ldg(row + p) : make_float2(0.f, 0.f);
+        py[u] = in ? __ldg(row + N + p) : make_float2(0.f, 0.f);
+        pz[u] = in ? __ldg(row + 2 * N + p) : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < kRowBatch; ++u) {
-        two_sum_acc(sx, ex, vx[u].x);
-        two_sum_acc(sy, ey, vy[u].x);
-        two_sum_acc(sz, ez, vz[u].x);
-        ex += vx[u].y;
-        ey += vy[u].y;
-        ez += vz[u].y;
+        two_sum_acc(sx, ex, px[u].x);
+        two_sum_acc(sy, ey, py[u].x);
+        two_sum_acc(sz, ez, pz[u].x);
+        ex += px[u].y;
+        ey += py[u].y;
+        ez += pz[u].y;
       }
     }
     anx = static_cast<double>(sx) + static_cast<double>(ex);
@@ -118,37 +147,25 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     anz = static_cast<double>(sz) + static_cast<double>(ez);
   }
   if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
-  if (a.mode == kModeStep) {
-    const double vx = kick(a.vx[p], a.ax[p], anx, a.half_dt);
-    const double vy = kick(a.vy[p], a.ay[p], any, a.half_dt);
-    const double vz = kick(a.vz[p], a.az[p], anz, a.half_dt);
-    double rx, ry, rz;
+  if (step) {
+    vx = kick(vx, aox, anx, a.half_dt);
+    vy = kick(vy, aoy, any, a.half_dt);
+    vz = kick(vz, aoz, anz, a.half_dt);
+    const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
+    const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
+    const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
     if (PREC == 0) {
-      const double4_32a r = static_cast<const double4_32a *>(a.cur)[p];
-      rx = r.x;
-      ry = r.y;
-      rz = r.z;
-      static_cast<double4_32a *>(a.nxt)[p] =
-          make_double4_32a(drift(rx, vx, anx, a.dt, a.half_dt2), drift(ry, vy, any, a.dt, a.half_dt2),
-                           drift(rz, vz, anz, a.dt, a.half_dt2), r.w);
+      static_cast<double4_32a *>(a.nxt)[p] = make_double4_32a(nx, ny, nz, mu);
     } else {
-      rx = a.Rx[p];
-      ry = a.Ry[p];
-      rz = a.Rz[p];
-      const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
-      const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
-      const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
       a.Rx[p] = nx;
       a.Ry[p] = ny;
       a.Rz[p] = nz;
-      const size_t o = pair_off(a.qidx[p]);
-      const float *e = static_cast<const float *>(a.cur) + o;
       float *w = static_cast<float *>(a.nxt) + o;
       const float hxn = hi_part(nx), hyn = hi_part(ny), hzn = hi_part(nz);
       w[kXh] = hxn;
       w[kYh] = hyn;
       w[kZh] = hzn;
-      w[kMu] = e[kMu];
+      w[kMu] = muf;
       w[kXl] = lo_part(nx, hxn);
       w[kYl] = lo_part(ny, hyn);
       w[kZl] = lo_part(nz, hzn);

@@ -38,16 +38,23 @@ struct Seg {
 };
 static_assert(sizeof(Seg) == 16, "Seg layout");
 
-// Arguments of one force launch (Eq. 1 partial sums).  CTA c processes the
-// segments segs[seg_off[c] .. seg_off[c+1]) in order (an equal share of the
-// whole work, stream-K style).
+// Arguments of one force launch (Eq. 1 partial sums).  The work is cut into
+// pieces; piece k is the segment list segs[seg_off[k] .. seg_off[k+1]).
+// Pieces 0..gridDim.x-1 are the CTAs' equal static shares (CTA c takes piece
+// c); pieces gridDim.x .. gridDim.x+n_dyn-1 are small chunks of the rest of
+// the work, pulled in order from an atomic counter by whichever CTA is free,
+// so CTAs that the warp scheduler favoured absorb the others' lag.  Each
+// segment writes a fixed partial row, so results do not depend on which CTA
+// ran it.
 struct ForceArgs {
   const void *cur;  // staged sources: FP64 double4 (x,y,z,Gm) per body; mixed pair blocks
   double *partial;  // [rows][3][N]: doubles (FP64) or float pairs (mixed), 24 B per row and body
   unsigned *flags;
   const Blk *blks;
   const Seg *segs;
-  const int32_t *seg_off;  // [gridDim.x + 1]
+  const int32_t *seg_off;  // [gridDim.x + n_dyn + 1]
+  int32_t *dyn_ctr;        // [2]: next dynamic chunk, CTAs done (the last one resets both)
+  int32_t n_dyn;
   int32_t N;
   int32_t tj;
 };

@@ -9,7 +9,8 @@
 //
 // The array is shared by every call on a device and keeps the previous
 // call's contents; each call rewrites the staged sources and work tables it
-// reads and clears the fault flags, which must start at zero.  Calls whose work overlaps on the GPU
+// reads and clears the fault flags and the work counter, which must start
+// at zero.  Calls whose work overlaps on the GPU
 // (concurrent streams, or several host threads) race on the array and give
 // wrong results: serialise them.  Every GPU that loads this library holds the
 // array (kStaticScratchBytes) until the process exits.
@@ -38,6 +39,7 @@ constexpr size_t kOffBlks = kOffNsl + align256(2 * kMaxBodies);                 
 constexpr size_t kOffSegs = kOffBlks + align256(sizeof(nb::Blk) * kMaxBlocks);   // Seg [kMaxBlocks]
 constexpr size_t kOffSegOff = kOffSegs + align256(sizeof(nb::Seg) * kMaxBlocks);  // int32 [kMaxBlocks + 1]
 constexpr size_t kOffFlags = kOffSegOff + align256(sizeof(int32_t) * (kMaxBlocks + 1));  // unsigned
+constexpr size_t kOffDyn = kOffFlags + 16;                                       // int32 [2] chunk counter
 constexpr size_t kStaticScratchBytes = kOffFlags + 256;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -108,12 +110,14 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   nb::Seg *segs = reinterpret_cast<nb::Seg *>(s + kOffSegs);
   int32_t *seg_off = reinterpret_cast<int32_t *>(s + kOffSegOff);
   unsigned *flags = reinterpret_cast<unsigned *>(s + kOffFlags);
+  int32_t *dyn = reinterpret_cast<int32_t *>(s + kOffDyn);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int N = static_cast<int>(n);
   const int n_blocks = (N + kThreads - 1) / kThreads;
 
-  // The fault flags start at zero on every call; the tables are rewritten.
-  if (cudaMemsetAsync(flags, 0, sizeof(unsigned), st) != cudaSuccess) return fail(NBODY_ECUDA, "cudaMemsetAsync failed");
+  // The fault flags and the chunk counter start at zero on every call; the
+  // tables are rewritten.
+  if (cudaMemsetAsync(flags, 0, 256, st) != cudaSuccess) return fail(NBODY_ECUDA, "cudaMemsetAsync failed");
   const int span = N > n_blocks + 1 ? N : n_blocks + 1;
   static_tables_kernel<<<(span + 127) / 128, 128, 0, st>>>(N, blks, segs, seg_off, nsl);
   if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA, "table launch failed");
@@ -139,6 +143,8 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   fa.blks = blks;
   fa.segs = segs;
   fa.seg_off = seg_off;
+  fa.dyn_ctr = dyn;
+  fa.n_dyn = 0;
   fa.N = N;
   fa.tj = kTj;
   if (nb::launch_force(0, kThreads, 1, n_blocks, nb::force_smem_bytes(0, kTj), fa, st, false) != cudaSuccess)

@@ -2,18 +2,17 @@
 // Verlet kernel in kernels_misc.cu that sums its partials and applies
 // Eqs. 4 and 3).
 //
-// Work decomposition (stream-K style): the force work of a step is the list
+// Work decomposition (hybrid stream-K): the force work of a step is the list
 // of target blocks (at most THREADS*IPT consecutive bodies of one system,
 // sizes balanced within a system) times the sources of their system, laid
 // end to end and weighted by the warps a block keeps busy.  The host cuts
-// that line into gridDim.x equal shares; CTA c walks the segments of share c
-// in order and writes, per segment, one partial sum per target: FP64 for the
-// FP64 path, a float pair (hi, lo) for the mixed path, in row `slot` of the
+// most of that line into gridDim.x equal static shares (CTA c takes share
+// c) and the rest into small chunks that free CTAs pull from a counter.
+// Every segment writes one partial sum per target: FP64 for the FP64 path,
+// a float pair (hi, lo) for the mixed path, in its fixed row `slot` of the
 // partial array.  The Verlet kernel adds a body's rows in slot order (fixed
 // order, so results do not depend on scheduling).  No CTA ever waits for
-// another.  The intended grid is one CTA of up to 1024 threads per SM: all
-// warps of an SM then belong to one CTA, meet at every tile, and finish
-// their share together, so no SM idles while a neighbouring CTA still runs.
+// another.
 //
 // Sources stream through a kStages-deep shared-memory ring filled by 1-D bulk
 // copies (cp.async.bulk, completion on mbarriers) issued by one thread, `tj`
@@ -31,8 +30,9 @@
 // even length with inert sources (far away, massless: their term is 0).
 //
 // Launch chaining: griddepcontrol.wait before the first read of data the
-// previous kernel wrote (staged sources), griddepcontrol.launch_dependents
-// once this CTA has started, so the Verlet kernel's launch overlaps our tail.
+// previous kernels wrote (staged sources), then griddepcontrol.
+// launch_dependents, so the Verlet kernel's launch overlaps our work; it
+// prefetches what this kernel does not write.
 #pragma once
 
 #include "nbody_dev.cuh"
@@ -117,20 +117,25 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
   const int tj = a.tj;  // sources per stage; both layouts take 32 bytes per source
   auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * tj * 32; };
 
+  __shared__ int s_piece;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
     mbar_init_fence();
     s_flag = 0;
   }
-  const int seg_begin = a.seg_off[blockIdx.x], seg_end = a.seg_off[blockIdx.x + 1];
-  grid_dependency_launch();  // the Verlet kernel may start launching
-  grid_dependency_wait();    // staged sources of this step are complete
+  grid_dependency_wait();    // staged sources of this step are complete (and the
+                             // previous Verlet kernel has finished)
+  grid_dependency_launch();  // so the Verlet kernel may start launching
   __syncthreads();
 
   uint32_t phase = 0;  // bit s: parity of the next completion of stage s
   bool aborted = false;
   const size_t N = static_cast<size_t>(a.N);
+  const int n_static = static_cast<int>(gridDim.x);
+  int piece = blockIdx.x;
 
+  while (!aborted) {
+  const int seg_begin = a.seg_off[piece], seg_end = a.seg_off[piece + 1];
   for (int si = seg_begin; si < seg_end && !aborted; ++si) {
     const Seg sg = a.segs[si];
     const Blk bk = a.blks[sg.blk];
@@ -339,6 +344,23 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         frow[N + pidx[k]] = make_float2(shy[k], sly[k]);
         frow[2 * N + pidx[k]] = make_float2(shz[k], slz[k]);
       }
+    }
+  }
+  // next piece: a dynamic chunk, while any is left
+  __syncthreads();
+  if (tid == 0) s_piece = n_static + atomicAdd(a.dyn_ctr, 1);
+  __syncthreads();
+  piece = s_piece;
+  if (piece >= n_static + a.n_dyn) break;
+  }
+
+  // The last CTA out resets the chunk counter for the next launch.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.dyn_ctr + 1, 1) == n_static - 1) {
+      atomicExch(a.dyn_ctr, 0);
+      atomicExch(a.dyn_ctr + 1, 0);
     }
   }
 }

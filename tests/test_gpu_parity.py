@@ -66,8 +66,8 @@ def _t(threads, ipt, tj, jsplit, cps):
 
 # Work decompositions exercised per precision (None: the library's default).
 TILES = {
-    "fp64": [None, _t(64, 1, 64, 1, 1), _t(128, 2, 128, 2, 2), _t(256, 1, 192, 1, 3), _t(512, 1, 1024, 1, 1)],
-    "mixed": [None, _t(128, 1, 64, 1, 1), _t(256, 2, 128, 2, 2), _t(512, 1, 192, 1, 2), _t(1024, 1, 1024, 1, 1),
+    "fp64": [None, _t(64, 1, 64, 0, 1), _t(128, 2, 128, 2, 2), _t(256, 1, 192, 8, 3), _t(512, 1, 1024, 1, 1)],
+    "mixed": [None, _t(128, 1, 64, 0, 1), _t(256, 2, 128, 2, 2), _t(512, 1, 192, 8, 2), _t(1024, 1, 2048, 1, 1),
               _t(512, 2, 512, 3, 1)],
 }
 CASES = [(p, t) for p in ("fp64", "mixed") for t in TILES[p]]
