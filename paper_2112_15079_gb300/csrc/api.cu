@@ -156,17 +156,19 @@ bool tiles_valid(const nbody_tiles &t, int precision) {
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
+  // Measured on GB300 at N = 10,425: FP64 is bound by the FP64 pipe (~90% busy)
+  // for any decomposition with >= 8 warps and some ILP per SM; the mixed path
+  // is best with two targets per thread and three 256-thread CTAs per SM.
   nbody_tiles t{};
-  t.jsplit = 4;  // a quarter of the work in 4 small chunks per CTA, pulled dynamically
+  t.jsplit = 0;  // static shares only (dynamic chunks add partial rows)
   t.tj = 1024;
+  t.ipt = 2;
   if (c->o.precision == NBODY_FP64) {
-    t.threads = 256;  // 8 warps keep GB300's 2-lane FP64 pipe ~90% busy
-    t.ipt = 1;
-    t.ctas_per_sm = 1;
+    t.threads = 128;
+    t.ctas_per_sm = 2;
   } else {
     t.threads = 256;
-    t.ipt = 1;
-    t.ctas_per_sm = 4;  // 64 registers: 4 CTAs (32 warps) per SM
+    t.ctas_per_sm = 3;
   }
   return t;
 }
@@ -709,11 +711,11 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   const bool mixed = c->o.precision == NBODY_MIXED;
   for (int th : {64, 128, 256, 512, 1024})
     for (int ip : {1, 2})
-      for (int tj : {512, 1024, 2048})
+      for (int tj : {512, 1024})
         for (int cps : {1, 2, 3, 4})
-          for (int waves : {0, 4, 8}) {
+          for (int waves : {0, 1}) {
             if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
-            if (!mixed && (tj != 1024 || waves != 4)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
+            if (!mixed && (tj != 1024 || waves != 0)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
             if (th * cps > 1024 || (mixed && th * cps < 512)) continue;
             nbody_tiles t;
             t.threads = th;
