@@ -44,23 +44,31 @@ size_t force_smem_bytes(int precision, int tj) {
 }
 
 // ---------------------------------------------------------------------------
-// Completes a step, one thread per body p: a_new = sum of the body's force
-// partials in row order (TwoSum: FP64 for the FP64 path, float pairs for the
-// mixed path, converted to FP64 once); then, for kModeStep,
+// Completes a step, kRowLanes threads per body p: a_new = sum of the body's force
+// partials (TwoSum: FP64 for the FP64 path, float pairs for the mixed path,
+// converted to FP64 once) in a fixed order; then, for kModeStep,
 //   Eq. 4  v_{i+1} = v_i + dt/2 (a_i + a_{i+1}),
 //   the caller's position receives r_{i+1} (the staged positions),
 //   Eq. 3  r_{i+2} = r_{i+1} + v_{i+1} dt + dt^2/2 a_{i+1} -> next stage.
-// All FP64 arithmetic of a step happens here, spread over every SM.  Sums
-// are formed in row order whatever the batching, so results are fixed.
+// All FP64 arithmetic of a step happens here, spread over every SM.
 // ---------------------------------------------------------------------------
-// Rows are read kRowBatch at a time before they are summed, so the loads of
-// a batch are in flight together instead of one L2 round trip per row.
-constexpr int kRowBatch = 4;
-constexpr int kVerletBlock = 64;  // small CTAs: a step's bodies spread over every SM
+// Each body's partial rows are summed by kRowLanes neighbouring threads: lane
+// l takes rows l, l + kRowLanes, ... (TwoSum), then the lanes are combined
+// by a fixed-shape shuffle tree, so the summation order never changes.
+constexpr int kRowLanes = 8;
+constexpr int kVerletBlock = 256;  // 32 bodies per CTA
+
+// (hi, lo) pair sums: FP64 pairs for the FP64 path, float pairs for mixed.
+template <typename T>
+__device__ __forceinline__ void pair_add(T &hi, T &lo, T vhi, T vlo) {
+  two_sum_acc(hi, lo, vhi);
+  lo += vlo;
+}
 
 template <int PREC>
 __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = gtid / kRowLanes, lane = gtid % kRowLanes;
   const bool live = p < a.N;
   const int pp = live ? p : 0;
   const size_t N = static_cast<size_t>(a.N);
@@ -71,7 +79,7 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
   double vx = 0.0, vy = 0.0, vz = 0.0, aox = 0.0, aoy = 0.0, aoz = 0.0, rx = 0.0, ry = 0.0, rz = 0.0, mu = 0.0;
   float muf = 0.f;
   size_t o = 0;
-  if (step) {
+  if (step && lane == 0) {
     vx = a.vx[pp];
     vy = a.vy[pp];
     vz = a.vz[pp];
@@ -93,28 +101,26 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     }
   }
   grid_dependency_wait();  // the force partials of this step are complete
-  if (!live) {
-    grid_dependency_launch();
-    return;
-  }
   double anx, any, anz;
   if (PREC == 0) {
     double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    for (int c0 = 0; c0 < rows; c0 += kRowBatch) {
-      double px[kRowBatch], py[kRowBatch], pz[kRowBatch];
-#pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) {
-        const double *row = a.partial + static_cast<size_t>(c0 + u) * 3 * N;
-        const bool in = c0 + u < rows;
-        px[u] = in ? __ldg(row + p) : 0.0;
-        py[u] = in ? __ldg(row + N + p) : 0.0;
-        pz[u] = in ? __ldg(row + 2 * N + p) : 0.0;
+    if (live) {
+      for (int c = lane; c < rows; c += kRowLanes) {
+        const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
+        two_sum_acc(sx, ex, __ldg(row + p));
+        two_sum_acc(sy, ey, __ldg(row + N + p));
+        two_sum_acc(sz, ez, __ldg(row + 2 * N + p));
       }
+    }
 #pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) {
-        two_sum_acc(sx, ex, px[u]);
-        two_sum_acc(sy, ey, py[u]);
-        two_sum_acc(sz, ez, pz[u]);
+    for (int off = 1; off < kRowLanes; off <<= 1) {
+      const double hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
+      const double hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
+      const double hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
+      if ((lane & (2 * off - 1)) == 0) {
+        pair_add(sx, ex, hx, lx);
+        pair_add(sy, ey, hy, ly);
+        pair_add(sz, ez, hz, lz);
       }
     }
     anx = sx + ex;
@@ -122,29 +128,33 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     anz = sz + ez;
   } else {
     float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-    for (int c0 = 0; c0 < rows; c0 += kRowBatch) {
-      float2 px[kRowBatch], py[kRowBatch], pz[kRowBatch];
-#pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) {
-        const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c0 + u) * 3 * N);
-        const bool in = c0 + u < rows;
-        px[u] = in ? __ldg(row + p) : make_float2(0.f, 0.f);
-        py[u] = in ? __ldg(row + N + p) : make_float2(0.f, 0.f);
-        pz[u] = in ? __ldg(row + 2 * N + p) : make_float2(0.f, 0.f);
+    if (live) {
+      for (int c = lane; c < rows; c += kRowLanes) {
+        const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
+        const float2 vx2 = __ldg(row + p), vy2 = __ldg(row + N + p), vz2 = __ldg(row + 2 * N + p);
+        pair_add(sx, ex, vx2.x, vx2.y);
+        pair_add(sy, ey, vy2.x, vy2.y);
+        pair_add(sz, ez, vz2.x, vz2.y);
       }
+    }
 #pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) {
-        two_sum_acc(sx, ex, px[u].x);
-        two_sum_acc(sy, ey, py[u].x);
-        two_sum_acc(sz, ez, pz[u].x);
-        ex += px[u].y;
-        ey += py[u].y;
-        ez += pz[u].y;
+    for (int off = 1; off < kRowLanes; off <<= 1) {
+      const float hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
+      const float hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
+      const float hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
+      if ((lane & (2 * off - 1)) == 0) {
+        pair_add(sx, ex, hx, lx);
+        pair_add(sy, ey, hy, ly);
+        pair_add(sz, ez, hz, lz);
       }
     }
     anx = static_cast<double>(sx) + static_cast<double>(ex);
     any = static_cast<double>(sy) + static_cast<double>(ey);
     anz = static_cast<double>(sz) + static_cast<double>(ez);
+  }
+  if (!live || lane != 0) {
+    grid_dependency_launch();
+    return;
   }
   if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
   if (step) {
@@ -188,7 +198,8 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {
   if (a.N <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((a.N + kVerletBlock - 1) / kVerletBlock);
+  const int64_t threads = static_cast<int64_t>(a.N) * kRowLanes;
+  cfg.gridDim = dim3(static_cast<unsigned>((threads + kVerletBlock - 1) / kVerletBlock));
   cfg.blockDim = dim3(kVerletBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
