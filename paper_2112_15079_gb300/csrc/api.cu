@@ -24,7 +24,30 @@ thread_local std::string g_init_error;
 
 constexpr int kGraphChunk = 64;  // steps per cached graph (even: stage parity repeats)
 
-struct Grad;  // adjoint workspace (grad.cu)
+// Stream-K work tables of one kernel family (force or VJP): target blocks,
+// segments per piece, the partial-row array and its row count per body.
+struct Work {
+  nb::Blk *blks = nullptr;
+  nb::Seg *segs = nullptr;
+  int32_t *seg_off = nullptr;
+  uint16_t *nsl = nullptr;  // [N] partial rows of each body
+  double *partial = nullptr;
+  int32_t *dyn_ctr = nullptr;  // [2] dynamic-chunk counter (self-resetting)
+  int n_blks = 0, rows = 0, grid = 0, n_dyn = 0;
+  size_t smem = 0;
+};
+
+// Adjoint workspace, allocated by the first nbody_grad and kept.
+struct Adjoint {
+  Work vj;                         // VJP work tables
+  double *rho = nullptr, *nu = nullptr, *gm = nullptr;  // [3N], [3N], [N]
+  void *w = nullptr;               // staged w (stage layout)
+  double *shadow = nullptr;        // [9][N]: x, y, z, vx, vy, vz, ax, ay, az of the recomputation
+  double *ckpt = nullptr;          // [n_ckpt][6][N]
+  int64_t n_ckpt = 0;
+  void *store = nullptr;           // [K + 1] staged positions of one segment
+  int64_t store_len = 0;
+};
 
 }  // namespace
 
@@ -62,19 +85,10 @@ struct nbody_ctx {
   Item *eitems = nullptr;
   int n_eitems = 0;
 
-  // tile-dependent scratch (stream-K work tables)
+  // tile-dependent scratch (stream-K work tables of the force kernel)
   nbody_tiles tiles{};
-  nb::Blk *blks = nullptr;
-  int n_blks = 0;
-  nb::Seg *segs = nullptr;
-  int32_t *seg_off = nullptr;
-  int32_t *dyn_ctr = nullptr;        // [2] dynamic-chunk counter of the force kernel (self-resetting)
-  int n_dyn = 0;
-  uint16_t *nsl = nullptr;           // [N] partial rows of each body
-  double *partial = nullptr;
-  int partial_rows = 0;
-  size_t smem = 0;
-  int grid = 0;
+  Work fw;
+  Adjoint adj;
 
   std::map<int, cudaGraphExec_t> graphs;
   std::string err;
@@ -173,24 +187,17 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
   return t;
 }
 
-// (Re)build the stream-K work tables for the current tiles.  Each system is
-// cut into target blocks of balanced size (at most threads*ipt bodies).  The
-// work line lists, block by block, the sources of the block's system in
-// units of 2 sources (mixed pair layout) or 1 (FP64), each unit weighted by
-// the warps the block keeps busy; it is cut into `grid` equal shares.
-nbody_status build_items(nbody_ctx *c) {
-  drop_graphs(c);
-  dfree(c, c->blks);
-  dfree(c, c->segs);
-  dfree(c, c->seg_off);
-  dfree(c, c->nsl);
-  dfree(c, c->partial);
-  c->blks = nullptr;
-  c->segs = nullptr;
-  c->seg_off = nullptr;
-  c->nsl = nullptr;
-  c->partial = nullptr;
-  const nbody_tiles &t = c->tiles;
+void free_work(nbody_ctx *c, Work &w);
+
+// Build stream-K work tables.  Each system is cut into target blocks of
+// balanced size (at most threads*ipt bodies).  The work line lists, block by
+// block, the sources of the block's system in units of 2 sources (mixed pair
+// layout) or 1 (FP64), each unit weighted by the warps the block keeps busy.
+// Three quarters of it (all of it when jsplit == 0) are cut into `grid` =
+// SMs * ctas_per_sm equal static shares, the rest into grid * jsplit chunks.
+// row_doubles: 8-byte words per body and partial row (3 force, 4 VJP).
+nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, int row_doubles) {
+  free_work(c, wk);
   const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
   const int64_t unit = c->o.precision == NBODY_MIXED ? 2 : 1;
   std::vector<nb::Blk> blks;
@@ -218,17 +225,11 @@ nbody_status build_items(nbody_ctx *c) {
       W += len * w;
     }
   }
-  // Resident CTAs: never more than fit at once (one static share per CTA).
-  c->smem = nb::force_smem_bytes(c->o.precision, t.tj);
-  NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, c->smem));
-  const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->smem);
   if (occ < 1) return fail(c, NBODY_EINVAL, "tiles do not fit on an SM (threads %d, ipt %d, tj %d)", t.threads, t.ipt, t.tj);
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
   int64_t units_total = 0;
   for (int64_t u : bunits) units_total += u;
   const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total, static_cast<int64_t>(c->nsm) * cps));
-  // Pieces: G static shares of the first (1 - f) of the line, then
-  // D = G * jsplit dynamic chunks of the rest (f = 1/4 when jsplit > 0).
   const int64_t D = std::min<int64_t>(static_cast<int64_t>(t.jsplit) * G, std::max<int64_t>(units_total - G, 0));
   const int64_t Ws = D > 0 ? W - W / 4 : W;
   std::vector<int64_t> cuts;  // piece boundaries on the line
@@ -260,7 +261,6 @@ nbody_status build_items(nbody_ctx *c) {
     }
   }
   seg_off[P] = static_cast<int32_t>(segs.size());
-  c->n_dyn = static_cast<int>(D);
   // Per body: how many partial rows its block has.
   std::vector<uint16_t> nsl(c->N);
   int rows = 1;
@@ -269,26 +269,48 @@ nbody_status build_items(nbody_ctx *c) {
     for (int32_t p = k.i0; p < k.i1; ++p) nsl[p] = static_cast<uint16_t>(k.nsplit);
   }
   if (rows > 65535) return fail(c, NBODY_EINVAL, "too many source splits (%d)", rows);
-  c->n_blks = static_cast<int>(blks.size());
-  c->partial_rows = rows;
-  c->grid = static_cast<int>(G);
+  wk.n_dyn = static_cast<int>(D);
+  wk.n_blks = static_cast<int>(blks.size());
+  wk.rows = rows;
+  wk.grid = static_cast<int>(G);
   nbody_status st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
-  if (!c->dyn_ctr) {
-    if ((st = dalloc(c, reinterpret_cast<void **>(&c->dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
-    NB_CUDA(c, cudaMemset(c->dyn_ctr, 0, sizeof(int32_t) * 2));
-  }
-  if ((st = dalloc(c, reinterpret_cast<void **>(&c->partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
-      NBODY_OK)
+  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial),
+                   sizeof(double) * row_doubles * static_cast<size_t>(rows) * c->N)) != NBODY_OK)
     return st;
-  NB_CUDA(c, cudaMemcpy(c->blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemcpy(c->segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemcpy(c->seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemcpy(c->nsl, nsl.data(), sizeof(uint16_t) * nsl.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemset(wk.dyn_ctr, 0, sizeof(int32_t) * 2));
+  NB_CUDA(c, cudaMemcpy(wk.blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemcpy(wk.segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemcpy(wk.seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
+  NB_CUDA(c, cudaMemcpy(wk.nsl, nsl.data(), sizeof(uint16_t) * nsl.size(), cudaMemcpyHostToDevice));
   return NBODY_OK;
+}
+
+void free_work(nbody_ctx *c, Work &w) {
+  dfree(c, w.blks);
+  dfree(c, w.segs);
+  dfree(c, w.seg_off);
+  dfree(c, w.nsl);
+  dfree(c, w.partial);
+  dfree(c, w.dyn_ctr);
+  w = Work{};
+}
+
+// Rebuild the force kernel's tables for the current tiles.
+nbody_status build_items(nbody_ctx *c) {
+  drop_graphs(c);
+  const nbody_tiles &t = c->tiles;
+  c->fw.smem = nb::force_smem_bytes(c->o.precision, t.tj);
+  NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, c->fw.smem));
+  const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->fw.smem);
+  const size_t smem = c->fw.smem;
+  nbody_status st = build_work(c, c->fw, t, occ, 3);
+  c->fw.smem = smem;
+  return st;
 }
 
 // Pointers of one state (the bound caller state, or the adjoint's shadow).
@@ -301,13 +323,13 @@ State bound_state(nbody_ctx *c) {
   return {c->x, c->y, c->z, c->vx, c->vy, c->vz, c->a, c->a + N, c->a + 2 * N};
 }
 
-nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check) {
+nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check, void *stage = nullptr) {
   const size_t N = c->N;
   nb::PrepArgs p{};
   p.x = s.x; p.y = s.y; p.z = s.z; p.vx = s.vx; p.vy = s.vy; p.vz = s.vz;
   p.ax = s.ax; p.ay = s.ay; p.az = s.az;
   p.m = c->m;
-  p.stage = c->stage[0];
+  p.stage = stage ? stage : c->stage[0];
   p.qidx = c->qidx;
   p.Rx = c->R;
   p.Ry = c->R ? c->R + N : nullptr;
@@ -322,33 +344,33 @@ nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check) {
   return p;
 }
 
-nb::ForceArgs force_args(nbody_ctx *c, int cur) {
+nb::ForceArgs force_args(nbody_ctx *c, const void *cur) {
   nb::ForceArgs a{};
-  a.cur = c->stage[cur];
-  a.partial = c->partial;
+  a.cur = cur;
+  a.partial = c->fw.partial;
   a.flags = c->flags;
-  a.blks = c->blks;
-  a.segs = c->segs;
-  a.seg_off = c->seg_off;
-  a.dyn_ctr = c->dyn_ctr;
-  a.n_dyn = c->n_dyn;
+  a.blks = c->fw.blks;
+  a.segs = c->fw.segs;
+  a.seg_off = c->fw.seg_off;
+  a.dyn_ctr = c->fw.dyn_ctr;
+  a.n_dyn = c->fw.n_dyn;
   a.N = c->N;
   a.tj = c->tiles.tj;
   return a;
 }
 
-nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, int cur, int mode) {
+nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, const void *cur, void *nxt, int mode) {
   const size_t N = c->N;
   nb::VerletArgs a{};
   a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
   a.ax = s.ax; a.ay = s.ay; a.az = s.az;
-  a.cur = c->stage[cur];
-  a.nxt = c->stage[1 - cur];
+  a.cur = cur;
+  a.nxt = nxt;
   a.Rx = c->R;
   a.Ry = c->R ? c->R + N : nullptr;
   a.Rz = c->R ? c->R + 2 * N : nullptr;
-  a.partial = c->partial;
-  a.nsl = c->nsl;
+  a.partial = c->fw.partial;
+  a.nsl = c->fw.nsl;
   a.qidx = c->qidx;
   a.flags = c->flags;
   a.N = c->N;
@@ -359,18 +381,19 @@ nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, int cur, int mode) {
   return a;
 }
 
-// One Verlet step (or, kModeForce, only a = Eq. 1) from stage `cur`: the
-// force kernel, then the per-body Verlet kernel, chained.
-nbody_status launch_one_step(nbody_ctx *c, const State &s, int cur, int mode, cudaStream_t st) {
-  NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->grid, c->smem, force_args(c, cur), st,
-                              true));
-  NB_CUDA(c, nb::launch_verlet(c->o.precision, verlet_args(c, s, cur, mode), st, true));
+// One Verlet step (or, kModeForce, only a = Eq. 1) from the staged sources
+// `cur`, staging the next positions into `nxt`: the force kernel, then the
+// per-body Verlet kernel, chained.
+nbody_status launch_one_step(nbody_ctx *c, const State &s, const void *cur, void *nxt, int mode, cudaStream_t st) {
+  NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
+                              force_args(c, cur), st, true));
+  NB_CUDA(c, nb::launch_verlet(c->o.precision, verlet_args(c, s, cur, nxt, mode), st, true));
   return NBODY_OK;
 }
 
 nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) {
   for (int i = 0; i < n; ++i) {
-    nbody_status r = launch_one_step(c, s, i & 1, nb::kModeStep, st);
+    nbody_status r = launch_one_step(c, s, c->stage[i & 1], c->stage[1 - (i & 1)], nb::kModeStep, st);
     if (r != NBODY_OK) return r;
   }
   return NBODY_OK;
@@ -401,7 +424,9 @@ nbody_status graph_for(nbody_ctx *c, int n, cudaGraphExec_t *out) {
 }
 
 // Force-only launch: a = Eq. 1 at the positions staged in stage[0].
-nbody_status launch_force(nbody_ctx *c, const State &s) { return launch_one_step(c, s, 0, nb::kModeForce, c->stream); }
+nbody_status launch_force(nbody_ctx *c, const State &s) {
+  return launch_one_step(c, s, c->stage[0], c->stage[1], nb::kModeForce, c->stream);
+}
 
 // Synchronise and turn device flags into a status (flags are cleared).
 nbody_status check_flags(nbody_ctx *c, bool init_phase) {
@@ -505,6 +530,60 @@ void destroy(nbody_ctx *c) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   delete c;
+}
+
+constexpr int kVjpTile = 512;  // sources per shared-memory stage of the VJP kernel
+
+// Adjoint workspace: VJP tables (fixed tiles), adjoint state, the
+// recomputation's shadow state, checkpoints for n_steps and the segment store.
+nbody_status ensure_adjoint(nbody_ctx *c, int64_t n_steps) {
+  Adjoint &A = c->adj;
+  const int prec = c->o.precision;
+  const size_t N = c->N;
+  const int64_t K = c->o.ckpt_every;
+  nbody_status st;
+  if (!A.vj.blks) {
+    nbody_tiles t{};
+    t.threads = nb::vjp_threads(prec);
+    t.ipt = 1;
+    t.tj = kVjpTile;
+    t.jsplit = 0;
+    t.ctas_per_sm = 32;
+    const size_t smem = nb::vjp_smem_bytes(prec, t.tj);
+    int occ = 0;
+    NB_CUDA(c, nb::vjp_prepare(prec, smem, &occ));
+    if ((st = build_work(c, A.vj, t, occ, 4)) != NBODY_OK) return st;
+    A.vj.smem = smem;
+    const size_t wbytes = (prec == NBODY_FP64 ? 32 : 16) * static_cast<size_t>(c->n_stage);
+    if ((st = dalloc(c, reinterpret_cast<void **>(&A.rho), sizeof(double) * 3 * N)) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&A.nu), sizeof(double) * 3 * N)) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&A.gm), sizeof(double) * N)) != NBODY_OK) return st;
+    if ((st = dalloc(c, &A.w, wbytes)) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&A.shadow), sizeof(double) * 9 * N)) != NBODY_OK) return st;
+    NB_CUDA(c, cudaMemset(A.w, 0, wbytes));  // padding entries stay 0
+  }
+  const int64_t need_ckpt = (n_steps + K - 1) / K + 1;
+  if (A.n_ckpt < need_ckpt) {
+    dfree(c, A.ckpt);
+    A.ckpt = nullptr;
+    A.n_ckpt = 0;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&A.ckpt), sizeof(double) * 6 * N * need_ckpt)) != NBODY_OK) return st;
+    A.n_ckpt = need_ckpt;
+  }
+  const int64_t need_store = std::min<int64_t>(K, std::max<int64_t>(n_steps, 1)) + 1;
+  if (A.store_len < need_store) {
+    dfree(c, A.store);
+    A.store = nullptr;
+    A.store_len = 0;
+    const size_t stage_bytes = 32 * static_cast<size_t>(c->n_stage);
+    if ((st = dalloc(c, &A.store, stage_bytes * need_store)) != NBODY_OK) return st;
+    if (prec == NBODY_MIXED)
+      for (int64_t j = 0; j < need_store; ++j)
+        NB_CUDA(c, nb::launch_pad_fill(static_cast<unsigned char *>(A.store) + stage_bytes * j, c->n_stage / 2,
+                                       c->stream));
+    A.store_len = need_store;
+  }
+  return NBODY_OK;
 }
 
 }  // namespace
@@ -766,8 +845,94 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
 nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, const double *dL_dv_T, double *dL_dr0,
                         double *dL_dv0, double *dL_dm) {
   if (!c) return NBODY_EINVAL;
-  (void)n_steps; (void)dL_dr_T; (void)dL_dv_T; (void)dL_dr0; (void)dL_dv0; (void)dL_dm;
-  return fail(c, NBODY_EINVAL, "nbody_grad: not available in this build");
+  if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
+  if (!dL_dr_T || !dL_dr0 || !dL_dv0 || !dL_dm) return fail(c, NBODY_EINVAL, "a gradient pointer is NULL");
+  if (n_steps > (int64_t(1) << 31)) return fail(c, NBODY_EINVAL, "n_steps too large");
+  nbody_status st;
+  if ((st = ensure_adjoint(c, n_steps)) != NBODY_OK) return st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  Adjoint &A = c->adj;
+  const int prec = c->o.precision;
+  const size_t N = c->N, b = sizeof(double) * N;
+  const int64_t T = n_steps, K = c->o.ckpt_every;
+  const State sh = {A.shadow, A.shadow + N, A.shadow + 2 * N, A.shadow + 3 * N, A.shadow + 4 * N,
+                    A.shadow + 5 * N, A.shadow + 6 * N, A.shadow + 7 * N, A.shadow + 8 * N};
+  const size_t stage_bytes = 32 * static_cast<size_t>(c->n_stage);
+  auto store = [&](int64_t j) { return static_cast<unsigned char *>(A.store) + stage_bytes * j; };
+  auto ckpt = [&](int64_t k) { return A.ckpt + static_cast<size_t>(k) * 6 * N; };
+
+  // Forward from the snapshot (r0, v0), keeping (r, v) every K steps.
+  NB_CUDA(c, cudaMemcpyAsync(A.shadow, c->snap, 6 * b, cudaMemcpyDeviceToDevice, c->stream));
+  NB_CUDA(c, nb::launch_prep(prec, prep_args(c, sh, 0, 0), c->stream));
+  if ((st = launch_one_step(c, sh, c->stage[0], c->stage[1], nb::kModeForce, c->stream)) != NBODY_OK) return st;
+  NB_CUDA(c, cudaMemcpyAsync(ckpt(0), A.shadow, 6 * b, cudaMemcpyDeviceToDevice, c->stream));
+  const int64_t nseg = (T + K - 1) / K;
+  for (int64_t sgi = 0; sgi < nseg - 1; ++sgi) {  // the last segment needs no checkpoint at its end
+    NB_CUDA(c, nb::launch_prep(prec, prep_args(c, sh, 1, 0), c->stream));
+    int64_t left = K;
+    while (left > 0) {
+      const int n = static_cast<int>(std::min<int64_t>(left, kGraphChunk));
+      if ((st = launch_steps(c, sh, n, c->stream)) != NBODY_OK) return st;
+      left -= n;
+    }
+    NB_CUDA(c, cudaMemcpyAsync(ckpt(sgi + 1), A.shadow, 6 * b, cudaMemcpyDeviceToDevice, c->stream));
+  }
+
+  // Reverse sweep.
+  nb::AdjArgs ad{};
+  ad.rho = A.rho;
+  ad.nu = A.nu;
+  ad.gm = A.gm;
+  ad.w = A.w;
+  ad.partial = A.vj.partial;
+  ad.nsl = A.vj.nsl;
+  ad.qidx = c->qidx;
+  ad.flags = c->flags;
+  ad.N = c->N;
+  ad.G = c->o.G;
+  ad.dt = c->o.dt;
+  ad.half_dt = 0.5 * c->o.dt;
+  ad.half_dt2 = 0.5 * c->o.dt * c->o.dt;
+  ad.mode = T > 0 ? 0 : 1;
+  NB_CUDA(c, nb::launch_adjoint_init(prec, ad, dL_dr_T, dL_dv_T, c->stream));
+  nb::VjpArgs vj{};
+  vj.w = A.w;
+  vj.partial = A.vj.partial;
+  vj.flags = c->flags;
+  vj.blks = A.vj.blks;
+  vj.segs = A.vj.segs;
+  vj.seg_off = A.vj.seg_off;
+  vj.N = c->N;
+  vj.tj = kVjpTile;
+  auto product = [&](const void *pos, int mode) -> nbody_status {
+    vj.pos = pos;
+    NB_CUDA(c, nb::launch_vjp(prec, A.vj.grid, A.vj.smem, vj, c->stream));
+    ad.mode = mode;
+    NB_CUDA(c, nb::launch_adjoint(prec, ad, c->stream));
+    return NBODY_OK;
+  };
+  for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+    // Recompute the staged positions r_{s0} .. r_{s0+len} of this segment.
+    const int64_t s0 = sgi * K, len = std::min(K, T - s0);
+    NB_CUDA(c, cudaMemcpyAsync(A.shadow, ckpt(sgi), 6 * b, cudaMemcpyDeviceToDevice, c->stream));
+    NB_CUDA(c, nb::launch_prep(prec, prep_args(c, sh, 0, 0, store(0)), c->stream));
+    if ((st = launch_one_step(c, sh, store(0), store(1), nb::kModeForce, c->stream)) != NBODY_OK) return st;
+    NB_CUDA(c, nb::launch_prep(prec, prep_args(c, sh, 1, 0, store(1)), c->stream));
+    for (int64_t j = 1; j < len; ++j)
+      if ((st = launch_one_step(c, sh, store(j), store(j + 1), nb::kModeStep, c->stream)) != NBODY_OK) return st;
+    // Iterations i = s0+len-1 .. s0 use r_{i+1} = store[i+1-s0].
+    for (int64_t i = s0 + len - 1; i >= s0; --i)
+      if ((st = product(store(i + 1 - s0), i == 0 ? 1 : 0)) != NBODY_OK) return st;
+  }
+  if (T == 0)  // no segment staged r_0: the shadow still holds the snapshot
+    NB_CUDA(c, nb::launch_prep(prec, prep_args(c, sh, 0, 0, store(0)), c->stream));
+  if ((st = product(store(0), 2)) != NBODY_OK) return st;  // the last product, at r_0
+
+  NB_CUDA(c, cudaMemcpyAsync(dL_dr0, A.rho, 3 * b, cudaMemcpyDeviceToDevice, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(dL_dv0, A.nu, 3 * b, cudaMemcpyDeviceToDevice, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(dL_dm, A.gm, b, cudaMemcpyDeviceToDevice, c->stream));
+  if ((st = end_work(c)) != NBODY_OK) return st;
+  return check_flags(c, false);
 }
 
 void nbody_free(nbody_ctx *c) { destroy(c); }

@@ -82,6 +82,35 @@ struct VerletArgs {
   double dt, half_dt, half_dt2;
 };
 
+// Vector-Jacobian product of Eq. 1 at staged positions r_k (vjp.cu): for
+// every target q, J^T w and the mass term, as one partial row per segment of
+// the same kind of work tables as the force kernel ([rows][4][N]).
+struct VjpArgs {
+  const void *pos;  // positions staged by the forward pass (its layout)
+  const void *w;    // w per stage entry: FP64 double4, mixed float4 (x, y, z, 0)
+  double *partial;  // [rows][4][N]: doubles (FP64) or float pairs (mixed)
+  unsigned *flags;
+  const Blk *blks;
+  const Seg *segs;
+  const int32_t *seg_off;  // [gridDim.x + 1]
+  int32_t N;
+  int32_t tj;
+};
+
+// One step of the reverse sweep per body (vjp.cu).
+struct AdjArgs {
+  double *rho, *nu;  // [3][N] dL/dr, dL/dv
+  double *gm;        // [N] dL/dm
+  void *w;           // staged w for the next product (same layout as VjpArgs::w)
+  const double *partial;
+  const uint16_t *nsl;
+  const int32_t *qidx;  // mixed: stage index of body p; NULL: p
+  unsigned *flags;
+  int32_t N;
+  int32_t mode;  // 0: step, stage alpha'+dt/2 nu'; 1: step, stage alpha'; 2: last product only
+  double G, dt, half_dt, half_dt2;
+};
+
 // Staging / pre-drift over all N bodies: stage r (drift == 0) or
 // drift(r, v, a) (drift == 1), with mu = G m, at stage index qidx[p]
 // (mixed; FP64 stages in body order).
@@ -128,6 +157,12 @@ size_t force_smem_bytes(int precision, int tj);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);
+size_t vjp_smem_bytes(int precision, int tj);
+int vjp_threads(int precision);
+cudaError_t vjp_prepare(int precision, size_t smem, int *occ);  // raise the smem limit, resident CTAs/SM
+cudaError_t launch_vjp(int precision, int grid, size_t smem, const VjpArgs &a, cudaStream_t s);
+cudaError_t launch_adjoint(int precision, const AdjArgs &a, cudaStream_t s);
+cudaError_t launch_adjoint_init(int precision, const AdjArgs &a, const double *dr, const double *dv, cudaStream_t s);
 void set_last_error(const char *msg);  // message returned by nbody_last_error(NULL) on this thread
 
 constexpr int kStages = 2;          // shared-memory pipeline depth of the force kernels

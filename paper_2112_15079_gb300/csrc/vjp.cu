@@ -1,0 +1,342 @@
+// Adjoint of the Verlet trajectory: the vector-Jacobian product (VJP) of
+// Eq. 1 and the per-body reverse-sweep update.
+//
+// With d = r_j - r_q, s3 = |d|^-3, s5 = |d|^-5 and mu = G m, the Jacobian of
+// the pair term d |d|^-3 is K(d) = I s3 - 3 d d^T s5 (symmetric, K(-d) = K(d)),
+// so for an adjoint vector w on the accelerations
+//   (J^T w)_q = sum_{j != q} K(d) (mu_q w_j - mu_j w_q)
+//             = sum_j [ s3 u - 3 s5 (d.u) d ],  u = mu_q w_j - mu_j w_q,
+//   (dA/dm)^T w at q = -G sum_{j != q} s3 (w_j . d).
+// vjp_kernel evaluates both sums for every target q, using the same
+// stream-K work tables as the force kernel (segments of sources per target
+// block, one partial row per segment, here 4 values: the three components of
+// J^T w and the mass sum).  adjoint_kernel then sums a body's rows in a fixed
+// order and applies one step of the reverse sweep of Eqs. 3-4:
+//   rho += J^T w;  g_m += (dA/dm)^T w;
+//   nu' = nu + dt rho;  alpha' = dt/2 nu + dt^2/2 rho;  nu = nu';
+//   next w = alpha' + dt/2 nu'  (w = alpha' before the last product, at r_0).
+#include "nbody_dev.cuh"
+
+namespace nb {
+
+namespace {
+
+// Source tile: positions as staged by the forward pass (FP64 double4 or
+// mixed pair blocks, 32 B per source) followed by w (FP64 double4, mixed float4).
+template <int PREC>
+struct VjpLayout {
+  static constexpr int kWBytes = PREC == 0 ? 32 : 16;
+  static constexpr int kBytesPerSource = 32 + kWBytes;
+};
+
+template <int PREC, int THREADS>
+__global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  const int tj = a.tj;
+  constexpr int kW = VjpLayout<PREC>::kWBytes;
+  auto pos_ptr = [&](int s) { return smem + static_cast<size_t>(s) * tj * VjpLayout<PREC>::kBytesPerSource; };
+  auto w_ptr = [&](int s) { return pos_ptr(s) + static_cast<size_t>(tj) * 32; };
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+    s_flag = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool aborted = false;
+  const size_t N = static_cast<size_t>(a.N);
+  const int seg_end = a.seg_off[blockIdx.x + 1];
+
+  for (int si = a.seg_off[blockIdx.x]; si < seg_end && !aborted; ++si) {
+    const Seg sg = a.segs[si];
+    const Blk bk = a.blks[sg.blk];
+    const int q_end = bk.q0 + (bk.i1 - bk.i0);
+    const int p = bk.i0 + tid;
+    const bool valid = p < bk.i1;
+    const int pi = valid ? p : bk.i1 - 1;
+    const int tq = bk.q0 + (pi - bk.i0);
+
+    // target q: position, mu_q, w_q
+    double qx = 0, qy = 0, qz = 0, qmu = 0, wqx = 0, wqy = 0, wqz = 0;
+    float hx = 0, hy = 0, hz = 0, lx = 0, ly = 0, lz = 0, fmu = 0, fwx = 0, fwy = 0, fwz = 0;
+    if (PREC == 0) {
+      const double4_32a r = static_cast<const double4_32a *>(a.pos)[tq];
+      qx = r.x;
+      qy = r.y;
+      qz = r.z;
+      qmu = r.w;
+      const double4_32a w = static_cast<const double4_32a *>(a.w)[tq];
+      wqx = w.x;
+      wqy = w.y;
+      wqz = w.z;
+    } else {
+      const float *e = static_cast<const float *>(a.pos) + pair_off(tq);
+      hx = e[kXh];
+      hy = e[kYh];
+      hz = e[kZh];
+      lx = e[kXl];
+      ly = e[kYl];
+      lz = e[kZl];
+      fmu = e[kMu];
+      const float4 w = static_cast<const float4 *>(a.w)[tq];
+      fwx = w.x;
+      fwy = w.y;
+      fwz = w.z;
+    }
+    // FP64: per-tile sub-sums folded into (acc, cmp) pairs by TwoSum.
+    // Mixed: FP32 sub-sums of kFoldPairs*2 sources folded into float pairs.
+    double acc[4] = {0, 0, 0, 0}, cmp[4] = {0, 0, 0, 0};
+    float sh[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+
+    const int ntiles = (sg.s1 - sg.s0 + tj - 1) / tj;
+    auto issue = [&](int t) {
+      const int s = t % kStages;
+      const int j = sg.s0 + t * tj;
+      const uint32_t n = static_cast<uint32_t>(min(tj, sg.s1 - j));
+      mbar_arrive_expect_tx(&bar[s], n * (32u + kW));
+      bulk_g2s(pos_ptr(s), static_cast<const unsigned char *>(a.pos) + static_cast<size_t>(j) * 32, n * 32u, &bar[s]);
+      bulk_g2s(w_ptr(s), static_cast<const unsigned char *>(a.w) + static_cast<size_t>(j) * kW, n * kW, &bar[s]);
+    };
+    if (tid == 0)
+      for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
+
+    for (int t = 0; t < ntiles; ++t) {
+      const int s = t % kStages;
+      if (!mbar_wait(&bar[s], (phase >> s) & 1u)) atomicOr(&s_flag, 1);
+      phase ^= 1u << s;
+      const int jt0 = sg.s0 + t * tj;
+      const int cnt = min(tj, sg.s1 - jt0);
+      const bool diag = jt0 < q_end && jt0 + cnt > bk.q0;
+      if (PREC == 0) {
+        const double4_32a *sp = reinterpret_cast<const double4_32a *>(pos_ptr(s));
+        const double4_32a *sw = reinterpret_cast<const double4_32a *>(w_ptr(s));
+        double tacc[4] = {0, 0, 0, 0};
+        for (int jj = 0; jj < cnt; ++jj) {
+          const double4_32a r = sp[jj], w = sw[jj];
+          const double dx = r.x - qx, dy = r.y - qy, dz = r.z - qz;
+          double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+          if (diag) r2 = (jt0 + jj == tq) ? 1.0 : r2;
+          const double y = inv_r1(r2);
+          const double y2 = y * y;
+          const double s3 = y * y2;
+          const double s5 = s3 * y2;
+          const double ux = fma(-r.w, wqx, qmu * w.x);
+          const double uy = fma(-r.w, wqy, qmu * w.y);
+          const double uz = fma(-r.w, wqz, qmu * w.z);
+          const double t3 = 3.0 * s5 * fma(dz, uz, fma(dy, uy, dx * ux));
+          tacc[0] = fma(-t3, dx, fma(s3, ux, tacc[0]));
+          tacc[1] = fma(-t3, dy, fma(s3, uy, tacc[1]));
+          tacc[2] = fma(-t3, dz, fma(s3, uz, tacc[2]));
+          tacc[3] = fma(s3, fma(w.z, dz, fma(w.y, dy, w.x * dx)), tacc[3]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) two_sum_acc(acc[c], cmp[c], tacc[c]);
+      } else {
+        const float4 *sp = reinterpret_cast<const float4 *>(pos_ptr(s));  // 4 per pair block
+        const float4 *sw = reinterpret_cast<const float4 *>(w_ptr(s));
+        for (int g0 = 0; g0 < cnt; g0 += 2 * kFoldPairs) {
+          const int lim = min(2 * kFoldPairs, cnt - g0);
+          float tacc[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int jj = g0; jj < g0 + lim; ++jj) {
+            const float *pb = reinterpret_cast<const float *>(sp + 4 * (jj >> 1)) + (jj & 1);
+            const float4 w = sw[jj];
+            const float dx = (pb[kXh] - hx) + (pb[kXl] - lx);
+            const float dy = (pb[kYh] - hy) + (pb[kYl] - ly);
+            const float dz = (pb[kZh] - hz) + (pb[kZl] - lz);
+            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (diag) r2 = (jt0 + jj == tq) ? 1.0f : r2;
+            const float y = rsqrt_approx(r2);
+            const float y2 = y * y;
+            const float s3 = y * y2;
+            const float s5 = s3 * y2;
+            const float mu = pb[kMu];
+            const float ux = fmaf(-mu, fwx, fmu * w.x);
+            const float uy = fmaf(-mu, fwy, fmu * w.y);
+            const float uz = fmaf(-mu, fwz, fmu * w.z);
+            const float t3 = 3.0f * s5 * fmaf(dz, uz, fmaf(dy, uy, dx * ux));
+            tacc[0] = fmaf(-t3, dx, fmaf(s3, ux, tacc[0]));
+            tacc[1] = fmaf(-t3, dy, fmaf(s3, uy, tacc[1]));
+            tacc[2] = fmaf(-t3, dz, fmaf(s3, uz, tacc[2]));
+            tacc[3] = fmaf(s3, fmaf(w.z, dz, fmaf(w.y, dy, w.x * dx)), tacc[3]);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) two_sum_acc(sh[c], sl[c], tacc[c]);
+        }
+      }
+      __syncthreads();
+      if (s_flag & 1) {
+        aborted = true;
+        if (tid == 0) {
+          mbar_wait(&bar[s], ((phase >> s) & 1u) ^ 1u);
+          for (int u = t + 1; u < ntiles && u < t + kStages; ++u) {
+            const int su = u % kStages;
+            mbar_wait(&bar[su], (phase >> su) & 1u);
+            phase ^= 1u << su;
+          }
+        }
+        break;
+      }
+      if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+      if (tid == 0) atomicOr(a.flags, kFlagTimeout);
+      break;
+    }
+    if (valid) {
+      double *prow = a.partial + static_cast<size_t>(sg.slot) * 4 * N;
+      if (PREC == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) prow[c * N + p] = acc[c] + cmp[c];
+      } else {
+        float2 *frow = reinterpret_cast<float2 *>(prow);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) frow[c * N + p] = make_float2(sh[c], sl[c]);
+      }
+    }
+  }
+}
+
+// One reverse-sweep step per body (see the file comment).  mode 0: full
+// update and stage w = alpha' + dt/2 nu'; mode 1: the same but stage
+// w = alpha' (the next product is the last one, at r_0); mode 2: the last
+// product only (rho, g_m updated, nothing staged).
+template <int PREC>
+__global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.N) return;
+  const size_t N = static_cast<size_t>(a.N);
+  const int rows = a.nsl[p];
+  double s[4], e[4];
+  if (PREC == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = e[c] = 0.0;
+    for (int r = 0; r < rows; ++r) {
+      const double *row = a.partial + static_cast<size_t>(r) * 4 * N;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) two_sum_acc(s[c], e[c], row[c * N + p]);
+    }
+  } else {
+    float fs[4] = {0.f, 0.f, 0.f, 0.f}, fe[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int r = 0; r < rows; ++r) {
+      const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(r) * 4 * N);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 v = row[c * N + p];
+        two_sum_acc(fs[c], fe[c], v.x);
+        fe[c] += v.y;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      s[c] = static_cast<double>(fs[c]);
+      e[c] = static_cast<double>(fe[c]);
+    }
+  }
+  double jtw[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) jtw[c] = s[c] + e[c];
+  const double gsum = s[3] + e[3];
+  if (!finite3(jtw[0], jtw[1], jtw[2]) || !isfinite(gsum)) atomicOr(a.flags, kFlagNonFinite);
+  a.gm[p] += -a.G * gsum;
+  double rho[3], nu[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    rho[c] = a.rho[c * N + p] + jtw[c];
+    a.rho[c * N + p] = rho[c];
+    nu[c] = a.nu[c * N + p];
+  }
+  if (a.mode == 2) return;
+  double w[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double nun = fma(a.dt, rho[c], nu[c]);               // nu' = nu + dt rho
+    const double al = fma(a.half_dt2, rho[c], a.half_dt * nu[c]);  // alpha' = dt/2 nu + dt^2/2 rho
+    a.nu[c * N + p] = nun;
+    w[c] = a.mode == 0 ? fma(a.half_dt, nun, al) : al;         // next w
+  }
+  const int q = a.qidx ? a.qidx[p] : p;
+  if (PREC == 0)
+    static_cast<double4_32a *>(a.w)[q] = make_double4_32a(w[0], w[1], w[2], 0.0);
+  else
+    static_cast<float4 *>(a.w)[q] =
+        make_float4(static_cast<float>(w[0]), static_cast<float>(w[1]), static_cast<float>(w[2]), 0.f);
+}
+
+// rho = dL/dr_T, nu = dL/dv_T (or 0), g_m = 0, and the first w = dt/2 nu
+// (mode 0) or 0 (mode 1: no step, the only product is at r_0 with w = 0).
+template <int PREC>
+__global__ void adjoint_init_kernel(const AdjArgs a, const double *dr, const double *dv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.N) return;
+  const size_t N = static_cast<size_t>(a.N);
+  double w[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.rho[c * N + p] = dr[c * N + p];
+    const double nu = dv ? dv[c * N + p] : 0.0;
+    a.nu[c * N + p] = nu;
+    w[c] = a.mode == 0 ? a.half_dt * nu : 0.0;
+  }
+  a.gm[p] = 0.0;
+  const int q = a.qidx ? a.qidx[p] : p;
+  if (PREC == 0)
+    static_cast<double4_32a *>(a.w)[q] = make_double4_32a(w[0], w[1], w[2], 0.0);
+  else
+    static_cast<float4 *>(a.w)[q] =
+        make_float4(static_cast<float>(w[0]), static_cast<float>(w[1]), static_cast<float>(w[2]), 0.f);
+}
+
+}  // namespace
+
+size_t vjp_smem_bytes(int precision, int tj) {
+  return static_cast<size_t>(kStages) * tj * (precision == 0 ? VjpLayout<0>::kBytesPerSource : VjpLayout<1>::kBytesPerSource);
+}
+
+// The VJP runs with fixed tiles: FP64 128 threads, mixed 256 threads, IPT 1.
+int vjp_threads(int precision) { return precision == 0 ? 128 : 256; }
+
+cudaError_t vjp_prepare(int precision, size_t smem, int *occ) {
+  cudaError_t e;
+  if (precision == 0) {
+    e = cudaFuncSetAttribute(vjp_kernel<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, vjp_kernel<0, 128>, 128, smem);
+  } else {
+    e = cudaFuncSetAttribute(vjp_kernel<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, vjp_kernel<1, 256>, 256, smem);
+  }
+  return e;
+}
+
+cudaError_t launch_vjp(int precision, int grid, size_t smem, const VjpArgs &a, cudaStream_t s) {
+  if (precision == 0)
+    vjp_kernel<0, 128><<<grid, 128, smem, s>>>(a);
+  else
+    vjp_kernel<1, 256><<<grid, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(int precision, const AdjArgs &a, cudaStream_t s) {
+  if (a.N <= 0) return cudaSuccess;
+  const int grid = (a.N + 255) / 256;
+  if (precision == 0)
+    adjoint_kernel<0><<<grid, 256, 0, s>>>(a);
+  else
+    adjoint_kernel<1><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(int precision, const AdjArgs &a, const double *dr, const double *dv, cudaStream_t s) {
+  if (a.N <= 0) return cudaSuccess;
+  const int grid = (a.N + 255) / 256;
+  if (precision == 0)
+    adjoint_init_kernel<0><<<grid, 256, 0, s>>>(a, dr, dv);
+  else
+    adjoint_init_kernel<1><<<grid, 256, 0, s>>>(a, dr, dv);
+  return cudaGetLastError();
+}
+
+}  // namespace nb
