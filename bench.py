@@ -82,6 +82,11 @@ def parse():
                          '"jsplit":4,"ctas_per_sm":1}; skips the autotuner')
     ap.add_argument("--tiles-fp64", default=None, help="JSON work decomposition for the FP64 path only")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint, 31-body and ensemble measurements")
+    ap.add_argument("--adjoint-steps", type=int, default=100)
+    ap.add_argument("--ensemble-systems", type=int, default=256)
+    ap.add_argument("--sweep", action="store_true", help="also time N = 16,384 / 65,536 / 262,144 / 1,048,576")
     return ap.parse_args()
 
 
@@ -317,6 +322,9 @@ def run_ours(args):
         if prec == "mixed" and not args.no_e2e:
             results["e2e"] = e2e(torch, b, s, stream, inner, args, dist, device, world)
         b.close()
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extras and not args.only:
+        extra = extras(torch, nbody, inputs, stream, device, args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(s, args.cpu_seconds)
@@ -381,6 +389,8 @@ def run_ours(args):
             line["gpu_launches"] += args.steps * (1 + f["inner"])
         if "e2e" in results:
             line["e2e"] = results["e2e"]
+        if extra:
+            line.update(extra)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -420,6 +430,85 @@ def e2e(torch, b, s, stream, inner, args, dist, device, world):
     return {"value": N * (N - 1) * inner * args.steps * world / el, "unit": UNIT,
             "h2d_bytes_per_step": int(h_state.numel() * 8 + h_m.numel() * 8),
             "d2h_bytes_per_step": int(h_out.numel() * 8), "ms_per_step": el / args.steps * 1e3}
+
+
+def timed(torch, stream, fn, reps=1):
+    """Event-timed seconds of fn() on `stream` (after a synchronize)."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def extras(torch, nbody, inputs, stream, device, args):
+    """Adjoint cost, the 31-body model, the uneven ensemble and (optionally) the N sweep."""
+    out = {}
+    # adjoint on the 10,425-body model: backward wall / (T x forward step)
+    s = inputs.solar_system(args.n)
+    idx, tgt = inputs.loss_targets(s)
+    T = args.adjoint_steps
+    for prec in ("mixed", "fp64"):
+        TT = T if prec == "mixed" else max(1, T // 10)
+        with torch.cuda.stream(stream):
+            b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, ckpt_every=100, device=device)
+            fwd = timed(torch, stream, lambda: b.step(TT)) / TT
+            gr = torch.zeros((3, s.n), dtype=torch.float64, device=device)
+            gr[:, torch.as_tensor(idx, device=device)] = 1.0
+            b.grad(TT, gr)  # allocate the workspace
+            bwd = timed(torch, stream, lambda: b.grad(TT, gr))
+        out.setdefault("adjoint", {})[prec] = {"steps": TT, "backward_s": bwd, "forward_step_ms": fwd * 1e3,
+                                               "cost_per_forward_step": bwd / (TT * fwd), "ckpt_every": 100}
+        b.close()
+    # the 31-body model (one FP64 system: single-launch cluster kernel), 3650 steps
+    s31 = inputs.solar_system(31)
+    with torch.cuda.stream(stream):
+        b = nbody.NBody(s31.r, s31.v, s31.m, G=s31.G, dt=s31.dt, precision="fp64", device=device)
+        b.step(10)
+        t = timed(torch, stream, lambda: b.step(3650))
+        b2 = nbody.NBody(s31.r, s31.v, s31.m, G=s31.G, dt=s31.dt, precision="fp64", small=False, device=device)
+        b2.step(10)
+        t2 = timed(torch, stream, lambda: b2.step(3650))
+    out["solar_system_n31"] = {"steps": 3650, "seconds": t, "verlet_steps_per_s": 3650 / t,
+                               "interactions_per_s": 31 * 30 * 3650 / t, "precision": "fp64",
+                               "general_path_verlet_steps_per_s": 3650 / t2}
+    b.close()
+    b2.close()
+    # uneven ensemble, mixed, one context
+    ens = inputs.ensemble(args.ensemble_systems)
+    off, r, v, m = inputs.concat(ens)
+    pairs = sum(e.n * (e.n - 1) for e in ens)
+    with torch.cuda.stream(stream):
+        b = nbody.NBody(r, v, m, off, G=inputs.G_AU_DAY, dt=inputs.DT_DAY, precision="mixed", device=device)
+        b.step(2)
+        n_ens = 5
+        t = timed(torch, stream, lambda: b.step(n_ens))
+    out["ensemble"] = {"systems": len(ens), "bodies": int(off[-1]), "steps": n_ens,
+                       "interactions_per_s": pairs * n_ens / t, "verlet_steps_per_s": n_ens / t,
+                       "ms_per_step": t / n_ens * 1e3, "precision": "mixed", "tiles": b.tiles}
+    b.close()
+    if args.sweep:
+        for n in (16384, 65536, 262144, 1048576):
+            sn = inputs.solar_system(n)
+            row = {}
+            for prec in ("mixed", "fp64"):
+                if prec == "fp64" and n > 65536:
+                    continue  # ~30 s per step at 1M bodies
+                with torch.cuda.stream(stream):
+                    b = nbody.NBody(sn.r, sn.v, sn.m, G=sn.G, dt=sn.dt, precision=prec, device=device)
+                    k = 2 if n >= 262144 else 5
+                    b.step(1)
+                    t = timed(torch, stream, lambda: b.step(k))
+                per = n * (n - 1) * k / t
+                row[prec] = {"interactions_per_s": per, "ms_per_step": t / k * 1e3,
+                             "roofline_frac": per * FLOPS_PER_INTERACTION * 1e-12 / PEAK_TFLOPS[prec]}
+                b.close()
+            out.setdefault("sweep", {})[str(n)] = row
+    return out
 
 
 def main():

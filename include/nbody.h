@@ -71,6 +71,10 @@ typedef struct {
 
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
 #define NBODY_FLAG_NO_GRAPH 1
+/* Never use the single-launch small-system kernel (one FP64 system of at
+ * most 64 bodies runs every step of an nbody_step call in one launch of a
+ * 16-CTA cluster unless this flag is set). */
+#define NBODY_FLAG_NO_SMALL 2
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work
  * of a step -- every target block (at most threads * ipt bodies of one
@@ -111,9 +115,11 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
 
 /* Advance every system by n_steps velocity-Verlet steps (Eqs. 3, 1, 4), in
  * place.  n_steps == 0 is a no-op; n_steps < 0 is EINVAL.  Asynchronous.
- * Each step is one launch of the fused force + kick + drift kernel;
- * consecutive steps are replayed from cached CUDA graphs unless
- * NBODY_FLAG_NO_GRAPH is set or the stream is already being captured. */
+ * Each step is a force launch (Eq. 1) and a per-body Verlet launch (Eqs.
+ * 4, 3), chained; consecutive steps are replayed from cached CUDA graphs
+ * unless NBODY_FLAG_NO_GRAPH is set or the stream is already being
+ * captured.  One FP64 system of at most 64 bodies instead runs all n_steps
+ * in a single cluster launch (see NBODY_FLAG_NO_SMALL). */
 nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
 
 /* Copy the acceleration at the current positions (Eq. 1, as used by the

@@ -90,6 +90,7 @@ struct nbody_ctx {
   Work fw;
   Adjoint adj;
 
+  bool small = false;  // the single-launch small-system kernel serves nbody_step
   std::map<int, cudaGraphExec_t> graphs;
   std::string err;
 };
@@ -613,7 +614,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (o->precision != NBODY_FP64 && o->precision != NBODY_MIXED)
     return fail(nullptr, NBODY_EINVAL, "unknown precision %d", o->precision);
   if (o->ckpt_every < 0) return fail(nullptr, NBODY_EINVAL, "ckpt_every must be >= 0");
-  if (o->reserved != 0 || (o->flags & ~NBODY_FLAG_NO_GRAPH))
+  if (o->reserved != 0 || (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL)))
     return fail(nullptr, NBODY_EINVAL, "unknown flags / reserved field not 0");
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;
@@ -667,6 +668,12 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (st != NBODY_OK) return bail(st);
   c->tiles = default_tiles(c);
   if ((st = build_items(c)) != NBODY_OK) return bail(st);
+  c->small = c->n_sys == 1 && c->N <= nb::small_max_bodies() && c->o.precision == NBODY_FP64 &&
+             !(c->o.flags & NBODY_FLAG_NO_SMALL);
+  if (c->small && nb::small_prepare() != cudaSuccess) {  // no 16-CTA clusters here: general path
+    cudaGetLastError();
+    c->small = false;
+  }
   if ((st = refresh(c)) != NBODY_OK) return bail(st);
   *out = c;
   return NBODY_OK;
@@ -679,6 +686,23 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
   const State s = bound_state(c);
+  if (c->small) {
+    nb::SmallArgs sa{};
+    sa.x = s.x; sa.y = s.y; sa.z = s.z; sa.vx = s.vx; sa.vy = s.vy; sa.vz = s.vz;
+    sa.ax = s.ax; sa.ay = s.ay; sa.az = s.az;
+    sa.m = c->m;
+    sa.flags = c->flags;
+    sa.N = c->N;
+    sa.n_steps = n_steps;
+    sa.G = c->o.G;
+    sa.dt = c->o.dt;
+    sa.half_dt = 0.5 * c->o.dt;
+    sa.half_dt2 = 0.5 * c->o.dt * c->o.dt;
+    cudaError_t e = nb::launch_small(sa, c->stream);
+    if (e == cudaSuccess) return end_work(c);
+    cudaGetLastError();  // cluster launch refused: fall back to the general path for good
+    c->small = false;
+  }
   NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   NB_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));

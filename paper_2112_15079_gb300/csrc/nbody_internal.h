@@ -111,6 +111,17 @@ struct AdjArgs {
   double G, dt, half_dt, half_dt2;
 };
 
+// Small-N persistent kernel (smalln.cu): all steps of one FP64 system in one
+// cluster launch; state read from and written back to these arrays.
+struct SmallArgs {
+  double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
+  const double *m;
+  unsigned *flags;
+  int32_t N;
+  int64_t n_steps;
+  double G, dt, half_dt, half_dt2;
+};
+
 // Staging / pre-drift over all N bodies: stage r (drift == 0) or
 // drift(r, v, a) (drift == 1), with mu = G m, at stage index qidx[p]
 // (mixed; FP64 stages in body order).
@@ -157,6 +168,9 @@ size_t force_smem_bytes(int precision, int tj);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);
+int small_max_bodies();
+cudaError_t small_prepare();
+cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
 size_t vjp_smem_bytes(int precision, int tj);
 int vjp_threads(int precision);
 cudaError_t vjp_prepare(int precision, size_t smem, int *occ);  // raise the smem limit, resident CTAs/SM

@@ -26,6 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 NBODY_OK, NBODY_EINVAL, NBODY_ENOMEM, NBODY_ECUDA, NBODY_ENONFINITE, NBODY_ETIMEOUT = range(6)
 NBODY_FP64, NBODY_MIXED = 0, 1
 NBODY_FLAG_NO_GRAPH = 1
+NBODY_FLAG_NO_SMALL = 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT"}
 PRECISIONS = {"fp64": NBODY_FP64, "mixed": NBODY_MIXED}
 
@@ -122,7 +123,7 @@ class NBody:
     [6, N] float64 CUDA tensor (rows x, y, z, vx, vy, vz), updated in place."""
 
     def __init__(self, r, v, m, offsets=None, *, G: float, dt: float, precision: str = "fp64",
-                 ckpt_every: int = 0, graphs: bool = True, device=None, stream=None):
+                 ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None):
         torch = _torch()
         device = torch.device(device if device is not None else "cuda")
         self.device = device
@@ -141,7 +142,8 @@ class NBody:
         self.G, self.dt, self.precision = float(G), float(dt), precision
         self._stream = stream if stream is not None else torch.cuda.current_stream(device)
         opts = nbody_opts(G=self.G, dt=self.dt, precision=PRECISIONS[precision], ckpt_every=int(ckpt_every),
-                          flags=0 if graphs else NBODY_FLAG_NO_GRAPH, reserved=0)
+                          flags=(0 if graphs else NBODY_FLAG_NO_GRAPH) | (0 if small else NBODY_FLAG_NO_SMALL),
+                          reserved=0)
         self._ctx = _P()
         s = self.state
         ptrs = [s[k].data_ptr() for k in range(6)] + [self.m.data_ptr()]

@@ -117,6 +117,33 @@ def test_fp64_trajectory_31_bodies_3650_steps(nb):
     assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-10 * np.abs(v_ref).max()
 
 
+@pytest.mark.parametrize("n", [2, 31, 64])
+def test_small_system_kernel_vs_general_and_oracle(nb, n):
+    """One FP64 system of <= 64 bodies runs every step in one cluster launch;
+    it matches the oracle and the general two-kernel path."""
+    s = inputs.solar_system(31, seed=70 + n) if n == 31 else None
+    if n == 64:
+        s = inputs.solar_system(64, seed=71, n_moons=0)
+    if n == 2:
+        r = np.array([[0.0, 1.0], [0.0, 0.0], [0.0, 0.0]])
+        v = np.array([[0.0, 0.0], [0.0, 0.0172], [0.0, 0.0]])
+        s = inputs.System(r=r, v=v, m=np.array([1.0, 3e-6]))
+    steps = 1000
+    small = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    gen = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64", small=False)
+    for b in (small, gen):
+        b.step(400)
+        b.step(steps - 400)
+        b.sync()
+    r_ref, v_ref, a_ref = oracle.verlet(s.G, s.dt, steps, s.r, s.v, s.m)
+    for b in (small, gen):
+        assert np.abs(b.r.cpu().numpy() - r_ref).max() <= 1e-11 * max(1.0, np.abs(r_ref).max())
+        assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-11 * np.abs(v_ref).max()
+        a = b.accel().cpu().numpy()
+        assert np.max(np.linalg.norm(a - a_ref, axis=0) / np.linalg.norm(a_ref, axis=0)) <= FP64_TOL
+    assert np.abs(small.r.cpu().numpy() - gen.r.cpu().numpy()).max() <= 1e-11 * max(1.0, np.abs(r_ref).max())
+
+
 def test_mixed_energy_drift_31_bodies(nb):
     """Energy drift of the mixed path within 2x the oracle's (3650 steps)."""
     s = inputs.solar_system(31)
