@@ -165,6 +165,17 @@ nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
 nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *best,
                             double *best_ms);
 
+/* Kernel durations of the general path, for roofline accounting (not part of
+ * the method).  Advances the bound state by n_steps Verlet steps (Eqs. 3-4)
+ * exactly as nbody_step does, but launches each step's two kernels, the
+ * Eq. 1 force kernel and the per-body Verlet kernel, unchained and without a
+ * graph, each bracketed by CUDA events on the context's stream.  The small
+ * single-cluster path is not used.  HOST out[4] receives: [0] mean force
+ * kernel duration (ms), [1] mean Verlet kernel duration (ms), [2] mean time
+ * per step from the first event to the last (ms), [3] n_steps.
+ * n_steps >= 1, else NBODY_EINVAL.  Synchronous. */
+nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
+
 /* Largest system nbody_accel_static accepts. */
 #define NBODY_STATIC_MAX_BODIES 65536
 

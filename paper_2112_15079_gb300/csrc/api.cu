@@ -171,16 +171,17 @@ bool tiles_valid(const nbody_tiles &t, int precision) {
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
-  // Measured on GB300 at N = 10,425: FP64 is bound by the FP64 pipe (~90% busy)
-  // for any decomposition with >= 8 warps and some ILP per SM; the mixed path
-  // is best with two targets per thread and three 256-thread CTAs per SM.
+  // Measured on GB300 at N = 10,425 and 65,536: FP64 is bound by the FP64 pipe
+  // (~90% busy) with three 128-thread CTAs per SM; the mixed path is best with
+  // two targets per thread and three 256-thread CTAs per SM.
   nbody_tiles t{};
   t.jsplit = 0;  // static shares only (dynamic chunks add partial rows)
   t.tj = 1024;
   t.ipt = 2;
   if (c->o.precision == NBODY_FP64) {
     t.threads = 128;
-    t.ctas_per_sm = 2;
+    t.ipt = 1;
+    t.ctas_per_sm = 3;
   } else {
     t.threads = 256;
     t.ctas_per_sm = 3;
@@ -385,10 +386,17 @@ nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, const void *cur, void *
 // One Verlet step (or, kModeForce, only a = Eq. 1) from the staged sources
 // `cur`, staging the next positions into `nxt`: the force kernel, then the
 // per-body Verlet kernel, chained.
-nbody_status launch_one_step(nbody_ctx *c, const State &s, const void *cur, void *nxt, int mode, cudaStream_t st) {
+// With `ev` (three events) the kernels run unchained, bracketed by ev[0],
+// ev[1] and ev[2], so that each one's duration can be read alone.
+nbody_status launch_one_step(nbody_ctx *c, const State &s, const void *cur, void *nxt, int mode, cudaStream_t st,
+                             const cudaEvent_t *ev = nullptr) {
+  const bool chained = ev == nullptr;
+  if (ev) NB_CUDA(c, cudaEventRecord(ev[0], st));
   NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
-                              force_args(c, cur), st, true));
-  NB_CUDA(c, nb::launch_verlet(c->o.precision, verlet_args(c, s, cur, nxt, mode), st, true));
+                              force_args(c, cur), st, chained));
+  if (ev) NB_CUDA(c, cudaEventRecord(ev[1], st));
+  NB_CUDA(c, nb::launch_verlet(c->o.precision, verlet_args(c, s, cur, nxt, mode), st, chained));
+  if (ev) NB_CUDA(c, cudaEventRecord(ev[2], st));
   return NBODY_OK;
 }
 
@@ -864,6 +872,49 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
   return NBODY_OK;
+}
+
+nbody_status nbody_kernel_times(nbody_ctx *c, int32_t n_steps, double *out) {
+  if (!c || !out) return NBODY_EINVAL;
+  if (n_steps < 1) return fail(c, NBODY_EINVAL, "n_steps must be >= 1");
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  const State s = bound_state(c);
+  std::vector<cudaEvent_t> ev(3 * static_cast<size_t>(n_steps), nullptr);
+  for (cudaEvent_t &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (cudaEvent_t &f : ev)
+        if (f) cudaEventDestroy(f);
+      return fail(c, NBODY_ECUDA, "cudaEventCreate failed");
+    }
+  auto run = [&]() -> nbody_status {
+    NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
+    for (int32_t i = 0; i < n_steps; ++i) {
+      const int k = (i % kGraphChunk) & 1;  // same staging parity as nbody_step
+      nbody_status r = launch_one_step(c, s, c->stage[k], c->stage[1 - k], nb::kModeStep, c->stream, &ev[3 * i]);
+      if (r != NBODY_OK) return r;
+    }
+    NB_CUDA(c, cudaEventSynchronize(ev.back()));
+    double f = 0, v = 0;
+    for (int32_t i = 0; i < n_steps; ++i) {
+      float a = 0.f, b = 0.f;
+      NB_CUDA(c, cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]));
+      NB_CUDA(c, cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]));
+      f += a;
+      v += b;
+    }
+    float all = 0.f;
+    NB_CUDA(c, cudaEventElapsedTime(&all, ev.front(), ev.back()));
+    out[0] = f / n_steps;
+    out[1] = v / n_steps;
+    out[2] = static_cast<double>(all) / n_steps;
+    out[3] = n_steps;
+    return NBODY_OK;
+  };
+  st = run();
+  for (cudaEvent_t &e : ev) cudaEventDestroy(e);
+  if (st != NBODY_OK) return st;
+  return end_work(c);
 }
 
 nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, const double *dL_dv_T, double *dL_dr0,

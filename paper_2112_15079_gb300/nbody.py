@@ -58,6 +58,7 @@ _SIGS = {
     "nbody_get_tiles": (_S, [_P, ctypes.POINTER(nbody_tiles)]),
     "nbody_set_tiles": (_S, [_P, ctypes.POINTER(nbody_tiles)]),
     "nbody_autotune": (_S, [_P, ctypes.c_int32, ctypes.POINTER(nbody_tiles), ctypes.POINTER(ctypes.c_double)]),
+    "nbody_kernel_times": (_S, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "nbody_free": (None, [_P]),
     "nbody_last_error": (ctypes.c_char_p, [_P]),
     "nbody_peaks": (_S, [ctypes.POINTER(ctypes.c_double)]),
@@ -211,6 +212,14 @@ class NBody:
         ms = ctypes.c_double()
         check(nbody_autotune(self._ctx, int(probe_steps), ctypes.byref(t), ctypes.byref(ms)), self._ctx)
         return t.as_dict(), ms.value
+
+    def kernel_times(self, n_steps: int) -> dict:
+        """Advance n_steps Verlet steps with each kernel timed alone (CUDA
+        events on this context's stream): mean force-kernel, Verlet-kernel and
+        per-step milliseconds."""
+        out = (ctypes.c_double * 4)()
+        check(nbody_kernel_times(self._ctx, int(n_steps), out), self._ctx)
+        return {"force_ms": out[0], "verlet_ms": out[1], "step_ms": out[2], "steps": int(out[3])}
 
     def close(self) -> None:
         if getattr(self, "_ctx", None):

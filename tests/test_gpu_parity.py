@@ -174,6 +174,12 @@ def test_split_calls_and_graphs_bitwise(nb, precision):
         b.close()
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0], outs[2])
+    b = _make(nb, s, precision)
+    kt = b.kernel_times(130)  # the timed, unchained launches compute the same steps
+    assert np.array_equal(b.state.cpu().numpy(), outs[0])
+    assert kt["steps"] == 130 and kt["force_ms"] > 0 and kt["verlet_ms"] > 0
+    assert kt["step_ms"] >= kt["force_ms"] + kt["verlet_ms"] - 1e-3
+    b.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
