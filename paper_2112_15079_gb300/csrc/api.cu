@@ -71,6 +71,7 @@ struct nbody_ctx {
 
   // scratch
   std::vector<void *> allocs;
+  int alloc_seq = 0;  // device allocations made so far (fault injection counts these)
   double *a = nullptr;               // [3][N] acceleration at the current positions
   void *stage[2] = {nullptr, nullptr};  // ping-pong staged sources (layout per precision)
   int64_t n_stage = 0;               // stage entries (mixed: systems padded to even length)
@@ -118,14 +119,11 @@ nbody_status fail(nbody_ctx *c, nbody_status st, const char *fmt, ...) {
 
 // Optional host-side fault injection for tests: NBODY_INJECT_ALLOC_FAIL=k
 // makes the k-th device allocation of a context fail with NBODY_ENOMEM.
-int g_alloc_count = 0;
-
 nbody_status dalloc(nbody_ctx *c, void **p, size_t bytes) {
   *p = nullptr;
-  ++g_alloc_count;
+  const int seq = ++c->alloc_seq;
   if (const char *inj = std::getenv("NBODY_INJECT_ALLOC_FAIL")) {
-    if (std::atoi(inj) == g_alloc_count)
-      return fail(c, NBODY_ENOMEM, "injected allocation failure (allocation %d)", g_alloc_count);
+    if (std::atoi(inj) == seq) return fail(c, NBODY_ENOMEM, "injected allocation failure (allocation %d)", seq);
   }
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
@@ -275,21 +273,27 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   wk.n_blks = static_cast<int>(blks.size());
   wk.rows = rows;
   wk.grid = static_cast<int>(G);
-  nbody_status st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
-  if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial),
-                   sizeof(double) * row_doubles * static_cast<size_t>(rows) * c->N)) != NBODY_OK)
-    return st;
-  NB_CUDA(c, cudaMemset(wk.dyn_ctr, 0, sizeof(int32_t) * 2));
-  NB_CUDA(c, cudaMemcpy(wk.blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemcpy(wk.segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemcpy(wk.seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
-  NB_CUDA(c, cudaMemcpy(wk.nsl, nsl.data(), sizeof(uint16_t) * nsl.size(), cudaMemcpyHostToDevice));
-  return NBODY_OK;
+  auto upload = [&]() -> nbody_status {
+    nbody_status st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK)
+      return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial),
+                     sizeof(double) * row_doubles * static_cast<size_t>(rows) * c->N)) != NBODY_OK)
+      return st;
+    NB_CUDA(c, cudaMemset(wk.dyn_ctr, 0, sizeof(int32_t) * 2));
+    NB_CUDA(c, cudaMemcpy(wk.blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy(wk.segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy(wk.seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
+    NB_CUDA(c, cudaMemcpy(wk.nsl, nsl.data(), sizeof(uint16_t) * nsl.size(), cudaMemcpyHostToDevice));
+    return NBODY_OK;
+  };
+  const nbody_status st = upload();
+  if (st != NBODY_OK) free_work(c, wk);  // all or nothing: no half-built tables
+  return st;
 }
 
 void free_work(nbody_ctx *c, Work &w) {
@@ -302,17 +306,22 @@ void free_work(nbody_ctx *c, Work &w) {
   w = Work{};
 }
 
-// Rebuild the force kernel's tables for the current tiles.
-nbody_status build_items(nbody_ctx *c) {
+// Build the force kernel's tables for tiles t and make t current.  The new
+// tables are built aside: on failure the context keeps its previous tiles
+// and tables, which stay a matching pair.
+nbody_status build_items(nbody_ctx *c, const nbody_tiles &t) {
   drop_graphs(c);
-  const nbody_tiles &t = c->tiles;
-  c->fw.smem = nb::force_smem_bytes(c->o.precision, t.tj);
-  NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, c->fw.smem));
-  const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, c->fw.smem);
-  const size_t smem = c->fw.smem;
-  nbody_status st = build_work(c, c->fw, t, occ, 3);
-  c->fw.smem = smem;
-  return st;
+  const size_t smem = nb::force_smem_bytes(c->o.precision, t.tj);
+  NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, smem));
+  const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, smem);
+  Work nw;
+  const nbody_status st = build_work(c, nw, t, occ, 3);
+  if (st != NBODY_OK) return st;
+  nw.smem = smem;
+  free_work(c, c->fw);
+  c->fw = nw;
+  c->tiles = t;
+  return NBODY_OK;
 }
 
 // Pointers of one state (the bound caller state, or the adjoint's shadow).
@@ -551,7 +560,12 @@ nbody_status ensure_adjoint(nbody_ctx *c, int64_t n_steps) {
   const size_t N = c->N;
   const int64_t K = c->o.ckpt_every;
   nbody_status st;
-  if (!A.vj.blks) {
+  if (!A.shadow) {  // first use, or an earlier attempt failed part way: start clean
+    free_work(c, A.vj);
+    for (void *q : {static_cast<void *>(A.rho), static_cast<void *>(A.nu), static_cast<void *>(A.gm), A.w})
+      dfree(c, q);
+    A.rho = A.nu = A.gm = nullptr;
+    A.w = nullptr;
     nbody_tiles t{};
     t.threads = nb::vjp_threads(prec);
     t.ipt = 1;
@@ -627,7 +641,6 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;
   if (!c) return fail(nullptr, NBODY_ENOMEM, "host allocation failed");
-  g_alloc_count = 0;
   c->n_sys = n_systems;
   c->offsets.assign(offsets, offsets + n_systems + 1);
   c->N = static_cast<int32_t>(offsets[n_systems]);
@@ -674,8 +687,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   }
   nbody_status st = alloc_scratch(c);
   if (st != NBODY_OK) return bail(st);
-  c->tiles = default_tiles(c);
-  if ((st = build_items(c)) != NBODY_OK) return bail(st);
+  if ((st = build_items(c, default_tiles(c))) != NBODY_OK) return bail(st);
   c->small = c->n_sys == 1 && c->N <= nb::small_max_bodies() && c->o.precision == NBODY_FP64 &&
              !(c->o.flags & NBODY_FLAG_NO_SMALL);
   if (c->small && nb::small_prepare() != cudaSuccess) {  // no 16-CTA clusters here: general path
@@ -799,8 +811,7 @@ nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
   if (!t || !tiles_valid(*t, c->o.precision))
     return fail(c, NBODY_EINVAL, "invalid tiles (see nbody.h: supported threads/ipt pairs, tj 64..2048 step 64, jsplit 0..64, ctas_per_sm 1..32)");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->tiles = *t;
-  return build_items(c);
+  return build_items(c, *t);
 }
 
 nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best, double *best_ms) {
@@ -842,8 +853,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   nbody_tiles win = c->tiles;
   double win_ms = 1e300;
   for (const nbody_tiles &t : cand) {
-    c->tiles = t;
-    if ((st = build_items(c)) != NBODY_OK) break;
+    if ((st = build_items(c, t)) != NBODY_OK) break;
     if ((st = nbody_step(c, 1)) != NBODY_OK) break;  // warm-up (also builds the graph)
     cudaEventRecord(e0, c->stream);
     if ((st = nbody_step(c, probe_steps)) != NBODY_OK) break;
@@ -866,8 +876,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   dfree(c, save);
   if (st != NBODY_OK) return st;
   if (st2 != NBODY_OK) return st2;
-  c->tiles = win;
-  if ((st = build_items(c)) != NBODY_OK) return st;
+  if ((st = build_items(c, win)) != NBODY_OK) return st;
   if ((st = check_flags(c, false)) != NBODY_OK) return st;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;

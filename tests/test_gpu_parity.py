@@ -379,6 +379,82 @@ def test_edge_cases_and_errors(nb):
     del torch
 
 
+def test_injected_allocation_failures(nb, monkeypatch):
+    """NBODY_INJECT_ALLOC_FAIL=k fails a context's k-th device allocation with
+    ENOMEM.  A failed init releases what it allocated; a failed set_tiles
+    keeps the previous tiles and tables (still a matching pair, results
+    unchanged); a failed first nbody_grad leaves the context able to run the
+    next one, with the gradient of an undisturbed context."""
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(1500, seed=9)
+    ref = _make(nb, s, "mixed")
+    ref.step(5)
+    want = ref.state.cpu().numpy()
+    gr = np.zeros((3, s.n))
+    gr[:, :40] = 1.0
+    want_g = [g.cpu().numpy() for g in ref.grad(3, gr)]
+    ref.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+
+    k = 1
+    while True:  # every allocation of init in turn
+        monkeypatch.setenv("NBODY_INJECT_ALLOC_FAIL", str(k))
+        try:
+            b = _make(nb, s, "mixed")
+        except nb.NBodyError as e:
+            assert e.status == nb.NBODY_ENOMEM and "injected" in str(e)
+            k += 1
+            assert k < 64
+            continue
+        break
+    b.close()
+    n_init = k - 1  # allocations init makes
+    assert n_init >= 5
+
+    new_tiles = {"threads": 512, "ipt": 2, "tj": 512, "jsplit": 0, "ctas_per_sm": 2}
+    for j in range(1, 7):  # each allocation of a table rebuild
+        monkeypatch.delenv("NBODY_INJECT_ALLOC_FAIL")
+        b = _make(nb, s, "mixed")
+        old = b.tiles
+        monkeypatch.setenv("NBODY_INJECT_ALLOC_FAIL", str(n_init + j))
+        with pytest.raises(nb.NBodyError) as ei:
+            b.tiles = new_tiles
+        assert ei.value.status == nb.NBODY_ENOMEM
+        assert b.tiles == old
+        b.step(5)
+        assert np.array_equal(b.state.cpu().numpy(), want)
+        b.close()
+
+    j, failed = 1, 0
+    while True:  # each allocation of the first nbody_grad
+        monkeypatch.delenv("NBODY_INJECT_ALLOC_FAIL", raising=False)
+        b = _make(nb, s, "mixed")
+        monkeypatch.setenv("NBODY_INJECT_ALLOC_FAIL", str(n_init + j))
+        try:
+            got = b.grad(3, gr)
+        except nb.NBodyError as e:
+            assert e.status == nb.NBODY_ENOMEM
+            failed += 1
+            monkeypatch.delenv("NBODY_INJECT_ALLOC_FAIL")
+            got = b.grad(3, gr)
+            for x, y in zip(got, want_g):
+                assert np.array_equal(x.cpu().numpy(), y)
+            b.close()
+            j += 1
+            assert j < 64
+            continue
+        for x, y in zip(got, want_g):
+            assert np.array_equal(x.cpu().numpy(), y)
+        b.close()
+        break
+    assert failed >= 8
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 16 << 20  # nothing leaked
+
+
 def test_nondefault_stream(nb):
     torch = pytest.importorskip("torch")
     s = inputs.solar_system(700, seed=5)
