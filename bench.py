@@ -506,20 +506,30 @@ def extras(torch, nbody, inputs, stream, device, args):
                        "ms_per_step": t / n_ens * 1e3, "precision": "mixed", "tiles": b.tiles}
     b.close()
     if args.sweep:
+        # Autotuned up to 65,536 bodies; larger N reuse the 65,536-body winner
+        # (tuning there would cost minutes).  FP64 at 1M bodies is one ~30 s step.
+        tuned = {}
         for n in (16384, 65536, 262144, 1048576):
             sn = inputs.solar_system(n)
             row = {}
             for prec in ("mixed", "fp64"):
-                if prec == "fp64" and n > 65536:
-                    continue  # ~30 s per step at 1M bodies
+                if prec == "fp64" and n == 262144:
+                    continue
                 with torch.cuda.stream(stream):
                     b = nbody.NBody(sn.r, sn.v, sn.m, G=sn.G, dt=sn.dt, precision=prec, device=device)
-                    k = 2 if n >= 262144 else 5
-                    b.step(1)
+                    if n <= 65536:
+                        tuned[prec] = b.autotune(probe_steps=4 if prec == "mixed" else 1)[0]
+                    else:
+                        b.tiles = tuned[prec]
+                        b.reset()
+                    k = 1 if prec == "fp64" and n > 65536 else 2 if n >= 262144 else 5
+                    if k > 1:
+                        b.step(1)  # warm-up (the FP64 1M step is long enough without one)
                     t = timed(torch, stream, lambda: b.step(k))
                 per = n * (n - 1) * k / t
                 row[prec] = {"interactions_per_s": per, "ms_per_step": t / k * 1e3,
-                             "roofline_frac": per * FLOPS_PER_INTERACTION * 1e-12 / PEAK_TFLOPS[prec]}
+                             "roofline_frac": per * FLOPS_PER_INTERACTION * 1e-12 / PEAK_TFLOPS[prec],
+                             "tiles": b.tiles}
                 b.close()
             out.setdefault("sweep", {})[str(n)] = row
     return out

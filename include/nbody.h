@@ -86,7 +86,8 @@ typedef struct {
  * schedule. */
 typedef struct {
   int32_t threads;     /* threads per CTA; (threads, ipt) pairs built: FP64 (64|128|256|512, 1),
-                        * (128|256, 2); mixed (128|256|512|1024, 1), (256|512, 2) */
+                        * (128|256, 2); mixed (128|256|512|1024, 1), (256|384|512|768, 2),
+                        * (128|256, 4) */
   int32_t ipt;         /* target bodies per thread */
   int32_t tj;          /* source bodies per shared-memory stage: multiple of 64, 64..2048 */
   int32_t jsplit;      /* dynamic chunks per CTA, 0..64 */

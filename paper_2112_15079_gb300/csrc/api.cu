@@ -831,22 +831,22 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   };
   std::vector<nbody_tiles> cand;
   const bool mixed = c->o.precision == NBODY_MIXED;
-  for (int th : {64, 128, 256, 512, 1024})
-    for (int ip : {1, 2})
+  for (int th : {64, 128, 256, 384, 512, 768, 1024})
+    for (int ip : {1, 2, 4})
       for (int tj : {512, 1024})
-        for (int cps : {1, 2, 3, 4})
-          for (int waves : {0, 1}) {
-            if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
-            if (!mixed && (tj != 1024 || waves != 0)) continue;  // FP64: bound by the FP64 pipe, tiling matters little
-            if (th * cps > 1024 || (mixed && th * cps < 512)) continue;
-            nbody_tiles t;
-            t.threads = th;
-            t.ipt = ip;
-            t.tj = tj;
-            t.ctas_per_sm = cps;
-            t.jsplit = waves;
-            cand.push_back(t);
-          }
+        for (int cps : {1, 2, 3, 4}) {
+          if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
+          if (!mixed && tj != 1024) continue;  // FP64: bound by the FP64 pipe, tiling matters little
+          // at most 1024 threads per SM; the mixed path wants >= 512 threads or >= 1024 targets per SM
+          if (th * cps > 1024 || (mixed && th * cps < 512 && th * cps * ip < 1024)) continue;
+          nbody_tiles t;
+          t.threads = th;
+          t.ipt = ip;
+          t.tj = tj;
+          t.ctas_per_sm = cps;
+          t.jsplit = 0;  // dynamic chunks measured slower on GB300 (more partial rows)
+          cand.push_back(t);
+        }
   cudaEvent_t e0, e1;
   NB_CUDA(c, cudaEventCreate(&e0));
   NB_CUDA(c, cudaEventCreate(&e1));

@@ -98,12 +98,13 @@ __device__ __forceinline__ void interact_pair(const ulonglong2 &v0, const ulongl
   az = fma2(f, dz, az);
 }
 
-// Register budget: the mixed kernel wants a full SM of warps (64 registers
-// at 1024 threads per SM for IPT 1, 80 for IPT 2 at 768); the FP64 kernel
+// Register budget: the mixed kernel wants many warps per SM (64 registers
+// at 1024 threads per SM for IPT 1, 85 for IPT 2 at 768, up to 255 for
+// IPT 4 at 256); the FP64 kernel
 // saturates GB300's narrow FP64 pipe with few warps and takes what it needs.
 template <int PREC, int THREADS, int IPT>
 struct MinBlocks {
-  static constexpr int raw = PREC == 1 ? ((IPT == 1 ? 1024 : IPT == 2 ? 768 : 512) / THREADS) : 1;
+  static constexpr int raw = PREC == 1 ? ((IPT == 1 ? 1024 : IPT == 2 ? 768 : 256) / THREADS) : 1;
   static constexpr int value = raw < 1 ? 1 : raw;
 };
 
@@ -140,6 +141,22 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     const Seg sg = a.segs[si];
     const Blk bk = a.blks[sg.blk];
     const int q_end = bk.q0 + (bk.i1 - bk.i0);  // stage indices of the block's targets: [q0, q_end)
+
+    // The first source tiles go out before the targets are loaded, so their
+    // copy overlaps the target loads.  The ring is free: every tile of the
+    // previous segment was consumed before the last __syncthreads.
+    const int ntiles = (sg.s1 - sg.s0 + tj - 1) / tj;
+    auto issue = [&](int t) {  // tid 0 only
+      const int s = t % kStages;
+      const int j = sg.s0 + t * tj;
+      const uint32_t bytes = static_cast<uint32_t>(min(tj, sg.s1 - j)) * 32u;
+      mbar_arrive_expect_tx(&bar[s], bytes);
+      bulk_g2s(stage_ptr(s), static_cast<const unsigned char *>(a.cur) + static_cast<size_t>(j) * 32, bytes,
+               &bar[s]);
+    };
+    if (tid == 0) {
+      for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
+    }
 
     // ---- targets into registers ---------------------------------------
     int pidx[IPT], tq[IPT];
@@ -196,19 +213,6 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     }
 
     // ---- source loop over [s0, s1) in tiles of tj ---------------------
-    const int ntiles = (sg.s1 - sg.s0 + tj - 1) / tj;
-    auto issue = [&](int t) {  // tid 0 only
-      const int s = t % kStages;
-      const int j = sg.s0 + t * tj;
-      const uint32_t bytes = static_cast<uint32_t>(min(tj, sg.s1 - j)) * 32u;
-      mbar_arrive_expect_tx(&bar[s], bytes);
-      bulk_g2s(stage_ptr(s), static_cast<const unsigned char *>(a.cur) + static_cast<size_t>(j) * 32, bytes,
-               &bar[s]);
-    };
-    if (tid == 0) {
-      for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
-    }
-
     for (int t = 0; t < ntiles; ++t) {
       const int s = t % kStages;
       if (!mbar_wait(&bar[s], (phase >> s) & 1u)) atomicOr(&s_flag, 1);

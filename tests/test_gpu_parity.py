@@ -68,7 +68,8 @@ def _t(threads, ipt, tj, jsplit, cps):
 TILES = {
     "fp64": [None, _t(64, 1, 64, 0, 1), _t(128, 2, 128, 2, 2), _t(256, 1, 192, 8, 3), _t(512, 1, 1024, 1, 1)],
     "mixed": [None, _t(128, 1, 64, 0, 1), _t(256, 2, 128, 2, 2), _t(512, 1, 192, 8, 2), _t(1024, 1, 2048, 1, 1),
-              _t(512, 2, 512, 3, 1)],
+              _t(512, 2, 512, 3, 1), _t(384, 2, 256, 0, 2), _t(768, 2, 1024, 0, 1), _t(128, 4, 512, 0, 2),
+              _t(256, 4, 64, 2, 1)],
 }
 CASES = [(p, t) for p in ("fp64", "mixed") for t in TILES[p]]
 
@@ -453,6 +454,29 @@ def test_injected_allocation_failures(nb, monkeypatch):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     assert abs(torch.cuda.mem_get_info()[0] - free0) <= 16 << 20  # nothing leaked
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_restores_state_and_keeps_parity(nb, precision):
+    """The autotuner times candidates on the bound state, puts the state back
+    bitwise, and its winner is a valid decomposition: parity with the oracle
+    and bitwise equal steps to a context given the same tiles."""
+    s = inputs.solar_system(2131, seed=17)
+    b = _make(nb, s, precision)
+    b.step(3)
+    before = b.state.cpu().numpy()
+    tiles, ms = b.autotune(probe_steps=2)
+    assert ms > 0 and b.tiles == tiles
+    assert np.array_equal(b.state.cpu().numpy(), before)
+    b.step(20)
+    c = _make(nb, s, precision)
+    c.step(3)
+    c.tiles = tiles  # same history: default tiles for 3 steps, then the winner's
+    c.step(20)
+    assert np.array_equal(c.state.cpu().numpy(), b.state.cpu().numpy())
+    d = _make(nb, s, precision, tiles)  # the winner's Eq. 1 against the oracle
+    _check_accel(precision, d.accel().cpu().numpy(), oracle.accel(s.G, s.r, s.m, openmp=True),
+                 oracle.term_norm(s.G, s.r, s.m, openmp=True))
 
 
 def test_nondefault_stream(nb):
