@@ -34,6 +34,7 @@ struct Work {
   double *partial = nullptr;
   int32_t *dyn_ctr = nullptr;  // [2] dynamic-chunk counter (self-resetting)
   int n_blks = 0, rows = 0, grid = 0, n_dyn = 0;
+  int occ = 0;  // CTAs of the kernel that fit on one SM
   size_t smem = 0;
 };
 
@@ -169,9 +170,10 @@ bool tiles_valid(const nbody_tiles &t, int precision) {
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
-  // Measured on GB300 at N = 10,425 and 65,536: FP64 is bound by the FP64 pipe
+  // Measured on GB300 from N = 16,384 to 1M: FP64 is bound by the FP64 pipe
   // (~90% busy) with three 128-thread CTAs per SM; the mixed path is best with
-  // two targets per thread and three 256-thread CTAs per SM.
+  // one 512-thread CTA per SM, two targets per thread (117 registers, so one
+  // CTA is all that fits: no co-resident CTAs for the scheduler to favour).
   nbody_tiles t{};
   t.jsplit = 0;  // static shares only (dynamic chunks add partial rows)
   t.tj = 1024;
@@ -181,8 +183,8 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
     t.ipt = 1;
     t.ctas_per_sm = 3;
   } else {
-    t.threads = 256;
-    t.ctas_per_sm = 3;
+    t.threads = 512;
+    t.ctas_per_sm = 1;
   }
   return t;
 }
@@ -273,6 +275,7 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   wk.n_blks = static_cast<int>(blks.size());
   wk.rows = rows;
   wk.grid = static_cast<int>(G);
+  wk.occ = occ;
   auto upload = [&]() -> nbody_status {
     nbody_status st;
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.blks), sizeof(nb::Blk) * blks.size())) != NBODY_OK) return st;
@@ -386,6 +389,7 @@ nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, const void *cur, void *
   a.flags = c->flags;
   a.N = c->N;
   a.mode = mode;
+  a.release_early = c->fw.occ == 1 ? 1 : 0;
   a.dt = c->o.dt;
   a.half_dt = 0.5 * c->o.dt;
   a.half_dt2 = 0.5 * c->o.dt * c->o.dt;
@@ -833,7 +837,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   const bool mixed = c->o.precision == NBODY_MIXED;
   for (int th : {64, 128, 256, 384, 512, 768, 1024})
     for (int ip : {1, 2, 4})
-      for (int tj : {512, 1024})
+      for (int tj : {128, 256, 512, 1024})
         for (int cps : {1, 2, 3, 4}) {
           if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
           if (!mixed && tj != 1024) continue;  // FP64: bound by the FP64 pipe, tiling matters little

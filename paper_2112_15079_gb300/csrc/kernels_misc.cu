@@ -67,6 +67,11 @@ __device__ __forceinline__ void pair_add(T &hi, T &lo, T vhi, T vlo) {
 
 template <int PREC>
 __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
+  // When at most one force CTA fits on an SM, the next force grid can only
+  // land one CTA per SM, however early it launches: let it launch now, so its
+  // launch overlaps this kernel (its own griddepcontrol.wait still waits for
+  // our completion).  Otherwise release only at the end (below).
+  if (a.release_early) grid_dependency_launch();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = gtid / kRowLanes, lane = gtid % kRowLanes;
   const bool live = p < a.N;
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     anz = static_cast<double>(sz) + static_cast<double>(ez);
   }
   if (!live || lane != 0) {
-    grid_dependency_launch();
+    if (!a.release_early) grid_dependency_launch();
     return;
   }
   if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
@@ -190,9 +195,11 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
   a.ax[p] = anx;
   a.ay[p] = any;
   a.az[p] = anz;
-  // Only now may the next force launch be placed: its CTAs then land on an
-  // idle GPU, one share per slot, as the equal-share decomposition assumes.
-  grid_dependency_launch();
+  // Otherwise only now may the next force launch be placed: its CTAs then
+  // land on an idle GPU, one share per slot, as the equal-share decomposition
+  // assumes (an early launch let several CTAs pile onto the SMs that freed
+  // first).
+  if (!a.release_early) grid_dependency_launch();
 }
 
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {

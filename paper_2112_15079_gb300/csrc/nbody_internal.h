@@ -79,6 +79,7 @@ struct VerletArgs {
   unsigned *flags;
   int32_t N;
   int32_t mode;
+  int32_t release_early;  // 1: the next force grid may launch at once (it fits one CTA per SM)
   double dt, half_dt, half_dt2;
 };
 
