@@ -1,4 +1,6 @@
 // Staging / pre-drift kernel, energy kernels, and the force-launch dispatcher.
+#include <type_traits>
+
 #include "nbody_dev.cuh"
 
 namespace nb {
@@ -44,19 +46,24 @@ size_t force_smem_bytes(int precision, int tj) {
 }
 
 // ---------------------------------------------------------------------------
-// Completes a step, kRowLanes threads per body p: a_new = sum of the body's force
-// partials (TwoSum: FP64 for the FP64 path, float pairs for the mixed path,
-// converted to FP64 once) in a fixed order; then, for kModeStep,
-//   Eq. 4  v_{i+1} = v_i + dt/2 (a_i + a_{i+1}),
-//   the caller's position receives r_{i+1} (the staged positions),
-//   Eq. 3  r_{i+2} = r_{i+1} + v_{i+1} dt + dt^2/2 a_{i+1} -> next stage.
-// All FP64 arithmetic of a step happens here, spread over every SM.
+// Completes a step for kVerletBodies consecutive bodies per CTA.
+//   Phase A (all threads, kRowLanes per body): a_new = the sum of the body's
+//   force partials in a fixed order.  Lane l takes rows l, l + kRowLanes, ...
+//   (TwoSum: FP64 pairs for the FP64 path, float pairs for the mixed path),
+//   then a fixed-shape shuffle tree combines the lanes, so the summation
+//   order never changes.
+//   Phase B (warp 0, one body per lane): for kModeStep,
+//     Eq. 4  v_{i+1} = v_i + dt/2 (a_i + a_{i+1}),
+//     the caller's position receives r_{i+1} (the staged positions),
+//     Eq. 3  r_{i+2} = r_{i+1} + v_{i+1} dt + dt^2/2 a_{i+1} -> next stage.
+// The FP64 pipe runs a warp instruction for all 32 lanes whatever the
+// active mask, so phase B keeps every lane busy with its own body; GB300's
+// FP64 rate (1/64 of FP32) makes that the difference between ~1.5 us and
+// ~6 us per step at N = 10k.
 // ---------------------------------------------------------------------------
-// Each body's partial rows are summed by kRowLanes neighbouring threads: lane
-// l takes rows l, l + kRowLanes, ... (TwoSum), then the lanes are combined
-// by a fixed-shape shuffle tree, so the summation order never changes.
 constexpr int kRowLanes = 8;
-constexpr int kVerletBlock = 256;  // 32 bodies per CTA
+constexpr int kVerletBlock = 256;
+constexpr int kVerletBodies = kVerletBlock / kRowLanes;  // 32: one per lane of warp 0
 
 // (hi, lo) pair sums: FP64 pairs for the FP64 path, float pairs for mixed.
 template <typename T>
@@ -72,95 +79,95 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
   // launch overlaps this kernel (its own griddepcontrol.wait still waits for
   // our completion).  Otherwise release only at the end (below).
   if (a.release_early) grid_dependency_launch();
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = gtid / kRowLanes, lane = gtid % kRowLanes;
+  typedef typename std::conditional<PREC == 0, double, float>::type T;
+  __shared__ T s_hi[3][kVerletBodies], s_lo[3][kVerletBodies];
+  const int p0 = blockIdx.x * kVerletBodies;
+  const int b = threadIdx.x / kRowLanes, lane = threadIdx.x % kRowLanes;
+  const int p = p0 + b;  // phase A body
   const bool live = p < a.N;
-  const int pp = live ? p : 0;
   const size_t N = static_cast<size_t>(a.N);
+  const int warp = threadIdx.x >> 5;
+  const int q = p0 + (threadIdx.x & 31);  // phase B body (warp 0)
+  const bool own = warp == 0 && q < a.N;
+  const bool step = a.mode == kModeStep;
+
   // Before the wait: everything this step's force kernel does not write (it
   // writes only the partial rows), so these loads overlap its tail.
-  const int rows = a.nsl[pp];
-  const bool step = a.mode == kModeStep;
+  const int rows = live ? a.nsl[p] : 0;
   double vx = 0.0, vy = 0.0, vz = 0.0, aox = 0.0, aoy = 0.0, aoz = 0.0, rx = 0.0, ry = 0.0, rz = 0.0, mu = 0.0;
   float muf = 0.f;
   size_t o = 0;
-  if (step && lane == 0) {
-    vx = a.vx[pp];
-    vy = a.vy[pp];
-    vz = a.vz[pp];
-    aox = a.ax[pp];
-    aoy = a.ay[pp];
-    aoz = a.az[pp];
+  if (own && step) {
+    vx = a.vx[q];
+    vy = a.vy[q];
+    vz = a.vz[q];
+    aox = a.ax[q];
+    aoy = a.ay[q];
+    aoz = a.az[q];
     if (PREC == 0) {
-      const double4_32a r = static_cast<const double4_32a *>(a.cur)[pp];
+      const double4_32a r = static_cast<const double4_32a *>(a.cur)[q];
       rx = r.x;
       ry = r.y;
       rz = r.z;
       mu = r.w;
     } else {
-      rx = a.Rx[pp];
-      ry = a.Ry[pp];
-      rz = a.Rz[pp];
-      o = pair_off(a.qidx[pp]);
+      rx = a.Rx[q];
+      ry = a.Ry[q];
+      rz = a.Rz[q];
+      o = pair_off(a.qidx[q]);
       muf = static_cast<const float *>(a.cur)[o + kMu];
     }
   }
   grid_dependency_wait();  // the force partials of this step are complete
-  double anx, any, anz;
+
+  // ---- phase A: the partial rows of body p --------------------------------
+  T sx = 0, sy = 0, sz = 0, ex = 0, ey = 0, ez = 0;
   if (PREC == 0) {
-    double sx = 0.0, sy = 0.0, sz = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    if (live) {
-      for (int c = lane; c < rows; c += kRowLanes) {
-        const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
-        two_sum_acc(sx, ex, __ldg(row + p));
-        two_sum_acc(sy, ey, __ldg(row + N + p));
-        two_sum_acc(sz, ez, __ldg(row + 2 * N + p));
-      }
+    for (int c = lane; c < rows; c += kRowLanes) {
+      const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
+      two_sum_acc(sx, ex, static_cast<T>(__ldg(row + p)));
+      two_sum_acc(sy, ey, static_cast<T>(__ldg(row + N + p)));
+      two_sum_acc(sz, ez, static_cast<T>(__ldg(row + 2 * N + p)));
     }
-#pragma unroll
-    for (int off = 1; off < kRowLanes; off <<= 1) {
-      const double hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
-      const double hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
-      const double hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
-      if ((lane & (2 * off - 1)) == 0) {
-        pair_add(sx, ex, hx, lx);
-        pair_add(sy, ey, hy, ly);
-        pair_add(sz, ez, hz, lz);
-      }
-    }
-    anx = sx + ex;
-    any = sy + ey;
-    anz = sz + ez;
   } else {
-    float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-    if (live) {
-      for (int c = lane; c < rows; c += kRowLanes) {
-        const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
-        const float2 vx2 = __ldg(row + p), vy2 = __ldg(row + N + p), vz2 = __ldg(row + 2 * N + p);
-        pair_add(sx, ex, vx2.x, vx2.y);
-        pair_add(sy, ey, vy2.x, vy2.y);
-        pair_add(sz, ez, vz2.x, vz2.y);
-      }
+    for (int c = lane; c < rows; c += kRowLanes) {
+      const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
+      const float2 vx2 = __ldg(row + p), vy2 = __ldg(row + N + p), vz2 = __ldg(row + 2 * N + p);
+      pair_add<T>(sx, ex, vx2.x, vx2.y);
+      pair_add<T>(sy, ey, vy2.x, vy2.y);
+      pair_add<T>(sz, ez, vz2.x, vz2.y);
     }
-#pragma unroll
-    for (int off = 1; off < kRowLanes; off <<= 1) {
-      const float hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
-      const float hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
-      const float hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
-      if ((lane & (2 * off - 1)) == 0) {
-        pair_add(sx, ex, hx, lx);
-        pair_add(sy, ey, hy, ly);
-        pair_add(sz, ez, hz, lz);
-      }
-    }
-    anx = static_cast<double>(sx) + static_cast<double>(ex);
-    any = static_cast<double>(sy) + static_cast<double>(ey);
-    anz = static_cast<double>(sz) + static_cast<double>(ez);
   }
-  if (!live || lane != 0) {
+#pragma unroll
+  for (int off = 1; off < kRowLanes; off <<= 1) {
+    const T hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
+    const T hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
+    const T hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
+    if ((lane & (2 * off - 1)) == 0) {
+      pair_add<T>(sx, ex, hx, lx);
+      pair_add<T>(sy, ey, hy, ly);
+      pair_add<T>(sz, ez, hz, lz);
+    }
+  }
+  if (lane == 0) {
+    s_hi[0][b] = sx;
+    s_lo[0][b] = ex;
+    s_hi[1][b] = sy;
+    s_lo[1][b] = ey;
+    s_hi[2][b] = sz;
+    s_lo[2][b] = ez;
+  }
+  __syncthreads();
+  if (!own) {
     if (!a.release_early) grid_dependency_launch();
     return;
   }
+
+  // ---- phase B: Eqs. 4 and 3 for body q, one body per lane ------------------
+  const int k = threadIdx.x;
+  const double anx = static_cast<double>(s_hi[0][k]) + static_cast<double>(s_lo[0][k]);
+  const double any = static_cast<double>(s_hi[1][k]) + static_cast<double>(s_lo[1][k]);
+  const double anz = static_cast<double>(s_hi[2][k]) + static_cast<double>(s_lo[2][k]);
   if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
   if (step) {
     vx = kick(vx, aox, anx, a.half_dt);
@@ -170,11 +177,11 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
     const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
     if (PREC == 0) {
-      static_cast<double4_32a *>(a.nxt)[p] = make_double4_32a(nx, ny, nz, mu);
+      static_cast<double4_32a *>(a.nxt)[q] = make_double4_32a(nx, ny, nz, mu);
     } else {
-      a.Rx[p] = nx;
-      a.Ry[p] = ny;
-      a.Rz[p] = nz;
+      a.Rx[q] = nx;
+      a.Ry[q] = ny;
+      a.Rz[q] = nz;
       float *w = static_cast<float *>(a.nxt) + o;
       const float hxn = hi_part(nx), hyn = hi_part(ny), hzn = hi_part(nz);
       w[kXh] = hxn;
@@ -185,16 +192,16 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
       w[kYl] = lo_part(ny, hyn);
       w[kZl] = lo_part(nz, hzn);
     }
-    a.x[p] = rx;
-    a.y[p] = ry;
-    a.z[p] = rz;
-    a.vx[p] = vx;
-    a.vy[p] = vy;
-    a.vz[p] = vz;
+    a.x[q] = rx;
+    a.y[q] = ry;
+    a.z[q] = rz;
+    a.vx[q] = vx;
+    a.vy[q] = vy;
+    a.vz[q] = vz;
   }
-  a.ax[p] = anx;
-  a.ay[p] = any;
-  a.az[p] = anz;
+  a.ax[q] = anx;
+  a.ay[q] = any;
+  a.az[q] = anz;
   // Otherwise only now may the next force launch be placed: its CTAs then
   // land on an idle GPU, one share per slot, as the equal-share decomposition
   // assumes (an early launch let several CTAs pile onto the SMs that freed
@@ -205,8 +212,7 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {
   if (a.N <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  const int64_t threads = static_cast<int64_t>(a.N) * kRowLanes;
-  cfg.gridDim = dim3(static_cast<unsigned>((threads + kVerletBlock - 1) / kVerletBlock));
+  cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + kVerletBodies - 1) / kVerletBodies));
   cfg.blockDim = dim3(kVerletBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
