@@ -265,6 +265,31 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
           bool need_mask = false;
 #pragma unroll
           for (int k = 0; k < IPT; ++k) need_mask |= mlo[k] < P0 + lim && mhi[k] >= P0;
+          // Pairs [b0, b1) of the group: unmasked, or with the self test.
+          // Both visit the pairs in ascending order and give the same terms
+          // for non-self pairs, so the split does not change the sum.
+          auto unmasked = [&](int b0, int b1) {
+#pragma unroll 4
+            for (int b = b0; b < b1; ++b) {
+              const ulonglong2 *pb = src + 4 * (g0 + b);
+              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
+#pragma unroll
+              for (int k = 0; k < IPT; ++k)
+                interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
+                                     pax[k], pay[k], paz[k]);
+            }
+          };
+          auto masked = [&](int b0, int b1) {
+            for (int b = b0; b < b1; ++b) {
+              const ulonglong2 *pb = src + 4 * (g0 + b);
+              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
+              const int P = P0 + b;
+#pragma unroll
+              for (int k = 0; k < IPT; ++k)
+                interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], 2 * P == tq[k],
+                                    2 * P + 1 == tq[k], pax[k], pay[k], paz[k]);
+            }
+          };
           if (!need_mask && lim == kFoldPairs) {
 #pragma unroll 4
             for (int b = 0; b < kFoldPairs; ++b) {
@@ -276,25 +301,19 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
                                      pax[k], pay[k], paz[k]);
             }
           } else {
-            for (int b = 0; b < lim; ++b) {
-              const ulonglong2 *pb = src + 4 * (g0 + b);
-              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
-              const int P = P0 + b;
-              bool in_mask = false;  // warp-uniform
+            // Only the pairs that may hold one of this warp's own targets
+            // (per k an ascending, warp-uniform range) take the self test.
+            int cur = 0;
 #pragma unroll
-              for (int k = 0; k < IPT; ++k) in_mask |= P >= mlo[k] && P <= mhi[k];
-              if (!in_mask) {
-#pragma unroll
-                for (int k = 0; k < IPT; ++k)
-                  interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
-                                       pax[k], pay[k], paz[k]);
-              } else {
-#pragma unroll
-                for (int k = 0; k < IPT; ++k)
-                  interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k],
-                                      2 * P == tq[k], 2 * P + 1 == tq[k], pax[k], pay[k], paz[k]);
+            for (int k = 0; k < IPT; ++k) {
+              const int r0 = max(mlo[k] - P0, cur), r1 = min(mhi[k] - P0 + 1, lim);
+              if (r0 < r1) {
+                unmasked(cur, r0);
+                masked(r0, r1);
+                cur = r1;
               }
             }
+            unmasked(cur, lim);
           }
 #pragma unroll
           for (int k = 0; k < IPT; ++k) {  // fold the packed sub-sums into the float pairs
