@@ -316,7 +316,7 @@ def run_ours(args):
                 b.tiles = json.loads(forced)
                 b.reset()
             elif not args.no_autotune:
-                b.autotune(probe_steps=8 if prec == "mixed" else 2)
+                b.autotune(probe_steps=16 if prec == "mixed" else 2)
             tiles[prec] = b.tiles
             for _ in range(args.warmup):
                 b.step(inner)

@@ -862,7 +862,9 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   double win_ms = 1e300;
   for (const nbody_tiles &t : cand) {
     if ((st = build_items(c, t)) != NBODY_OK) break;
-    if ((st = nbody_step(c, 1)) != NBODY_OK) break;  // warm-up (also builds the graph)
+    // Warm-up with the timed step count, so the timed call replays a cached
+    // graph instead of capturing one while the GPU waits.
+    if ((st = nbody_step(c, probe_steps)) != NBODY_OK) break;
     cudaEventRecord(e0, c->stream);
     if ((st = nbody_step(c, probe_steps)) != NBODY_OK) break;
     cudaEventRecord(e1, c->stream);
