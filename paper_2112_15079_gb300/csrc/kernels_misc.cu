@@ -46,24 +46,30 @@ size_t force_smem_bytes(int precision, int tj) {
 }
 
 // ---------------------------------------------------------------------------
-// Completes a step for kVerletBodies consecutive bodies per CTA.
-//   Phase A (all threads, kRowLanes per body): a_new = the sum of the body's
-//   force partials in a fixed order.  Lane l takes rows l, l + kRowLanes, ...
-//   (TwoSum: FP64 pairs for the FP64 path, float pairs for the mixed path),
-//   then a fixed-shape shuffle tree combines the lanes, so the summation
-//   order never changes.
-//   Phase B (warp 0, one body per lane): for kModeStep,
+// Completes a step for VerletShape<PREC>::kBodies consecutive bodies per CTA.
+//   Phase A (kLanes threads per body): a_new = the sum of the body's force
+//   partials in a fixed order.  Lane l takes rows l, l + kLanes, ... (TwoSum:
+//   FP64 pairs for the FP64 path, float pairs for the mixed path), its loads
+//   issued kUnroll rows at a time; for kLanes > 1 a fixed-shape shuffle tree
+//   then combines the lanes, so the summation order never changes.
+//   Phase B (one body per thread): for kModeStep,
 //     Eq. 4  v_{i+1} = v_i + dt/2 (a_i + a_{i+1}),
 //     the caller's position receives r_{i+1} (the staged positions),
 //     Eq. 3  r_{i+2} = r_{i+1} + v_{i+1} dt + dt^2/2 a_{i+1} -> next stage.
-// The FP64 pipe runs a warp instruction for all 32 lanes whatever the
-// active mask, so phase B keeps every lane busy with its own body; GB300's
-// FP64 rate (1/64 of FP32) makes that the difference between ~1.5 us and
-// ~6 us per step at N = 10k.
+// GB300 runs FP64 at 1/64 of the FP32 rate and charges a warp instruction
+// for all 32 lanes whatever the active mask, so FP64 work runs one body per
+// lane: the mixed path sums its float-pair rows 8 lanes per body (short
+// latency) and hands the sums to warp 0 for phase B; the FP64 path, whose
+// row sums are FP64 themselves, sums one body per lane.
 // ---------------------------------------------------------------------------
-constexpr int kRowLanes = 8;
 constexpr int kVerletBlock = 256;
-constexpr int kVerletBodies = kVerletBlock / kRowLanes;  // 32: one per lane of warp 0
+
+template <int PREC>
+struct VerletShape {
+  static constexpr int kLanes = PREC == 0 ? 1 : 8;   // threads per body in phase A
+  static constexpr int kUnroll = PREC == 0 ? 8 : 4;  // rows per lane whose loads go out together
+  static constexpr int kBodies = kVerletBlock / kLanes;
+};
 
 // (hi, lo) pair sums: FP64 pairs for the FP64 path, float pairs for mixed.
 template <typename T>
@@ -80,15 +86,17 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
   // our completion).  Otherwise release only at the end (below).
   if (a.release_early) grid_dependency_launch();
   typedef typename std::conditional<PREC == 0, double, float>::type T;
-  __shared__ T s_hi[3][kVerletBodies], s_lo[3][kVerletBodies];
-  const int p0 = blockIdx.x * kVerletBodies;
-  const int b = threadIdx.x / kRowLanes, lane = threadIdx.x % kRowLanes;
+  typedef typename std::conditional<PREC == 0, double, float2>::type E;  // one partial-row entry
+  constexpr int L = VerletShape<PREC>::kLanes, U = VerletShape<PREC>::kUnroll;
+  constexpr int NB = VerletShape<PREC>::kBodies;
+  __shared__ T s_hi[3][NB], s_lo[3][NB];
+  const int p0 = blockIdx.x * NB;
+  const int b = threadIdx.x / L, lane = threadIdx.x % L;
   const int p = p0 + b;  // phase A body
   const bool live = p < a.N;
   const size_t N = static_cast<size_t>(a.N);
-  const int warp = threadIdx.x >> 5;
-  const int q = p0 + (threadIdx.x & 31);  // phase B body (warp 0)
-  const bool own = warp == 0 && q < a.N;
+  const int q = p0 + threadIdx.x;  // phase B body
+  const bool own = threadIdx.x < NB && q < a.N;
   const bool step = a.mode == kModeStep;
 
   // Before the wait: everything this step's force kernel does not write (it
@@ -122,31 +130,46 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
 
   // ---- phase A: the partial rows of body p --------------------------------
   T sx = 0, sy = 0, sz = 0, ex = 0, ey = 0, ez = 0;
-  if (PREC == 0) {
-    for (int c = lane; c < rows; c += kRowLanes) {
-      const double *row = a.partial + static_cast<size_t>(c) * 3 * N;
-      two_sum_acc(sx, ex, static_cast<T>(__ldg(row + p)));
-      two_sum_acc(sy, ey, static_cast<T>(__ldg(row + N + p)));
-      two_sum_acc(sz, ez, static_cast<T>(__ldg(row + 2 * N + p)));
+  const E *part = reinterpret_cast<const E *>(a.partial);  // row c of body p: part[c*3N + k*N + p]
+  auto add = [&](T &s, T &e, const E &v) {
+    if constexpr (PREC == 0) {
+      two_sum_acc(s, e, v);
+    } else {
+      pair_add<T>(s, e, v.x, v.y);
     }
-  } else {
-    for (int c = lane; c < rows; c += kRowLanes) {
-      const float2 *row = reinterpret_cast<const float2 *>(a.partial + static_cast<size_t>(c) * 3 * N);
-      const float2 vx2 = __ldg(row + p), vy2 = __ldg(row + N + p), vz2 = __ldg(row + 2 * N + p);
-      pair_add<T>(sx, ex, vx2.x, vx2.y);
-      pair_add<T>(sy, ey, vy2.x, vy2.y);
-      pair_add<T>(sz, ez, vz2.x, vz2.y);
+  };
+  for (int c0 = lane; c0 < rows; c0 += U * L) {
+    E vx_[U], vy_[U], vz_[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {  // all loads first, then the sums in row order
+      const int c = c0 + u * L;
+      if (c < rows) {
+        const E *row = part + static_cast<size_t>(c) * 3 * N;
+        vx_[u] = __ldg(row + p);
+        vy_[u] = __ldg(row + N + p);
+        vz_[u] = __ldg(row + 2 * N + p);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c0 + u * L < rows) {
+        add(sx, ex, vx_[u]);
+        add(sy, ey, vy_[u]);
+        add(sz, ez, vz_[u]);
+      }
     }
   }
+  if constexpr (L > 1) {
 #pragma unroll
-  for (int off = 1; off < kRowLanes; off <<= 1) {
-    const T hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
-    const T hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
-    const T hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
-    if ((lane & (2 * off - 1)) == 0) {
-      pair_add<T>(sx, ex, hx, lx);
-      pair_add<T>(sy, ey, hy, ly);
-      pair_add<T>(sz, ez, hz, lz);
+    for (int off = 1; off < L; off <<= 1) {
+      const T hx = __shfl_down_sync(0xffffffffu, sx, off), lx = __shfl_down_sync(0xffffffffu, ex, off);
+      const T hy = __shfl_down_sync(0xffffffffu, sy, off), ly = __shfl_down_sync(0xffffffffu, ey, off);
+      const T hz = __shfl_down_sync(0xffffffffu, sz, off), lz = __shfl_down_sync(0xffffffffu, ez, off);
+      if ((lane & (2 * off - 1)) == 0) {
+        pair_add<T>(sx, ex, hx, lx);
+        pair_add<T>(sy, ey, hy, ly);
+        pair_add<T>(sz, ez, hz, lz);
+      }
     }
   }
   if (lane == 0) {
@@ -163,7 +186,7 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     return;
   }
 
-  // ---- phase B: Eqs. 4 and 3 for body q, one body per lane ------------------
+  // ---- phase B: Eqs. 4 and 3 for body q, one body per thread ----------------
   const int k = threadIdx.x;
   const double anx = static_cast<double>(s_hi[0][k]) + static_cast<double>(s_lo[0][k]);
   const double any = static_cast<double>(s_hi[1][k]) + static_cast<double>(s_lo[1][k]);
@@ -212,7 +235,8 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {
   if (a.N <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + kVerletBodies - 1) / kVerletBodies));
+  const int64_t nb = precision == 0 ? VerletShape<0>::kBodies : VerletShape<1>::kBodies;
+  cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + nb - 1) / nb));
   cfg.blockDim = dim3(kVerletBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
