@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=100)
     ap.add_argument("--ensemble-systems", type=int, default=256)
     ap.add_argument("--sweep", action="store_true", help="also time N = 16,384 / 65,536 / 262,144 / 1,048,576")
+    ap.add_argument("--dt-sweep", action="store_true",
+                    help="also report the maximum energy drift against dt (FP64 and mixed, no moons)")
     return ap.parse_args()
 
 
@@ -507,6 +509,31 @@ def extras(torch, nbody, inputs, stream, device, args):
                        "interactions_per_s": pairs * n_ens / t, "verlet_steps_per_s": n_ens / t,
                        "ms_per_step": t / n_ens * 1e3, "precision": "mixed", "tiles": b.tiles}
     b.close()
+    if args.dt_sweep:
+        # Energy accuracy against dt (Section 4's criterion): the 10,425-body
+        # construction without moons (their periods fall below dt), 73 days,
+        # maximum |E - E0|/|E0| over 20 samples per run.
+        sd = inputs.solar_system(args.n, n_moons=0)
+        rows = []
+        for dt in (0.8, 0.4, 0.2, 0.1, 0.05):
+            row = {"dt_day": dt}
+            n_steps = int(round(73.0 / dt))
+            every = max(1, n_steps // 20)
+            for prec in ("fp64", "mixed"):
+                with torch.cuda.stream(stream):
+                    b = nbody.NBody(sd.r, sd.v, sd.m, G=sd.G, dt=dt, precision=prec, device=device)
+                    e0 = b.energy()[0]
+                    worst = 0.0
+                    for _ in range(n_steps // every):
+                        b.step(every)
+                        worst = max(worst, abs(b.energy()[0] - e0) / abs(e0))
+                    b.close()
+                row[prec] = worst
+            rows.append(row)
+        for a, b2 in zip(rows, rows[1:]):
+            b2["fp64_order"] = float(np.log2(a["fp64"] / b2["fp64"]))
+            b2["mixed_order"] = float(np.log2(a["mixed"] / b2["mixed"]))
+        out["dt_sweep"] = {"bodies": sd.n, "days": 73.0, "max_rel_energy_drift": rows}
     if args.sweep:
         # Autotuned up to 65,536 bodies; larger N reuse the 65,536-body winner
         # (tuning there would cost minutes).  FP64 at 1M bodies is one ~30 s step.

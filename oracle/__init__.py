@@ -76,6 +76,8 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
             lib.oracle_verlet.argtypes = ([_I64, ctypes.c_double, ctypes.c_double, _I64]
                                           + [_D] * 10)
             lib.oracle_verlet.restype = ctypes.c_int
+            lib.oracle_rk4.argtypes = lib.oracle_verlet.argtypes
+            lib.oracle_rk4.restype = ctypes.c_int
             lib.oracle_energy.argtypes = [_I64, ctypes.c_double] + [_D] * 9
             lib.oracle_energy.restype = None
             lib.oracle_vjp.argtypes = [_I64, ctypes.c_double] + [_D] * 11
@@ -156,6 +158,23 @@ def verlet(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: n
                                     _c(m), _c(a[0]), _c(a[1]), _c(a[2]))
     if rc != 0:
         raise MemoryError("oracle_verlet: allocation failed")
+    return r, v, a
+
+
+def rk4(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: np.ndarray,
+        openmp: bool = False):
+    """Classical fourth-order Runge-Kutta (the higher-order method Section 2
+    names) on y = (r, v), y' = (v, A(r)), for n_steps from (r, v) [3, n];
+    returns (r, v, a) after the steps, a = Eq. 1 at the final positions."""
+    r = _f64(r).copy()
+    v = _f64(v).copy()
+    m = _f64(m)
+    a = np.zeros_like(r)
+    rc = _lib(openmp).oracle_rk4(m.shape[0], G, dt, int(n_steps),
+                                 _c(r[0]), _c(r[1]), _c(r[2]), _c(v[0]), _c(v[1]), _c(v[2]),
+                                 _c(m), _c(a[0]), _c(a[1]), _c(a[2]))
+    if rc != 0:
+        raise MemoryError("oracle_rk4: allocation failed")
     return r, v, a
 
 

@@ -146,6 +146,61 @@ int oracle_verlet(int64_t n, double G, double dt, int64_t n_steps, double *x,
   return 0;
 }
 
+/* The fourth-order Runge-Kutta method that Section 2 names as the
+ * higher-order alternative to Verlet, applied to the first-order system
+ * y = (r, v), y' = f(y) = (v, A(r)) with A = Eq. 1, n_steps steps of dt:
+ *   k1 = f(y),  k2 = f(y + dt/2 k1),  k3 = f(y + dt/2 k2),  k4 = f(y + dt k3),
+ *   y <- y + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ * Four evaluations of Eq. 1 per step.  On return (ax, ay, az) = A(r) at the
+ * final positions.  Returns 0, or -1 if scratch could not be allocated. */
+int oracle_rk4(int64_t n, double G, double dt, int64_t n_steps, double *x,
+               double *y, double *z, double *vx, double *vy, double *vz,
+               const double *m, double *ax, double *ay, double *az) {
+  /* scratch: stage position (3n), stage velocity (3n), stage acceleration
+   * (3n), and the weighted sums of the stage derivatives for r and v (6n) */
+  const size_t n3 = (size_t)(3 * n > 0 ? 3 * n : 1);
+  double *buf = (double *)malloc(sizeof(double) * 5 * n3);
+  if (!buf) return -1;
+  double *sr = buf, *sv = buf + n3, *sa = buf + 2 * n3, *dr = buf + 3 * n3,
+         *dv = buf + 4 * n3;
+  double *r[3] = {x, y, z}, *v[3] = {vx, vy, vz};
+  const double c_stage[4] = {0.0, 0.5, 0.5, 1.0}; /* where k_s is taken */
+  const double w_stage[4] = {1.0, 2.0, 2.0, 1.0}; /* its weight (/6) */
+  for (int64_t step = 0; step < n_steps; step++) {
+    for (size_t i = 0; i < 3 * (size_t)n; i++) dr[i] = dv[i] = 0.0;
+    for (int s = 0; s < 4; s++) {
+      /* stage state y + c_s dt k_{s-1}, with k_{s-1} = (sv, sa) */
+      for (int k = 0; k < 3; k++)
+        for (int64_t p = 0; p < n; p++) {
+          const size_t i = (size_t)k * n + p;
+          if (s == 0) {
+            sr[i] = r[k][p];
+            sv[i] = v[k][p];
+          } else {
+            const double kr = sv[i], kv = sa[i];
+            sr[i] = r[k][p] + c_stage[s] * dt * kr;
+            sv[i] = v[k][p] + c_stage[s] * dt * kv;
+          }
+        }
+      oracle_accel(n, G, sr, sr + n, sr + 2 * n, m, sa, sa + n, sa + 2 * n);
+      /* k_s = (sv, sa) */
+      for (size_t i = 0; i < 3 * (size_t)n; i++) {
+        dr[i] += w_stage[s] * sv[i];
+        dv[i] += w_stage[s] * sa[i];
+      }
+    }
+    for (int k = 0; k < 3; k++)
+      for (int64_t p = 0; p < n; p++) {
+        const size_t i = (size_t)k * n + p;
+        r[k][p] = r[k][p] + dt / 6.0 * dr[i];
+        v[k][p] = v[k][p] + dt / 6.0 * dv[i];
+      }
+  }
+  oracle_accel(n, G, x, y, z, m, ax, ay, az);
+  free(buf);
+  return 0;
+}
+
 /* Total energy, the accuracy criterion of Section 2 and Section 4:
  *   E_kin = sum_p (1/2) m_p |v_p|^2
  *   E_pot = - sum_{p < j} G m_p m_j / |r_j - r_p|

@@ -426,3 +426,68 @@ def test_grad_openmp_identical():
     b = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+# ---------------------------------------------------------------------------
+# Fourth-order Runge-Kutta (the higher-order method Section 2 names)
+# ---------------------------------------------------------------------------
+def test_rk4_circular_orbit_fourth_order():
+    """Circular two-body orbit: after exactly one period (dt = P/n) the exact
+    state is the initial one; RK4's return error falls as dt^4 (16x per
+    halving), where a wrong stage weight or stage point drops the order."""
+    G, a = 2.9591220828e-4, 1.0
+    r, v, m = _two_body(1.0, 1e-3, a, 0.0, G)
+    P = 2 * math.pi * math.sqrt(a**3 / (G * m.sum()))
+    errs = []
+    for n in (80, 160, 320):
+        rr, vv, _ = oracle.rk4(G, P / n, n, r, v, m)
+        errs.append(np.abs(rr - r).max() / a)
+    assert errs[-1] < 1e-7
+    for e1, e2 in zip(errs, errs[1:]):  # -> 16 as dt -> 0 (third order: 8, fifth: 32)
+        assert 12.0 < e1 / e2 < 22.0, errs
+
+
+def test_rk4_eccentric_energy_error_fourth_order():
+    """Eccentric orbit (e = 0.5): the largest energy error over one period
+    shrinks as dt^4."""
+    G, a, e = 2.9591220828e-4, 1.0, 0.5
+    r, v, m = _two_body(1.0, 1e-3, a, e, G)
+    P = 2 * math.pi * math.sqrt(a**3 / (G * m.sum()))
+    E0 = sum(oracle.energy(G, r, v, m))
+    errs = []
+    for n in (200, 400, 800):
+        rr, vv = r, v
+        worst = 0.0
+        for _ in range(n):
+            rr, vv, _ = oracle.rk4(G, P / n, 1, rr, vv, m)
+            worst = max(worst, abs(sum(oracle.energy(G, rr, vv, m)) - E0) / abs(E0))
+        errs.append(worst)
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 12.0 < e1 / e2 < 20.0, errs
+
+
+def test_rk4_conserves_linear_momentum():
+    """Runge-Kutta methods keep linear invariants, and Eq. 1 is antisymmetric
+    (sum_p m_p a_p = 0), so sum_p m_p v_p stays at its initial value to
+    roundoff."""
+    s = inputs.solar_system(31, seed=23)
+    P0 = (s.m * s.v).sum(axis=1)
+    scale = np.abs(s.m * s.v).sum()
+    _, vv, _ = oracle.rk4(s.G, s.dt, 300, s.r, s.v, s.m)
+    assert np.abs((s.m * vv).sum(axis=1) - P0).max() <= 1e-13 * scale
+
+
+def test_rk4_and_verlet_converge_to_the_same_trajectory():
+    """Both methods approximate the same solution: their difference after a
+    fixed time is dominated by Verlet's O(dt^2) error (4x per halving), which
+    ties the RK4 oracle to the separately pinned Verlet oracle."""
+    s = inputs.solar_system(31, seed=24)
+    T = 40.0
+    diffs = []
+    for dt in (0.4, 0.2, 0.1):
+        n = int(round(T / dt))
+        r_rk, _, _ = oracle.rk4(s.G, dt, n, s.r, s.v, s.m)
+        r_vv, _, _ = oracle.verlet(s.G, dt, n, s.r, s.v, s.m)
+        diffs.append(np.abs(r_rk - r_vv).max())
+    for d1, d2 in zip(diffs, diffs[1:]):
+        assert 3.0 < d1 / d2 < 5.0, diffs
