@@ -496,6 +496,16 @@ def extras(torch, nbody, inputs, stream, device, args):
                                "general_path_verlet_steps_per_s": 3650 / t2}
     b.close()
     b2.close()
+    # RK4 (Section 2's higher-order method): four Eq. 1 evaluations per step
+    for prec, k in (("mixed", 50), ("fp64", 5)):
+        with torch.cuda.stream(stream):
+            b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, integrator="rk4", device=device)
+            b.step(k)
+            t = timed(torch, stream, lambda: b.step(k))
+        out.setdefault("rk4", {})[prec] = {"steps": k, "ms_per_step": t / k * 1e3,
+                                           "interactions_per_s": 4 * s.n * (s.n - 1) * k / t,
+                                           "force_evaluations_per_step": 4}
+        b.close()
     # uneven ensemble, mixed, one context
     ens = inputs.ensemble(args.ensemble_systems)
     off, r, v, m = inputs.concat(ens)
@@ -519,20 +529,21 @@ def extras(torch, nbody, inputs, stream, device, args):
             row = {"dt_day": dt}
             n_steps = int(round(73.0 / dt))
             every = max(1, n_steps // 20)
-            for prec in ("fp64", "mixed"):
+            for prec, integ in (("fp64", "verlet"), ("mixed", "verlet"), ("fp64", "rk4"), ("mixed", "rk4")):
                 with torch.cuda.stream(stream):
-                    b = nbody.NBody(sd.r, sd.v, sd.m, G=sd.G, dt=dt, precision=prec, device=device)
+                    b = nbody.NBody(sd.r, sd.v, sd.m, G=sd.G, dt=dt, precision=prec, integrator=integ,
+                                    device=device)
                     e0 = b.energy()[0]
                     worst = 0.0
                     for _ in range(n_steps // every):
                         b.step(every)
                         worst = max(worst, abs(b.energy()[0] - e0) / abs(e0))
                     b.close()
-                row[prec] = worst
+                row[prec if integ == "verlet" else prec + "_rk4"] = worst
             rows.append(row)
         for a, b2 in zip(rows, rows[1:]):
-            b2["fp64_order"] = float(np.log2(a["fp64"] / b2["fp64"]))
-            b2["mixed_order"] = float(np.log2(a["mixed"] / b2["mixed"]))
+            for key in ("fp64", "mixed", "fp64_rk4", "mixed_rk4"):
+                b2[key + "_order"] = float(np.log2(a[key] / b2[key]))
         out["dt_sweep"] = {"bodies": sd.n, "days": 73.0, "max_rel_energy_drift": rows}
     if args.sweep:
         # Autotuned up to 65,536 bodies; larger N reuse the 65,536-body winner

@@ -60,13 +60,23 @@ typedef enum {
   NBODY_MIXED = 1
 } nbody_precision;
 
+typedef enum {
+  /* Velocity Verlet, Eqs. 3-4: one evaluation of Eq. 1 per step. */
+  NBODY_VERLET = 0,
+  /* Classical fourth-order Runge-Kutta on y = (r, v), y' = (v, A(r)) -- the
+   * higher-order method Section 2 names: k1 = f(y), k2 = f(y + dt/2 k1),
+   * k3 = f(y + dt/2 k2), k4 = f(y + dt k3), y += dt/6 (k1 + 2 k2 + 2 k3 + k4).
+   * Four evaluations of Eq. 1 per step; error O(dt^4). */
+  NBODY_RK4 = 1
+} nbody_integrator;
+
 typedef struct {
   double G;           /* gravitational constant, > 0 */
   double dt;          /* step size, finite and != 0 (negative runs backwards) */
   int32_t precision;  /* nbody_precision */
   int32_t ckpt_every; /* adjoint checkpoint interval in steps; 0 selects 100 */
   int32_t flags;      /* bitwise OR of NBODY_FLAG_* */
-  int32_t reserved;   /* must be 0 */
+  int32_t integrator; /* nbody_integrator (0, the zero value, is Verlet) */
 } nbody_opts;
 
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
@@ -114,13 +124,16 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
                         double *vz, const double *m, const nbody_opts *o,
                         void *cuda_stream);
 
-/* Advance every system by n_steps velocity-Verlet steps (Eqs. 3, 1, 4), in
+/* Advance every system by n_steps steps of the context's integrator, in
  * place.  n_steps == 0 is a no-op; n_steps < 0 is EINVAL.  Asynchronous.
- * Each step is a force launch (Eq. 1) and a per-body Verlet launch (Eqs.
- * 4, 3), chained; consecutive steps are replayed from cached CUDA graphs
+ * Velocity Verlet (Eqs. 3, 1, 4): each step is a force launch (Eq. 1) and a
+ * per-body Verlet launch (Eqs. 4, 3), chained.  RK4: each step is four
+ * (force launch, per-body stage launch) pairs; the last evaluation is Eq. 1
+ * at the new positions, so the context's acceleration always belongs to the
+ * current state.  Consecutive steps are replayed from cached CUDA graphs
  * unless NBODY_FLAG_NO_GRAPH is set or the stream is already being
- * captured.  One FP64 system of at most 64 bodies instead runs all n_steps
- * in a single cluster launch (see NBODY_FLAG_NO_SMALL). */
+ * captured.  One FP64 Verlet system of at most 64 bodies instead runs all
+ * n_steps in a single cluster launch (see NBODY_FLAG_NO_SMALL). */
 nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
 
 /* Copy the acceleration at the current positions (Eq. 1, as used by the
@@ -146,7 +159,8 @@ nbody_status nbody_energy(nbody_ctx *ctx, double *e_host);
  *   dL_dr_T  DEVICE, 3N (x|y|z blocks): dL/dr_T.
  *   dL_dv_T  DEVICE, 3N, or NULL for zero.
  *   dL_dr0, dL_dv0  DEVICE, 3N outputs; dL_dm DEVICE, N output.
- * Runs in the context's precision.  Synchronous. */
+ * Runs in the context's precision.  Verlet contexts only: EINVAL for RK4.
+ * Synchronous. */
 nbody_status nbody_grad(nbody_ctx *ctx, int64_t n_steps, const double *dL_dr_T,
                         const double *dL_dv_T, double *dL_dr0, double *dL_dv0,
                         double *dL_dm);
@@ -174,7 +188,8 @@ nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *be
  * single-cluster path is not used.  HOST out[4] receives: [0] mean force
  * kernel duration (ms), [1] mean Verlet kernel duration (ms), [2] mean time
  * per step from the first event to the last (ms), [3] n_steps.
- * n_steps >= 1, else NBODY_EINVAL.  Synchronous. */
+ * n_steps >= 1, else NBODY_EINVAL.  Verlet contexts only: EINVAL for RK4.
+ * Synchronous. */
 nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
 
 /* Largest system nbody_accel_static accepts. */

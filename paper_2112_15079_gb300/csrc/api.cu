@@ -79,6 +79,7 @@ struct nbody_ctx {
   std::vector<int64_t> soff;         // stage offset of each system
   int32_t *qidx = nullptr;           // [N] stage index of each body (mixed)
   double *R = nullptr;               // [3][N] mixed: FP64 positions of the staged step
+  double *rk = nullptr;              // RK4: [3][3N] stage velocity V, sums AR and AV
   double *snap = nullptr;            // [6][N] r0, v0 for nbody_grad
   unsigned *flags = nullptr;
   int64_t *offsets_dev = nullptr;
@@ -400,6 +401,29 @@ nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, const void *cur, void *
   return a;
 }
 
+nb::RkArgs rk_args(nbody_ctx *c, const State &s, const void *cur, void *nxt, int stage) {
+  const size_t N = c->N;
+  nb::RkArgs a{};
+  a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
+  a.ax = s.ax; a.ay = s.ay; a.az = s.az;
+  a.m = c->m;
+  a.V = c->rk;
+  a.AR = c->rk + 3 * N;
+  a.AV = c->rk + 6 * N;
+  a.cur = cur;
+  a.nxt = nxt;
+  a.partial = c->fw.partial;
+  a.nsl = c->fw.nsl;
+  a.qidx = c->qidx;
+  a.flags = c->flags;
+  a.N = c->N;
+  a.stage = stage;
+  a.release_early = c->fw.occ == 1 ? 1 : 0;
+  a.G = c->o.G;
+  a.dt = c->o.dt;
+  return a;
+}
+
 // One Verlet step (or, kModeForce, only a = Eq. 1) from the staged sources
 // `cur`, staging the next positions into `nxt`: the force kernel, then the
 // per-body Verlet kernel, chained.
@@ -417,9 +441,25 @@ nbody_status launch_one_step(nbody_ctx *c, const State &s, const void *cur, void
   return NBODY_OK;
 }
 
+// One RK4 step from stage 1 (staged r_2, V = v_2, AR, AV set): four (force,
+// stage-completion) pairs, s = 2..5, ping-ponging between the two stages
+// (an even count, so every step starts from stage[0]).
+nbody_status launch_rk4_step(nbody_ctx *c, const State &s, cudaStream_t st) {
+  for (int k = 0; k < 4; ++k) {
+    const void *cur = c->stage[k & 1];
+    void *nxt = c->stage[1 - (k & 1)];
+    NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
+                                force_args(c, cur), st, true));
+    NB_CUDA(c, nb::launch_rk_stage(c->o.precision, rk_args(c, s, cur, nxt, 2 + k), st, true));
+  }
+  return NBODY_OK;
+}
+
 nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) {
   for (int i = 0; i < n; ++i) {
-    nbody_status r = launch_one_step(c, s, c->stage[i & 1], c->stage[1 - (i & 1)], nb::kModeStep, st);
+    nbody_status r = c->o.integrator == NBODY_RK4
+                         ? launch_rk4_step(c, s, st)
+                         : launch_one_step(c, s, c->stage[i & 1], c->stage[1 - (i & 1)], nb::kModeStep, st);
     if (r != NBODY_OK) return r;
   }
   return NBODY_OK;
@@ -517,6 +557,7 @@ nbody_status alloc_scratch(nbody_ctx *c) {
     NB_CUDA(c, cudaMemcpy(c->qidx, q.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     for (int b = 0; b < 2; ++b) NB_CUDA(c, nb::launch_pad_fill(c->stage[b], c->n_stage / 2, c->stream));
   }
+  if (c->o.integrator == NBODY_RK4) NB_ALLOC(c->rk, sizeof(double) * 9 * N);
   NB_ALLOC(c->snap, sizeof(double) * 6 * N);
   NB_ALLOC(c->flags, sizeof(unsigned));
   NB_ALLOC(c->offsets_dev, sizeof(int64_t) * (c->n_sys + 1));
@@ -644,8 +685,9 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (o->precision != NBODY_FP64 && o->precision != NBODY_MIXED)
     return fail(nullptr, NBODY_EINVAL, "unknown precision %d", o->precision);
   if (o->ckpt_every < 0) return fail(nullptr, NBODY_EINVAL, "ckpt_every must be >= 0");
-  if (o->reserved != 0 || (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL)))
-    return fail(nullptr, NBODY_EINVAL, "unknown flags / reserved field not 0");
+  if (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL)) return fail(nullptr, NBODY_EINVAL, "unknown flags");
+  if (o->integrator != NBODY_VERLET && o->integrator != NBODY_RK4)
+    return fail(nullptr, NBODY_EINVAL, "unknown integrator %d", o->integrator);
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;
   if (!c) return fail(nullptr, NBODY_ENOMEM, "host allocation failed");
@@ -697,7 +739,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (st != NBODY_OK) return bail(st);
   if ((st = build_items(c, default_tiles(c))) != NBODY_OK) return bail(st);
   c->small = c->n_sys == 1 && c->N <= nb::small_max_bodies() && c->o.precision == NBODY_FP64 &&
-             !(c->o.flags & NBODY_FLAG_NO_SMALL);
+             c->o.integrator == NBODY_VERLET && !(c->o.flags & NBODY_FLAG_NO_SMALL);
   if (c->small && nb::small_prepare() != cudaSuccess) {  // no 16-CTA clusters here: general path
     cudaGetLastError();
     c->small = false;
@@ -731,7 +773,10 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
     cudaGetLastError();  // cluster launch refused: fall back to the general path for good
     c->small = false;
   }
-  NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
+  if (c->o.integrator == NBODY_RK4)  // stage 1 of the first step, from (r, v, a)
+    NB_CUDA(c, nb::launch_rk_prep(c->o.precision, rk_args(c, s, nullptr, c->stage[0], 1), c->stream));
+  else  // Eq. 3 drift of the first step
+    NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   NB_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
   if ((c->o.flags & NBODY_FLAG_NO_GRAPH) || cs != cudaStreamCaptureStatusNone) {
@@ -895,6 +940,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
 
 nbody_status nbody_kernel_times(nbody_ctx *c, int32_t n_steps, double *out) {
   if (!c || !out) return NBODY_EINVAL;
+  if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "nbody_kernel_times times Verlet steps only");
   if (n_steps < 1) return fail(c, NBODY_EINVAL, "n_steps must be >= 1");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -942,6 +988,7 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
   if (!dL_dr_T || !dL_dr0 || !dL_dv0 || !dL_dm) return fail(c, NBODY_EINVAL, "a gradient pointer is NULL");
   if (n_steps > (int64_t(1) << 31)) return fail(c, NBODY_EINVAL, "n_steps too large");
+  if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "the adjoint covers Verlet (Eqs. 3-4) only");
   nbody_status st;
   if ((st = ensure_adjoint(c, n_steps)) != NBODY_OK) return st;
   if ((st = begin_work(c)) != NBODY_OK) return st;

@@ -78,59 +78,16 @@ __device__ __forceinline__ void pair_add(T &hi, T &lo, T vhi, T vlo) {
   lo += vlo;
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
-  // When at most one force CTA fits on an SM, the next force grid can only
-  // land one CTA per SM, however early it launches: let it launch now, so its
-  // launch overlaps this kernel (its own griddepcontrol.wait still waits for
-  // our completion).  Otherwise release only at the end (below).
-  if (a.release_early) grid_dependency_launch();
-  typedef typename std::conditional<PREC == 0, double, float>::type T;
+// Phase A of the per-body kernels: body p's force partials (rows 0..rows-1)
+// summed in a fixed order by L = VerletShape<PREC>::kLanes threads; the sum,
+// an unevaluated (hi, lo) pair per component, ends in lane 0.
+template <int PREC, typename T>
+__device__ __forceinline__ void sum_partial_rows(const double *partial, int rows, size_t N, int p, int lane, T &sx,
+                                                 T &ex, T &sy, T &ey, T &sz, T &ez) {
   typedef typename std::conditional<PREC == 0, double, float2>::type E;  // one partial-row entry
   constexpr int L = VerletShape<PREC>::kLanes, U = VerletShape<PREC>::kUnroll;
-  constexpr int NB = VerletShape<PREC>::kBodies;
-  __shared__ T s_hi[3][NB], s_lo[3][NB];
-  const int p0 = blockIdx.x * NB;
-  const int b = threadIdx.x / L, lane = threadIdx.x % L;
-  const int p = p0 + b;  // phase A body
-  const bool live = p < a.N;
-  const size_t N = static_cast<size_t>(a.N);
-  const int q = p0 + threadIdx.x;  // phase B body
-  const bool own = threadIdx.x < NB && q < a.N;
-  const bool step = a.mode == kModeStep;
-
-  // Before the wait: everything this step's force kernel does not write (it
-  // writes only the partial rows), so these loads overlap its tail.
-  const int rows = live ? a.nsl[p] : 0;
-  double vx = 0.0, vy = 0.0, vz = 0.0, aox = 0.0, aoy = 0.0, aoz = 0.0, rx = 0.0, ry = 0.0, rz = 0.0, mu = 0.0;
-  float muf = 0.f;
-  size_t o = 0;
-  if (own && step) {
-    vx = a.vx[q];
-    vy = a.vy[q];
-    vz = a.vz[q];
-    aox = a.ax[q];
-    aoy = a.ay[q];
-    aoz = a.az[q];
-    if (PREC == 0) {
-      const double4_32a r = static_cast<const double4_32a *>(a.cur)[q];
-      rx = r.x;
-      ry = r.y;
-      rz = r.z;
-      mu = r.w;
-    } else {
-      rx = a.Rx[q];
-      ry = a.Ry[q];
-      rz = a.Rz[q];
-      o = pair_off(a.qidx[q]);
-      muf = static_cast<const float *>(a.cur)[o + kMu];
-    }
-  }
-  grid_dependency_wait();  // the force partials of this step are complete
-
-  // ---- phase A: the partial rows of body p --------------------------------
-  T sx = 0, sy = 0, sz = 0, ex = 0, ey = 0, ez = 0;
-  const E *part = reinterpret_cast<const E *>(a.partial);  // row c of body p: part[c*3N + k*N + p]
+  sx = sy = sz = ex = ey = ez = 0;
+  const E *part = reinterpret_cast<const E *>(partial);  // row c of body p: part[c*3N + k*N + p]
   auto add = [&](T &s, T &e, const E &v) {
     if constexpr (PREC == 0) {
       two_sum_acc(s, e, v);
@@ -172,6 +129,80 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
       }
     }
   }
+}
+
+// Stage position (rx, ry, rz) of body q for the next force launch, with mu
+// copied from the current stage: FP64 double4 at q, or the mixed hi/lo pair
+// block at qidx[q] (mixed: *o is the pair offset, *muf the staged mu).
+template <int PREC>
+__device__ __forceinline__ void stage_position(void *nxt, int q, size_t o, double rx, double ry, double rz, double mu,
+                                               float muf) {
+  if (PREC == 0) {
+    static_cast<double4_32a *>(nxt)[q] = make_double4_32a(rx, ry, rz, mu);
+  } else {
+    float *w = static_cast<float *>(nxt) + o;
+    const float hx = hi_part(rx), hy = hi_part(ry), hz = hi_part(rz);
+    w[kXh] = hx;
+    w[kYh] = hy;
+    w[kZh] = hz;
+    w[kMu] = muf;
+    w[kXl] = lo_part(rx, hx);
+    w[kYl] = lo_part(ry, hy);
+    w[kZl] = lo_part(rz, hz);
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
+  // When at most one force CTA fits on an SM, the next force grid can only
+  // land one CTA per SM, however early it launches: let it launch now, so its
+  // launch overlaps this kernel (its own griddepcontrol.wait still waits for
+  // our completion).  Otherwise release only at the end (below).
+  if (a.release_early) grid_dependency_launch();
+  typedef typename std::conditional<PREC == 0, double, float>::type T;
+  constexpr int L = VerletShape<PREC>::kLanes, NB = VerletShape<PREC>::kBodies;
+  __shared__ T s_hi[3][NB], s_lo[3][NB];
+  const int p0 = blockIdx.x * NB;
+  const int b = threadIdx.x / L, lane = threadIdx.x % L;
+  const int p = p0 + b;  // phase A body
+  const bool live = p < a.N;
+  const size_t N = static_cast<size_t>(a.N);
+  const int q = p0 + threadIdx.x;  // phase B body
+  const bool own = threadIdx.x < NB && q < a.N;
+  const bool step = a.mode == kModeStep;
+
+  // Before the wait: everything this step's force kernel does not write (it
+  // writes only the partial rows), so these loads overlap its tail.
+  const int rows = live ? a.nsl[p] : 0;
+  double vx = 0.0, vy = 0.0, vz = 0.0, aox = 0.0, aoy = 0.0, aoz = 0.0, rx = 0.0, ry = 0.0, rz = 0.0, mu = 0.0;
+  float muf = 0.f;
+  size_t o = 0;
+  if (own && step) {
+    vx = a.vx[q];
+    vy = a.vy[q];
+    vz = a.vz[q];
+    aox = a.ax[q];
+    aoy = a.ay[q];
+    aoz = a.az[q];
+    if (PREC == 0) {
+      const double4_32a r = static_cast<const double4_32a *>(a.cur)[q];
+      rx = r.x;
+      ry = r.y;
+      rz = r.z;
+      mu = r.w;
+    } else {
+      rx = a.Rx[q];
+      ry = a.Ry[q];
+      rz = a.Rz[q];
+      o = pair_off(a.qidx[q]);
+      muf = static_cast<const float *>(a.cur)[o + kMu];
+    }
+  }
+  grid_dependency_wait();  // the force partials of this step are complete
+
+  // ---- phase A: the partial rows of body p --------------------------------
+  T sx, sy, sz, ex, ey, ez;
+  sum_partial_rows<PREC, T>(a.partial, rows, N, p, lane, sx, ex, sy, ey, sz, ez);
   if (lane == 0) {
     s_hi[0][b] = sx;
     s_lo[0][b] = ex;
@@ -199,22 +230,12 @@ __global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a
     const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
     const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
     const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
-    if (PREC == 0) {
-      static_cast<double4_32a *>(a.nxt)[q] = make_double4_32a(nx, ny, nz, mu);
-    } else {
+    if (PREC == 1) {
       a.Rx[q] = nx;
       a.Ry[q] = ny;
       a.Rz[q] = nz;
-      float *w = static_cast<float *>(a.nxt) + o;
-      const float hxn = hi_part(nx), hyn = hi_part(ny), hzn = hi_part(nz);
-      w[kXh] = hxn;
-      w[kYh] = hyn;
-      w[kZh] = hzn;
-      w[kMu] = muf;
-      w[kXl] = lo_part(nx, hxn);
-      w[kYl] = lo_part(ny, hyn);
-      w[kZl] = lo_part(nz, hzn);
     }
+    stage_position<PREC>(a.nxt, q, o, nx, ny, nz, mu, muf);
     a.x[q] = rx;
     a.y[q] = ry;
     a.z[q] = rz;
@@ -245,6 +266,166 @@ cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bo
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
   return precision == 0 ? cudaLaunchKernelEx(&cfg, verlet_kernel<0>, a) : cudaLaunchKernelEx(&cfg, verlet_kernel<1>, a);
+}
+
+// ---------------------------------------------------------------------------
+// Classical RK4 (the higher-order method Section 2 names) on y = (r, v),
+// y' = (v, A(r)): stage completion, s = 2..5 (stage 1 is rk_prep or the end
+// of s = 5).  Phase A as in the Verlet kernel; phase B, one body per thread:
+//   s = 2, 3: AR += 2 v_s, AV += 2 a_s; r_{s+1} = r + c v_s, v_{s+1} = v + c a_s
+//             (c = dt/2 at s = 2, dt at s = 3);
+//   s = 4:    r <- r + dt/6 (AR + v_4), v <- v + dt/6 (AV + a_4), stage r;
+//   s = 5:    a <- a_5 = A(r); then stage 1 of the next step:
+//             AR = v, AV = a, v_2 = v + dt/2 a, stage r_2 = r + dt/2 v.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(kVerletBlock) rk_stage_kernel(const RkArgs a) {
+  if (a.release_early) grid_dependency_launch();
+  typedef typename std::conditional<PREC == 0, double, float>::type T;
+  constexpr int L = VerletShape<PREC>::kLanes, NB = VerletShape<PREC>::kBodies;
+  __shared__ T s_hi[3][NB], s_lo[3][NB];
+  const int p0 = blockIdx.x * NB;
+  const int b = threadIdx.x / L, lane = threadIdx.x % L;
+  const int p = p0 + b;
+  const bool live = p < a.N;
+  const size_t N = static_cast<size_t>(a.N);
+  const int q = p0 + threadIdx.x;
+  const bool own = threadIdx.x < NB && q < a.N;
+  const int rows = live ? a.nsl[p] : 0;
+  // Prefetch what the force launch does not write (the state, the RK sums).
+  double rn[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, vs[3] = {0, 0, 0}, ar[3] = {0, 0, 0}, av[3] = {0, 0, 0}, mu = 0.0;
+  float muf = 0.f;
+  size_t o = 0;
+  if (own) {
+    rn[0] = a.x[q];
+    rn[1] = a.y[q];
+    rn[2] = a.z[q];
+    vn[0] = a.vx[q];
+    vn[1] = a.vy[q];
+    vn[2] = a.vz[q];
+    if (a.stage <= 4) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        vs[k] = a.V[k * N + q];
+        ar[k] = a.AR[k * N + q];
+        av[k] = a.AV[k * N + q];
+      }
+    }
+    if (PREC == 0) {
+      mu = static_cast<const double4_32a *>(a.cur)[q].w;
+    } else {
+      o = pair_off(a.qidx[q]);
+      muf = static_cast<const float *>(a.cur)[o + kMu];
+    }
+  }
+  grid_dependency_wait();  // the force partials of this stage are complete
+  T sx, sy, sz, ex, ey, ez;
+  sum_partial_rows<PREC, T>(a.partial, rows, N, p, lane, sx, ex, sy, ey, sz, ez);
+  if (lane == 0) {
+    s_hi[0][b] = sx;
+    s_lo[0][b] = ex;
+    s_hi[1][b] = sy;
+    s_lo[1][b] = ey;
+    s_hi[2][b] = sz;
+    s_lo[2][b] = ez;
+  }
+  __syncthreads();
+  if (!own) {
+    if (!a.release_early) grid_dependency_launch();
+    return;
+  }
+  const int k0 = threadIdx.x;
+  double as[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) as[k] = static_cast<double>(s_hi[k][k0]) + static_cast<double>(s_lo[k][k0]);
+  if (!finite3(as[0], as[1], as[2])) atomicOr(a.flags, kFlagNonFinite);
+  double rnext[3];
+  if (a.stage == 2 || a.stage == 3) {
+    const double c = a.stage == 2 ? 0.5 * a.dt : a.dt;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a.AR[k * N + q] = ar[k] + 2.0 * vs[k];
+      a.AV[k * N + q] = av[k] + 2.0 * as[k];
+      rnext[k] = rn[k] + c * vs[k];
+      a.V[k * N + q] = vn[k] + c * as[k];
+    }
+  } else if (a.stage == 4) {
+    const double h = a.dt / 6.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      rnext[k] = rn[k] + h * (ar[k] + vs[k]);
+      vn[k] = vn[k] + h * (av[k] + as[k]);
+    }
+    a.x[q] = rnext[0];
+    a.y[q] = rnext[1];
+    a.z[q] = rnext[2];
+    a.vx[q] = vn[0];
+    a.vy[q] = vn[1];
+    a.vz[q] = vn[2];
+  } else {  // s = 5: A at the new state, then stage 1 of the next step
+    a.ax[q] = as[0];
+    a.ay[q] = as[1];
+    a.az[q] = as[2];
+    const double c = 0.5 * a.dt;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a.AR[k * N + q] = vn[k];
+      a.AV[k * N + q] = as[k];
+      rnext[k] = rn[k] + c * vn[k];
+      a.V[k * N + q] = vn[k] + c * as[k];
+    }
+  }
+  stage_position<PREC>(a.nxt, q, o, rnext[0], rnext[1], rnext[2], mu, muf);
+  if (!a.release_early) grid_dependency_launch();
+}
+
+cudaError_t launch_rk_stage(int precision, const RkArgs &a, cudaStream_t s, bool chained) {
+  if (a.N <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  const int64_t nb = precision == 0 ? VerletShape<0>::kBodies : VerletShape<1>::kBodies;
+  cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + nb - 1) / nb));
+  cfg.blockDim = dim3(kVerletBlock);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return precision == 0 ? cudaLaunchKernelEx(&cfg, rk_stage_kernel<0>, a)
+                        : cudaLaunchKernelEx(&cfg, rk_stage_kernel<1>, a);
+}
+
+// RK4 stage 1 from the state (r, v, a = A(r)): AR = v, AV = a,
+// V = v + dt/2 a, and the staged sources r_2 = r + dt/2 v with mu = G m.
+template <int PREC>
+__global__ void rk_prep_kernel(const RkArgs a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.N) return;
+  const size_t N = static_cast<size_t>(a.N);
+  const double rn[3] = {a.x[q], a.y[q], a.z[q]}, vn[3] = {a.vx[q], a.vy[q], a.vz[q]};
+  const double an[3] = {a.ax[q], a.ay[q], a.az[q]};
+  const double c = 0.5 * a.dt;
+  double r2[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    a.AR[k * N + q] = vn[k];
+    a.AV[k * N + q] = an[k];
+    r2[k] = rn[k] + c * vn[k];
+    a.V[k * N + q] = vn[k] + c * an[k];
+  }
+  const double mu = a.G * a.m[q];
+  const size_t o = PREC == 0 ? 0 : pair_off(a.qidx[q]);
+  stage_position<PREC>(a.nxt, q, o, r2[0], r2[1], r2[2], mu, static_cast<float>(mu));
+}
+
+cudaError_t launch_rk_prep(int precision, const RkArgs &a, cudaStream_t s) {
+  if (a.N <= 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((static_cast<int64_t>(a.N) + 255) / 256);
+  if (precision == 0)
+    rk_prep_kernel<0><<<grid, 256, 0, s>>>(a);
+  else
+    rk_prep_kernel<1><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

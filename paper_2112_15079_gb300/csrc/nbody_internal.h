@@ -162,6 +162,35 @@ cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s);
 cudaError_t launch_force(int precision, int threads, int ipt, int grid, size_t smem, const ForceArgs &a,
                          cudaStream_t s, bool chained);
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained);
+
+// Classical RK4 on y = (r, v), y' = (v, A(r)) (kernels_misc.cu).  rk_stage
+// kernel, stage s = 2..5: sums the force partials of body p into a_s (as the
+// Verlet kernel does; for s = 5 that is A at the new state), then
+//   s = 2, 3: AR += 2 v_s, AV += 2 a_s; r_{s+1} = r + c v_s, v_{s+1} = v + c a_s
+//             (c = dt/2 for s = 2, dt for s = 3) -> stage r_{s+1}, V = v_{s+1};
+//   s = 4:    r += dt/6 (AR + v_4), v += dt/6 (AV + a_4) -> caller state, stage r;
+//   s = 5:    a = a_5; then stage 1 of the next step (as rk_prep).
+// rk_prep (stage 1 from the state): AR = v, AV = a, V = v + dt/2 a, stage
+// r_2 = r + dt/2 v.
+struct RkArgs {
+  double *x, *y, *z, *vx, *vy, *vz;  // the state (r, v): read, written at s = 4
+  double *ax, *ay, *az;              // A(r) of the state: read by rk_prep, written at s = 5
+  const double *m;                   // rk_prep only (mu = G m is staged)
+  double *V;                         // [3N] velocity of the current stage
+  double *AR, *AV;                   // [3N] weighted sums of the stage derivatives
+  const void *cur;                   // staged sources of this stage (mu is copied from here)
+  void *nxt;                         // stage written for the next force launch
+  const double *partial;
+  const uint16_t *nsl;
+  const int32_t *qidx;  // [N] stage index of body p (mixed); NULL: p
+  unsigned *flags;
+  int32_t N;
+  int32_t stage;
+  int32_t release_early;
+  double G, dt;
+};
+cudaError_t launch_rk_stage(int precision, const RkArgs &a, cudaStream_t s, bool chained);
+cudaError_t launch_rk_prep(int precision, const RkArgs &a, cudaStream_t s);
 cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem);  // raise the dynamic smem limit
 int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 bool force_config_supported(int precision, int threads, int ipt);

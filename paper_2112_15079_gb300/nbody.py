@@ -29,11 +29,13 @@ NBODY_FLAG_NO_GRAPH = 1
 NBODY_FLAG_NO_SMALL = 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT"}
 PRECISIONS = {"fp64": NBODY_FP64, "mixed": NBODY_MIXED}
+NBODY_VERLET, NBODY_RK4 = 0, 1
+INTEGRATORS = {"verlet": NBODY_VERLET, "rk4": NBODY_RK4}
 
 
 class nbody_opts(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("integrator", ctypes.c_int32)]
 
 
 class nbody_tiles(ctypes.Structure):
@@ -124,7 +126,8 @@ class NBody:
     [6, N] float64 CUDA tensor (rows x, y, z, vx, vy, vz), updated in place."""
 
     def __init__(self, r, v, m, offsets=None, *, G: float, dt: float, precision: str = "fp64",
-                 ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None):
+                 ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None,
+                 integrator: str = "verlet"):
         torch = _torch()
         device = torch.device(device if device is not None else "cuda")
         self.device = device
@@ -140,11 +143,11 @@ class NBody:
         off = np.array([0, n] if offsets is None else offsets, dtype=np.int64)
         self.offsets = off
         self.n_systems = len(off) - 1
-        self.G, self.dt, self.precision = float(G), float(dt), precision
+        self.G, self.dt, self.precision, self.integrator = float(G), float(dt), precision, integrator
         self._stream = stream if stream is not None else torch.cuda.current_stream(device)
         opts = nbody_opts(G=self.G, dt=self.dt, precision=PRECISIONS[precision], ckpt_every=int(ckpt_every),
                           flags=(0 if graphs else NBODY_FLAG_NO_GRAPH) | (0 if small else NBODY_FLAG_NO_SMALL),
-                          reserved=0)
+                          integrator=INTEGRATORS[integrator])
         self._ctx = _P()
         s = self.state
         ptrs = [s[k].data_ptr() for k in range(6)] + [self.m.data_ptr()]

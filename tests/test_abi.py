@@ -56,7 +56,7 @@ def test_errors_without_context_are_reported():
     from paper_2112_15079_gb300 import nbody
     ctx = ctypes.c_void_p()
     off = (ctypes.c_int64 * 2)(0, 2)
-    opts = nbody.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, reserved=0)
+    opts = nbody.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, integrator=0)
     st = nbody.nbody_init(ctypes.byref(ctx), 0, off, *([None] * 7), ctypes.byref(opts), None)
     assert st == nbody.NBODY_EINVAL
     assert b"n_systems" in nbody.nbody_last_error(None)

@@ -366,7 +366,7 @@ def test_edge_cases_and_errors(nb):
     h = np.zeros(2)
     ctx = ctypes.c_void_p()
     off = (ctypes.c_int64 * 2)(0, 2)
-    opts = nb.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, reserved=0)
+    opts = nb.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, integrator=0)
     st = nb.nbody_init(ctypes.byref(ctx), 1, off, *([h.ctypes.data] * 7), ctypes.byref(opts), None)
     assert st == nb.NBODY_EINVAL and not ctx.value
     # a collision during the run surfaces as ENONFINITE on the next sync

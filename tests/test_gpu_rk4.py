@@ -1,0 +1,130 @@
+"""GPU parity of the RK4 integrator (the higher-order method Section 2 names)
+against the oracle's classical RK4.
+
+FP64: positions of the 31-body model within 1e-10 AU after 3650 steps;
+several tiles with ragged tails (2,131 and 5,003 bodies) within 1e-12 AU and
+1e-13 AU/day after 10 steps; the acceleration the context keeps for the new
+state matches Eq. 1 there (1e-13); the maximum energy drift matches the
+oracle's at dt = 0.8, 0.4, 0.2 day and is far below Verlet's.
+Mixed: one step from the oracle's state moves each body within the bound
+its force error allows: |dr_p| <= 2 dt^2 * 2e-6 * T_p and |dv_p| <= 2 dt * 2e-6
+* T_p (T_p = sum_j |term_pj|, 2e-6 the mixed force tolerance, each stage
+derivative entering with total weight 1)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_15079_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_15079_gb300 import build
+    build.build()
+    from paper_2112_15079_gb300 import nbody
+    return nbody
+
+
+def _rk(nb, s, precision, **kw):
+    return nb.NBody(s.r, s.v, s.m, G=s.G, dt=kw.pop("dt", s.dt), precision=precision, integrator="rk4", **kw)
+
+
+def test_rk4_fp64_31_bodies_3650_steps(nb):
+    s = inputs.solar_system(31)
+    b = _rk(nb, s, "fp64")
+    b.step(3650)
+    r_ref, v_ref, _ = oracle.rk4(s.G, s.dt, 3650, s.r, s.v, s.m)
+    assert np.abs(b.r.cpu().numpy() - r_ref).max() <= 1e-10
+
+
+@pytest.mark.parametrize("n", [2131, 5003])
+def test_rk4_fp64_tiles_vs_oracle(nb, n):
+    s = inputs.solar_system(n, seed=300 + n)
+    b = _rk(nb, s, "fp64")
+    b.step(10)
+    r_ref, v_ref, a_ref = oracle.rk4(s.G, s.dt, 10, s.r, s.v, s.m, openmp=True)
+    assert np.abs(b.r.cpu().numpy() - r_ref).max() <= 1e-12
+    assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-13
+    r_gpu = b.r.cpu().numpy()
+    a_at = oracle.accel(s.G, r_gpu, s.m, openmp=True)  # Eq. 1 at the GPU's new state
+    a_gpu = b.accel().cpu().numpy()
+    err = np.linalg.norm(a_gpu - a_at, axis=0) / np.linalg.norm(a_at, axis=0)
+    assert err.max() <= 1e-13, err.max()
+
+
+@pytest.mark.parametrize("n", [2131, 5003])
+def test_rk4_mixed_one_step_within_force_bound(nb, n):
+    s = inputs.solar_system(n, seed=310 + n)
+    b = _rk(nb, s, "mixed")
+    b.step(1)
+    r_ref, v_ref, _ = oracle.rk4(s.G, s.dt, 1, s.r, s.v, s.m, openmp=True)
+    T = oracle.term_norm(s.G, s.r, s.m, openmp=True)
+    dr = np.linalg.norm(b.r.cpu().numpy() - r_ref, axis=0)
+    dv = np.linalg.norm(b.v.cpu().numpy() - v_ref, axis=0)
+    assert np.all(dr <= 2 * s.dt**2 * 2e-6 * T + 1e-15 * np.linalg.norm(r_ref, axis=0)), (dr / T).max()
+    assert np.all(dv <= 2 * s.dt * 2e-6 * T + 1e-15 * np.linalg.norm(v_ref, axis=0)), (dv / T).max()
+
+
+def _drift(step_fn, energy_fn, n_steps):
+    every = max(1, n_steps // 20)
+    e0 = energy_fn()
+    worst = 0.0
+    for _ in range(n_steps // every):
+        step_fn(every)
+        worst = max(worst, abs(energy_fn() - e0) / abs(e0))
+    return worst
+
+
+def test_rk4_energy_drift_matches_oracle_and_beats_verlet(nb):
+    s = inputs.solar_system(500, seed=31, n_moons=0)
+    for dt in (0.8, 0.4, 0.2):
+        n = int(round(36.5 / dt))
+        b = _rk(nb, s, "fp64", dt=dt)
+        g = _drift(b.step, lambda: b.energy()[0], n)
+        st = {"r": s.r.copy(), "v": s.v.copy()}
+
+        def ostep(k):
+            st["r"], st["v"], _ = oracle.rk4(s.G, dt, k, st["r"], st["v"], s.m, openmp=True)
+
+        ref = _drift(ostep, lambda: sum(oracle.energy(s.G, st["r"], st["v"], s.m)), n)
+        assert abs(g - ref) <= 1e-3 * ref + 1e-14, (dt, g, ref)
+        vv = nb.NBody(s.r, s.v, s.m, G=s.G, dt=dt, precision="fp64")
+        gv = _drift(vv.step, lambda: vv.energy()[0], n)
+        assert g < 0.01 * gv, (dt, g, gv)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_rk4_graphs_and_split_calls_bitwise(nb, precision):
+    s = inputs.solar_system(2131, seed=33)
+    outs = []
+    for graphs, chunks in ((True, [70]), (True, [64, 6]), (False, [13, 57])):
+        b = _rk(nb, s, precision, graphs=graphs)
+        for c in chunks:
+            b.step(c)
+        outs.append(b.state.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+def test_rk4_unsupported_calls(nb):
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(200, seed=34)
+    b = _rk(nb, s, "fp64")
+    with pytest.raises(nb.NBodyError) as ei:
+        b.grad(3, torch.ones((3, s.n), dtype=torch.float64, device="cuda"))
+    assert ei.value.status == nb.NBODY_EINVAL
+    with pytest.raises(nb.NBodyError) as ei:
+        b.kernel_times(2)
+    assert ei.value.status == nb.NBODY_EINVAL
+    import ctypes
+    off = (ctypes.c_int64 * 2)(0, s.n)
+    opts = nb.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, integrator=2)
+    ctx = ctypes.c_void_p()
+    st = nb.nbody_init(ctypes.byref(ctx), 1, off, *([b.state[0].data_ptr()] * 6 + [b.m.data_ptr()]),
+                       ctypes.byref(opts), None)
+    assert st == nb.NBODY_EINVAL and not ctx.value
