@@ -15,14 +15,79 @@
 //   rho += J^T w;  g_m += (dA/dm)^T w;
 //   nu' = nu + dt rho;  alpha' = dt/2 nu + dt^2/2 rho;  nu = nu';
 //   next w = alpha' + dt/2 nu'  (w = alpha' before the last product, at r_0).
-#include "nbody_dev.cuh"
+#include "step_kernel.cuh"  // packed f32x2 helpers (f2, pk, upk, add2, mul2, fma2)
 
 namespace nb {
 
 namespace {
 
+// Mixed path: w is staged in pair blocks like the positions, 32 bytes per two
+// consecutive stage entries, [wx0 wx1 wy0 wy1 | wz0 wz1 0 0], so one 16-byte
+// shared load yields packed (f32x2) operands for a source pair.
+__device__ __forceinline__ void w_pair_store(void *w, int q, float wx, float wy, float wz) {
+  float *b = static_cast<float *>(w) + 8 * static_cast<size_t>(q >> 1) + (q & 1);
+  b[0] = wx;
+  b[2] = wy;
+  b[4] = wz;
+}
+__device__ __forceinline__ float3 w_pair_load(const void *w, int q) {
+  const float *b = static_cast<const float *>(w) + 8 * static_cast<size_t>(q >> 1) + (q & 1);
+  return make_float3(b[0], b[2], b[4]);
+}
+
+// The VJP terms of one target against a source pair (mixed path), both terms
+// accumulated into packed pairs: with d = r_j - r_q from the hi/lo split,
+// s3 = |d|^-3, s5 = |d|^-5, u = mu_q w_j - mu_j w_q,
+//   acc_xyz += s3 u - 3 s5 (d.u) d,   acc_m += s3 (w_j . d).
+// v0..v3: the pair's position block; w0 = (wx, wy), w1 = (wz, 0) of the pair.
+// MASK: a source that is the target itself gets r2 = 1 and |d|^-1 = 0, so
+// all of its terms are exactly 0.
+template <bool MASK>
+__device__ __forceinline__ void vjp_pair(const ulonglong2 &v0, const ulonglong2 &v1, const ulonglong2 &v2,
+                                         const ulonglong2 &v3, const ulonglong2 &w0, const ulonglong2 &w1, f2 nxh,
+                                         f2 nyh, f2 nzh, f2 nxl, f2 nyl, f2 nzl, f2 muq, f2 nwqx, f2 nwqy, f2 nwqz,
+                                         f2 m3, bool self_a, bool self_b, f2 (&acc)[4]) {
+  const f2 dx = add2(add2(v0.x, nxh), add2(v2.x, nxl));
+  const f2 dy = add2(add2(v0.y, nyh), add2(v2.y, nyl));
+  const f2 dz = add2(add2(v1.x, nzh), add2(v3.x, nzl));
+  f2 r2 = mul2(dx, dx);
+  r2 = fma2(dy, dy, r2);
+  r2 = fma2(dz, dz, r2);
+  float ra, rb;
+  upk(r2, ra, rb);
+  if (MASK) {
+    ra = self_a ? 1.0f : ra;
+    rb = self_b ? 1.0f : rb;
+  }
+  float ya = rsqrt_approx(ra), yb = rsqrt_approx(rb);
+  if (MASK) {
+    ya = self_a ? 0.0f : ya;
+    yb = self_b ? 0.0f : yb;
+  }
+  const f2 y = pk(ya, yb);
+  const f2 y2 = mul2(y, y);
+  const f2 s3 = mul2(y, y2);
+  const f2 s5 = mul2(s3, y2);
+  const f2 mu = v1.y;  // (mu_j0, mu_j1)
+  const f2 ux = fma2(mu, nwqx, mul2(muq, w0.x));
+  const f2 uy = fma2(mu, nwqy, mul2(muq, w0.y));
+  const f2 uz = fma2(mu, nwqz, mul2(muq, w1.x));
+  f2 du = mul2(dx, ux);
+  du = fma2(dy, uy, du);
+  du = fma2(dz, uz, du);
+  const f2 t3 = mul2(mul2(s5, du), m3);  // -3 s5 (d.u)
+  acc[0] = fma2(t3, dx, fma2(s3, ux, acc[0]));
+  acc[1] = fma2(t3, dy, fma2(s3, uy, acc[1]));
+  acc[2] = fma2(t3, dz, fma2(s3, uz, acc[2]));
+  f2 dw = mul2(w0.x, dx);
+  dw = fma2(w0.y, dy, dw);
+  dw = fma2(w1.x, dz, dw);
+  acc[3] = fma2(s3, dw, acc[3]);
+}
+
 // Source tile: positions as staged by the forward pass (FP64 double4 or
-// mixed pair blocks, 32 B per source) followed by w (FP64 double4, mixed float4).
+// mixed pair blocks, 32 B per source) followed by w (FP64 double4; mixed pair
+// blocks of 16 B per source).
 template <int PREC>
 struct VjpLayout {
   static constexpr int kWBytes = PREC == 0 ? 32 : 16;
@@ -59,6 +124,9 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs a) {
     const bool valid = p < bk.i1;
     const int pi = valid ? p : bk.i1 - 1;
     const int tq = bk.q0 + (pi - bk.i0);
+    // Mixed path: the stage pairs that may hold one of this warp's targets.
+    const int mlo = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(tq))) >> 1;
+    const int mhi = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(tq))) >> 1;
 
     // target q: position, mu_q, w_q
     double qx = 0, qy = 0, qz = 0, qmu = 0, wqx = 0, wqy = 0, wqz = 0;
@@ -82,7 +150,7 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs a) {
       ly = e[kYl];
       lz = e[kZl];
       fmu = e[kMu];
-      const float4 w = static_cast<const float4 *>(a.w)[tq];
+      const float3 w = w_pair_load(a.w, tq);
       fwx = w.x;
       fwy = w.y;
       fwz = w.z;
@@ -136,35 +204,50 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) two_sum_acc(acc[c], cmp[c], tacc[c]);
       } else {
-        const float4 *sp = reinterpret_cast<const float4 *>(pos_ptr(s));  // 4 per pair block
-        const float4 *sw = reinterpret_cast<const float4 *>(w_ptr(s));
-        for (int g0 = 0; g0 < cnt; g0 += 2 * kFoldPairs) {
-          const int lim = min(2 * kFoldPairs, cnt - g0);
-          float tacc[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int jj = g0; jj < g0 + lim; ++jj) {
-            const float *pb = reinterpret_cast<const float *>(sp + 4 * (jj >> 1)) + (jj & 1);
-            const float4 w = sw[jj];
-            const float dx = (pb[kXh] - hx) + (pb[kXl] - lx);
-            const float dy = (pb[kYh] - hy) + (pb[kYl] - ly);
-            const float dz = (pb[kZh] - hz) + (pb[kZl] - lz);
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (diag) r2 = (jt0 + jj == tq) ? 1.0f : r2;
-            const float y = rsqrt_approx(r2);
-            const float y2 = y * y;
-            const float s3 = y * y2;
-            const float s5 = s3 * y2;
-            const float mu = pb[kMu];
-            const float ux = fmaf(-mu, fwx, fmu * w.x);
-            const float uy = fmaf(-mu, fwy, fmu * w.y);
-            const float uz = fmaf(-mu, fwz, fmu * w.z);
-            const float t3 = 3.0f * s5 * fmaf(dz, uz, fmaf(dy, uy, dx * ux));
-            tacc[0] = fmaf(-t3, dx, fmaf(s3, ux, tacc[0]));
-            tacc[1] = fmaf(-t3, dy, fmaf(s3, uy, tacc[1]));
-            tacc[2] = fmaf(-t3, dz, fmaf(s3, uz, tacc[2]));
-            tacc[3] = fmaf(s3, fmaf(w.z, dz, fmaf(w.y, dy, w.x * dx)), tacc[3]);
+        const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(pos_ptr(s));  // 4 per pair block
+        const ulonglong2 *sw = reinterpret_cast<const ulonglong2 *>(w_ptr(s));    // 2 per pair block
+        const f2 nxh = pk(-hx, -hx), nyh = pk(-hy, -hy), nzh = pk(-hz, -hz);
+        const f2 nxl = pk(-lx, -lx), nyl = pk(-ly, -ly), nzl = pk(-lz, -lz);
+        const f2 muq = pk(fmu, fmu), nwqx = pk(-fwx, -fwx), nwqy = pk(-fwy, -fwy), nwqz = pk(-fwz, -fwz);
+        const f2 m3 = pk(-3.0f, -3.0f);
+        const int npairs = cnt >> 1;
+        const int P0t = jt0 >> 1;  // stage pair index of the tile's first pair
+        for (int g0 = 0; g0 < npairs; g0 += kFoldPairs) {
+          const int lim = min(kFoldPairs, npairs - g0);
+          f2 pacc[4] = {0ull, 0ull, 0ull, 0ull};
+          // Only pairs that may hold one of this warp's own targets take the
+          // self test (a warp's 32 consecutive targets span <= 17 pairs).
+          const int r0 = max(mlo - P0t - g0, 0), r1 = min(mhi - P0t - g0 + 1, lim);
+          auto run = [&](int b0, int b1, bool masked) {
+            if (!masked) {
+#pragma unroll 2
+              for (int b = b0; b < b1; ++b) {
+                const ulonglong2 *pb = sp + 4 * (g0 + b), *wb = sw + 2 * (g0 + b);
+                vjp_pair<false>(pb[0], pb[1], pb[2], pb[3], wb[0], wb[1], nxh, nyh, nzh, nxl, nyl, nzl, muq, nwqx,
+                                nwqy, nwqz, m3, false, false, pacc);
+              }
+            } else {
+              for (int b = b0; b < b1; ++b) {
+                const ulonglong2 *pb = sp + 4 * (g0 + b), *wb = sw + 2 * (g0 + b);
+                const int P = P0t + g0 + b;
+                vjp_pair<true>(pb[0], pb[1], pb[2], pb[3], wb[0], wb[1], nxh, nyh, nzh, nxl, nyl, nzl, muq, nwqx,
+                               nwqy, nwqz, m3, 2 * P == tq, 2 * P + 1 == tq, pacc);
+              }
+            }
+          };
+          if (r0 < r1) {
+            run(0, r0, false);
+            run(r0, r1, true);
+            run(r1, lim, false);
+          } else {
+            run(0, lim, false);
           }
 #pragma unroll
-          for (int c = 0; c < 4; ++c) two_sum_acc(sh[c], sl[c], tacc[c]);
+          for (int c = 0; c < 4; ++c) {  // fold the packed sub-sums into the float pairs
+            float e, o;
+            upk(pacc[c], e, o);
+            two_sum_acc(sh[c], sl[c], e + o);
+          }
         }
       }
       __syncthreads();
@@ -262,8 +345,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
   if (PREC == 0)
     static_cast<double4_32a *>(a.w)[q] = make_double4_32a(w[0], w[1], w[2], 0.0);
   else
-    static_cast<float4 *>(a.w)[q] =
-        make_float4(static_cast<float>(w[0]), static_cast<float>(w[1]), static_cast<float>(w[2]), 0.f);
+    w_pair_store(a.w, q, static_cast<float>(w[0]), static_cast<float>(w[1]), static_cast<float>(w[2]));
 }
 
 // rho = dL/dr_T, nu = dL/dv_T (or 0), g_m = 0, and the first w = dt/2 nu
@@ -286,8 +368,7 @@ __global__ void adjoint_init_kernel(const AdjArgs a, const double *dr, const dou
   if (PREC == 0)
     static_cast<double4_32a *>(a.w)[q] = make_double4_32a(w[0], w[1], w[2], 0.0);
   else
-    static_cast<float4 *>(a.w)[q] =
-        make_float4(static_cast<float>(w[0]), static_cast<float>(w[1]), static_cast<float>(w[2]), 0.f);
+    w_pair_store(a.w, q, static_cast<float>(w[0]), static_cast<float>(w[1]), static_cast<float>(w[2]));
 }
 
 }  // namespace
