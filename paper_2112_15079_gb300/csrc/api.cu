@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/nbody.h: context lifetime,
-// validation, scratch ownership, work-item tables, CUDA-graph replay of
-// Verlet steps, energy, tiles/autotuning and device-fault reporting.
+// validation, scratch ownership, stream-K work tables, CUDA-graph replay of
+// Verlet and RK4 steps, the adjoint sweep, energy, tiles/autotuning and
+// device-fault reporting.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

@@ -7,7 +7,7 @@
 
 namespace nb {
 
-// Device-side fault flags (bitwise OR into Scratch::flags).
+// Device-side fault flags (bitwise OR into the context's flags word).
 enum : unsigned {
   kFlagNonFinite = 1u,  // an acceleration (or input) was NaN/Inf
   kFlagTimeout = 2u,    // a bounded mbarrier wait ran out
