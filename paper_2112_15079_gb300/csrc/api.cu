@@ -887,10 +887,12 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   const bool mixed = c->o.precision == NBODY_MIXED;
   for (int th : {64, 128, 256, 384, 512, 768, 1024})
     for (int ip : {1, 2, 4})
-      for (int tj : {128, 256, 512, 1024})
+      for (int tj : {128, 256, 512, 1024, 2048})
         for (int cps : {1, 2, 3, 4}) {
           if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
-          if (!mixed && tj != 1024) continue;  // FP64: bound by the FP64 pipe, tiling matters little
+          // FP64 is bound by the FP64 pipe: only the barrier spacing (tj) and the warp count matter
+          if (!mixed && tj < 512) continue;
+          if (mixed && tj > 1024) continue;
           // at most 1024 threads per SM; the mixed path wants >= 512 threads or >= 1024 targets per SM
           if (th * cps > 1024 || (mixed && th * cps < 512 && th * cps * ip < 1024)) continue;
           nbody_tiles t;
