@@ -172,10 +172,10 @@ bool tiles_valid(const nbody_tiles &t, int precision) {
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
-  // Measured on GB300 from N = 16,384 to 1M: FP64 is bound by the FP64 pipe
-  // (~90% busy) with three 128-thread CTAs per SM; the mixed path is best with
-  // one 512-thread CTA per SM, two targets per thread (117 registers, so one
-  // CTA is all that fits: no co-resident CTAs for the scheduler to favour).
+  // The autotuner's picks on GB300: FP64 is bound by the FP64 pipe (~90% busy)
+  // with three 128-thread CTAs per SM at every size; the mixed path takes two
+  // 512-thread CTAs per SM with one target per thread up to ~16k bodies (short
+  // shares, more warps) and one 1024-thread CTA per SM from 64k bodies on.
   nbody_tiles t{};
   t.jsplit = 0;  // static shares only (dynamic chunks add partial rows)
   t.tj = 1024;
@@ -185,8 +185,10 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
     t.ipt = 1;
     t.ctas_per_sm = 3;
   } else {
-    t.threads = 512;
-    t.ctas_per_sm = 1;
+    t.ipt = 1;
+    const bool small = c->N <= 32768;
+    t.threads = small ? 512 : 1024;
+    t.ctas_per_sm = small ? 2 : 1;
   }
   return t;
 }

@@ -62,13 +62,14 @@ size_t force_smem_bytes(int precision, int tj) {
 // latency) and hands the sums to warp 0 for phase B; the FP64 path, whose
 // row sums are FP64 themselves, sums one body per lane.
 // ---------------------------------------------------------------------------
-constexpr int kVerletBlock = 256;
-
 template <int PREC>
 struct VerletShape {
+  // FP64: one lane per body and 64 bodies per CTA, so the FP64 work spreads
+  // over ~N/64 CTAs (every SM at N = 10k); mixed: 8 lanes per body, 32 bodies.
+  static constexpr int kBlock = PREC == 0 ? 64 : 256;
   static constexpr int kLanes = PREC == 0 ? 1 : 8;   // threads per body in phase A
   static constexpr int kUnroll = PREC == 0 ? 8 : 4;  // rows per lane whose loads go out together
-  static constexpr int kBodies = kVerletBlock / kLanes;
+  static constexpr int kBodies = kBlock / kLanes;
 };
 
 // (hi, lo) pair sums: FP64 pairs for the FP64 path, float pairs for mixed.
@@ -153,7 +154,7 @@ __device__ __forceinline__ void stage_position(void *nxt, int q, size_t o, doubl
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kVerletBlock) verlet_kernel(const VerletArgs a) {
+__global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const VerletArgs a) {
   // When at most one force CTA fits on an SM, the next force grid can only
   // land one CTA per SM, however early it launches: let it launch now, so its
   // launch overlaps this kernel (its own griddepcontrol.wait still waits for
@@ -258,7 +259,7 @@ cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bo
   cudaLaunchConfig_t cfg = {};
   const int64_t nb = precision == 0 ? VerletShape<0>::kBodies : VerletShape<1>::kBodies;
   cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + nb - 1) / nb));
-  cfg.blockDim = dim3(kVerletBlock);
+  cfg.blockDim = dim3(precision == 0 ? VerletShape<0>::kBlock : VerletShape<1>::kBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -279,7 +280,7 @@ cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bo
 //             AR = v, AV = a, v_2 = v + dt/2 a, stage r_2 = r + dt/2 v.
 // ---------------------------------------------------------------------------
 template <int PREC>
-__global__ void __launch_bounds__(kVerletBlock) rk_stage_kernel(const RkArgs a) {
+__global__ void __launch_bounds__(VerletShape<PREC>::kBlock) rk_stage_kernel(const RkArgs a) {
   if (a.release_early) grid_dependency_launch();
   typedef typename std::conditional<PREC == 0, double, float>::type T;
   constexpr int L = VerletShape<PREC>::kLanes, NB = VerletShape<PREC>::kBodies;
@@ -384,7 +385,7 @@ cudaError_t launch_rk_stage(int precision, const RkArgs &a, cudaStream_t s, bool
   cudaLaunchConfig_t cfg = {};
   const int64_t nb = precision == 0 ? VerletShape<0>::kBodies : VerletShape<1>::kBodies;
   cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + nb - 1) / nb));
-  cfg.blockDim = dim3(kVerletBlock);
+  cfg.blockDim = dim3(precision == 0 ? VerletShape<0>::kBlock : VerletShape<1>::kBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
