@@ -269,7 +269,9 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
           // Both visit the pairs in ascending order and give the same terms
           // for non-self pairs, so the split does not change the sum.
           auto unmasked = [&](int b0, int b1) {
-#pragma unroll 4
+            // (IPT 1 is capped at 64 registers: unrolling this rarer path
+            // would spill.)
+#pragma unroll(IPT == 1 ? 1 : 4)
             for (int b = b0; b < b1; ++b) {
               const ulonglong2 *pb = src + 4 * (g0 + b);
               const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
