@@ -128,3 +128,23 @@ def test_rk4_unsupported_calls(nb):
     st = nb.nbody_init(ctypes.byref(ctx), 1, off, *([b.state[0].data_ptr()] * 6 + [b.m.data_ptr()]),
                        ctypes.byref(opts), None)
     assert st == nb.NBODY_EINVAL and not ctx.value
+
+
+def test_rk4_edge_cases(nb):
+    """One body (no force): RK4 moves it on its straight line; massless bodies
+    (every term of Eq. 1 is 0) likewise, in both precisions; n_steps = 0 is a
+    no-op."""
+    one = nb.NBody(np.array([[1.0], [2.0], [3.0]]), np.array([[0.1], [0.0], [-0.2]]), np.array([1.0]),
+                   G=1.0, dt=0.5, precision="fp64", integrator="rk4")
+    one.step(4)
+    np.testing.assert_allclose(one.r.cpu().numpy()[:, 0], [1.2, 2.0, 2.6], rtol=1e-15)
+    assert np.all(one.accel().cpu().numpy() == 0.0)
+    one.step(0)
+    rng = np.random.default_rng(5)
+    r = rng.uniform(-3, 3, (3, 300))
+    v = rng.uniform(-0.1, 0.1, (3, 300))
+    for prec in ("fp64", "mixed"):
+        b = nb.NBody(r, v, np.zeros(300), G=1.0, dt=0.25, precision=prec, integrator="rk4")
+        b.step(8)
+        np.testing.assert_allclose(b.r.cpu().numpy(), r + 2.0 * v, rtol=0, atol=1e-14)
+        np.testing.assert_array_equal(b.v.cpu().numpy(), v)
