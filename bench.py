@@ -512,6 +512,8 @@ def extras(torch, nbody, inputs, stream, device, args):
     pairs = sum(e.n * (e.n - 1) for e in ens)
     with torch.cuda.stream(stream):
         b = nbody.NBody(r, v, m, off, G=inputs.G_AU_DAY, dt=inputs.DT_DAY, precision="mixed", device=device)
+        if not args.no_autotune:
+            b.autotune(probe_steps=1)  # the work line of uneven systems has its own best tiles
         b.step(2)
         n_ens = 5
         t = timed(torch, stream, lambda: b.step(n_ens))
