@@ -162,41 +162,53 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
   if (a.release_early) grid_dependency_launch();
   typedef typename std::conditional<PREC == 0, double, float>::type T;
   constexpr int L = VerletShape<PREC>::kLanes, NB = VerletShape<PREC>::kBodies;
+  // Phase B: FP64 path one thread per body (all three components); mixed
+  // path warp c < 3 takes component c of the CTA's 32 bodies, lane = body,
+  // so each warp issues a third of the FP64 instructions (GB300's FP64 pipe
+  // spends 64 cycles on every warp instruction, so this is the latency).
+  constexpr bool kSplit = PREC == 1;
   __shared__ T s_hi[3][NB], s_lo[3][NB];
   const int p0 = blockIdx.x * NB;
   const int b = threadIdx.x / L, lane = threadIdx.x % L;
   const int p = p0 + b;  // phase A body
   const bool live = p < a.N;
   const size_t N = static_cast<size_t>(a.N);
-  const int q = p0 + threadIdx.x;  // phase B body
-  const bool own = threadIdx.x < NB && q < a.N;
+  const int warp = threadIdx.x >> 5;
+  const int k = kSplit ? (threadIdx.x & 31) : threadIdx.x;  // phase B body within the CTA
+  const int q = p0 + k;
+  const int comp = kSplit ? warp : 0;
+  const bool own = (kSplit ? warp < 3 : threadIdx.x < NB) && q < a.N;
   const bool step = a.mode == kModeStep;
+  // This thread's component arrays (mixed split; the FP64 path uses all three).
+  auto pick = [&](double *x, double *y, double *z) { return comp == 0 ? x : comp == 1 ? y : z; };
+  double *const Xc = pick(a.x, a.y, a.z), *const Vc = pick(a.vx, a.vy, a.vz), *const Ac = pick(a.ax, a.ay, a.az);
+  double *const Rc = pick(a.Rx, a.Ry, a.Rz);
 
   // Before the wait: everything this step's force kernel does not write (it
   // writes only the partial rows), so these loads overlap its tail.
   const int rows = live ? a.nsl[p] : 0;
-  double vx = 0.0, vy = 0.0, vz = 0.0, aox = 0.0, aoy = 0.0, aoz = 0.0, rx = 0.0, ry = 0.0, rz = 0.0, mu = 0.0;
+  double v[3] = {0, 0, 0}, ao[3] = {0, 0, 0}, r[3] = {0, 0, 0}, mu = 0.0;
   float muf = 0.f;
   size_t o = 0;
   if (own && step) {
-    vx = a.vx[q];
-    vy = a.vy[q];
-    vz = a.vz[q];
-    aox = a.ax[q];
-    aoy = a.ay[q];
-    aoz = a.az[q];
-    if (PREC == 0) {
-      const double4_32a r = static_cast<const double4_32a *>(a.cur)[q];
-      rx = r.x;
-      ry = r.y;
-      rz = r.z;
-      mu = r.w;
-    } else {
-      rx = a.Rx[q];
-      ry = a.Ry[q];
-      rz = a.Rz[q];
+    if (kSplit) {
+      v[0] = Vc[q];
+      ao[0] = Ac[q];
+      r[0] = Rc[q];
       o = pair_off(a.qidx[q]);
-      muf = static_cast<const float *>(a.cur)[o + kMu];
+      if (comp == 0) muf = static_cast<const float *>(a.cur)[o + kMu];
+    } else {
+      v[0] = a.vx[q];
+      v[1] = a.vy[q];
+      v[2] = a.vz[q];
+      ao[0] = a.ax[q];
+      ao[1] = a.ay[q];
+      ao[2] = a.az[q];
+      const double4_32a rr = static_cast<const double4_32a *>(a.cur)[q];
+      r[0] = rr.x;
+      r[1] = rr.y;
+      r[2] = rr.z;
+      mu = rr.w;
     }
   }
   grid_dependency_wait();  // the force partials of this step are complete
@@ -218,35 +230,47 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
     return;
   }
 
-  // ---- phase B: Eqs. 4 and 3 for body q, one body per thread ----------------
-  const int k = threadIdx.x;
-  const double anx = static_cast<double>(s_hi[0][k]) + static_cast<double>(s_lo[0][k]);
-  const double any = static_cast<double>(s_hi[1][k]) + static_cast<double>(s_lo[1][k]);
-  const double anz = static_cast<double>(s_hi[2][k]) + static_cast<double>(s_lo[2][k]);
-  if (!finite3(anx, any, anz)) atomicOr(a.flags, kFlagNonFinite);
-  if (step) {
-    vx = kick(vx, aox, anx, a.half_dt);
-    vy = kick(vy, aoy, any, a.half_dt);
-    vz = kick(vz, aoz, anz, a.half_dt);
-    const double nx = drift(rx, vx, anx, a.dt, a.half_dt2);
-    const double ny = drift(ry, vy, any, a.dt, a.half_dt2);
-    const double nz = drift(rz, vz, anz, a.dt, a.half_dt2);
-    if (PREC == 1) {
-      a.Rx[q] = nx;
-      a.Ry[q] = ny;
-      a.Rz[q] = nz;
+  // ---- phase B: Eqs. 4 and 3 ---------------------------------------------------
+  if (kSplit) {  // component `comp` of body q
+    const double an = static_cast<double>(s_hi[comp][k]) + static_cast<double>(s_lo[comp][k]);
+    if (!isfinite(an)) atomicOr(a.flags, kFlagNonFinite);
+    if (step) {
+      const double vn = kick(v[0], ao[0], an, a.half_dt);
+      const double nr = drift(r[0], vn, an, a.dt, a.half_dt2);
+      Rc[q] = nr;
+      float *w = static_cast<float *>(a.nxt) + o;
+      const float h = hi_part(nr);
+      w[kXh + 2 * comp] = h;
+      w[kXl + 2 * comp] = lo_part(nr, h);
+      if (comp == 0) w[kMu] = muf;
+      Xc[q] = r[0];
+      Vc[q] = vn;
     }
-    stage_position<PREC>(a.nxt, q, o, nx, ny, nz, mu, muf);
-    a.x[q] = rx;
-    a.y[q] = ry;
-    a.z[q] = rz;
-    a.vx[q] = vx;
-    a.vy[q] = vy;
-    a.vz[q] = vz;
+    Ac[q] = an;
+  } else {  // body q, all three components
+    double an[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) an[c] = static_cast<double>(s_hi[c][k]) + static_cast<double>(s_lo[c][k]);
+    if (!finite3(an[0], an[1], an[2])) atomicOr(a.flags, kFlagNonFinite);
+    if (step) {
+      double nr[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[c] = kick(v[c], ao[c], an[c], a.half_dt);
+        nr[c] = drift(r[c], v[c], an[c], a.dt, a.half_dt2);
+      }
+      stage_position<PREC>(a.nxt, q, o, nr[0], nr[1], nr[2], mu, muf);
+      a.x[q] = r[0];
+      a.y[q] = r[1];
+      a.z[q] = r[2];
+      a.vx[q] = v[0];
+      a.vy[q] = v[1];
+      a.vz[q] = v[2];
+    }
+    a.ax[q] = an[0];
+    a.ay[q] = an[1];
+    a.az[q] = an[2];
   }
-  a.ax[q] = anx;
-  a.ay[q] = any;
-  a.az[q] = anz;
   // Otherwise only now may the next force launch be placed: its CTAs then
   // land on an idle GPU, one share per slot, as the equal-share decomposition
   // assumes (an early launch let several CTAs pile onto the SMs that freed
@@ -284,39 +308,45 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) rk_stage_kernel(con
   if (a.release_early) grid_dependency_launch();
   typedef typename std::conditional<PREC == 0, double, float>::type T;
   constexpr int L = VerletShape<PREC>::kLanes, NB = VerletShape<PREC>::kBodies;
+  constexpr bool kSplit = PREC == 1;  // mixed: warp c < 3 takes component c (as the Verlet kernel)
   __shared__ T s_hi[3][NB], s_lo[3][NB];
   const int p0 = blockIdx.x * NB;
   const int b = threadIdx.x / L, lane = threadIdx.x % L;
   const int p = p0 + b;
   const bool live = p < a.N;
   const size_t N = static_cast<size_t>(a.N);
-  const int q = p0 + threadIdx.x;
-  const bool own = threadIdx.x < NB && q < a.N;
+  const int warp = threadIdx.x >> 5;
+  const int k0 = kSplit ? (threadIdx.x & 31) : threadIdx.x;
+  const int q = p0 + k0;
+  const int comp = kSplit ? warp : 0;
+  const bool own = (kSplit ? warp < 3 : threadIdx.x < NB) && q < a.N;
   const int rows = live ? a.nsl[p] : 0;
-  // Prefetch what the force launch does not write (the state, the RK sums).
-  double rn[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, vs[3] = {0, 0, 0}, ar[3] = {0, 0, 0}, av[3] = {0, 0, 0}, mu = 0.0;
+  auto sel = [](int c, double *x, double *y, double *z) { return c == 0 ? x : c == 1 ? y : z; };
+  // Prefetch what the force launch does not write (the state, the RK sums):
+  // component comp (mixed) or all three (FP64).
+  constexpr int NC = kSplit ? 1 : 3;
+  double rn[NC], vn[NC], vs[NC], ar[NC], av[NC], mu = 0.0;
   float muf = 0.f;
   size_t o = 0;
-  if (own) {
-    rn[0] = a.x[q];
-    rn[1] = a.y[q];
-    rn[2] = a.z[q];
-    vn[0] = a.vx[q];
-    vn[1] = a.vy[q];
-    vn[2] = a.vz[q];
-    if (a.stage <= 4) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        vs[k] = a.V[k * N + q];
-        ar[k] = a.AR[k * N + q];
-        av[k] = a.AV[k * N + q];
+  for (int j = 0; j < NC; ++j) rn[j] = vn[j] = vs[j] = ar[j] = av[j] = 0.0;
+  if (own) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int c = kSplit ? comp : j;
+      rn[j] = sel(c, a.x, a.y, a.z)[q];
+      vn[j] = sel(c, a.vx, a.vy, a.vz)[q];
+      if (a.stage <= 4) {
+        vs[j] = a.V[c * N + q];
+        ar[j] = a.AR[c * N + q];
+        av[j] = a.AV[c * N + q];
       }
     }
     if (PREC == 0) {
       mu = static_cast<const double4_32a *>(a.cur)[q].w;
     } else {
       o = pair_off(a.qidx[q]);
-      muf = static_cast<const float *>(a.cur)[o + kMu];
+      if (comp == 0) muf = static_cast<const float *>(a.cur)[o + kMu];
     }
   }
   grid_dependency_wait();  // the force partials of this stage are complete
@@ -335,48 +365,44 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) rk_stage_kernel(con
     if (!a.release_early) grid_dependency_launch();
     return;
   }
-  const int k0 = threadIdx.x;
-  double as[3];
+  bool finite = true;
+  double rnext[NC];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) as[k] = static_cast<double>(s_hi[k][k0]) + static_cast<double>(s_lo[k][k0]);
-  if (!finite3(as[0], as[1], as[2])) atomicOr(a.flags, kFlagNonFinite);
-  double rnext[3];
-  if (a.stage == 2 || a.stage == 3) {
-    const double c = a.stage == 2 ? 0.5 * a.dt : a.dt;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      a.AR[k * N + q] = ar[k] + 2.0 * vs[k];
-      a.AV[k * N + q] = av[k] + 2.0 * as[k];
-      rnext[k] = rn[k] + c * vs[k];
-      a.V[k * N + q] = vn[k] + c * as[k];
-    }
-  } else if (a.stage == 4) {
-    const double h = a.dt / 6.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      rnext[k] = rn[k] + h * (ar[k] + vs[k]);
-      vn[k] = vn[k] + h * (av[k] + as[k]);
-    }
-    a.x[q] = rnext[0];
-    a.y[q] = rnext[1];
-    a.z[q] = rnext[2];
-    a.vx[q] = vn[0];
-    a.vy[q] = vn[1];
-    a.vz[q] = vn[2];
-  } else {  // s = 5: A at the new state, then stage 1 of the next step
-    a.ax[q] = as[0];
-    a.ay[q] = as[1];
-    a.az[q] = as[2];
-    const double c = 0.5 * a.dt;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      a.AR[k * N + q] = vn[k];
-      a.AV[k * N + q] = as[k];
-      rnext[k] = rn[k] + c * vn[k];
-      a.V[k * N + q] = vn[k] + c * as[k];
+  for (int j = 0; j < NC; ++j) {
+    const int c = kSplit ? comp : j;
+    const size_t i = c * N + q;
+    const double as = static_cast<double>(s_hi[c][k0]) + static_cast<double>(s_lo[c][k0]);
+    finite = finite && isfinite(as);
+    if (a.stage == 2 || a.stage == 3) {
+      const double cc = a.stage == 2 ? 0.5 * a.dt : a.dt;
+      a.AR[i] = ar[j] + 2.0 * vs[j];
+      a.AV[i] = av[j] + 2.0 * as;
+      rnext[j] = rn[j] + cc * vs[j];
+      a.V[i] = vn[j] + cc * as;
+    } else if (a.stage == 4) {
+      const double h = a.dt / 6.0;
+      rnext[j] = rn[j] + h * (ar[j] + vs[j]);
+      sel(c, a.x, a.y, a.z)[q] = rnext[j];
+      sel(c, a.vx, a.vy, a.vz)[q] = vn[j] + h * (av[j] + as);
+    } else {  // s = 5: A at the new state, then stage 1 of the next step
+      sel(c, a.ax, a.ay, a.az)[q] = as;
+      const double cc = 0.5 * a.dt;
+      a.AR[i] = vn[j];
+      a.AV[i] = as;
+      rnext[j] = rn[j] + cc * vn[j];
+      a.V[i] = vn[j] + cc * as;
     }
   }
-  stage_position<PREC>(a.nxt, q, o, rnext[0], rnext[1], rnext[2], mu, muf);
+  if (!finite) atomicOr(a.flags, kFlagNonFinite);
+  if (kSplit) {
+    float *w = static_cast<float *>(a.nxt) + o;
+    const float h = hi_part(rnext[0]);
+    w[kXh + 2 * comp] = h;
+    w[kXl + 2 * comp] = lo_part(rnext[0], h);
+    if (comp == 0) w[kMu] = muf;
+  } else {
+    stage_position<PREC>(a.nxt, q, o, rnext[0], rnext[NC > 1 ? 1 : 0], rnext[NC > 2 ? 2 : 0], mu, muf);
+  }
   if (!a.release_early) grid_dependency_launch();
 }
 
