@@ -464,7 +464,8 @@ def timed(torch, stream, fn, reps=1):
 
 
 def extras(torch, nbody, inputs, stream, device, args):
-    """Adjoint cost, the 31-body model, the uneven ensemble and (optionally) the N sweep."""
+    """Adjoint cost, the 31-body model, RK4, the uneven ensemble, N = 1M in both precisions,
+    and (optionally) the full N sweep and the dt sweep."""
     out = {}
     # adjoint on the 10,425-body model: backward wall / (T x forward step)
     s = inputs.solar_system(args.n)
@@ -547,11 +548,13 @@ def extras(torch, nbody, inputs, stream, device, args):
             for key in ("fp64", "mixed", "fp64_rk4", "mixed_rk4"):
                 b2[key + "_order"] = float(np.log2(a[key] / b2[key]))
         out["dt_sweep"] = {"bodies": sd.n, "days": 73.0, "max_rel_energy_drift": rows}
-    if args.sweep:
-        # Autotuned up to 65,536 bodies; larger N reuse the 65,536-body winner
-        # (tuning there would cost minutes).  FP64 at 1M bodies is one ~30 s step.
+    # N sweep.  By default only N = 1,048,576 (the metric's second size, mixed
+    # and FP64, the library's default tiles: tuning there would cost minutes);
+    # --sweep adds 16,384 / 65,536 (autotuned) and 262,144 (their winner).
+    # FP64 at 1M bodies is one ~31 s step.
+    if not args.no_extras:
         tuned = {}
-        for n in (16384, 65536, 262144, 1048576):
+        for n in ((16384, 65536, 262144, 1048576) if args.sweep else (1048576,)):
             sn = inputs.solar_system(n)
             row = {}
             for prec in ("mixed", "fp64"):
@@ -561,7 +564,7 @@ def extras(torch, nbody, inputs, stream, device, args):
                     b = nbody.NBody(sn.r, sn.v, sn.m, G=sn.G, dt=sn.dt, precision=prec, device=device)
                     if n <= 65536:
                         tuned[prec] = b.autotune(probe_steps=4 if prec == "mixed" else 1)[0]
-                    else:
+                    elif prec in tuned:
                         b.tiles = tuned[prec]
                         b.reset()
                     k = 1 if prec == "fp64" and n > 65536 else 2 if n >= 262144 else 5
