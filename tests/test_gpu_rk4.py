@@ -148,3 +148,30 @@ def test_rk4_edge_cases(nb):
         b.step(8)
         np.testing.assert_allclose(b.r.cpu().numpy(), r + 2.0 * v, rtol=0, atol=1e-14)
         np.testing.assert_array_equal(b.v.cpu().numpy(), v)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_rk4_batched_uneven_systems(nb, precision):
+    """Uneven independent systems (one with two bodies) in one RK4 context:
+    each matches the oracle's RK4 run on its own (FP64: 10 steps within
+    1e-12 AU; mixed: one step within the force-error bound)."""
+    spec = [(31, 41), (700, 42), (1531, 43)]
+    systems = [inputs.solar_system(n, seed=sd, n_moons=0) for n, sd in spec]
+    systems.insert(1, inputs.System(r=np.array([[1.0, 1.3], [0.0, 0.1], [0.0, 0.0]]),
+                                    v=np.array([[0.0, 0.0], [0.01, -0.01], [0.0, 0.001]]),
+                                    m=np.array([1e-3, 2e-3])))
+    off, r, v, m = inputs.concat(systems)
+    G, dt = inputs.G_AU_DAY, inputs.DT_DAY
+    steps = 10 if precision == "fp64" else 1
+    b = nb.NBody(r, v, m, off, G=G, dt=dt, precision=precision, integrator="rk4")
+    b.step(steps)
+    rg, vg = b.r.cpu().numpy(), b.v.cpu().numpy()
+    for k, sysk in enumerate(systems):
+        sl = slice(off[k], off[k + 1])
+        r_ref, v_ref, _ = oracle.rk4(G, dt, steps, sysk.r, sysk.v, sysk.m)
+        if precision == "fp64":
+            assert np.abs(rg[:, sl] - r_ref).max() <= 1e-12 * max(1.0, np.abs(r_ref).max())
+        else:
+            T = oracle.term_norm(G, sysk.r, sysk.m)
+            dr = np.linalg.norm(rg[:, sl] - r_ref, axis=0)
+            assert np.all(dr <= 2 * dt**2 * 2e-6 * T + 1e-15 * np.linalg.norm(r_ref, axis=0)), k
