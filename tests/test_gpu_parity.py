@@ -318,6 +318,37 @@ def test_mixed_1m_sampled_rows(nb):
     _check_accel("mixed", a[:, rows], ref, tn)
 
 
+def test_fp64_1m_sampled_rows(nb):
+    """The N = 1,048,576 model in the FP64 path (one ~31 s force evaluation at
+    init, the bench's FP64 launch configuration): sampled rows against the
+    oracle's Eq. 1 for those rows, to the FP64 tolerance."""
+    s = inputs.solar_system(1 << 20, seed=32)
+    b = _make(nb, s, "fp64")
+    a = b.accel().cpu().numpy()
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([np.arange(0, 131), rng.choice(s.n, 61, replace=False), [s.n - 1]])
+    ref = oracle.accel_rows(s.G, s.r, s.m, rows, openmp=True)
+    tn = oracle.term_norm(s.G, s.r, s.m, rows, openmp=True)
+    _check_accel("fp64", a[:, rows], ref, tn)
+
+
+def test_ensemble_full_size_sampled_rows(nb):
+    """The 256-system uneven ensemble at full size (2.8M bodies, one context,
+    mixed, the bench's configuration): Eq. 1 at init for sampled bodies of 16
+    systems against the oracle run on each system alone."""
+    ens = inputs.ensemble(256)
+    off, r, v, m = inputs.concat(ens)
+    b = nb.NBody(r, v, m, off, G=inputs.G_AU_DAY, dt=inputs.DT_DAY, precision="mixed")
+    a = b.accel().cpu().numpy()
+    rng = np.random.default_rng(2)
+    for k in rng.choice(256, 16, replace=False):
+        e = ens[k]
+        rows = np.concatenate([np.arange(0, 131, 13), rng.choice(e.n, 20, replace=False), [e.n - 1]])
+        ref = oracle.accel_rows(e.G, e.r, e.m, rows, openmp=True)
+        tn = oracle.term_norm(e.G, e.r, e.m, rows, openmp=True)
+        _check_accel("mixed", a[:, off[k] + rows], ref, tn)
+
+
 def test_fp64_time_reversibility(nb):
     s = inputs.solar_system(131, seed=12, n_moons=0)  # resolved orbits only
     b = _make(nb, s, "fp64")

@@ -175,3 +175,21 @@ def test_rk4_batched_uneven_systems(nb, precision):
             T = oracle.term_norm(G, sysk.r, sysk.m)
             dr = np.linalg.norm(rg[:, sl] - r_ref, axis=0)
             assert np.all(dr <= 2 * dt**2 * 2e-6 * T + 1e-15 * np.linalg.norm(r_ref, axis=0)), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_rk4_full_size_10425(nb, precision):
+    """The 10,425-body model (moons included): FP64 3 RK4 steps within
+    1e-12 AU of the oracle; mixed one step within the force-error bound."""
+    s = inputs.solar_system(10425)
+    steps = 3 if precision == "fp64" else 1
+    b = _rk(nb, s, precision)
+    b.step(steps)
+    r_ref, _, _ = oracle.rk4(s.G, s.dt, steps, s.r, s.v, s.m, openmp=True)
+    rg = b.r.cpu().numpy()
+    if precision == "fp64":
+        assert np.abs(rg - r_ref).max() <= 1e-12
+    else:
+        T = oracle.term_norm(s.G, s.r, s.m, openmp=True)
+        dr = np.linalg.norm(rg - r_ref, axis=0)
+        assert np.all(dr <= 2 * s.dt**2 * 2e-6 * T + 1e-15 * np.linalg.norm(r_ref, axis=0)), (dr / T).max()
