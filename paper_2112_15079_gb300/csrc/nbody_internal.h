@@ -57,6 +57,7 @@ struct ForceArgs {
   int32_t n_dyn;
   int32_t N;
   int32_t tj;
+  int32_t stall;  // test hook: CTA 0 never issues its first source tile (its bounded wait runs out)
 };
 
 enum Mode : int32_t {

@@ -510,6 +510,34 @@ def test_autotune_restores_state_and_keeps_parity(nb, precision):
                  oracle.term_norm(s.G, s.r, s.m, openmp=True))
 
 
+def test_bounded_wait_timeout_reports_and_recovers(nb, monkeypatch):
+    """A device wait that nothing completes: NBODY_INJECT_WAIT_STALL=k leaves
+    the first source tile of CTA 0 unissued in the context's k-th force
+    launch.  That CTA's bounded mbarrier wait runs out (2 s), it drains and
+    leaves, the next synchronous call reports ETIMEOUT, and the context stays
+    usable: after nbody_reset its steps equal a fresh context's from the same
+    state."""
+    import time
+    s = inputs.solar_system(2131, seed=51)
+    monkeypatch.setenv("NBODY_INJECT_WAIT_STALL", "3")  # init: launch 1; steps: 2, 3
+    b = _make(nb, s, "mixed", graphs=False)
+    monkeypatch.delenv("NBODY_INJECT_WAIT_STALL")
+    b.step(1)
+    b.sync()
+    t0 = time.time()
+    b.step(1)
+    with pytest.raises(nb.NBodyError) as ei:
+        b.sync()
+    assert ei.value.status == nb.NBODY_ETIMEOUT
+    assert time.time() - t0 < 60
+    b.reset()
+    before = b.state.cpu().numpy()
+    b.step(5)
+    c = nb.NBody(before[0:3], before[3:6], s.m, G=s.G, dt=s.dt, precision="mixed", graphs=False)
+    c.step(5)
+    assert np.array_equal(b.state.cpu().numpy(), c.state.cpu().numpy())
+
+
 def test_nondefault_stream(nb):
     torch = pytest.importorskip("torch")
     s = inputs.solar_system(700, seed=5)
