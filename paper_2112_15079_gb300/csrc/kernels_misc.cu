@@ -1,4 +1,7 @@
-// Staging / pre-drift kernel, energy kernels, and the force-launch dispatcher.
+// Per-body kernels around the Eq. 1 force launches: the Verlet step
+// completion (Eqs. 4 and 3), the RK4 stage completion and stage-1 prep, the
+// staging / pre-drift kernel, the energy kernels, and the force-launch
+// dispatcher.
 #include <type_traits>
 
 #include "nbody_dev.cuh"
