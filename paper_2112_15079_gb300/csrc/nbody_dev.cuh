@@ -14,17 +14,12 @@ namespace nb {
 // mbarrier and 1-D bulk copies global -> shared (cp.async.bulk, the TMA unit)
 // ---------------------------------------------------------------------------
 
-// A wait on an mbarrier is declared lost after kWaitNs of global time (a
-// tile lands in microseconds), or after kWaitPolls polls should the timer
-// not advance; either way the kernel records a fault and winds down.
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
-constexpr uint32_t kWaitPolls = 1u << 26;
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
+// Upper bound on mbarrier.try_wait polls before a wait is declared lost.
+// Each poll of a phase that does not complete suspends the thread for the
+// hardware's own limit (measured on GB300: ~1.9 us), so 2^20 polls are
+// ~2 s, while a source tile lands in microseconds.  (An explicit timer or
+// suspend-time hint in this loop cost the force kernels registers.)
+constexpr uint32_t kWaitPolls = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -58,17 +53,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Wait for the phase with the given parity to complete; false if the poll
 // budget ran out (the caller records kFlagTimeout and winds down).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  unsigned long long t0 = 0;
-  for (uint32_t i = 0; i < kWaitPolls; ++i) {
+  for (uint32_t i = 0; i < kWaitPolls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u) {  // the timer is read only on waits that are already long
-      const unsigned long long t = global_ns();
-      if (t0 == 0)
-        t0 = t;
-      else if (t - t0 > kWaitNs)
-        return false;
-    }
-  }
   return false;
 }
 
