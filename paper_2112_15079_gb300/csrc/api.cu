@@ -74,8 +74,8 @@ struct nbody_ctx {
   // scratch
   std::vector<void *> allocs;
   int alloc_seq = 0;  // device allocations made so far (fault injection counts these)
-  int64_t force_seq = 0;     // force launches prepared so far
-  int64_t stall_at = 0;      // test hook (NBODY_INJECT_WAIT_STALL=k): the k-th force launch stalls
+  int64_t vjp_seq = 0;       // adjoint products launched so far
+  int64_t stall_at = 0;      // test hook (NBODY_INJECT_WAIT_STALL=k): the k-th product stalls
   double *a = nullptr;               // [3][N] acceleration at the current positions
   void *stage[2] = {nullptr, nullptr};  // ping-pong staged sources (layout per precision)
   int64_t n_stage = 0;               // stage entries (mixed: systems padded to even length)
@@ -370,7 +370,6 @@ nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check, void 
 
 nb::ForceArgs force_args(nbody_ctx *c, const void *cur) {
   nb::ForceArgs a{};
-  a.stall = ++c->force_seq == c->stall_at ? 1 : 0;
   a.cur = cur;
   a.partial = c->fw.partial;
   a.flags = c->flags;
@@ -705,8 +704,10 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (c->o.ckpt_every == 0) c->o.ckpt_every = 100;
   c->user_stream = static_cast<cudaStream_t>(cuda_stream);
   // Optional host-side test hook: NBODY_INJECT_WAIT_STALL=k leaves the first
-  // source tile of CTA 0 unissued in the context's k-th force launch, so that
-  // CTA's bounded wait runs out and the next synchronous call reports ETIMEOUT.
+  // source tile of CTA 0 unissued in the context's k-th adjoint product (VJP
+  // launch), so that CTA's bounded wait runs out and nbody_grad reports
+  // ETIMEOUT.  (It lives in the adjoint kernel so the force kernels carry no
+  // test code.)
   if (const char *inj = std::getenv("NBODY_INJECT_WAIT_STALL")) c->stall_at = std::atoll(inj);
 
   auto bail = [&](nbody_status st) {
@@ -1059,6 +1060,7 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   vj.tj = kVjpTile;
   auto product = [&](const void *pos, int mode) -> nbody_status {
     vj.pos = pos;
+    vj.stall = ++c->vjp_seq == c->stall_at ? 1 : 0;
     NB_CUDA(c, nb::launch_vjp(prec, A.vj.grid, A.vj.smem, vj, c->stream));
     ad.mode = mode;
     NB_CUDA(c, nb::launch_adjoint(prec, ad, c->stream));

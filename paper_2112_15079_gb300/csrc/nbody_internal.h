@@ -57,7 +57,6 @@ struct ForceArgs {
   int32_t n_dyn;
   int32_t N;
   int32_t tj;
-  int32_t stall;  // test hook: CTA 0 never issues its first source tile (its bounded wait runs out)
 };
 
 enum Mode : int32_t {
@@ -89,7 +88,7 @@ struct VerletArgs {
 // the same kind of work tables as the force kernel ([rows][4][N]).
 struct VjpArgs {
   const void *pos;  // positions staged by the forward pass (its layout)
-  const void *w;    // w per stage entry: FP64 double4, mixed float4 (x, y, z, 0)
+  const void *w;    // w per stage entry: FP64 double4; mixed pair blocks (16 B per entry)
   double *partial;  // [rows][4][N]: doubles (FP64) or float pairs (mixed)
   unsigned *flags;
   const Blk *blks;
@@ -97,6 +96,7 @@ struct VjpArgs {
   const int32_t *seg_off;  // [gridDim.x + 1]
   int32_t N;
   int32_t tj;
+  int32_t stall;  // test hook: CTA 0 never issues its first tile, so its bounded wait runs out
 };
 
 // One step of the reverse sweep per body (vjp.cu).

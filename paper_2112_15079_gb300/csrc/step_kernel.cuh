@@ -131,7 +131,6 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
 
   uint32_t phase = 0;  // bit s: parity of the next completion of stage s
   bool aborted = false;
-  bool stall = a.stall != 0 && blockIdx.x == 0;
   const size_t N = static_cast<size_t>(a.N);
   const int n_static = static_cast<int>(gridDim.x);
   int piece = blockIdx.x;
@@ -156,10 +155,8 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
                &bar[s]);
     };
     if (tid == 0) {
-      for (int t = 0; t < kStages && t < ntiles; ++t)
-        if (!(stall && t == 0)) issue(t);  // (the test hook leaves tile 0 of CTA 0 unissued)
+      for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
     }
-    stall = false;
 
     // ---- targets into registers ---------------------------------------
     int pidx[IPT], tq[IPT];

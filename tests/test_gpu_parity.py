@@ -512,30 +512,31 @@ def test_autotune_restores_state_and_keeps_parity(nb, precision):
 
 def test_bounded_wait_timeout_reports_and_recovers(nb, monkeypatch):
     """A device wait that nothing completes: NBODY_INJECT_WAIT_STALL=k leaves
-    the first source tile of CTA 0 unissued in the context's k-th force
-    launch.  That CTA's bounded mbarrier wait runs out (2 s), it drains and
-    leaves, the next synchronous call reports ETIMEOUT, and the context stays
-    usable: after nbody_reset its steps equal a fresh context's from the same
-    state."""
+    the first source tile of CTA 0 unissued in the context's k-th adjoint
+    product.  That CTA's bounded mbarrier wait runs out (~2 s), it drains and
+    leaves, nbody_grad reports ETIMEOUT, and the context stays usable: the
+    next gradient and the next steps equal a fresh context's bitwise."""
     import time
+    torch = pytest.importorskip("torch")
     s = inputs.solar_system(2131, seed=51)
-    monkeypatch.setenv("NBODY_INJECT_WAIT_STALL", "3")  # init: launch 1; steps: 2, 3
-    b = _make(nb, s, "mixed", graphs=False)
+    gr = torch.ones((3, s.n), dtype=torch.float64)
+    fresh = _make(nb, s, "mixed")
+    want_g = [t.cpu().numpy() for t in fresh.grad(3, gr)]
+    fresh.step(5)
+    want_s = fresh.state.cpu().numpy()
+    monkeypatch.setenv("NBODY_INJECT_WAIT_STALL", "2")  # the second product of the first gradient
+    b = _make(nb, s, "mixed")
     monkeypatch.delenv("NBODY_INJECT_WAIT_STALL")
-    b.step(1)
-    b.sync()
     t0 = time.time()
-    b.step(1)
     with pytest.raises(nb.NBodyError) as ei:
-        b.sync()
+        b.grad(3, gr)
     assert ei.value.status == nb.NBODY_ETIMEOUT
     assert time.time() - t0 < 60
-    b.reset()
-    before = b.state.cpu().numpy()
+    got = [t.cpu().numpy() for t in b.grad(3, gr)]
+    for x, y in zip(got, want_g):
+        assert np.array_equal(x, y)
     b.step(5)
-    c = nb.NBody(before[0:3], before[3:6], s.m, G=s.G, dt=s.dt, precision="mixed", graphs=False)
-    c.step(5)
-    assert np.array_equal(b.state.cpu().numpy(), c.state.cpu().numpy())
+    assert np.array_equal(b.state.cpu().numpy(), want_s)
 
 
 def test_nondefault_stream(nb):
