@@ -29,6 +29,12 @@
  * - The library owns its scratch, graphs and snapshots; nbody_free releases
  *   them.  The caller must keep the bound state buffers alive until then.
  * - A context is not thread-safe; use one context per host thread.
+ * - Fault-injection hooks for tests (environment variables, unset in normal
+ *   use): NBODY_INJECT_ALLOC_FAIL=k fails a context's k-th device allocation
+ *   with NBODY_ENOMEM; NBODY_INJECT_WAIT_STALL=k (read by nbody_init) leaves
+ *   one source copy of the context's k-th adjoint product unissued, so that
+ *   kernel's bounded wait runs out (~2 s) and nbody_grad returns
+ *   NBODY_ETIMEOUT.
  */
 #ifndef NBODY_H
 #define NBODY_H
