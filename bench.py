@@ -484,6 +484,13 @@ def extras(torch, nbody, inputs, stream, device, args):
         out.setdefault("adjoint", {})[prec] = {"steps": TT, "backward_s": bwd, "forward_step_ms": fwd * 1e3,
                                                "cost_per_forward_step": bwd / (TT * fwd), "ckpt_every": 100}
         b.close()
+        if prec == "mixed":  # one segment: every staged position kept, (T+1) x 32 B x N, no recomputation
+            with torch.cuda.stream(stream):
+                b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, ckpt_every=TT, device=device)
+                b.grad(TT, gr)
+                bwd1 = timed(torch, stream, lambda: b.grad(TT, gr))
+            out["adjoint"][prec]["cost_per_forward_step_ckpt_every_T"] = bwd1 / (TT * fwd)
+            b.close()
     # the 31-body model (one FP64 system: single-launch cluster kernel), 3650 steps
     s31 = inputs.solar_system(31)
     with torch.cuda.stream(stream):
