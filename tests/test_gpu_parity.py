@@ -539,6 +539,30 @@ def test_bounded_wait_timeout_reports_and_recovers(nb, monkeypatch):
     assert np.array_equal(b.state.cpu().numpy(), want_s)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reset_after_the_caller_changes_state_and_masses(nb, precision):
+    """nbody_reset re-reads the bound state: new positions and masses (a third
+    of them zero: test particles) give Eq. 1 at the new state, and the snapshot
+    for nbody_grad is the new state."""
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(2131, seed=61)
+    b = _make(nb, s, precision)
+    b.step(3)
+    rng = np.random.default_rng(8)
+    r2 = s.r * (1 + 1e-3 * rng.normal(size=s.r.shape))
+    m2 = s.m.copy()
+    m2[rng.choice(s.n, s.n // 3, replace=False)] = 0.0
+    b.state[0:3].copy_(torch.tensor(r2))
+    b.m.copy_(torch.tensor(m2))
+    b.reset()
+    ref = oracle.accel(s.G, r2, m2, openmp=True)
+    _check_accel(precision, b.accel().cpu().numpy(), ref, oracle.term_norm(s.G, r2, m2, openmp=True))
+    c = nb.NBody(b.r.cpu().numpy(), b.v.cpu().numpy(), m2, G=s.G, dt=s.dt, precision=precision)
+    gr = torch.ones((3, s.n), dtype=torch.float64)
+    for x, y in zip(b.grad(2, gr), c.grad(2, gr)):
+        assert torch.equal(x, y)
+
+
 def test_nondefault_stream(nb):
     torch = pytest.importorskip("torch")
     s = inputs.solar_system(700, seed=5)
