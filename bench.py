@@ -5,9 +5,13 @@ Workload (the paper's 10,425-body Solar-System model, Section 2, as seeded
 synthetic stand-in): N = 10,425 bodies (Sun, 30 major bodies, 100 moons,
 10,294 main-belt asteroids), dt = 0.1 day.  One benchmark "step" is one
 ``nbody_step(S)`` call advancing the system by S velocity-Verlet steps
-(default S = 100, i.e. 10 days); each Verlet step is one launch of the fused
-force + kick + drift kernel.  The headline ``value`` is the mixed-precision
-path; the FP64 path is measured the same way and reported under "fp64".
+(default S = 100, i.e. 10 days); each Verlet step is an Eq. 1 force launch
+and a per-body Verlet launch (kick, drift, staging), chained with
+programmatic dependent launch and replayed from CUDA graphs.  The headline
+``value`` is the mixed-precision path; the FP64 path is measured the same way
+and reported under "fp64".  The roofline object describes the force kernel:
+its flops per launch over its mean event-timed duration (the same workload,
+each kernel launched alone by ``nbody_kernel_times``).
 
     interactions/s = N (N - 1) * S * K / (timed seconds)
 
