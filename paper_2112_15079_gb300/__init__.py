@@ -11,4 +11,4 @@ Submodules:
 Nothing is imported eagerly, so the CPU-only parts stay importable on a
 machine without the built library.
 """
-__all__ = ["inputs", "nbody"]
+__all__ = ["inputs", "nbody", "autograd"]
