@@ -78,6 +78,8 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
             lib.oracle_verlet.restype = ctypes.c_int
             lib.oracle_rk4.argtypes = lib.oracle_verlet.argtypes
             lib.oracle_rk4.restype = ctypes.c_int
+            lib.oracle_leapfrog.argtypes = lib.oracle_verlet.argtypes
+            lib.oracle_leapfrog.restype = ctypes.c_int
             lib.oracle_energy.argtypes = [_I64, ctypes.c_double] + [_D] * 9
             lib.oracle_energy.restype = None
             lib.oracle_vjp.argtypes = [_I64, ctypes.c_double] + [_D] * 11
@@ -158,6 +160,23 @@ def verlet(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: n
                                     _c(m), _c(a[0]), _c(a[1]), _c(a[2]))
     if rc != 0:
         raise MemoryError("oracle_verlet: allocation failed")
+    return r, v, a
+
+
+def leapfrog(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: np.ndarray,
+             openmp: bool = False):
+    """Drift-kick-drift leapfrog (Section 2 names leapfrog beside Verlet) for
+    n_steps from (r, v) [3, n]; returns (r, v, a) after the steps, a = Eq. 1
+    at the last half-step positions."""
+    r = _f64(r).copy()
+    v = _f64(v).copy()
+    m = _f64(m)
+    a = np.zeros_like(r)
+    rc = _lib(openmp).oracle_leapfrog(m.shape[0], G, dt, int(n_steps),
+                                      _c(r[0]), _c(r[1]), _c(r[2]), _c(v[0]), _c(v[1]), _c(v[2]),
+                                      _c(m), _c(a[0]), _c(a[1]), _c(a[2]))
+    if rc != 0:
+        raise MemoryError("oracle_leapfrog: allocation failed")
     return r, v, a
 
 

@@ -146,6 +146,32 @@ int oracle_verlet(int64_t n, double G, double dt, int64_t n_steps, double *x,
   return 0;
 }
 
+/* The leapfrog method Section 2 names beside Verlet, in its
+ * drift-kick-drift form: the force is taken at the half-step positions,
+ *   r_{n+1/2} = r_n + (dt/2) v_n,
+ *   v_{n+1}   = v_n + dt A(r_{n+1/2}),
+ *   r_{n+1}   = r_{n+1/2} + (dt/2) v_{n+1},
+ * so positions and velocities are reported at the same (integer) times.
+ * One evaluation of Eq. 1 per step; on return (ax, ay, az) = A at the last
+ * half-step positions.  Returns 0, or -1 if scratch could not be allocated. */
+int oracle_leapfrog(int64_t n, double G, double dt, int64_t n_steps, double *x,
+                    double *y, double *z, double *vx, double *vy, double *vz,
+                    const double *m, double *ax, double *ay, double *az) {
+  double *r[3] = {x, y, z}, *v[3] = {vx, vy, vz}, *a[3] = {ax, ay, az};
+  const double h = 0.5 * dt;
+  for (int64_t step = 0; step < n_steps; step++) {
+    for (int k = 0; k < 3; k++) /* drift half a step */
+      for (int64_t p = 0; p < n; p++) r[k][p] = r[k][p] + h * v[k][p];
+    oracle_accel(n, G, x, y, z, m, ax, ay, az); /* Eq. 1 at r_{n+1/2} */
+    for (int k = 0; k < 3; k++)
+      for (int64_t p = 0; p < n; p++) {
+        v[k][p] = v[k][p] + dt * a[k][p]; /* kick a full step */
+        r[k][p] = r[k][p] + h * v[k][p]; /* drift the other half */
+      }
+  }
+  return 0;
+}
+
 /* The fourth-order Runge-Kutta method that Section 2 names as the
  * higher-order alternative to Verlet, applied to the first-order system
  * y = (r, v), y' = f(y) = (v, A(r)) with A = Eq. 1, n_steps steps of dt:

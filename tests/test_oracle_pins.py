@@ -491,3 +491,46 @@ def test_rk4_and_verlet_converge_to_the_same_trajectory():
         diffs.append(np.abs(r_rk - r_vv).max())
     for d1, d2 in zip(diffs, diffs[1:]):
         assert 3.0 < d1 / d2 < 5.0, diffs
+
+
+# ---------------------------------------------------------------------------
+# Leapfrog, drift-kick-drift (named in Section 2 beside Verlet)
+# ---------------------------------------------------------------------------
+def test_leapfrog_circular_orbit_second_order():
+    """Return error after one exact period of a circular orbit falls as dt^2."""
+    G, a = 2.9591220828e-4, 1.0
+    r, v, m = _two_body(1.0, 1e-3, a, 0.0, G)
+    P = 2 * math.pi * math.sqrt(a**3 / (G * m.sum()))
+    errs = []
+    for n in (200, 400, 800):
+        rr, _, _ = oracle.leapfrog(G, P / n, n, r, v, m)
+        errs.append(np.abs(rr - r).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5, errs
+
+
+def test_leapfrog_time_reversible():
+    """Drift-kick-drift is symmetric: n steps with dt, then n with -dt, return
+    to the start."""
+    s = inputs.solar_system(31, seed=25)
+    r, v, _ = oracle.leapfrog(s.G, s.dt, 400, s.r, s.v, s.m)
+    rb, vb, _ = oracle.leapfrog(s.G, -s.dt, 400, r, v, s.m)
+    assert np.abs(rb - s.r).max() <= 1e-12 * np.abs(s.r).max()
+    assert np.abs(vb - s.v).max() <= 1e-12 * np.abs(s.v).max()
+
+
+def test_leapfrog_conserves_momentum_and_converges_to_verlet():
+    """The kick uses antisymmetric pair forces (sum m a = 0), so sum m v is
+    constant; and the leapfrog and Verlet trajectories differ by O(dt^2)."""
+    s = inputs.solar_system(31, seed=26)
+    _, vv, _ = oracle.leapfrog(s.G, s.dt, 300, s.r, s.v, s.m)
+    P0 = (s.m * s.v).sum(axis=1)
+    assert np.abs((s.m * vv).sum(axis=1) - P0).max() <= 1e-13 * np.abs(s.m * s.v).sum()
+    diffs = []
+    for dt in (0.4, 0.2, 0.1):
+        n = int(round(40.0 / dt))
+        r_lf, _, _ = oracle.leapfrog(s.G, dt, n, s.r, s.v, s.m)
+        r_vv, _, _ = oracle.verlet(s.G, dt, n, s.r, s.v, s.m)
+        diffs.append(np.abs(r_lf - r_vv).max())
+    for d1, d2 in zip(diffs, diffs[1:]):
+        assert 3.0 < d1 / d2 < 5.0, diffs
