@@ -73,7 +73,12 @@ typedef enum {
    * higher-order method Section 2 names: k1 = f(y), k2 = f(y + dt/2 k1),
    * k3 = f(y + dt/2 k2), k4 = f(y + dt k3), y += dt/6 (k1 + 2 k2 + 2 k3 + k4).
    * Four evaluations of Eq. 1 per step; error O(dt^4). */
-  NBODY_RK4 = 1
+  NBODY_RK4 = 1,
+  /* Leapfrog (Section 2), drift-kick-drift with synchronised output:
+   * r_{n+1/2} = r_n + dt/2 v_n; v_{n+1} = v_n + dt A(r_{n+1/2});
+   * r_{n+1} = r_{n+1/2} + dt/2 v_{n+1}.  One evaluation of Eq. 1 per step,
+   * taken at the half-step positions; error O(dt^2); time-symmetric. */
+  NBODY_LEAPFROG = 2
 } nbody_integrator;
 
 typedef struct {
@@ -133,7 +138,8 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
 /* Advance every system by n_steps steps of the context's integrator, in
  * place.  n_steps == 0 is a no-op; n_steps < 0 is EINVAL.  Asynchronous.
  * Velocity Verlet (Eqs. 3, 1, 4): each step is a force launch (Eq. 1) and a
- * per-body Verlet launch (Eqs. 4, 3), chained.  RK4: each step is four
+ * per-body Verlet launch (Eqs. 4, 3), chained; leapfrog likewise, with the
+ * force at the half-step positions.  RK4: each step is four
  * (force launch, per-body stage launch) pairs; the last evaluation is Eq. 1
  * at the new positions, so the context's acceleration always belongs to the
  * current state.  Consecutive steps are replayed from cached CUDA graphs
@@ -143,7 +149,9 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
 nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
 
 /* Copy the acceleration at the current positions (Eq. 1, as used by the
- * last step) into DEVICE arrays ax, ay, az of N doubles.  Asynchronous. */
+ * last step) into DEVICE arrays ax, ay, az of N doubles.  (Leapfrog: Eq. 1
+ * at the last half-step positions, the only force it evaluates.)
+ * Asynchronous. */
 nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
 
 /* Re-read the bound state after the caller changed x..vz or m: recompute
@@ -165,7 +173,8 @@ nbody_status nbody_energy(nbody_ctx *ctx, double *e_host);
  *   dL_dr_T  DEVICE, 3N (x|y|z blocks): dL/dr_T.
  *   dL_dv_T  DEVICE, 3N, or NULL for zero.
  *   dL_dr0, dL_dv0  DEVICE, 3N outputs; dL_dm DEVICE, N output.
- * Runs in the context's precision.  Verlet contexts only: EINVAL for RK4.
+ * Runs in the context's precision.  Verlet contexts only: EINVAL for RK4
+ * and leapfrog.
  * Synchronous. */
 nbody_status nbody_grad(nbody_ctx *ctx, int64_t n_steps, const double *dL_dr_T,
                         const double *dL_dv_T, double *dL_dr0, double *dL_dv0,
@@ -194,7 +203,8 @@ nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *be
  * single-cluster path is not used.  HOST out[4] receives: [0] mean force
  * kernel duration (ms), [1] mean Verlet kernel duration (ms), [2] mean time
  * per step from the first event to the last (ms), [3] n_steps.
- * n_steps >= 1, else NBODY_EINVAL.  Verlet contexts only: EINVAL for RK4.
+ * n_steps >= 1, else NBODY_EINVAL.  Verlet contexts only: EINVAL for RK4
+ * and leapfrog.
  * Synchronous. */
 nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
 

@@ -462,9 +462,11 @@ nbody_status launch_rk4_step(nbody_ctx *c, const State &s, cudaStream_t st) {
 
 nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) {
   for (int i = 0; i < n; ++i) {
-    nbody_status r = c->o.integrator == NBODY_RK4
-                         ? launch_rk4_step(c, s, st)
-                         : launch_one_step(c, s, c->stage[i & 1], c->stage[1 - (i & 1)], nb::kModeStep, st);
+    nbody_status r =
+        c->o.integrator == NBODY_RK4
+            ? launch_rk4_step(c, s, st)
+            : launch_one_step(c, s, c->stage[i & 1], c->stage[1 - (i & 1)],
+                              c->o.integrator == NBODY_LEAPFROG ? nb::kModeLeapfrog : nb::kModeStep, st);
     if (r != NBODY_OK) return r;
   }
   return NBODY_OK;
@@ -691,7 +693,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
     return fail(nullptr, NBODY_EINVAL, "unknown precision %d", o->precision);
   if (o->ckpt_every < 0) return fail(nullptr, NBODY_EINVAL, "ckpt_every must be >= 0");
   if (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL)) return fail(nullptr, NBODY_EINVAL, "unknown flags");
-  if (o->integrator != NBODY_VERLET && o->integrator != NBODY_RK4)
+  if (o->integrator != NBODY_VERLET && o->integrator != NBODY_RK4 && o->integrator != NBODY_LEAPFROG)
     return fail(nullptr, NBODY_EINVAL, "unknown integrator %d", o->integrator);
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;
@@ -786,6 +788,8 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
   }
   if (c->o.integrator == NBODY_RK4)  // stage 1 of the first step, from (r, v, a)
     NB_CUDA(c, nb::launch_rk_prep(c->o.precision, rk_args(c, s, nullptr, c->stage[0], 1), c->stream));
+  else if (c->o.integrator == NBODY_LEAPFROG)  // the first half-step drift
+    NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 2, 0), c->stream));
   else  // Eq. 3 drift of the first step
     NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -135,6 +135,27 @@ __device__ __forceinline__ void sum_partial_rows(const double *partial, int rows
   }
 }
 
+// One component of the per-body update after a force evaluation `an` at the
+// staged position r (from velocity v, previous acceleration ao):
+//   Verlet (Eqs. 4, 3): v' = v + dt/2 (ao + an); the state position is r;
+//     the next staged position is r + v' dt + dt^2/2 an.
+//   Leapfrog, drift-kick-drift (r is the half-step position r_{n+1/2}):
+//     v' = v + dt an; the state position is r + dt/2 v'; the next staged
+//     position is that plus dt/2 v' (the next half step).
+// Returns the state position; v becomes v', *next the next staged position.
+__device__ __forceinline__ double step_component(bool leap, double r, double &v, double ao, double an, double dt,
+                                                 double half_dt, double half_dt2, double *next) {
+  if (leap) {
+    v = fma(dt, an, v);
+    const double x = fma(half_dt, v, r);
+    *next = fma(half_dt, v, x);
+    return x;
+  }
+  v = kick(v, ao, an, half_dt);
+  *next = drift(r, v, an, dt, half_dt2);
+  return r;
+}
+
 // Stage position (rx, ry, rz) of body q for the next force launch, with mu
 // copied from the current stage: FP64 double4 at q, or the mixed hi/lo pair
 // block at qidx[q] (mixed: *o is the pair offset, *muf the staged mu).
@@ -181,7 +202,8 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
   const int q = p0 + k;
   const int comp = kSplit ? warp : 0;
   const bool own = (kSplit ? warp < 3 : threadIdx.x < NB) && q < a.N;
-  const bool step = a.mode == kModeStep;
+  const bool step = a.mode != kModeForce;
+  const bool leap = a.mode == kModeLeapfrog;
   // This thread's component arrays (mixed split; the FP64 path uses all three).
   auto pick = [&](double *x, double *y, double *z) { return comp == 0 ? x : comp == 1 ? y : z; };
   double *const Xc = pick(a.x, a.y, a.z), *const Vc = pick(a.vx, a.vy, a.vz), *const Ac = pick(a.ax, a.ay, a.az);
@@ -238,15 +260,15 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
     const double an = static_cast<double>(s_hi[comp][k]) + static_cast<double>(s_lo[comp][k]);
     if (!isfinite(an)) atomicOr(a.flags, kFlagNonFinite);
     if (step) {
-      const double vn = kick(v[0], ao[0], an, a.half_dt);
-      const double nr = drift(r[0], vn, an, a.dt, a.half_dt2);
+      double vn = v[0], nr;
+      const double x = step_component(leap, r[0], vn, ao[0], an, a.dt, a.half_dt, a.half_dt2, &nr);
       Rc[q] = nr;
       float *w = static_cast<float *>(a.nxt) + o;
       const float h = hi_part(nr);
       w[kXh + 2 * comp] = h;
       w[kXl + 2 * comp] = lo_part(nr, h);
       if (comp == 0) w[kMu] = muf;
-      Xc[q] = r[0];
+      Xc[q] = x;
       Vc[q] = vn;
     }
     Ac[q] = an;
@@ -256,16 +278,14 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
     for (int c = 0; c < 3; ++c) an[c] = static_cast<double>(s_hi[c][k]) + static_cast<double>(s_lo[c][k]);
     if (!finite3(an[0], an[1], an[2])) atomicOr(a.flags, kFlagNonFinite);
     if (step) {
-      double nr[3];
+      double nr[3], x[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        v[c] = kick(v[c], ao[c], an[c], a.half_dt);
-        nr[c] = drift(r[c], v[c], an[c], a.dt, a.half_dt2);
-      }
+      for (int c = 0; c < 3; ++c)
+        x[c] = step_component(leap, r[c], v[c], ao[c], an[c], a.dt, a.half_dt, a.half_dt2, &nr[c]);
       stage_position<PREC>(a.nxt, q, o, nr[0], nr[1], nr[2], mu, muf);
-      a.x[q] = r[0];
-      a.y[q] = r[1];
-      a.z[q] = r[2];
+      a.x[q] = x[0];
+      a.y[q] = x[1];
+      a.z[q] = x[2];
       a.vx[q] = v[0];
       a.vy[q] = v[1];
       a.vz[q] = v[2];
@@ -475,10 +495,15 @@ __global__ void prep_kernel(const PrepArgs a) {
     const bool ok = finite3(rx, ry, rz) && finite3(a.vx[p], a.vy[p], a.vz[p]) && isfinite(m) && m >= 0.0;
     if (!ok) atomicOr(a.flags, kFlagBadInput);
   }
-  if (a.drift) {
+  if (a.drift == 1) {  // Eq. 3
     rx = drift(rx, a.vx[p], a.ax[p], a.dt, a.half_dt2);
     ry = drift(ry, a.vy[p], a.ay[p], a.dt, a.half_dt2);
     rz = drift(rz, a.vz[p], a.az[p], a.dt, a.half_dt2);
+  } else if (a.drift == 2) {  // leapfrog: the first half-step drift
+    const double h = 0.5 * a.dt;
+    rx = fma(h, a.vx[p], rx);
+    ry = fma(h, a.vy[p], ry);
+    rz = fma(h, a.vz[p], rz);
   }
   const double mu = a.G * m;
   if (PREC == 0) {

@@ -62,6 +62,7 @@ struct ForceArgs {
 enum Mode : int32_t {
   kModeForce = 0,  // write a = Eq. 1 only
   kModeStep = 1,   // Eq. 4 kick with the new a, then Eq. 3 drift into the next stage
+  kModeLeapfrog = 2,  // drift-kick-drift: full kick at the half-step force, two half drifts
 };
 
 // Arguments of the per-body Verlet kernel that completes a step: sums the
@@ -134,7 +135,7 @@ struct PrepArgs {
   double *Rx, *Ry, *Rz;
   unsigned *flags;
   int32_t N;
-  int32_t drift;
+  int32_t drift;  // 0: stage r; 1: stage the Eq. 3 drift of r; 2: stage r + dt/2 v (leapfrog)
   int32_t check;  // validate inputs (finite state, m >= 0)
   double G, dt, half_dt2;
 };

@@ -29,8 +29,8 @@ NBODY_FLAG_NO_GRAPH = 1
 NBODY_FLAG_NO_SMALL = 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT"}
 PRECISIONS = {"fp64": NBODY_FP64, "mixed": NBODY_MIXED}
-NBODY_VERLET, NBODY_RK4 = 0, 1
-INTEGRATORS = {"verlet": NBODY_VERLET, "rk4": NBODY_RK4}
+NBODY_VERLET, NBODY_RK4, NBODY_LEAPFROG = 0, 1, 2
+INTEGRATORS = {"verlet": NBODY_VERLET, "rk4": NBODY_RK4, "leapfrog": NBODY_LEAPFROG}
 
 
 class nbody_opts(ctypes.Structure):

@@ -123,7 +123,7 @@ def test_rk4_unsupported_calls(nb):
     assert ei.value.status == nb.NBODY_EINVAL
     import ctypes
     off = (ctypes.c_int64 * 2)(0, s.n)
-    opts = nb.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, integrator=2)
+    opts = nb.nbody_opts(G=1.0, dt=0.1, precision=0, ckpt_every=0, flags=0, integrator=3)
     ctx = ctypes.c_void_p()
     st = nb.nbody_init(ctypes.byref(ctx), 1, off, *([b.state[0].data_ptr()] * 6 + [b.m.data_ptr()]),
                        ctypes.byref(opts), None)
