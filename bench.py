@@ -544,7 +544,8 @@ def extras(torch, nbody, inputs, stream, device, args):
             row = {"dt_day": dt}
             n_steps = int(round(73.0 / dt))
             every = max(1, n_steps // 20)
-            for prec, integ in (("fp64", "verlet"), ("mixed", "verlet"), ("fp64", "rk4"), ("mixed", "rk4")):
+            for prec, integ in (("fp64", "verlet"), ("mixed", "verlet"), ("fp64", "rk4"), ("mixed", "rk4"),
+                                ("fp64", "leapfrog"), ("mixed", "leapfrog")):
                 with torch.cuda.stream(stream):
                     b = nbody.NBody(sd.r, sd.v, sd.m, G=sd.G, dt=dt, precision=prec, integrator=integ,
                                     device=device)
@@ -554,10 +555,10 @@ def extras(torch, nbody, inputs, stream, device, args):
                         b.step(every)
                         worst = max(worst, abs(b.energy()[0] - e0) / abs(e0))
                     b.close()
-                row[prec if integ == "verlet" else prec + "_rk4"] = worst
+                row[prec if integ == "verlet" else prec + "_" + integ] = worst
             rows.append(row)
         for a, b2 in zip(rows, rows[1:]):
-            for key in ("fp64", "mixed", "fp64_rk4", "mixed_rk4"):
+            for key in ("fp64", "mixed", "fp64_rk4", "mixed_rk4", "fp64_leapfrog", "mixed_leapfrog"):
                 b2[key + "_order"] = float(np.log2(a[key] / b2[key]))
         out["dt_sweep"] = {"bodies": sd.n, "days": 73.0, "max_rel_energy_drift": rows}
     # N sweep.  By default only N = 1,048,576 (the metric's second size, mixed
