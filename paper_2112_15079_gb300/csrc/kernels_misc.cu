@@ -177,7 +177,7 @@ __device__ __forceinline__ void stage_position(void *nxt, int q, size_t o, doubl
   }
 }
 
-template <int PREC>
+template <int PREC, int MODE>  // MODE: kModeForce, kModeStep or kModeLeapfrog (a.mode)
 __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const VerletArgs a) {
   // When at most one force CTA fits on an SM, the next force grid can only
   // land one CTA per SM, however early it launches: let it launch now, so its
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
   const int q = p0 + k;
   const int comp = kSplit ? warp : 0;
   const bool own = (kSplit ? warp < 3 : threadIdx.x < NB) && q < a.N;
-  const bool step = a.mode != kModeForce;
-  const bool leap = a.mode == kModeLeapfrog;
+  constexpr bool step = MODE != kModeForce;
+  constexpr bool leap = MODE == kModeLeapfrog;
   // This thread's component arrays (mixed split; the FP64 path uses all three).
   auto pick = [&](double *x, double *y, double *z) { return comp == 0 ? x : comp == 1 ? y : z; };
   double *const Xc = pick(a.x, a.y, a.z), *const Vc = pick(a.vx, a.vy, a.vz), *const Ac = pick(a.ax, a.ay, a.az);
@@ -313,7 +313,16 @@ cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bo
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  return precision == 0 ? cudaLaunchKernelEx(&cfg, verlet_kernel<0>, a) : cudaLaunchKernelEx(&cfg, verlet_kernel<1>, a);
+#define NB_VERLET(P, M) \
+  if (precision == P && a.mode == M) return cudaLaunchKernelEx(&cfg, verlet_kernel<P, M>, a);
+  NB_VERLET(0, kModeForce)
+  NB_VERLET(0, kModeStep)
+  NB_VERLET(0, kModeLeapfrog)
+  NB_VERLET(1, kModeForce)
+  NB_VERLET(1, kModeStep)
+  NB_VERLET(1, kModeLeapfrog)
+#undef NB_VERLET
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
