@@ -31,9 +31,11 @@
  * - A context is not thread-safe; use one context per host thread.
  * - Fault-injection hooks for tests (environment variables, unset in normal
  *   use): NBODY_INJECT_ALLOC_FAIL=k fails a context's k-th device allocation
- *   with NBODY_ENOMEM; NBODY_INJECT_WAIT_STALL=k (read by nbody_init) leaves
- *   one source copy of the context's k-th adjoint product unissued, so that
- *   kernel's bounded wait runs out (~2 s) and nbody_grad returns
+ *   with NBODY_ENOMEM; NBODY_INJECT_WAIT_STALL=k (read by nbody_init) stalls
+ *   one bounded device wait in the context's k-th launch that has one (an
+ *   adjoint product: one source copy left unissued; a small-system
+ *   nbody_step call: one barrier arrival left out), so that wait runs out
+ *   (~2 s), the kernel winds down, and nbody_grad / nbody_sync returns
  *   NBODY_ETIMEOUT.
  */
 #ifndef NBODY_H
@@ -93,8 +95,8 @@ typedef struct {
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
 #define NBODY_FLAG_NO_GRAPH 1
 /* Never use the single-launch small-system kernel (one FP64 system of at
- * most 64 bodies runs every step of an nbody_step call in one launch of a
- * 16-CTA cluster unless this flag is set). */
+ * most 64 bodies runs every step of an nbody_step call in one launch of an
+ * 8-CTA (N <= 32) or 16-CTA cluster unless this flag is set). */
 #define NBODY_FLAG_NO_SMALL 2
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work

@@ -74,8 +74,8 @@ struct nbody_ctx {
   // scratch
   std::vector<void *> allocs;
   int alloc_seq = 0;  // device allocations made so far (fault injection counts these)
-  int64_t vjp_seq = 0;       // adjoint products launched so far
-  int64_t stall_at = 0;      // test hook (NBODY_INJECT_WAIT_STALL=k): the k-th product stalls
+  int64_t wait_seq = 0;      // launches with a stallable bounded wait (adjoint products, small-system steps)
+  int64_t stall_at = 0;      // test hook (NBODY_INJECT_WAIT_STALL=k): the k-th of them stalls
   double *a = nullptr;               // [3][N] acceleration at the current positions
   void *stage[2] = {nullptr, nullptr};  // ping-pong staged sources (layout per precision)
   int64_t n_stage = 0;               // stage entries (mixed: systems padded to even length)
@@ -705,11 +705,12 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   c->o = *o;
   if (c->o.ckpt_every == 0) c->o.ckpt_every = 100;
   c->user_stream = static_cast<cudaStream_t>(cuda_stream);
-  // Optional host-side test hook: NBODY_INJECT_WAIT_STALL=k leaves the first
-  // source tile of CTA 0 unissued in the context's k-th adjoint product (VJP
-  // launch), so that CTA's bounded wait runs out and nbody_grad reports
-  // ETIMEOUT.  (It lives in the adjoint kernel so the force kernels carry no
-  // test code.)
+  // Optional host-side test hook: NBODY_INJECT_WAIT_STALL=k stalls one
+  // bounded wait in the context's k-th launch that has one: the first source
+  // tile of CTA 0 stays unissued in an adjoint product (VJP launch), or CTA 0
+  // leaves out one barrier arrival in a small-system step call.  The wait
+  // runs out and nbody_grad / nbody_sync report ETIMEOUT.  (The force kernels
+  // carry no test code.)
   if (const char *inj = std::getenv("NBODY_INJECT_WAIT_STALL")) c->stall_at = std::atoll(inj);
 
   auto bail = [&](nbody_status st) {
@@ -781,6 +782,7 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
     sa.dt = c->o.dt;
     sa.half_dt = 0.5 * c->o.dt;
     sa.half_dt2 = 0.5 * c->o.dt * c->o.dt;
+    sa.stall = ++c->wait_seq == c->stall_at ? 1 : 0;
     cudaError_t e = nb::launch_small(sa, c->stream);
     if (e == cudaSuccess) return end_work(c);
     cudaGetLastError();  // cluster launch refused: fall back to the general path for good
@@ -1064,7 +1066,7 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   vj.tj = kVjpTile;
   auto product = [&](const void *pos, int mode) -> nbody_status {
     vj.pos = pos;
-    vj.stall = ++c->vjp_seq == c->stall_at ? 1 : 0;
+    vj.stall = ++c->wait_seq == c->stall_at ? 1 : 0;
     NB_CUDA(c, nb::launch_vjp(prec, A.vj.grid, A.vj.smem, vj, c->stream));
     ad.mode = mode;
     NB_CUDA(c, nb::launch_adjoint(prec, ad, c->stream));

@@ -123,6 +123,7 @@ struct SmallArgs {
   int32_t N;
   int64_t n_steps;
   double G, dt, half_dt, half_dt2;
+  int32_t stall;  // test hook: CTA 0 skips one barrier arrival (the waits run out)
 };
 
 // Staging / pre-drift over all N bodies: stage r (drift == 0) or

@@ -539,6 +539,35 @@ def test_bounded_wait_timeout_reports_and_recovers(nb, monkeypatch):
     assert np.array_equal(b.state.cpu().numpy(), want_s)
 
 
+def test_small_system_wait_timeout_reports_and_recovers(nb, monkeypatch):
+    """The single-launch 31-body kernel exchanges positions through mbarrier
+    waits.  NBODY_INJECT_WAIT_STALL=1 makes CTA 0 leave out one arrival in
+    the first nbody_step call: its bounded wait runs out (~2 s), the other
+    CTAs' next wait too, the kernel winds down, and nbody_sync reports
+    ETIMEOUT.  After the state is restored and reset, the context steps
+    bitwise like a fresh one."""
+    import time
+    s = inputs.solar_system(31, seed=52)
+    fresh = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    fresh.step(100)
+    want = fresh.state.cpu().numpy()
+    monkeypatch.setenv("NBODY_INJECT_WAIT_STALL", "1")
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    monkeypatch.delenv("NBODY_INJECT_WAIT_STALL")
+    t0 = time.time()
+    b.step(10)
+    with pytest.raises(nb.NBodyError) as ei:
+        b.sync()
+    assert ei.value.status == nb.NBODY_ETIMEOUT
+    assert time.time() - t0 < 60
+    torch = pytest.importorskip("torch")
+    b.state[0:3].copy_(torch.tensor(s.r))
+    b.state[3:6].copy_(torch.tensor(s.v))
+    b.reset()
+    b.step(100)
+    assert np.array_equal(b.state.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_reset_after_the_caller_changes_state_and_masses(nb, precision):
     """nbody_reset re-reads the bound state: new positions and masses (a third
