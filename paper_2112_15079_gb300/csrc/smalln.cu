@@ -11,18 +11,19 @@
 // seed), Eqs. 3-4 the same kick/drift functions.
 //
 // Exchange.  After the Eq. 3 drift each target's owner pushes its new
-// position into every CTA's copy with st.async, each store completing 8
-// bytes of a transaction on the receiving CTA's mbarrier for that buffer; a
-// CTA reads the buffer once the barrier's phase completes (24 N bytes: every
-// component of every target).  There is no cluster-wide barrier per step:
-// a store is one-way.  Reuse is safe without one: a CTA writes a peer's
-// buffer for step k+2 only after its own wait for step k+1 completed, which
-// needs the peer's step-(k+1) stores, issued after the peer's warps finished
-// reading that buffer at step k (their stored values depend on those reads).
-// The same argument keeps a barrier's phases in order, so a wait on the
-// phase parity (step / 2) mod 2 is unambiguous.  Waits are bounded
-// (kWaitPolls); a wait that runs out sets kFlagTimeout and the kernel winds
-// down.
+// position into the copy of every CTA that owns a target, with st.async,
+// each store completing 8 bytes of a transaction on the receiving CTA's
+// mbarrier for that buffer; a CTA reads the buffer once the barrier's phase
+// completes (24 N bytes: every component of every target).  There is no
+// cluster-wide barrier per step: a store is one-way.  Only warps that own a
+// target take part, and every one of them is waited for by all the others.
+// Reuse is then safe: a warp writes a peer's buffer for step k+2 only after
+// its own wait for step k+1 completed, which needs every owner's step-(k+1)
+// stores, issued after that owner finished reading its buffer at step k
+// (the stored values depend on those reads).  For the same reason no owner
+// can be two phases behind another, so a wait on the phase parity
+// (step / 2) mod 2 is unambiguous.  Waits are bounded (kWaitPolls); a wait
+// that runs out sets kFlagTimeout and the kernel winds down.
 //
 // At this size a step is a chain of dependent FP64 instructions, and GB300's
 // FP64 pipe takes 64 cycles for every warp instruction whatever its active
@@ -119,12 +120,14 @@ __global__ void __launch_bounds__(32 * kTargetsPerCta) smalln_kernel(const Small
     v = pick_ptr(c, a.vx, a.vy, a.vz)[p];
     acc = pick_ptr(c, a.ax, a.ay, a.az)[p];
   }
-  // This lane's slot of pos[0] / pos[1] and the mbarriers, in the one or two
-  // CTAs (ranks lane % 8 and lane % 8 + 8) that it writes to.
+  // Only the CTAs that own a target (ranks below nact) take part in the
+  // exchange.  This lane's slot of pos[0] / pos[1] and the mbarriers, in the
+  // one or two of them (ranks lane % 8 and lane % 8 + 8) that it writes to.
+  const int nact = min(csize, n);
   const int rk = lane & 7;
-  const bool two = csize > 8;
+  const bool one = rk < nact, two = rk + 8 < nact;
   uint32_t pa0 = 0, pa1 = 0, pb0 = 0, pb1 = 0, ba0 = 0, ba1 = 0, bb0 = 0, bb1 = 0;
-  if (upd) {
+  if (upd && one) {
     const double *m0 = reinterpret_cast<const double *>(&pos[0][p]) + c;
     const double *m1 = reinterpret_cast<const double *>(&pos[1][p]) + c;
     pa0 = rank_addr(m0, rk);
@@ -138,18 +141,23 @@ __global__ void __launch_bounds__(32 * kTargetsPerCta) smalln_kernel(const Small
       bb1 = rank_addr(&bar[1], rk + 8);
     }
   }
-  const uint32_t tx = 24u * static_cast<uint32_t>(n);  // bytes each CTA receives per step
+  const uint32_t tx = 24u * static_cast<uint32_t>(n);  // bytes each active CTA receives per step
   const bool stall = a.stall != 0 && rank == 0;
   cluster.sync();
+  // Warps without a target leave the step loop at once: no other warp waits
+  // for them, so a waiting one could fall two phases behind and misread the
+  // parity.  (Warp 0 of an active CTA owns a target, so its thread 0, which
+  // announces the CTA's expected bytes, always takes part.)
+  const int64_t n_steps = own ? a.n_steps : 0;
   int b = 0;
-  for (int64_t step = 0; step < a.n_steps; ++step) {
+  for (int64_t step = 0; step < n_steps; ++step) {
     const int nb = 1 - b;
     if (threadIdx.x == 0 && !(stall && step == 0)) mbar_arrive_expect_tx(&bar[nb], tx);
     // Eq. 3 drift of component c; the group's 8 lanes store it into every
-    // CTA's copy, each store counted on the receiving CTA's mbarrier.
+    // active CTA's copy, each store counted on the receiving CTA's mbarrier.
     if (upd) {
       r = drift(r, v, acc, a.dt, a.half_dt2);
-      st_async_f64(nb ? pa1 : pa0, r, nb ? ba1 : ba0);
+      if (one) st_async_f64(nb ? pa1 : pa0, r, nb ? ba1 : ba0);
       if (two) st_async_f64(nb ? pb1 : pb0, r, nb ? bb1 : bb0);
     }
     // bar[nb] is used every other step: its phase parity is (step / 2) mod 2.
@@ -161,12 +169,10 @@ __global__ void __launch_bounds__(32 * kTargetsPerCta) smalln_kernel(const Small
     b = nb;
     // Eq. 1 at the new positions: lanes split the sources.
     double s0 = 0, s1 = 0, s2 = 0;
-    if (own) {
-      const double4_32a me = pos[b][p];
-      for (int j = lane; j < n; j += 32) {
-        if (j == p) continue;
-        interact_fp64<false>(pos[b][j], me.x, me.y, me.z, false, s0, s1, s2);
-      }
+    const double4_32a me = pos[b][p];
+    for (int j = lane; j < n; j += 32) {
+      if (j == p) continue;
+      interact_fp64<false>(pos[b][j], me.x, me.y, me.z, false, s0, s1, s2);
     }
     // Butterfly reduce-scatter over the lanes.  Level 16: lanes with bit 4
     // clear keep components (0, 1), the others (2, 3 = zero padding).

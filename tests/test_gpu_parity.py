@@ -118,13 +118,14 @@ def test_fp64_trajectory_31_bodies_3650_steps(nb):
     assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-10 * np.abs(v_ref).max()
 
 
-@pytest.mark.parametrize("n", [2, 31, 64])
+@pytest.mark.parametrize("n", [2, 31, 32, 33, 64])
 def test_small_system_kernel_vs_general_and_oracle(nb, n):
-    """One FP64 system of <= 64 bodies runs every step in one cluster launch;
-    it matches the oracle and the general two-kernel path."""
+    """One FP64 system of <= 64 bodies runs every step in one cluster launch
+    (8 CTAs up to 32 bodies, 16 beyond); it matches the oracle and the
+    general two-kernel path."""
     s = inputs.solar_system(31, seed=70 + n) if n == 31 else None
-    if n == 64:
-        s = inputs.solar_system(64, seed=71, n_moons=0)
+    if n in (32, 33, 64):
+        s = inputs.solar_system(n, seed=71, n_moons=0)
     if n == 2:
         r = np.array([[0.0, 1.0], [0.0, 0.0], [0.0, 0.0]])
         v = np.array([[0.0, 0.0], [0.0, 0.0172], [0.0, 0.0]])
@@ -356,6 +357,18 @@ def test_fp64_time_reversibility(nb):
     back = nb.NBody(b.r, b.v, s.m, G=s.G, dt=-s.dt, precision="fp64")
     back.step(300)
     assert np.abs(back.r.cpu().numpy() - s.r).max() <= 1e-11 * np.abs(s.r).max()
+
+
+def test_small_system_time_reversibility(nb):
+    """The single-launch kernel (31 bodies, FP64): 3650 steps forward, then
+    3650 with -dt from the end state, return to the start."""
+    s = inputs.solar_system(31, seed=13)
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    b.step(3650)
+    back = nb.NBody(b.r, b.v, s.m, G=s.G, dt=-s.dt, precision="fp64")
+    back.step(3650)
+    assert np.abs(back.r.cpu().numpy() - s.r).max() <= 1e-11 * np.abs(s.r).max()
+    assert np.abs(back.v.cpu().numpy() - s.v).max() <= 1e-11 * np.abs(s.v).max()
 
 
 def test_edge_cases_and_errors(nb):
