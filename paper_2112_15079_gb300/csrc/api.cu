@@ -325,11 +325,7 @@ nbody_status build_items(nbody_ctx *c, const nbody_tiles &t) {
   const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, smem);
   Work nw;
   const nbody_status st = build_work(c, nw, t, occ, 3);
-  if (st != NBODY_OK) {
-    // The kernel instance may be the current one: give it back its size.
-    if (c->fw.blks) nb::force_set_smem(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.smem);
-    return st;
-  }
+  if (st != NBODY_OK) return st;  // (the shared-memory limit was only raised)
   nw.smem = smem;
   free_work(c, c->fw);
   c->fw = nw;

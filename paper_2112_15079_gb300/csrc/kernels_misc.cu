@@ -2,6 +2,7 @@
 // completion (Eqs. 4 and 3), the RK4 stage completion and stage-1 prep, the
 // staging / pre-drift kernel, the energy kernels, and the force-launch
 // dispatcher.
+#include <mutex>
 #include <type_traits>
 
 #include "nbody_dev.cuh"
@@ -27,6 +28,9 @@ cudaError_t launch_force(int precision, int threads, int ipt, int grid, size_t s
 }
 
 cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem) {
+  // Read-and-raise of a limit shared by every context (and host thread).
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
   return run_force(precision, 1, threads, ipt, 0, smem, ForceArgs{}, nullptr, false, nullptr);
 }
 

@@ -371,6 +371,64 @@ def test_small_system_time_reversibility(nb):
     assert np.abs(back.v.cpu().numpy() - s.v).max() <= 1e-11 * np.abs(s.v).max()
 
 
+@pytest.mark.parametrize("n,precision,integrator", [(31, "fp64", "verlet"), (2131, "mixed", "verlet"),
+                                                    (2131, "fp64", "verlet"), (2131, "mixed", "rk4")])
+def test_steps_captured_in_a_caller_graph(nb, n, precision, integrator):
+    """A caller may capture nbody_step into its own CUDA graph (the call is
+    asynchronous and allocates nothing): during capture the library launches
+    its kernels directly (the single-launch cluster kernel for 31 bodies),
+    and each replay advances the state exactly like a direct call."""
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(n, seed=90 + n)
+    k = 7
+    ref = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision, integrator=integrator)
+    for _ in range(3):
+        ref.step(k)
+    ref.sync()
+    side = torch.cuda.Stream()
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision, integrator=integrator, stream=side)
+    b.step(k)  # one direct call first, so the capture is not the first use of the context
+    b.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        b.step(k)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    b.sync()
+    assert np.array_equal(b.state.cpu().numpy(), ref.state.cpu().numpy())
+
+
+def test_contexts_with_different_tiles_share_the_kernels(nb):
+    """The force kernel's shared-memory limit belongs to the kernel instance,
+    which every context of the process shares.  A context built later with
+    smaller source tiles must not take away what an earlier one launches with
+    (mixed: 1024 then 64 sources per stage), nor may a context take it from
+    the allocation-free entry point (FP64, 256 sources per stage)."""
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(2131, seed=95)
+    big = {"threads": 512, "ipt": 1, "tj": 1024, "jsplit": 0, "ctas_per_sm": 2}
+    small = dict(big, tj=64)
+    want = {}
+    for name, t in (("big", big), ("small", small)):
+        r = _make(nb, s, "mixed", t)
+        r.step(5)
+        want[name] = r.state.cpu().numpy()
+        r.close()
+    a = _make(nb, s, "mixed", big)
+    b = _make(nb, s, "mixed", small)  # built after a, needing less shared memory
+    a.step(5)
+    b.step(5)
+    assert np.array_equal(a.state.cpu().numpy(), want["big"])
+    assert np.array_equal(b.state.cpu().numpy(), want["small"])
+    f = _make(nb, s, "fp64", {"threads": 128, "ipt": 1, "tj": 64, "jsplit": 0, "ctas_per_sm": 3})
+    rt = torch.tensor(s.r, dtype=torch.float64, device="cuda")
+    mt = torch.tensor(s.m, dtype=torch.float64, device="cuda")
+    got = nb.accel_static(rt, mt, s.G).cpu().numpy()
+    ref = f.accel().cpu().numpy()
+    assert np.max(_rel_err(got, ref)) <= FP64_TOL
+
+
 def test_edge_cases_and_errors(nb):
     torch = pytest.importorskip("torch")
     # single body: no force, straight-line motion
