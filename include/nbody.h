@@ -29,6 +29,10 @@
  * - The library owns its scratch, graphs and snapshots; nbody_free releases
  *   them.  The caller must keep the bound state buffers alive until then.
  * - A context is not thread-safe; use one context per host thread.
+ * - A context belongs to the CUDA device that is current at nbody_init (its
+ *   state buffers and stream must live there).  Every later call on it makes
+ *   that device current for the call's duration and restores the calling
+ *   thread's device afterwards.
  * - Fault-injection hooks for tests (environment variables, unset in normal
  *   use): NBODY_INJECT_ALLOC_FAIL=k fails a context's k-th device allocation
  *   with NBODY_ENOMEM; NBODY_INJECT_WAIT_STALL=k (read by nbody_init) stalls

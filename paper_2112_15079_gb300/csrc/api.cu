@@ -661,6 +661,25 @@ nbody_status ensure_adjoint(nbody_ctx *c, int64_t n_steps) {
   return NBODY_OK;
 }
 
+// Makes the context's device (current at nbody_init) current for one call
+// and gives the calling thread its own device back afterwards, so a context
+// may be driven from a thread that works on another GPU.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev_ = cur;
+  }
+  ~DeviceGuard() {
+    if (prev_ >= 0) cudaSetDevice(prev_);
+  }
+  DeviceGuard(const DeviceGuard &) = delete;
+  DeviceGuard &operator=(const DeviceGuard &) = delete;
+
+ private:
+  int prev_ = -1;
+};
+
 }  // namespace
 
 // ===========================================================================
@@ -761,6 +780,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
 
 nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return NBODY_OK;
   nbody_status st;
@@ -817,6 +837,7 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
 
 nbody_status nbody_accel(nbody_ctx *c, double *ax, double *ay, double *az) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (!ax || !ay || !az) return fail(c, NBODY_EINVAL, "output pointer is NULL");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -829,11 +850,13 @@ nbody_status nbody_accel(nbody_ctx *c, double *ax, double *ay, double *az) {
 
 nbody_status nbody_reset(nbody_ctx *c) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   return refresh(c);
 }
 
 nbody_status nbody_energy(nbody_ctx *c, double *e_host) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (!e_host) return fail(c, NBODY_EINVAL, "e_host is NULL");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -863,6 +886,7 @@ nbody_status nbody_energy(nbody_ctx *c, double *e_host) {
 
 nbody_status nbody_sync(nbody_ctx *c) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   return check_flags(c, false);
 }
 
@@ -874,6 +898,7 @@ nbody_status nbody_get_tiles(const nbody_ctx *c, nbody_tiles *t) {
 
 nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (!t || !tiles_valid(*t, c->o.precision))
     return fail(c, NBODY_EINVAL, "invalid tiles (see nbody.h: supported threads/ipt pairs, tj 64..2048 step 64, jsplit 0..64, ctas_per_sm 1..32)");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -882,6 +907,7 @@ nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
 
 nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best, double *best_ms) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (probe_steps < 1) return fail(c, NBODY_EINVAL, "probe_steps must be >= 1");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   const size_t N = c->N, b = sizeof(double) * N;
@@ -955,6 +981,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
 
 nbody_status nbody_kernel_times(nbody_ctx *c, int32_t n_steps, double *out) {
   if (!c || !out) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "nbody_kernel_times times Verlet steps only");
   if (n_steps < 1) return fail(c, NBODY_EINVAL, "n_steps must be >= 1");
   nbody_status st;
@@ -1000,6 +1027,7 @@ nbody_status nbody_kernel_times(nbody_ctx *c, int32_t n_steps, double *out) {
 nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, const double *dL_dv_T, double *dL_dr0,
                         double *dL_dv0, double *dL_dm) {
   if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
   if (!dL_dr_T || !dL_dr0 || !dL_dv0 || !dL_dm) return fail(c, NBODY_EINVAL, "a gradient pointer is NULL");
   if (n_steps > (int64_t(1) << 31)) return fail(c, NBODY_EINVAL, "n_steps too large");
@@ -1092,7 +1120,11 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   return check_flags(c, false);
 }
 
-void nbody_free(nbody_ctx *c) { destroy(c); }
+void nbody_free(nbody_ctx *c) {
+  if (!c) return;
+  const DeviceGuard dg(c->dev);
+  destroy(c);
+}
 
 const char *nbody_last_error(const nbody_ctx *c) { return c ? c->err.c_str() : g_init_error.c_str(); }
 
