@@ -915,10 +915,15 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   double *save = nullptr;
   nbody_status st = dalloc(c, reinterpret_cast<void **>(&save), 9 * b);
   if (st != NBODY_OK) return st;
+  // The copies go on the context's stream, so the probes are ordered after
+  // them (a device-to-device cudaMemcpy may return before it completes, and
+  // the context's stream does not wait for the legacy default stream).
   double *src[9] = {c->x, c->y, c->z, c->vx, c->vy, c->vz, c->a, c->a + N, c->a + 2 * N};
-  for (int k = 0; k < 9; ++k) NB_CUDA(c, cudaMemcpy(save + k * N, src[k], b, cudaMemcpyDeviceToDevice));
+  for (int k = 0; k < 9; ++k)
+    NB_CUDA(c, cudaMemcpyAsync(save + k * N, src[k], b, cudaMemcpyDeviceToDevice, c->stream));
   auto restore = [&]() -> nbody_status {
-    for (int k = 0; k < 9; ++k) NB_CUDA(c, cudaMemcpy(src[k], save + k * N, b, cudaMemcpyDeviceToDevice));
+    for (int k = 0; k < 9; ++k)
+      NB_CUDA(c, cudaMemcpyAsync(src[k], save + k * N, b, cudaMemcpyDeviceToDevice, c->stream));
     return NBODY_OK;
   };
   std::vector<nbody_tiles> cand;
@@ -969,6 +974,8 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   nbody_status st2 = restore();
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess && st2 == NBODY_OK)
+    st2 = fail(c, NBODY_ECUDA, "autotune restore failed");
   dfree(c, save);
   if (st != NBODY_OK) return st;
   if (st2 != NBODY_OK) return st2;
