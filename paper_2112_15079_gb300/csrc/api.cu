@@ -202,7 +202,8 @@ void free_work(nbody_ctx *c, Work &w);
 // block, the sources of the block's system in units of 2 sources (mixed pair
 // layout) or 1 (FP64), each unit weighted by the warps the block keeps busy.
 // Three quarters of it (all of it when jsplit == 0) are cut into `grid` =
-// SMs * ctas_per_sm equal static shares, the rest into grid * jsplit chunks.
+// SMs * ctas_per_sm equal static shares (fewer for small systems, see
+// below), the rest into grid * jsplit chunks.
 // row_doubles: 8-byte words per body and partial row (3 force, 4 VJP).
 nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, int row_doubles) {
   free_work(c, wk);
@@ -237,7 +238,20 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
   int64_t units_total = 0;
   for (int64_t u : bunits) units_total += u;
-  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total, static_cast<int64_t>(c->nsm) * cps));
+  // Pieces must not get too short: every piece of a block adds a partial row
+  // that the per-body kernel adds for each of the block's bodies, and below a
+  // few thousand bodies those sums (FP64 TwoSum at GB300's 1/64 FP64 rate, on
+  // the FP64 path) cost more than the extra pieces gain in parallelism.  A
+  // piece gets at least c * sqrt(U) units, U the longest block's units: c = 1/2
+  // for mixed; for FP64 c = 1 below 800 units, 2 below 2000, 3 beyond (the
+  // best of c = 1, 1.5, 2, 3 measured from 65 to 5,003 bodies; from about
+  // 5,000 bodies on the shares are longer than that anyway).
+  int64_t umax = 1;
+  for (int64_t u : bunits) umax = std::max(umax, u);
+  const double cmin = c->o.precision == NBODY_MIXED ? 0.5 : umax < 800 ? 1.0 : umax < 2000 ? 2.0 : 3.0;
+  const int64_t umin = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(cmin * std::sqrt(static_cast<double>(umax)))));
+  const int64_t G =
+      std::max<int64_t>(1, std::min<int64_t>(units_total / umin, static_cast<int64_t>(c->nsm) * cps));
   const int64_t D = std::min<int64_t>(static_cast<int64_t>(t.jsplit) * G, std::max<int64_t>(units_total - G, 0));
   const int64_t Ws = D > 0 ? W - W / 4 : W;
   std::vector<int64_t> cuts;  // piece boundaries on the line
