@@ -99,7 +99,7 @@ typedef struct {
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
 #define NBODY_FLAG_NO_GRAPH 1
 /* Never use the single-launch small-system kernel (one FP64 system of at
- * most 64 bodies runs every step of an nbody_step call in one launch of an
+ * most 256 bodies runs every step of an nbody_step call in one launch of an
  * 8-CTA (N <= 32) or 16-CTA cluster unless this flag is set). */
 #define NBODY_FLAG_NO_SMALL 2
 
@@ -150,7 +150,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
  * at the new positions, so the context's acceleration always belongs to the
  * current state.  Consecutive steps are replayed from cached CUDA graphs
  * unless NBODY_FLAG_NO_GRAPH is set or the stream is already being
- * captured.  One FP64 Verlet system of at most 64 bodies instead runs all
+ * captured.  One FP64 Verlet system of at most 256 bodies instead runs all
  * n_steps in a single cluster launch (see NBODY_FLAG_NO_SMALL). */
 nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
 

@@ -118,13 +118,14 @@ def test_fp64_trajectory_31_bodies_3650_steps(nb):
     assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-10 * np.abs(v_ref).max()
 
 
-@pytest.mark.parametrize("n", [2, 31, 32, 33, 64])
+@pytest.mark.parametrize("n", [2, 31, 32, 33, 64, 65, 131, 256])
 def test_small_system_kernel_vs_general_and_oracle(nb, n):
-    """One FP64 system of <= 64 bodies runs every step in one cluster launch
-    (8 CTAs up to 32 bodies, 16 beyond); it matches the oracle and the
-    general two-kernel path."""
+    """One FP64 system of <= 256 bodies runs every step in one cluster launch
+    (8 CTAs up to 32 bodies, 16 beyond; 4 warps per CTA up to 64 bodies, then
+    one per 16 targets); it matches the oracle and the general two-kernel
+    path."""
     s = inputs.solar_system(31, seed=70 + n) if n == 31 else None
-    if n in (32, 33, 64):
+    if n > 31:
         s = inputs.solar_system(n, seed=71, n_moons=0)
     if n == 2:
         r = np.array([[0.0, 1.0], [0.0, 0.0], [0.0, 0.0]])
