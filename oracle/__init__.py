@@ -13,6 +13,9 @@ Functions (all FP64 numpy arrays, structure-of-arrays):
 * ``accel_rows`` -- Eq. 1 for a sample of target bodies.
 * ``term_norm``  -- sum of the magnitudes of the terms of Eq. 1 (error scale).
 * ``verlet``     -- Eqs. 3-4, velocity-Verlet steps (Eq. 1 for the force).
+* ``rk4``        -- classical fourth-order Runge-Kutta steps on (r, v), the
+                    higher-order method Section 2 names.
+* ``leapfrog``   -- drift-kick-drift leapfrog steps (Section 2).
 * ``energy``     -- total energy (kinetic, potential), the accuracy criterion
                     of Sections 2 and 4.
 * ``vjp``        -- vector-Jacobian product of Eq. 1 w.r.t. positions and masses.
