@@ -190,8 +190,11 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs a) {
           const double4_32a r = sp[jj], w = sw[jj];
           const double dx = r.x - qx, dy = r.y - qy, dz = r.z - qz;
           double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-          if (diag) r2 = (jt0 + jj == tq) ? 1.0 : r2;
-          const double y = inv_r1(r2);
+          // The target itself: r2 = 1 and |d|^-1 = 0, so all its terms are 0
+          // (u = mu_q w_q - mu_q w_q need not round to exactly 0).
+          const bool self = diag && jt0 + jj == tq;
+          r2 = self ? 1.0 : r2;
+          const double y = self ? 0.0 : inv_r1(r2);
           const double y2 = y * y;
           const double s3 = y * y2;
           const double s5 = s3 * y2;
