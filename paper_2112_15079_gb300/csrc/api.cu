@@ -197,100 +197,22 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
 
 void free_work(nbody_ctx *c, Work &w);
 
-// Build stream-K work tables.  Each system is cut into target blocks of
-// balanced size (at most threads*ipt bodies).  The work line lists, block by
-// block, the sources of the block's system in units of 2 sources (mixed pair
-// layout) or 1 (FP64), each unit weighted by the warps the block keeps busy.
-// Three quarters of it (all of it when jsplit == 0) are cut into `grid` =
-// SMs * ctas_per_sm equal static shares (fewer for small systems, see
-// below), the rest into grid * jsplit chunks.
+// Build stream-K work tables (the plan is work_plan.h's) and upload them.
 // row_doubles: 8-byte words per body and partial row (3 force, 4 VJP).
 nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, int row_doubles) {
   free_work(c, wk);
-  const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
-  const int64_t unit = c->o.precision == NBODY_MIXED ? 2 : 1;
-  std::vector<nb::Blk> blks;
-  std::vector<int64_t> bj0, bunits, bw, bstart;  // per block: first source, units, weight, line start
-  int64_t W = 0;
-  for (int64_t s = 0; s < c->n_sys; ++s) {
-    const int64_t b = c->offsets[s], e = c->offsets[s + 1], ns = e - b;
-    const int64_t len = (ns + unit - 1) / unit;  // units of this system's (padded) source range
-    const int64_t nb_s = (ns + B - 1) / B;
-    for (int64_t k = 0; k < nb_s; ++k) {
-      const int64_t i0 = b + ns * k / nb_s, i1 = b + ns * (k + 1) / nb_s;
-      nb::Blk blk;
-      blk.i0 = static_cast<int32_t>(i0);
-      blk.i1 = static_cast<int32_t>(i1);
-      blk.q0 = static_cast<int32_t>(c->soff[s] + (i0 - b));
-      blk.nsplit = 0;
-      blks.push_back(blk);
-      // warps with at least one target: thread t holds targets t + k*threads
-      const int64_t busy = std::min<int64_t>(t.threads, i1 - i0);
-      const int64_t w = (busy + 31) / 32;
-      bj0.push_back(c->soff[s]);
-      bunits.push_back(len);
-      bw.push_back(w);
-      bstart.push_back(W);
-      W += len * w;
-    }
-  }
   if (occ < 1) return fail(c, NBODY_EINVAL, "tiles do not fit on an SM (threads %d, ipt %d, tj %d)", t.threads, t.ipt, t.tj);
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
-  int64_t units_total = 0;
-  for (int64_t u : bunits) units_total += u;
-  // Pieces must not get too short: every piece of a block adds a partial row
-  // that the per-body kernel adds for each of the block's bodies, and below a
-  // few thousand bodies those sums (FP64 TwoSum at GB300's 1/64 FP64 rate, on
-  // the FP64 path) cost more than the extra pieces gain in parallelism.  A
-  // piece gets at least c * sqrt(U) units, U the longest block's units: c = 1/2
-  // for mixed; for FP64 c = 1 below 800 units, 2 below 2000, 3 beyond (the
-  // best of c = 1, 1.5, 2, 3 measured from 65 to 5,003 bodies; from about
-  // 5,000 bodies on the shares are longer than that anyway).
-  int64_t umax = 1;
-  for (int64_t u : bunits) umax = std::max(umax, u);
-  const double cmin = c->o.precision == NBODY_MIXED ? 0.5 : umax < 800 ? 1.0 : umax < 2000 ? 2.0 : 3.0;
-  const int64_t umin = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(cmin * std::sqrt(static_cast<double>(umax)))));
-  const int64_t G =
-      std::max<int64_t>(1, std::min<int64_t>(units_total / umin, static_cast<int64_t>(c->nsm) * cps));
-  const int64_t D = std::min<int64_t>(static_cast<int64_t>(t.jsplit) * G, std::max<int64_t>(units_total - G, 0));
-  const int64_t Ws = D > 0 ? W - W / 4 : W;
-  std::vector<int64_t> cuts;  // piece boundaries on the line
-  for (int64_t g = 0; g <= G; ++g) cuts.push_back(Ws * g / G);
-  for (int64_t d = 1; d <= D; ++d) cuts.push_back(Ws + (W - Ws) * d / D);
-  const int64_t P = static_cast<int64_t>(cuts.size()) - 1;
-  // Unit boundary of line position x inside block k (the same rounding for
-  // both neighbours of a cut, so segments tile each block exactly).
-  auto cut = [&](size_t k, int64_t x) {
-    const int64_t off = std::min(std::max<int64_t>(x - bstart[k], 0), bunits[k] * bw[k]);
-    return (off + bw[k] / 2) / bw[k];
-  };
-  std::vector<nb::Seg> segs;
-  std::vector<int32_t> seg_off(P + 1, 0);
-  size_t b = 0;
-  for (int64_t g = 0; g < P; ++g) {
-    const int64_t lo = cuts[g], hi = cuts[g + 1];
-    seg_off[g] = static_cast<int32_t>(segs.size());
-    while (b < blks.size() && bstart[b] + bunits[b] * bw[b] <= lo) ++b;
-    for (size_t k = b; k < blks.size() && bstart[k] < hi; ++k) {
-      const int64_t u0 = cut(k, lo), u1 = cut(k, hi);
-      if (u1 <= u0) continue;
-      nb::Seg sg;
-      sg.blk = static_cast<int32_t>(k);
-      sg.s0 = static_cast<int32_t>(bj0[k] + u0 * unit);
-      sg.s1 = static_cast<int32_t>(bj0[k] + std::min(u1 * unit, bunits[k] * unit));
-      sg.slot = blks[k].nsplit++;
-      segs.push_back(sg);
-    }
-  }
-  seg_off[P] = static_cast<int32_t>(segs.size());
-  // Per body: how many partial rows its block has.
-  std::vector<uint16_t> nsl(c->N);
-  int rows = 1;
-  for (const nb::Blk &k : blks) {
-    rows = std::max(rows, static_cast<int>(k.nsplit));
-    for (int32_t p = k.i0; p < k.i1; ++p) nsl[p] = static_cast<uint16_t>(k.nsplit);
-  }
-  if (rows > 65535) return fail(c, NBODY_EINVAL, "too many source splits (%d)", rows);
+  nb::WorkPlan plan;
+  const std::string why = nb::plan_work(c->offsets, c->soff, c->o.precision == NBODY_MIXED, t.threads, t.ipt,
+                                        t.jsplit, static_cast<int64_t>(c->nsm) * cps, plan);
+  if (!why.empty()) return fail(c, NBODY_EINVAL, "%s", why.c_str());
+  const std::vector<nb::Blk> &blks = plan.blks;
+  const std::vector<nb::Seg> &segs = plan.segs;
+  const std::vector<int32_t> &seg_off = plan.seg_off;
+  const std::vector<uint16_t> &nsl = plan.nsl;
+  const int rows = plan.rows;
+  const int64_t G = plan.grid, D = plan.n_dyn;
   wk.n_dyn = static_cast<int>(D);
   wk.n_blks = static_cast<int>(blks.size());
   wk.rows = rows;

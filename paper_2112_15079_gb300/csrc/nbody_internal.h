@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "work_plan.h"
+
 namespace nb {
 
 // Device-side fault flags (bitwise OR into the context's flags word).
@@ -22,21 +24,7 @@ struct Item {
 };
 static_assert(sizeof(Item) == 32, "Item layout");
 
-// Force kernels: a target block of one system (at most threads * ipt
-// consecutive bodies [i0, i1); q0 = stage index of body i0) whose source
-// range is cut into `nsplit` contiguous segments processed by different CTAs.
-struct Blk {
-  int32_t i0, i1, q0, nsplit;
-};
-static_assert(sizeof(Blk) == 16, "Blk layout");
-
-// One segment: sources [s0, s1) (stage indices) of block `blk`; `slot` is the
-// segment's rank within the block: the partial-sum row it writes, and its
-// place in the fixed summation order.
-struct Seg {
-  int32_t blk, s0, s1, slot;
-};
-static_assert(sizeof(Seg) == 16, "Seg layout");
+// Blk (target block) and Seg (segment of a block's sources): work_plan.h.
 
 // Arguments of one force launch (Eq. 1 partial sums).  The work is cut into
 // pieces; piece k is the segment list segs[seg_off[k] .. seg_off[k+1]).

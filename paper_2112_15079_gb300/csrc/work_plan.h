@@ -1,0 +1,144 @@
+// Host-side plan of one stream-K force (or VJP) launch: target blocks, their
+// source segments, the pieces (CTA shares) that hold the segments, and the
+// partial rows per body.  Plain C++ without CUDA, so the library and a CPU
+// test build the same code.
+//
+// The plan: each system's targets are cut into blocks of balanced size (at
+// most threads * ipt bodies).  The work line lists, block by block, the
+// sources of the block's system in units of `unit` sources (2 on the mixed
+// path, whose stage pairs sources; 1 on the FP64 path), each unit weighted by
+// the warps the block keeps busy.  Three quarters of the line (all of it when
+// jsplit == 0) are cut into `grid` equal static shares, the rest into
+// grid * jsplit chunks handed out at run time.  A segment is the part of one
+// block inside one piece; its slot is its rank within the block, which fixes
+// the partial row it writes and its place in the summation order.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace nb {
+
+// Force kernels: a target block of one system (at most threads * ipt
+// consecutive bodies [i0, i1); q0 = stage index of body i0) whose source
+// range is cut into `nsplit` contiguous segments processed by different CTAs.
+struct Blk {
+  int32_t i0, i1, q0, nsplit;
+};
+static_assert(sizeof(Blk) == 16, "Blk layout");
+
+// One segment: sources [s0, s1) (stage indices) of block `blk`; `slot` is the
+// segment's rank within the block: the partial-sum row it writes, and its
+// place in the fixed summation order.
+struct Seg {
+  int32_t blk, s0, s1, slot;
+};
+static_assert(sizeof(Seg) == 16, "Seg layout");
+
+struct WorkPlan {
+  std::vector<Blk> blks;
+  std::vector<Seg> segs;
+  std::vector<int32_t> seg_off;  // [grid + n_dyn + 1]: piece k holds segs[seg_off[k] .. seg_off[k+1])
+  std::vector<uint16_t> nsl;     // [N]: partial rows of each body (its block's nsplit)
+  int rows = 1;                  // the largest nsplit
+  int64_t grid = 0;              // static shares (one per CTA)
+  int64_t n_dyn = 0;             // dynamic chunks
+};
+
+// offsets: [n_sys + 1] body offsets of the systems; soff: [n_sys + 1] their
+// stage offsets (the mixed stage pads every system to an even length).
+// slots: SMs x resident CTAs per SM the launch may use.  Returns an empty
+// string on success, else the reason the plan cannot be made.
+inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vector<int64_t> &soff, bool mixed,
+                             int threads, int ipt, int jsplit, int64_t slots, WorkPlan &out) {
+  out = WorkPlan{};
+  const int64_t n_sys = static_cast<int64_t>(offsets.size()) - 1;
+  const int64_t B = static_cast<int64_t>(threads) * ipt;
+  const int64_t unit = mixed ? 2 : 1;
+  if (n_sys < 1 || B < 1 || slots < 1) return "empty work";
+  std::vector<int64_t> bj0, bunits, bw, bstart;  // per block: first source, units, weight, line start
+  int64_t W = 0;
+  for (int64_t s = 0; s < n_sys; ++s) {
+    const int64_t b = offsets[s], e = offsets[s + 1], ns = e - b;
+    const int64_t len = (ns + unit - 1) / unit;  // units of this system's (padded) source range
+    const int64_t nb_s = (ns + B - 1) / B;
+    for (int64_t k = 0; k < nb_s; ++k) {
+      const int64_t i0 = b + ns * k / nb_s, i1 = b + ns * (k + 1) / nb_s;
+      Blk blk;
+      blk.i0 = static_cast<int32_t>(i0);
+      blk.i1 = static_cast<int32_t>(i1);
+      blk.q0 = static_cast<int32_t>(soff[s] + (i0 - b));
+      blk.nsplit = 0;
+      out.blks.push_back(blk);
+      // warps with at least one target: thread t holds targets t + k*threads
+      const int64_t busy = std::min<int64_t>(threads, i1 - i0);
+      const int64_t w = (busy + 31) / 32;
+      bj0.push_back(soff[s]);
+      bunits.push_back(len);
+      bw.push_back(w);
+      bstart.push_back(W);
+      W += len * w;
+    }
+  }
+  int64_t units_total = 0;
+  for (int64_t u : bunits) units_total += u;
+  // Pieces must not get too short: every piece of a block adds a partial row
+  // that the per-body kernel adds for each of the block's bodies, and below a
+  // few thousand bodies those sums (FP64 TwoSum at GB300's 1/64 FP64 rate, on
+  // the FP64 path) cost more than the extra pieces gain in parallelism.  A
+  // piece gets at least c * sqrt(U) units, U the longest block's units: c = 1/2
+  // for mixed; for FP64 c = 1 below 800 units, 2 below 2000, 3 beyond (the
+  // best of c = 1, 1.5, 2, 3 measured from 65 to 5,003 bodies; from about
+  // 5,000 bodies on the shares are longer than that anyway).
+  int64_t umax = 1;
+  for (int64_t u : bunits) umax = std::max(umax, u);
+  const double cmin = mixed ? 0.5 : umax < 800 ? 1.0 : umax < 2000 ? 2.0 : 3.0;
+  const int64_t umin = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(cmin * std::sqrt(static_cast<double>(umax)))));
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total / umin, slots));
+  const int64_t D = std::min<int64_t>(static_cast<int64_t>(jsplit) * G, std::max<int64_t>(units_total - G, 0));
+  const int64_t Ws = D > 0 ? W - W / 4 : W;
+  std::vector<int64_t> cuts;  // piece boundaries on the line
+  for (int64_t g = 0; g <= G; ++g) cuts.push_back(Ws * g / G);
+  for (int64_t d = 1; d <= D; ++d) cuts.push_back(Ws + (W - Ws) * d / D);
+  const int64_t P = static_cast<int64_t>(cuts.size()) - 1;
+  // Unit boundary of line position x inside block k (the same rounding for
+  // both neighbours of a cut, so segments tile each block exactly).
+  auto cut = [&](size_t k, int64_t x) {
+    const int64_t off = std::min(std::max<int64_t>(x - bstart[k], 0), bunits[k] * bw[k]);
+    return (off + bw[k] / 2) / bw[k];
+  };
+  out.seg_off.assign(P + 1, 0);
+  size_t b = 0;
+  for (int64_t g = 0; g < P; ++g) {
+    const int64_t lo = cuts[g], hi = cuts[g + 1];
+    out.seg_off[g] = static_cast<int32_t>(out.segs.size());
+    while (b < out.blks.size() && bstart[b] + bunits[b] * bw[b] <= lo) ++b;
+    for (size_t k = b; k < out.blks.size() && bstart[k] < hi; ++k) {
+      const int64_t u0 = cut(k, lo), u1 = cut(k, hi);
+      if (u1 <= u0) continue;
+      Seg sg;
+      sg.blk = static_cast<int32_t>(k);
+      sg.s0 = static_cast<int32_t>(bj0[k] + u0 * unit);
+      sg.s1 = static_cast<int32_t>(bj0[k] + std::min(u1 * unit, bunits[k] * unit));
+      sg.slot = out.blks[k].nsplit++;
+      out.segs.push_back(sg);
+    }
+  }
+  out.seg_off[P] = static_cast<int32_t>(out.segs.size());
+  // Per body: how many partial rows its block has.
+  out.nsl.assign(static_cast<size_t>(offsets[n_sys]), 0);
+  out.rows = 1;
+  for (const Blk &k : out.blks) {
+    out.rows = std::max(out.rows, static_cast<int>(k.nsplit));
+    for (int32_t p = k.i0; p < k.i1; ++p) out.nsl[p] = static_cast<uint16_t>(k.nsplit);
+  }
+  if (out.rows > 65535) return "too many source splits (" + std::to_string(out.rows) + ")";
+  out.grid = G;
+  out.n_dyn = D;
+  return "";
+}
+
+}  // namespace nb

@@ -1,0 +1,29 @@
+// Test-only C entry point over the library's host work planner
+// (paper_2112_15079_gb300/csrc/work_plan.h).  tests/test_work_plan.py builds
+// it with g++ and checks the plan's invariants on the CPU; no CUDA involved.
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "work_plan.h"
+
+// meta[0..4] = blocks, segments, grid, dynamic chunks, rows.  Returns 0, or
+// 1 when the planner refuses, 2 when a capacity is too small.
+extern "C" int wp_plan(int64_t n_sys, const int64_t *offsets, const int64_t *soff, int mixed, int threads, int ipt,
+                       int jsplit, int64_t slots, int64_t cap_blks, int64_t cap_segs, int64_t cap_pieces,
+                       int32_t *blks, int32_t *segs, int32_t *seg_off, uint16_t *nsl, int64_t *meta) {
+  const std::vector<int64_t> off(offsets, offsets + n_sys + 1), so(soff, soff + n_sys + 1);
+  nb::WorkPlan p;
+  if (!nb::plan_work(off, so, mixed != 0, threads, ipt, jsplit, slots, p).empty()) return 1;
+  meta[0] = static_cast<int64_t>(p.blks.size());
+  meta[1] = static_cast<int64_t>(p.segs.size());
+  meta[2] = p.grid;
+  meta[3] = p.n_dyn;
+  meta[4] = p.rows;
+  if (meta[0] > cap_blks || meta[1] > cap_segs || static_cast<int64_t>(p.seg_off.size()) > cap_pieces + 1) return 2;
+  std::memcpy(blks, p.blks.data(), sizeof(nb::Blk) * p.blks.size());
+  std::memcpy(segs, p.segs.data(), sizeof(nb::Seg) * p.segs.size());
+  std::memcpy(seg_off, p.seg_off.data(), sizeof(int32_t) * p.seg_off.size());
+  std::memcpy(nsl, p.nsl.data(), sizeof(uint16_t) * p.nsl.size());
+  return 0;
+}
