@@ -37,7 +37,7 @@
  *   use): NBODY_INJECT_ALLOC_FAIL=k fails a context's k-th device allocation
  *   with NBODY_ENOMEM; NBODY_INJECT_WAIT_STALL=k (read by nbody_init) stalls
  *   one bounded device wait in the context's k-th launch that has one (an
- *   adjoint product: one source copy left unissued; a small-system
+ *   adjoint product: one source copy left unissued; a single-launch
  *   nbody_step call: one barrier arrival left out), so that wait runs out
  *   (~2 s), the kernel winds down, and nbody_grad / nbody_sync returns
  *   NBODY_ETIMEOUT.
@@ -98,9 +98,10 @@ typedef struct {
 
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
 #define NBODY_FLAG_NO_GRAPH 1
-/* Never use the single-launch small-system kernel (one FP64 system of at
- * most 256 bodies runs every step of an nbody_step call in one launch of an
- * 8-CTA (N <= 32) or 16-CTA cluster unless this flag is set). */
+/* Never use the single-launch kernels (one FP64 Verlet system of at most
+ * 4,096 bodies runs every step of an nbody_step call in one launch: of an
+ * 8- or 16-CTA cluster up to 96 bodies, of a cooperative grid beyond,
+ * unless this flag is set). */
 #define NBODY_FLAG_NO_SMALL 2
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work
@@ -150,8 +151,8 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
  * at the new positions, so the context's acceleration always belongs to the
  * current state.  Consecutive steps are replayed from cached CUDA graphs
  * unless NBODY_FLAG_NO_GRAPH is set or the stream is already being
- * captured.  One FP64 Verlet system of at most 256 bodies instead runs all
- * n_steps in a single cluster launch (see NBODY_FLAG_NO_SMALL). */
+ * captured.  One FP64 Verlet system of at most 4,096 bodies instead runs
+ * all n_steps in a single launch (see NBODY_FLAG_NO_SMALL). */
 nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
 
 /* Copy the acceleration at the current positions (Eq. 1, as used by the

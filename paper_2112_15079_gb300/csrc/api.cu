@@ -24,6 +24,7 @@ namespace {
 thread_local std::string g_init_error;
 
 constexpr int kGraphChunk = 64;  // steps per cached graph (even: stage parity repeats)
+constexpr int kSmallClusterMax = 96;  // bodies: the cluster kernel up to here, then the grid kernel
 
 // Stream-K work tables of one kernel family (force or VJP): target blocks,
 // segments per piece, the partial-row array and its row count per body.
@@ -74,7 +75,7 @@ struct nbody_ctx {
   // scratch
   std::vector<void *> allocs;
   int alloc_seq = 0;  // device allocations made so far (fault injection counts these)
-  int64_t wait_seq = 0;      // launches with a stallable bounded wait (adjoint products, small-system steps)
+  int64_t wait_seq = 0;      // launches with a stallable bounded wait (adjoint products, single-launch steps)
   int64_t stall_at = 0;      // test hook (NBODY_INJECT_WAIT_STALL=k): the k-th of them stalls
   double *a = nullptr;               // [3][N] acceleration at the current positions
   void *stage[2] = {nullptr, nullptr};  // ping-pong staged sources (layout per precision)
@@ -96,7 +97,11 @@ struct nbody_ctx {
   Work fw;
   Adjoint adj;
 
-  bool small = false;  // the single-launch small-system kernel serves nbody_step
+  bool small = false;  // the single-launch cluster kernel serves nbody_step
+  bool grid = false;   // the single-launch cooperative grid kernel serves nbody_step
+  int grid_warps = 0, grid_ctas = 0;
+  double *xg = nullptr;      // grid kernel: [2][3][N] position exchange
+  unsigned *gbar = nullptr;  // grid kernel: barrier arrivals
   std::map<int, cudaGraphExec_t> graphs;
   std::string err;
 };
@@ -659,7 +664,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   // Optional host-side test hook: NBODY_INJECT_WAIT_STALL=k stalls one
   // bounded wait in the context's k-th launch that has one: the first source
   // tile of CTA 0 stays unissued in an adjoint product (VJP launch), or CTA 0
-  // leaves out one barrier arrival in a small-system step call.  The wait
+  // leaves out one barrier arrival in a single-launch step call.  The wait
   // runs out and nbody_grad / nbody_sync report ETIMEOUT.  (The force kernels
   // carry no test code.)
   if (const char *inj = std::getenv("NBODY_INJECT_WAIT_STALL")) c->stall_at = std::atoll(inj);
@@ -703,11 +708,22 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   nbody_status st = alloc_scratch(c);
   if (st != NBODY_OK) return bail(st);
   if ((st = build_items(c, default_tiles(c))) != NBODY_OK) return bail(st);
-  c->small = c->n_sys == 1 && c->N <= nb::small_max_bodies() && c->o.precision == NBODY_FP64 &&
-             c->o.integrator == NBODY_VERLET && !(c->o.flags & NBODY_FLAG_NO_SMALL);
-  if (c->small && nb::small_prepare() != cudaSuccess) {  // no 16-CTA clusters here: general path
+  // One FP64 Verlet system: every step of a call in one launch, a cluster up
+  // to kSmallClusterMax bodies, a cooperative grid up to the grid kernel's
+  // limit (each faster than the general path there).
+  const bool single = c->n_sys == 1 && c->o.precision == NBODY_FP64 && c->o.integrator == NBODY_VERLET &&
+                      !(c->o.flags & NBODY_FLAG_NO_SMALL);
+  c->small = single && c->N <= std::min(kSmallClusterMax, nb::small_max_bodies());
+  if (c->small && nb::small_prepare() != cudaSuccess) {  // no 16-CTA clusters here: the next path
     cudaGetLastError();
     c->small = false;
+  }
+  c->grid = single && !c->small && c->N <= nb::grid_max_bodies() &&
+            nb::grid_shape(c->N, c->nsm, &c->grid_warps, &c->grid_ctas) == cudaSuccess;
+  cudaGetLastError();
+  if (c->grid) {
+    if ((st = dalloc(c, reinterpret_cast<void **>(&c->xg), sizeof(double) * 6 * c->N)) != NBODY_OK) return bail(st);
+    if ((st = dalloc(c, reinterpret_cast<void **>(&c->gbar), sizeof(unsigned))) != NBODY_OK) return bail(st);
   }
   if ((st = refresh(c)) != NBODY_OK) return bail(st);
   *out = c;
@@ -739,6 +755,37 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
     if (e == cudaSuccess) return end_work(c);
     cudaGetLastError();  // cluster launch refused: fall back to the general path for good
     c->small = false;
+  }
+  if (c->grid) {
+    nb::SmallArgs sa{};
+    sa.x = s.x; sa.y = s.y; sa.z = s.z; sa.vx = s.vx; sa.vy = s.vy; sa.vz = s.vz;
+    sa.ax = s.ax; sa.ay = s.ay; sa.az = s.az;
+    sa.m = c->m;
+    sa.flags = c->flags;
+    sa.xg = c->xg;
+    sa.gbar = c->gbar;
+    sa.N = c->N;
+    sa.G = c->o.G;
+    sa.dt = c->o.dt;
+    sa.half_dt = 0.5 * c->o.dt;
+    sa.half_dt2 = 0.5 * c->o.dt * c->o.dt;
+    // The barrier counts arrivals in 32 bits: steps x CTAs per launch < 2^31.
+    const int64_t chunk = std::max<int64_t>(1, (int64_t(1) << 31) / c->grid_ctas);
+    bool refused = false;
+    for (int64_t done = 0; done < n_steps;) {
+      sa.n_steps = std::min<int64_t>(chunk, n_steps - done);
+      sa.stall = ++c->wait_seq == c->stall_at ? 1 : 0;
+      NB_CUDA(c, cudaMemsetAsync(c->gbar, 0, sizeof(unsigned), c->stream));
+      if (nb::launch_grid(sa, c->grid_warps, c->grid_ctas, c->stream) != cudaSuccess) {
+        cudaGetLastError();  // cooperative launch refused: the general path, for good
+        c->grid = false;
+        refused = true;
+        n_steps -= done;
+        break;
+      }
+      done += sa.n_steps;
+    }
+    if (!refused) return end_work(c);
   }
   if (c->o.integrator == NBODY_RK4)  // stage 1 of the first step, from (r, v, a)
     NB_CUDA(c, nb::launch_rk_prep(c->o.precision, rk_args(c, s, nullptr, c->stage[0], 1), c->stream));
@@ -846,6 +893,17 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   const DeviceGuard dg(c->dev);
   if (probe_steps < 1) return fail(c, NBODY_EINVAL, "probe_steps must be >= 1");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  // Tiles shape only the general path (and nbody_accel / nbody_grad): time
+  // that path even where a single-launch kernel serves nbody_step.
+  struct PathGuard {
+    nbody_ctx *c;
+    bool small, grid;
+    ~PathGuard() {
+      c->small = small;
+      c->grid = grid;
+    }
+  } const keep{c, c->small, c->grid};
+  c->small = c->grid = false;
   const size_t N = c->N, b = sizeof(double) * N;
   // Save the bound state and a; every candidate starts from it.
   double *save = nullptr;

@@ -102,12 +102,15 @@ struct AdjArgs {
   double G, dt, half_dt, half_dt2;
 };
 
-// Small-N persistent kernel (smalln.cu): all steps of one FP64 system in one
-// cluster launch; state read from and written back to these arrays.
+// Single-launch kernels (smalln.cu): all steps of one FP64 system in one
+// launch, a thread-block cluster (small systems) or a cooperative grid
+// (mid-size systems); state read from and written back to these arrays.
 struct SmallArgs {
   double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
   const double *m;
   unsigned *flags;
+  double *xg;      // grid kernel: [2][3][N] position exchange buffers
+  unsigned *gbar;  // grid kernel: barrier arrivals, zero at launch
   int32_t N;
   int64_t n_steps;
   double G, dt, half_dt, half_dt2;
@@ -192,6 +195,11 @@ cudaError_t run_peaks(double *out);
 int small_max_bodies();
 cudaError_t small_prepare();
 cudaError_t launch_small(const SmallArgs &a, cudaStream_t s);
+int grid_max_bodies();
+// Shape of the grid kernel for N bodies on nsm SMs: warps (targets) per CTA
+// and CTAs, all resident at once; an error if no shape fits.
+cudaError_t grid_shape(int N, int nsm, int *warps, int *ctas);
+cudaError_t launch_grid(const SmallArgs &a, int warps, int ctas, cudaStream_t s);
 size_t vjp_smem_bytes(int precision, int tj);
 int vjp_threads(int precision);
 cudaError_t vjp_prepare(int precision, size_t smem, int *occ);  // raise the smem limit, resident CTAs/SM

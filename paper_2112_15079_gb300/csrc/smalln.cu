@@ -1,15 +1,18 @@
-// Small systems (N <= kSmallMax, FP64, one system): every velocity-Verlet
-// step of an nbody_step call inside ONE launch of one thread-block cluster.
+// Single-launch paths for one FP64 system: every velocity-Verlet step of an
+// nbody_step call inside ONE launch, of one thread-block cluster (small
+// systems, smalln_kernel) or of a cooperative grid (mid-size systems,
+// gridn_kernel, further below).  The host picks the cluster up to 96 bodies
+// and the grid from 97 to 4,096, where each is the fastest path measured.
 //
 // The Sun-plus-30-bodies model has 930 interactions per step; as separate
 // launches a step costs two kernel launches for microseconds of work.  Here
 // the cluster's CTAs (8 for N <= 32, else 16; one per SM) own the targets,
 // one warp per target (4 warps per CTA up to 64 bodies, then ceil(N / 16), at
 // most kMaxWarps): the warp's 32 lanes split the sources and sum them in
-// FP64.  Up to kSmallMax = 256 bodies this beats the general two-kernel path,
-// which spreads the pairs over every SM but pays two launches and the
-// partial-row sums per step (measured: 8.5x at 31 bodies, 2.7x at 131, 1.3x
-// at 256).  Every CTA keeps all positions in its shared
+// FP64 (up to kSmallMax = 256 bodies; beyond 96 the grid kernel is faster).
+// Against the general two-kernel path, which spreads the pairs over every SM
+// but pays two launches and the partial-row sums per step: 8.7x at 31 bodies,
+// 4.8x at 96.  Every CTA keeps all positions in its shared
 // memory (ping-pong buffers pos[0], pos[1]).  Eq. 1 uses the same FP64
 // interaction as the general kernel (binomial-series refinement of the MUFU
 // seed), Eqs. 3-4 the same kick/drift functions.
@@ -44,6 +47,8 @@
 // Test hook: with a.stall set, CTA 0 leaves out its arrival on the first
 // step's barrier, so its wait runs out (about 2 s), the others' next wait
 // too, and the host reads NBODY_ETIMEOUT.
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "nbody_dev.cuh"
@@ -89,6 +94,31 @@ __device__ __forceinline__ bool wait_cluster(uint64_t *bar, uint32_t parity) {
     if (ok) return true;
   }
   return false;
+}
+
+// Eq. 1 for target p by one warp: the lanes split the sources (positions
+// and G m in shared memory), then a butterfly reduce-scatter over the lanes
+// leaves component lane / 8 of a_p in every lane of that group (lanes 24..31:
+// a zero padding component).  Level 16: lanes with bit 4 clear keep
+// components (0, 1), the others (2, 3); level 8: bit 3 picks one of the two;
+// levels 4, 2, 1 finish the sum.  Fixed order, so deterministic.
+__device__ __forceinline__ double warp_accel(const double4_32a *pos, int n, int p, int lane) {
+  double s0 = 0, s1 = 0, s2 = 0;
+  const double4_32a me = pos[p];
+  for (int j = lane; j < n; j += 32) {
+    if (j == p) continue;
+    interact_fp64<false>(pos[j], me.x, me.y, me.z, false, s0, s1, s2);
+  }
+  const bool h = (lane & 16) != 0;
+  const double k0 = h ? s2 : s0, k1 = h ? 0.0 : s1;
+  const double g0 = h ? s0 : s2, g1 = h ? s1 : 0.0;
+  const double t0 = k0 + __shfl_xor_sync(0xffffffffu, g0, 16);
+  const double t1 = k1 + __shfl_xor_sync(0xffffffffu, g1, 16);
+  const bool g = (lane & 8) != 0;
+  double s = (g ? t1 : t0) + __shfl_xor_sync(0xffffffffu, g ? t0 : t1, 8);
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
 }
 
 template <typename T>
@@ -171,25 +201,8 @@ __global__ void __launch_bounds__(32 * kMaxWarps) smalln_kernel(const SmallArgs 
       break;
     }
     b = nb;
-    // Eq. 1 at the new positions: lanes split the sources.
-    double s0 = 0, s1 = 0, s2 = 0;
-    const double4_32a me = pos[b][p];
-    for (int j = lane; j < n; j += 32) {
-      if (j == p) continue;
-      interact_fp64<false>(pos[b][j], me.x, me.y, me.z, false, s0, s1, s2);
-    }
-    // Butterfly reduce-scatter over the lanes.  Level 16: lanes with bit 4
-    // clear keep components (0, 1), the others (2, 3 = zero padding).
-    const bool h = (lane & 16) != 0;
-    const double k0 = h ? s2 : s0, k1 = h ? 0.0 : s1;
-    const double g0 = h ? s0 : s2, g1 = h ? s1 : 0.0;
-    const double t0 = k0 + __shfl_xor_sync(0xffffffffu, g0, 16);
-    const double t1 = k1 + __shfl_xor_sync(0xffffffffu, g1, 16);
-    // Level 8: bit 3 picks one of the two; the lane now holds component c.
-    const bool g = (lane & 8) != 0;
-    double s = (g ? t1 : t0) + __shfl_xor_sync(0xffffffffu, g ? t0 : t1, 8);
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    // Eq. 1 at the new positions.
+    const double s = warp_accel(pos[b], n, p, lane);
     if (upd) {
       if (!isfinite(s) && (lane & 7) == 0) atomicOr(a.flags, kFlagNonFinite);
       v = kick(v, acc, s, a.half_dt);  // Eq. 4
@@ -202,6 +215,107 @@ __global__ void __launch_bounds__(32 * kMaxWarps) smalln_kernel(const SmallArgs 
     pick_ptr(c, a.ax, a.ay, a.az)[p] = acc;
   }
   cluster.sync();  // no CTA leaves while others may still write into its shared memory
+}
+
+// ---------------------------------------------------------------------------
+// Mid-size systems: the same per-warp step over a cooperative grid.
+//
+// The cluster kernel above uses 16 SMs; from about a hundred bodies the FP64
+// chain of its warps (one target each, ceil(N/32) sources per lane) grows
+// long, while the general path pays two launches and the partial-row sums
+// per step.  This kernel keeps one warp per target but spreads the targets
+// over as many CTAs as the GPU holds at once (a cooperative launch, so all
+// are resident): each step the owners store their drifted coordinates into
+// a global exchange buffer (double-buffered by step parity), one grid-wide
+// barrier publishes them, and every CTA loads all positions from L2 into
+// shared memory.  The barrier is a counter of arrivals: arrival k + 1 of
+// every CTA means all step-k stores are visible (fence before the arrival,
+// acquire load of the counter after).  Buffer reuse needs no second
+// barrier: a CTA stores into buffer b at step k + 2 only after barrier
+// k + 1, which every CTA reaches only after loading buffer b at step k.
+// Waits are bounded (kGridPolls); a wait that runs out sets kFlagTimeout and
+// the CTA leaves, so the others' waits run out too.
+// ---------------------------------------------------------------------------
+constexpr int kGridMax = 4096;                // bodies (a full copy of the positions per CTA)
+constexpr uint32_t kGridPolls = 1u << 21;  // an L2 round trip plus a 64 ns back-off each: about a second
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const unsigned *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bounded barrier of the whole cooperative grid; false if it ran out.
+__device__ __forceinline__ bool grid_barrier(unsigned *ctr, uint32_t target, bool arrive, int *s_abort) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (arrive) atomicAdd(ctr, 1u);
+    for (uint32_t i = 0; ld_acquire_gpu(ctr) < target; ++i) {
+      if (i == kGridPolls) {
+        *s_abort = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *s_abort == 0;
+}
+
+__global__ void __launch_bounds__(1024) gridn_kernel(const SmallArgs a) {
+  extern __shared__ __align__(32) unsigned char gsm[];
+  double4_32a *pos = reinterpret_cast<double4_32a *>(gsm);  // [N]: (x, y, z, G m)
+  __shared__ int s_abort;
+  const int warps = static_cast<int>(blockDim.x >> 5);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.N;
+  const size_t N = static_cast<size_t>(n);
+  const int p = static_cast<int>(blockIdx.x) * warps + warp;  // this warp's target (if < n)
+  const bool own = p < n;
+  const int c = lane >> 3;
+  const bool upd = own && c < 3;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) pos[j].w = a.G * a.m[j];
+  double r = 0, v = 0, acc = 0;
+  if (upd) {
+    r = pick_ptr(c, a.x, a.y, a.z)[p];
+    v = pick_ptr(c, a.vx, a.vy, a.vz)[p];
+    acc = pick_ptr(c, a.ax, a.ay, a.az)[p];
+  }
+  if (threadIdx.x == 0) s_abort = 0;
+  const bool stall = a.stall != 0 && blockIdx.x == 0;
+  for (int64_t step = 0; step < a.n_steps; ++step) {  // every thread of every CTA runs every step
+    double *xb = a.xg + static_cast<size_t>(step & 1) * 3 * N;
+    if (upd) {
+      r = drift(r, v, acc, a.dt, a.half_dt2);  // Eq. 3
+      if ((lane & 7) == 0) xb[c * N + p] = r;
+    }
+    const uint32_t target = static_cast<uint32_t>(step + 1) * gridDim.x;
+    if (!grid_barrier(a.gbar, target, !(stall && step == 0), &s_abort)) {
+      if (threadIdx.x == 0) atomicOr(a.flags, kFlagTimeout);
+      break;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {  // other CTAs' stores: read through L2
+      pos[j].x = __ldcg(xb + j);
+      pos[j].y = __ldcg(xb + N + j);
+      pos[j].z = __ldcg(xb + 2 * N + j);
+    }
+    __syncthreads();
+    if (own) {  // warp-uniform
+      const double s = warp_accel(pos, n, p, lane);  // Eq. 1
+      if (upd) {
+        if (!isfinite(s) && (lane & 7) == 0) atomicOr(a.flags, kFlagNonFinite);
+        v = kick(v, acc, s, a.half_dt);  // Eq. 4
+        acc = s;
+      }
+    }
+  }
+  if (upd && (lane & 7) == 0) {
+    pick_ptr(c, a.x, a.y, a.z)[p] = r;
+    pick_ptr(c, a.vx, a.vy, a.vz)[p] = v;
+    pick_ptr(c, a.ax, a.ay, a.az)[p] = acc;
+  }
 }
 
 }  // namespace
@@ -227,6 +341,45 @@ cudaError_t launch_small(const SmallArgs &a, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, smalln_kernel, a);
+}
+
+
+int grid_max_bodies() { return kGridMax; }
+
+cudaError_t grid_shape(int N, int nsm, int *warps, int *ctas) {
+  if (N < 1 || N > kGridMax) return cudaErrorInvalidValue;
+  const size_t smem = 32 * static_cast<size_t>(N);
+  cudaError_t e = cudaFuncSetAttribute(gridn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(32 * static_cast<size_t>(kGridMax)));
+  if (e != cudaSuccess) return e;
+  // One CTA per SM: ceil(N / SMs) targets per CTA, rounded up to a multiple
+  // of 4 warps so the SM's four sub-partitions (each with its own share of
+  // the FP64 pipe) carry equal loads.
+  const int w = std::max(4, (((N + nsm - 1) / nsm) + 3) / 4 * 4);
+  if (w > 32) return cudaErrorCooperativeLaunchTooLarge;
+  int occ = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gridn_kernel, 32 * w, smem)) != cudaSuccess) return e;
+  const int g = (N + w - 1) / w;
+  if (occ >= 1 && g <= occ * nsm) {
+    *warps = w;
+    *ctas = g;
+    return cudaSuccess;
+  }
+  return cudaErrorCooperativeLaunchTooLarge;
+}
+
+cudaError_t launch_grid(const SmallArgs &a, int warps, int ctas, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(32 * warps);
+  cfg.dynamicSmemBytes = 32 * static_cast<size_t>(a.N);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gridn_kernel, a);
 }
 
 }  // namespace nb

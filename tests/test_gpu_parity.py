@@ -35,8 +35,8 @@ def nb():
     return nbody
 
 
-def _make(nb, s, precision, tiles=None, graphs=True, offsets=None):
-    b = nb.NBody(s.r, s.v, s.m, offsets, G=s.G, dt=s.dt, precision=precision, graphs=graphs)
+def _make(nb, s, precision, tiles=None, graphs=True, offsets=None, small=True):
+    b = nb.NBody(s.r, s.v, s.m, offsets, G=s.G, dt=s.dt, precision=precision, graphs=graphs, small=small)
     if tiles:
         t = b.tiles
         t.update(tiles)
@@ -118,9 +118,9 @@ def test_fp64_trajectory_31_bodies_3650_steps(nb):
     assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-10 * np.abs(v_ref).max()
 
 
-@pytest.mark.parametrize("n", [2, 31, 32, 33, 64, 65, 131, 256])
+@pytest.mark.parametrize("n", [2, 31, 32, 33, 64, 65, 96])
 def test_small_system_kernel_vs_general_and_oracle(nb, n):
-    """One FP64 system of <= 256 bodies runs every step in one cluster launch
+    """One FP64 system of <= 96 bodies runs every step in one cluster launch
     (8 CTAs up to 32 bodies, 16 beyond; 4 warps per CTA up to 64 bodies, then
     one per 16 targets); it matches the oracle and the general two-kernel
     path."""
@@ -147,6 +147,59 @@ def test_small_system_kernel_vs_general_and_oracle(nb, n):
     assert np.abs(small.r.cpu().numpy() - gen.r.cpu().numpy()).max() <= 1e-11 * max(1.0, np.abs(r_ref).max())
 
 
+@pytest.mark.parametrize("n,steps", [(97, 1000), (257, 1000), (521, 400), (1031, 200), (4096, 10)])
+def test_grid_kernel_vs_general_and_oracle(nb, n, steps):
+    """One FP64 system of 97 to 4,096 bodies runs every step of a call in one
+    cooperative grid launch (one warp per target, positions exchanged through
+    L2 behind a grid barrier); it matches the oracle and the general path,
+    and a run split into two calls is bitwise the same as one call."""
+    s = inputs.solar_system(n, seed=73, n_moons=0)
+    grid = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    gen = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64", small=False)
+    whole = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    for b in (grid, gen):
+        b.step(steps // 3)
+        b.step(steps - steps // 3)
+        b.sync()
+    whole.step(steps)
+    whole.sync()
+    assert np.array_equal(grid.state.cpu().numpy(), whole.state.cpu().numpy())
+    r_ref, v_ref, a_ref = oracle.verlet(s.G, s.dt, steps, s.r, s.v, s.m, openmp=True)
+    for b in (grid, gen):
+        assert np.abs(b.r.cpu().numpy() - r_ref).max() <= 1e-11 * max(1.0, np.abs(r_ref).max())
+        assert np.abs(b.v.cpu().numpy() - v_ref).max() <= 1e-11 * np.abs(v_ref).max()
+        a = b.accel().cpu().numpy()
+        assert np.max(np.linalg.norm(a - a_ref, axis=0) / np.linalg.norm(a_ref, axis=0)) <= FP64_TOL
+
+
+def test_grid_kernel_wait_timeout_reports_and_recovers(nb, monkeypatch):
+    """NBODY_INJECT_WAIT_STALL=1 makes CTA 0 of the cooperative grid kernel
+    (257 bodies) skip its first barrier arrival: every CTA's bounded wait
+    runs out (about a second), the kernel winds down, nbody_sync reports
+    ETIMEOUT, and after the state is restored and reset the context steps
+    bitwise like a fresh one."""
+    import time
+    s = inputs.solar_system(257, seed=54, n_moons=0)
+    fresh = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    fresh.step(50)
+    want = fresh.state.cpu().numpy()
+    monkeypatch.setenv("NBODY_INJECT_WAIT_STALL", "1")
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    monkeypatch.delenv("NBODY_INJECT_WAIT_STALL")
+    t0 = time.time()
+    b.step(10)
+    with pytest.raises(nb.NBodyError) as ei:
+        b.sync()
+    assert ei.value.status == nb.NBODY_ETIMEOUT
+    assert time.time() - t0 < 60
+    torch = pytest.importorskip("torch")
+    b.state[0:3].copy_(torch.tensor(s.r))
+    b.state[3:6].copy_(torch.tensor(s.v))
+    b.reset()
+    b.step(50)
+    assert np.array_equal(b.state.cpu().numpy(), want)
+
+
 def test_mixed_energy_drift_31_bodies(nb):
     """Energy drift of the mixed path within 2x the oracle's (3650 steps)."""
     s = inputs.solar_system(31)
@@ -165,19 +218,20 @@ def test_mixed_energy_drift_31_bodies(nb):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_split_calls_and_graphs_bitwise(nb, precision):
-    """n steps in one call == the same steps over several calls == without
-    graphs: the kernels are deterministic and the drift is the same code."""
+    """On the general path (two launches per step): n steps in one call ==
+    the same steps over several calls == without graphs: the kernels are
+    deterministic and the drift is the same code."""
     s = inputs.solar_system(2131, seed=3)
     outs = []
     for graphs, chunks in ((True, [130]), (True, [64, 1, 65]), (False, [7, 123])):
-        b = _make(nb, s, precision, graphs=graphs)
+        b = _make(nb, s, precision, graphs=graphs, small=False)
         for c in chunks:
             b.step(c)
         outs.append(b.state.cpu().numpy())
         b.close()
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0], outs[2])
-    b = _make(nb, s, precision)
+    b = _make(nb, s, precision, small=False)
     kt = b.kernel_times(130)  # the timed, unchained launches compute the same steps
     assert np.array_equal(b.state.cpu().numpy(), outs[0])
     assert kt["steps"] == 130 and kt["force_ms"] > 0 and kt["verlet_ms"] > 0
