@@ -196,9 +196,10 @@ nbody_status nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *t);
 nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
 
 /* Time each candidate decomposition on the bound state for `probe_steps`
- * steps and keep the fastest.  The bound state is restored afterwards.
- * best (HOST, may be NULL) receives the winner, best_ms its time per step.
- * Synchronous. */
+ * steps of the general (two-kernel) path, the one tiles shape, and keep the
+ * fastest; a context whose nbody_step runs a single-launch kernel keeps
+ * doing so.  The bound state is restored afterwards.  best (HOST, may be
+ * NULL) receives the winner, best_ms its time per step.  Synchronous. */
 nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *best,
                             double *best_ms);
 
