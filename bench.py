@@ -469,8 +469,9 @@ def timed(torch, stream, fn, reps=1):
 
 
 def extras(torch, nbody, inputs, stream, device, args):
-    """Adjoint cost, the 31-body model, RK4, the uneven ensemble, N = 1M in both precisions,
-    and (optionally) the full N sweep and the dt sweep."""
+    """Adjoint cost, the 31-body model, a 521-body FP64 system, RK4, the uneven
+    ensemble, N = 1M in both precisions, and (optionally) the full N sweep and
+    the dt sweep."""
     out = {}
     # adjoint on the 10,425-body model: backward wall / (T x forward step)
     s = inputs.solar_system(args.n)
@@ -507,6 +508,19 @@ def extras(torch, nbody, inputs, stream, device, args):
     out["solar_system_n31"] = {"steps": 3650, "seconds": t, "verlet_steps_per_s": 3650 / t,
                                "interactions_per_s": 31 * 30 * 3650 / t, "precision": "fp64",
                                "general_path_verlet_steps_per_s": 3650 / t2}
+    b.close()
+    b2.close()
+    # a mid-size FP64 system (521 bodies): the single-launch cooperative grid kernel against the general path
+    s521 = inputs.solar_system(521, n_moons=0)
+    with torch.cuda.stream(stream):
+        b = nbody.NBody(s521.r, s521.v, s521.m, G=s521.G, dt=s521.dt, precision="fp64", device=device)
+        b.step(10)
+        t = timed(torch, stream, lambda: b.step(1000))
+        b2 = nbody.NBody(s521.r, s521.v, s521.m, G=s521.G, dt=s521.dt, precision="fp64", small=False, device=device)
+        b2.step(10)
+        t2 = timed(torch, stream, lambda: b2.step(1000))
+    out["fp64_n521"] = {"steps": 1000, "verlet_steps_per_s": 1000 / t, "interactions_per_s": 521 * 520 * 1000 / t,
+                        "path": "cooperative grid kernel", "general_path_verlet_steps_per_s": 1000 / t2}
     b.close()
     b2.close()
     # RK4 (Section 2's higher-order method): four Eq. 1 evaluations per step
