@@ -1,7 +1,9 @@
 // Host side of the C ABI declared in include/nbody.h: context lifetime,
-// validation, scratch ownership, stream-K work tables, CUDA-graph replay of
-// Verlet and RK4 steps, the adjoint sweep, energy, tiles/autotuning and
-// device-fault reporting.
+// validation, scratch ownership, stream-K work tables (planned by
+// work_plan.h), the choice between the single-launch kernels (one FP64
+// Verlet system of up to 4,096 bodies) and the general two-kernel path,
+// CUDA-graph replay of Verlet, leapfrog and RK4 steps, the adjoint sweep,
+// energy, tiles/autotuning and device-fault reporting.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
