@@ -11,11 +11,11 @@
 // most kMaxWarps): the warp's 32 lanes split the sources and sum them in
 // FP64 (up to kSmallMax = 256 bodies; beyond 96 the grid kernel is faster).
 // Against the general two-kernel path, which spreads the pairs over every SM
-// but pays two launches and the partial-row sums per step: 8.7x at 31 bodies,
-// 4.8x at 96.  Every CTA keeps all positions in its shared
-// memory (ping-pong buffers pos[0], pos[1]).  Eq. 1 uses the same FP64
-// interaction as the general kernel (binomial-series refinement of the MUFU
-// seed), Eqs. 3-4 the same kick/drift functions.
+// but pays two launches and the partial-row sums per step: 8.7x at 31
+// bodies, 4.8x at 96.  Every CTA keeps all positions in its shared memory
+// (ping-pong buffers pos[0], pos[1]).  Eq. 1 uses the same FP64 interaction
+// as the general kernel (binomial-series refinement of the MUFU seed),
+// Eqs. 3-4 the same kick/drift functions.
 //
 // Exchange.  After the Eq. 3 drift each target's owner pushes its new
 // position into the copy of every CTA that owns a target, with st.async,
