@@ -219,9 +219,9 @@ nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
 /* Largest system nbody_accel_static accepts. */
 #define NBODY_STATIC_MAX_BODIES 65536
 
-/* Eq. 1 accelerations of ONE system, FP64, without allocating device memory.
- * (The paper has no counterpart: this is a deployment variant of the force
- * kernel.)  Some callers cannot allocate: a host that reserves all device
+/* All-pairs gravitational accelerations of ONE system, FP64, without
+ * allocating device memory.  The paper has no counterpart: this is a
+ * deployment variant of the force kernel.  Some callers cannot allocate: a host that reserves all device
  * memory at start-up and forbids allocation afterwards (a real-time loop, a
  * service with a fixed memory budget), or a component running while another
  * allocator owns the device memory, where one more cudaMalloc may fail or

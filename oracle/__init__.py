@@ -20,7 +20,8 @@ Functions (all FP64 numpy arrays, structure-of-arrays):
                     of Sections 2 and 4.
 * ``vjp``        -- vector-Jacobian product of Eq. 1 w.r.t. positions and masses.
 * ``grad``       -- dL/d(r0, v0, m) of a loss on the final state by the
-                    discrete adjoint of Eqs. 1, 3, 4.
+                    discrete adjoint of Eqs. 1, 3, 4 (optionally with the
+                    magnitude sums that scale each element's rounding error).
 * ``fd_grad_dir``-- central finite difference of the same loss along a direction.
 """
 from __future__ import annotations
@@ -88,7 +89,7 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
             lib.oracle_vjp.argtypes = [_I64, ctypes.c_double] + [_D] * 11
             lib.oracle_vjp.restype = None
             lib.oracle_grad.argtypes = ([_I64, ctypes.c_double, ctypes.c_double, _I64]
-                                        + [_D] * 12)
+                                        + [_D] * 15)
             lib.oracle_grad.restype = ctypes.c_int
             lib.oracle_openmp_threads.argtypes = []
             lib.oracle_openmp_threads.restype = ctypes.c_int
@@ -227,8 +228,13 @@ def vjp(G: float, r: np.ndarray, m: np.ndarray, w: np.ndarray, openmp: bool = Fa
     return rho, gm
 
 
-def grad(G: float, dt: float, T: int, r0, v0, m, dL_dr_T, dL_dv_T=None, openmp: bool = False):
-    """(dL/dr0 [3, n], dL/dv0 [3, n], dL/dm [n]) through T Verlet steps."""
+def grad(G: float, dt: float, T: int, r0, v0, m, dL_dr_T, dL_dv_T=None, openmp: bool = False,
+         magnitudes: bool = False):
+    """(dL/dr0 [3, n], dL/dv0 [3, n], dL/dm [n]) through T Verlet steps.
+
+    magnitudes=True also returns, in the same sweep, the sums of the
+    magnitudes of the elementary terms of each element (same shapes): the
+    condition-free scale of each gradient element (see oracle_grad)."""
     r0 = _f64(r0)
     v0 = _f64(v0)
     m = _f64(m)
@@ -238,12 +244,16 @@ def grad(G: float, dt: float, T: int, r0, v0, m, dL_dr_T, dL_dv_T=None, openmp: 
     out_r = np.zeros((3, n))
     out_v = np.zeros((3, n))
     out_m = np.zeros(n)
+    mags = [np.zeros((3, n)), np.zeros((3, n)), np.zeros(n)] if magnitudes else None
     rc = _lib(openmp).oracle_grad(n, G, dt, int(T), _c(r0[0]), _c(r0[1]), _c(r0[2]),
                                   _c(v0[0]), _c(v0[1]), _c(v0[2]), _c(m), _c(gr),
                                   _c(gv) if gv is not None else None,
-                                  _c(out_r), _c(out_v), _c(out_m))
+                                  _c(out_r), _c(out_v), _c(out_m),
+                                  *([_c(a) for a in mags] if mags else [None, None, None]))
     if rc != 0:
         raise MemoryError("oracle_grad: allocation failed")
+    if magnitudes:
+        return out_r, out_v, out_m, mags[0], mags[1], mags[2]
     return out_r, out_v, out_m
 
 

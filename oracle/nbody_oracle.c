@@ -262,15 +262,23 @@ void oracle_energy(int64_t n, double G, const double *x, const double *y,
  * for q == p, so for an adjoint vector w on the accelerations
  *   (J^T w)_q  = G sum_{j != q} K(r_j - r_q) (m_q w_j - m_j w_q),
  *   (dA/dm)^T w at q = G sum_{p != q} w_p . (r_q - r_p) / |r_q - r_p|^3.
- * K is formed explicitly per pair, j ascending. */
-void oracle_vjp(int64_t n, double G, const double *x, const double *y,
-                const double *z, const double *m, const double *wx,
-                const double *wy, const double *wz, double *rx, double *ry,
-                double *rz, double *gm) {
+ * K is formed explicitly per pair, j ascending.
+ * With W = (Wx, Wy, Wz) non-NULL (elementwise magnitudes bounding |w|), the
+ * same loop also accumulates the magnitudes of every term of both sums into
+ * (Rx, Ry, Rz) and Gm:
+ *   G sum_{j != q} |K(d)| (m_q W_j + m_j W_q)   (|K| elementwise),
+ *   G sum_{p != q} W_p . |r_q - r_p| / |r_q - r_p|^3   (|.| elementwise). */
+static void vjp_impl(int64_t n, double G, const double *x, const double *y,
+                     const double *z, const double *m, const double *wx,
+                     const double *wy, const double *wz, double *rx,
+                     double *ry, double *rz, double *gm, const double *Wx,
+                     const double *Wy, const double *Wz, double *Rx,
+                     double *Ry, double *Rz, double *Gm) {
   int64_t q;
 #pragma omp parallel for schedule(dynamic, 16)
   for (q = 0; q < n; q++) {
     double sx = 0.0, sy = 0.0, sz = 0.0, sm = 0.0;
+    double ax = 0.0, ay = 0.0, az = 0.0, am = 0.0;
     for (int64_t j = 0; j < n; j++) {
       if (j == q) continue;
       const double d[3] = {x[j] - x[q], y[j] - y[q], z[j] - z[q]};
@@ -290,12 +298,35 @@ void oracle_vjp(int64_t n, double G, const double *x, const double *y,
       sz += G * (K[2][0] * u[0] + K[2][1] * u[1] + K[2][2] * u[2]);
       /* w_j . (r_q - r_j) |r_q - r_j|^-3 = -(w_j . d) i3 */
       sm += -G * (wx[j] * d[0] + wy[j] * d[1] + wz[j] * d[2]) * i3;
+      if (Wx) {
+        const double U[3] = {m[q] * Wx[j] + m[j] * Wx[q],
+                             m[q] * Wy[j] + m[j] * Wy[q],
+                             m[q] * Wz[j] + m[j] * Wz[q]};
+        ax += G * (fabs(K[0][0]) * U[0] + fabs(K[0][1]) * U[1] + fabs(K[0][2]) * U[2]);
+        ay += G * (fabs(K[1][0]) * U[0] + fabs(K[1][1]) * U[1] + fabs(K[1][2]) * U[2]);
+        az += G * (fabs(K[2][0]) * U[0] + fabs(K[2][1]) * U[1] + fabs(K[2][2]) * U[2]);
+        am += G * (Wx[j] * fabs(d[0]) + Wy[j] * fabs(d[1]) + Wz[j] * fabs(d[2])) * i3;
+      }
     }
     rx[q] += sx;
     ry[q] += sy;
     rz[q] += sz;
     gm[q] += sm;
+    if (Wx) {
+      Rx[q] += ax;
+      Ry[q] += ay;
+      Rz[q] += az;
+      Gm[q] += am;
+    }
   }
+}
+
+void oracle_vjp(int64_t n, double G, const double *x, const double *y,
+                const double *z, const double *m, const double *wx,
+                const double *wy, const double *wz, double *rx, double *ry,
+                double *rz, double *gm) {
+  vjp_impl(n, G, x, y, z, m, wx, wy, wz, rx, ry, rz, gm, NULL, NULL, NULL,
+           NULL, NULL, NULL, NULL);
 }
 
 /* Gradient of a loss L(r_T, v_T) with respect to (r_0, v_0, m) through T
@@ -311,18 +342,30 @@ void oracle_vjp(int64_t n, double G, const double *x, const double *y,
  *   finally rho += J(r_0)^T alpha;  gm += (dA/dm)(r_0)^T alpha.
  * The forward trajectory r_0..r_T is stored whole (no checkpointing).
  * dLdv_T may be NULL (zero).  Outputs are 3n (x block, y block, z block),
- * 3n and n doubles.  Returns 0, or -1 if memory could not be allocated. */
+ * 3n and n doubles.
+ * absr, absv, absm (all NULL, or 3n, 3n, n outputs): the same sweep run on
+ * magnitudes -- every quantity replaced by a non-negative bound on the
+ * magnitudes of the terms it is a sum of (seeds |dL/dr_T|, |dL/dv_T|; |dt|;
+ * the magnitude form of the products in vjp_impl).  Each output element is
+ * the sum of the magnitudes of all the elementary terms whose signed sum is
+ * the gradient element: the scale against which a rounding error in that
+ * element is judged when the terms cancel (condition number = abs / |grad|).
+ * Returns 0, or -1 if memory could not be allocated. */
 int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
                 const double *y0, const double *z0, const double *vx0,
                 const double *vy0, const double *vz0, const double *m,
                 const double *dLdr_T, const double *dLdv_T, double *dLdr0,
-                double *dLdv0, double *dLdm) {
+                double *dLdv0, double *dLdm, double *absr, double *absv,
+                double *absm) {
   const size_t N = (size_t)n;
+  const int mag = absr != NULL && absv != NULL && absm != NULL;
   double *traj = (double *)malloc(sizeof(double) * 3 * N * (size_t)(T + 1));
   double *work = (double *)malloc(sizeof(double) * 9 * N + 8);
-  if (!traj || !work) {
+  double *mw = mag ? (double *)malloc(sizeof(double) * 6 * N + 8) : NULL;
+  if (!traj || !work || (mag && !mw)) {
     free(traj);
     free(work);
+    free(mw);
     return -1;
   }
   double *x = work, *y = work + N, *z = work + 2 * N;
@@ -347,9 +390,12 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
       return -1;
     }
   }
-  /* reuse work as (nu, alpha, nu_next) */
+  /* reuse work as (nu, alpha, nu_next); magnitudes: R = absr, V = absv,
+   * A and the scratch copy of V in mw */
   double *nu = work, *al = work + 3 * N, *tmp = work + 6 * N;
   double *rho = dLdr0;
+  double *V = absv, *A = mw, *Vt = mw ? mw + 3 * N : NULL;
+  const double adt = fabs(dt);
   memcpy(rho, dLdr_T, sizeof(double) * 3 * N);
   if (dLdv_T)
     memcpy(nu, dLdv_T, sizeof(double) * 3 * N);
@@ -357,22 +403,44 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
     memset(nu, 0, sizeof(double) * 3 * N);
   memset(al, 0, sizeof(double) * 3 * N);
   memset(dLdm, 0, sizeof(double) * N);
+  if (mag) {
+    for (size_t k = 0; k < 3 * N; k++) {
+      absr[k] = fabs(dLdr_T[k]);
+      V[k] = dLdv_T ? fabs(dLdv_T[k]) : 0.0;
+      A[k] = 0.0;
+    }
+    memset(absm, 0, sizeof(double) * N);
+  }
   for (int64_t i = T - 1; i >= 0; i--) {
     for (size_t k = 0; k < 3 * N; k++) al[k] += 0.5 * dt * nu[k];
+    if (mag)
+      for (size_t k = 0; k < 3 * N; k++) A[k] += 0.5 * adt * V[k];
     const double *r = traj + 3 * N * (size_t)(i + 1);
-    oracle_vjp(n, G, r, r + N, r + 2 * N, m, al, al + N, al + 2 * N, rho,
-               rho + N, rho + 2 * N, dLdm);
+    vjp_impl(n, G, r, r + N, r + 2 * N, m, al, al + N, al + 2 * N, rho,
+             rho + N, rho + 2 * N, dLdm, A, A ? A + N : NULL,
+             A ? A + 2 * N : NULL, absr, absr ? absr + N : NULL,
+             absr ? absr + 2 * N : NULL, absm);
     for (size_t k = 0; k < 3 * N; k++) {
       tmp[k] = nu[k] + dt * rho[k];
       al[k] = 0.5 * dt * nu[k] + 0.5 * dt * dt * rho[k];
     }
     memcpy(nu, tmp, sizeof(double) * 3 * N);
+    if (mag) {
+      for (size_t k = 0; k < 3 * N; k++) {
+        Vt[k] = V[k] + adt * absr[k];
+        A[k] = 0.5 * adt * V[k] + 0.5 * dt * dt * absr[k];
+      }
+      memcpy(V, Vt, sizeof(double) * 3 * N);
+    }
   }
-  oracle_vjp(n, G, traj, traj + N, traj + 2 * N, m, al, al + N, al + 2 * N,
-             rho, rho + N, rho + 2 * N, dLdm);
+  vjp_impl(n, G, traj, traj + N, traj + 2 * N, m, al, al + N, al + 2 * N,
+           rho, rho + N, rho + 2 * N, dLdm, A, A ? A + N : NULL,
+           A ? A + 2 * N : NULL, absr, absr ? absr + N : NULL,
+           absr ? absr + 2 * N : NULL, absm);
   memcpy(dLdv0, nu, sizeof(double) * 3 * N);
   free(traj);
   free(work);
+  free(mw);
   return 0;
 }
 

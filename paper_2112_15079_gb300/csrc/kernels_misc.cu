@@ -571,6 +571,10 @@ cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s) {
 //   e_kin[p] = (1/2) m_p |v_p|^2,   e_pot[p] = -(1/2) m_p sum_{j != p} G m_j / |r_j - r_p|,
 // so that sum_p e_pot[p] = -sum_{p<j} G m_p m_j / |r_j - r_p|.  FP64, one
 // CTA per block of kEnergyBlock targets, sources staged through shared memory.
+// Each body's potential is compensated as the force is: the terms of one
+// source tile are summed plainly, and each tile's sub-sum enters a (hi, lo)
+// pair through TwoSum, so the many small asteroid terms of a moon's sum are
+// not lost below half an ulp of its host's term.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEnergyBlock) energy_kernel(const EnergyArgs a) {
   __shared__ double4_32a tile[kEnergyBlock];
@@ -579,27 +583,29 @@ __global__ void __launch_bounds__(kEnergyBlock) energy_kernel(const EnergyArgs a
   const bool valid = p < it.i1;
   const int pp = valid ? p : it.i0;
   const double px = a.x[pp], py = a.y[pp], pz = a.z[pp];
-  double phi = 0.0;
+  double phi = 0.0, phi_lo = 0.0;
   for (int j0 = it.j0; j0 < it.j1; j0 += kEnergyBlock) {
     const int j = j0 + threadIdx.x;
     __syncthreads();
     if (j < it.j1) tile[threadIdx.x] = make_double4_32a(a.x[j], a.y[j], a.z[j], a.G * a.m[j]);
     __syncthreads();
     const int cnt = min(kEnergyBlock, it.j1 - j0);
+    double t = 0.0;
     for (int u = 0; u < cnt; ++u) {
       const double4_32a s = tile[u];
       const double dx = s.x - px, dy = s.y - py, dz = s.z - pz;
       double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
       const bool self = (j0 + u) == pp;
       r2 = self ? 1.0 : r2;
-      phi += self ? 0.0 : s.w * inv_r1(r2);
+      t += self ? 0.0 : s.w * inv_r1(r2);
     }
+    two_sum_acc(phi, phi_lo, t);
   }
   if (valid) {
     const double m = a.m[p];
     const double v2 = fma(a.vz[p], a.vz[p], fma(a.vy[p], a.vy[p], a.vx[p] * a.vx[p]));
     a.e_kin[p] = 0.5 * m * v2;
-    a.e_pot[p] = -0.5 * m * phi;
+    a.e_pot[p] = -0.5 * m * (phi + phi_lo);
   }
 }
 

@@ -37,6 +37,8 @@ static_assert(sizeof(Item) == 32, "Item layout");
 struct ForceArgs {
   const void *cur;  // staged sources: FP64 double4 (x,y,z,Gm) per body; mixed pair blocks
   double *partial;  // [rows][3][N]: doubles (FP64) or float pairs (mixed), 24 B per row and body
+  const int32_t *perm;  // [stage entries] body of each stage entry (mixed, spatial order); NULL: the
+                        // block's targets are bodies i0.. in order
   unsigned *flags;
   const Blk *blks;
   const Seg *segs;
@@ -77,6 +79,7 @@ struct VerletArgs {
 // the same kind of work tables as the force kernel ([rows][4][N]).
 struct VjpArgs {
   const void *pos;  // positions staged by the forward pass (its layout)
+  const int32_t *perm;  // as ForceArgs::perm
   const void *w;    // w per stage entry: FP64 double4; mixed pair blocks (16 B per entry)
   double *partial;  // [rows][4][N]: doubles (FP64) or float pairs (mixed)
   unsigned *flags;
@@ -211,6 +214,15 @@ void set_last_error(const char *msg);  // message returned by nbody_last_error(N
 constexpr int kStages = 2;          // shared-memory pipeline depth of the force kernels
 constexpr int kFoldPairs = 64;      // mixed path: packed sub-sums of 64 source pairs folded into a float pair
 constexpr float kPadCoord = 1e15f;  // mixed padding source: far away and massless (term exactly 0)
+// Mixed force kernel: source groups of kBoxPairs pairs (64 sources) get a
+// bounding box per tile; a warp whose targets are far from a group's box
+// takes the hi-only path for it (see step_kernel.cuh).  kFarEps bounds the
+// relative error that dropping the lo parts adds to one term of Eq. 1;
+// kFarKappa = 2 / kFarEps + 1 is the separation, in units of the largest lo
+// parts, beyond which that bound holds.
+constexpr int kBoxPairs = 32;
+constexpr float kFarEps = 1e-6f;
+constexpr float kFarKappa = 2.0f / kFarEps + 1.0f;
 constexpr int kEnergyBlock = 256;
 
 }  // namespace nb

@@ -1,5 +1,5 @@
-// nbody_accel_static: Eq. 1 accelerations of one system without allocating
-// device memory.  Some callers cannot allocate: hosts that reserve all device
+// nbody_accel_static: all-pairs gravitational accelerations of one system,
+// FP64, without allocating device memory.  Some callers cannot allocate: hosts that reserve all device
 // memory up front and forbid allocation afterwards (real-time or embedded
 // loops, services with a fixed memory budget), and components that run while
 // another allocator owns the device memory, where an extra cudaMalloc may fail

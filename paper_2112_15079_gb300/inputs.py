@@ -106,18 +106,26 @@ def _unit_vectors(rng, k):
     return u / np.linalg.norm(u, axis=0)
 
 
-def moons(rng, r_host, v_host, m_host, m_host_kg, G=G_AU_DAY, count=100):
+def moons(rng, r_host, v_host, m_host, m_host_kg, G=G_AU_DAY, count=100, omega_dt_max=None):
     """``count`` moons on circular orbits around hosts heavier than 1e23 kg.
 
     Returns (r, v, m, stats) where stats counts moons whose period is shorter
     than 2 pi * 0.1 day (unresolved by the paper's step) and moons outside
-    their host's Hill sphere (computed with the host's distance from the Sun)."""
+    their host's Hill sphere (computed with the host's distance from the Sun).
+    ``omega_dt_max``: if given, each drawn radius is raised, where needed, to
+    the one at which the orbit's angular rate times the step (0.1 day) equals
+    it, so every moon orbit is resolved by the step (the same draws
+    otherwise)."""
     cand = np.nonzero(m_host_kg[1:] > 1e23)[0] + 1
     if cand.size == 0:
         raise ValueError("no major body heavier than 1e23 kg; draw another seed")
     host = rng.choice(cand, size=count, replace=True)
     R = _loguniform(rng, 1e-4, 5e-2, count)
     m = rng.uniform(1e15, 1e19, count) / MSUN_KG
+    if omega_dt_max is not None:
+        # omega = sqrt(G (M + m) / R^3) <= omega_dt_max / dt
+        r_min = np.cbrt(G * (m_host[host] + m) * (DT_DAY / omega_dt_max) ** 2)
+        R = np.maximum(R, r_min)
     u = _unit_vectors(rng, count)
     w = rng.normal(size=(3, count))
     w = w - u * np.sum(w * u, axis=0)
@@ -144,11 +152,13 @@ def asteroids(rng, G=G_AU_DAY, count=10294):
     return r, v, m
 
 
-def solar_system(n: int = 10425, seed: int = BASE_SEED, n_moons: int = 100) -> System:
+def solar_system(n: int = 10425, seed: int = BASE_SEED, n_moons: int = 100,
+                 moon_omega_dt_max: float | None = None) -> System:
     """A Solar-System-shaped system of ``n`` bodies.
 
     n == 31: Sun + 30 major bodies.  Otherwise Sun + 30 major bodies +
-    ``n_moons`` moons + (n - 31 - n_moons) asteroids, in that order."""
+    ``n_moons`` moons + (n - 31 - n_moons) asteroids, in that order.
+    ``moon_omega_dt_max``: see ``moons`` (None: the radii as drawn)."""
     rng = np.random.default_rng(seed)
     r, v, m, m_kg = major_bodies(rng)
     info = {"seed": seed, "n_major": 31, "n_moons": 0, "n_asteroids": 0}
@@ -156,7 +166,7 @@ def solar_system(n: int = 10425, seed: int = BASE_SEED, n_moons: int = 100) -> S
         raise ValueError("n must be >= 31")
     if n > 31:
         k_moons = min(n_moons, n - 31)
-        rm, vm, mm, stats = moons(rng, r, v, m, m_kg, count=k_moons)
+        rm, vm, mm, stats = moons(rng, r, v, m, m_kg, count=k_moons, omega_dt_max=moon_omega_dt_max)
         ra, va, ma = asteroids(rng, count=n - 31 - k_moons)
         r = np.concatenate([r, rm, ra], axis=1)
         v = np.concatenate([v, vm, va], axis=1)

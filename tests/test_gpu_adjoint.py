@@ -1,9 +1,28 @@
 """GPU adjoint (nbody_grad) against the oracle's adjoint, which is itself
 pinned by central differences of its forward map (tests/test_oracle_pins.py).
 
-Tolerance: relative error of the whole gradient vector (dL/dr0, dL/dv0,
-dL/dm concatenated, each scaled so the blocks weigh alike) within 1e-6 in
-FP64 and 1e-3 in mixed precision.
+Gate, element by element (every body, every component of dL/dr0 and dL/dv0,
+and dL/dm): with g the oracle's element and S its magnitude sum (the sum of
+the magnitudes of the elementary terms whose signed sum is g, from the same
+oracle sweep; S >= |g|, and S / |g| is the element's condition number),
+
+    |g_gpu - g| <= tol * S                   for every element,
+    |g_gpu - g| <= tol * |g|                 where S / |g| <= 1e3,
+
+with tol = 1e-6 (FP64) and 1e-3 (mixed).  This is the form of the
+acceleration gate (condition-free for all, relative where the sum is well
+conditioned): a rounding error of relative size u in each term moves an
+element by at most about u S, so S, not the largest element of the block, is
+the floor an element is judged against; a moon's dL/dm is gated on its own
+terms, not the Sun's.
+
+The 10,425-body model with the paper's moon set is integrated only for 100
+steps here: several of its moons orbit faster than the 0.1-day step resolves
+(omega dt > 2, where velocity Verlet is unstable), so over 1000 steps a
+1-ulp change of the initial state changes the oracle's own gradient by order
+one -- no two implementations can agree there.  The 1000-step configuration
+with checkpoints every 100 steps runs at full size on the same construction
+with every moon orbit resolved (omega dt <= 0.5).
 """
 import numpy as np
 import pytest
@@ -12,6 +31,9 @@ import oracle
 from paper_2112_15079_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-6, "mixed": 1e-3}
+COND_MAX = 1e3
 
 
 @pytest.fixture(scope="module")
@@ -36,24 +58,39 @@ def _loss_grads(s, T, idx, tgt, cv):
     return gr, gv
 
 
-def _rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
+def check_grad(precision, got, ref):
+    """Per-element gate (module docstring).  ref: the oracle's
+    (dr, dv, dm, Sr, Sv, Sm).  Returns the worst figures per block."""
+    tol = TOL[precision]
+    report = {}
+    for name, g, r, S in zip(("dr0", "dv0", "dm"), got, ref[:3], ref[3:]):
+        g, r, S = np.ravel(g), np.ravel(r), np.ravel(S)
+        err = np.abs(g - r)
+        cond = np.where(np.abs(r) > 0, S / np.where(np.abs(r) > 0, np.abs(r), 1.0), np.inf)
+        cf = err / np.where(S > 0, S, np.inf)  # S == 0 only where every term is 0: then g must be 0 too
+        assert np.all(err[S == 0] == 0), (precision, name, "nonzero where every term is zero")
+        good = cond <= COND_MAX
+        rel = np.where(good, err / np.where(good, np.abs(r), 1.0), 0.0)
+        report[name] = {"worst_condition_free": float(cf.max()), "worst_relative": float(rel.max()),
+                        "excluded": int((~good).sum()), "max_cond": float(cond[np.isfinite(cond)].max())}
+        assert cf.max() <= tol, (precision, name, report[name])
+        assert rel.max() <= tol, (precision, name, report[name])
+    return report
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("mixed", 1e-3)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("T,ckpt", [(1, 0), (25, 0), (230, 7)])
-def test_grad_vs_oracle(nb, precision, tol, T, ckpt):
+def test_grad_vs_oracle(nb, precision, T, ckpt):
     torch = pytest.importorskip("torch")
     s = inputs.solar_system(131, seed=61, n_moons=0)
     rng = np.random.default_rng(T)
     idx = np.sort(rng.choice(np.arange(31, s.n), 16, replace=False))
     tgt = s.r[:, idx] + rng.normal(0, 0.01, (3, idx.size))
     gr, gv = _loss_grads(s, T, idx, tgt, 3.0)
-    ref = oracle.grad(s.G, s.dt, T, s.r, s.v, s.m, gr, gv, openmp=True)
+    ref = oracle.grad(s.G, s.dt, T, s.r, s.v, s.m, gr, gv, openmp=True, magnitudes=True)
     b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision, ckpt_every=ckpt)
     got = [t.cpu().numpy() for t in b.grad(T, torch.tensor(gr), torch.tensor(gv))]
-    for g, r in zip(got, ref):
-        assert _rel(g, r) <= tol, (_rel(g, r), precision, T)
+    check_grad(precision, got, ref)
 
 
 def test_grad_zero_steps_is_identity(nb):
@@ -97,57 +134,85 @@ def test_autograd_function(nb):
     rr, vv, _ = oracle.verlet(s.G, s.dt, 40, s.r, s.v, s.m)
     gr[:, 40:60] = 2 * rr[:, 40:60]
     gv[:, 40:60] = 10.0 * vv[:, 40:60]
-    ref = oracle.grad(s.G, s.dt, 40, s.r, s.v, s.m, gr, gv)
-    for g, r in zip((r0.grad, v0.grad, m.grad), ref):
-        assert _rel(g.cpu().numpy(), r) <= 1e-6
+    ref = oracle.grad(s.G, s.dt, 40, s.r, s.v, s.m, gr, gv, magnitudes=True)
+    check_grad("fp64", [r0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m.grad.cpu().numpy()], ref)
 
 
-def test_grad_10425_bodies_64_asteroid_loss(nb):
-    """The 10,425-body model, 100 steps, loss on 64 seeded asteroids."""
+def test_grad_10425_bodies_with_moons_100_steps(nb):
+    """The 10,425-body model with its moons as drawn, 100 steps, checkpoints
+    every 30 steps, loss on 64 seeded asteroids; both precisions, every
+    element."""
     torch = pytest.importorskip("torch")
     s = inputs.solar_system(10425)
     idx, tgt = inputs.loss_targets(s)
     T = 100
-    gr, gv = _loss_grads(s, T, idx, tgt, 0.0)
-    ref = oracle.grad(s.G, s.dt, T, s.r, s.v, s.m, gr, None, openmp=True)
-    for precision, tol in (("fp64", 1e-6), ("mixed", 1e-3)):
+    gr, _ = _loss_grads(s, T, idx, tgt, 0.0)
+    ref = oracle.grad(s.G, s.dt, T, s.r, s.v, s.m, gr, None, openmp=True, magnitudes=True)
+    for precision in ("fp64", "mixed"):
         b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision, ckpt_every=30)
         got = [t.cpu().numpy() for t in b.grad(T, torch.tensor(gr))]
-        for g, r in zip(got, ref):
-            assert _rel(g, r) <= tol, (precision, _rel(g, r))
+        b.close()
+        print(precision, check_grad(precision, got, ref))
 
 
-def test_grad_vs_gpu_central_difference(nb):
-    """The adjoint against central differences of the GPU's own FP64 forward
-    map (h = 1e-7 relative), along random directions in (r0, v0, m):
+@pytest.fixture(scope="module")
+def c5_reference():
+    """The 1000-step, 10,425-body adjoint configuration (checkpoints every
+    100 steps) on the construction with resolved moon orbits: the oracle's
+    gradient and magnitude sums (a few minutes on the host cores)."""
+    s = inputs.solar_system(10425, moon_omega_dt_max=0.5)
+    idx, tgt = inputs.loss_targets(s)
+    T = 1000
+    gr, _ = _loss_grads(s, T, idx, tgt, 0.0)
+    ref = oracle.grad(s.G, s.dt, T, s.r, s.v, s.m, gr, None, openmp=True, magnitudes=True)
+    return s, T, gr, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grad_10425_bodies_1000_steps_checkpoints_every_100(nb, c5_reference, precision):
+    torch = pytest.importorskip("torch")
+    s, T, gr, ref = c5_reference
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision, ckpt_every=100)
+    got = [t.cpu().numpy() for t in b.grad(T, torch.tensor(gr))]
+    b.close()
+    print(precision, check_grad(precision, got, ref))
+
+
+@pytest.mark.parametrize("precision,h", [("fp64", 1e-7), ("mixed", 1e-5)])
+def test_grad_vs_gpu_central_difference(nb, precision, h):
+    """The adjoint against central differences of the GPU's own forward map
+    in the same precision, along random directions in (r0, v0, m):
     u . grad L = (L(x + h u) - L(x - h u)) / 2h for L = sum_k |r_k(T) - t_k|^2
     over 64 seeded bodies.  Separated bodies (no moons), so the map is smooth
-    on the scale of h."""
+    on the scale of h.  FP64 at h = 1e-7 within 1e-5; mixed at h = 1e-5 (the
+    FP32 rounding of the forward map, ~1e-7 relative per force, needs the
+    larger step to stay below the truncation error) within its adjoint
+    tolerance 1e-3."""
     torch = pytest.importorskip("torch")
     s = inputs.solar_system(300, seed=41, n_moons=0)
     T = 20
     idx, tgt = inputs.loss_targets(s)
 
     def loss(r, v, m):
-        b = nb.NBody(r, v, m, G=s.G, dt=s.dt, precision="fp64")
+        b = nb.NBody(r, v, m, G=s.G, dt=s.dt, precision=precision)
         b.step(T)
         rT = b.r.cpu().numpy()
         b.close()
         return float(((rT[:, idx] - tgt) ** 2).sum())
 
-    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision)
     b.step(T)
     rT = b.r.cpu().numpy()
     gr = np.zeros((3, s.n))
     gr[:, idx] = 2 * (rT[:, idx] - tgt)
-    b2 = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64")
+    b2 = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=precision)
     dr, dv, dm = (t.cpu().numpy() for t in b2.grad(T, torch.tensor(gr)))
     rng = np.random.default_rng(7)
+    tol = 1e-5 if precision == "fp64" else TOL["mixed"]
     for _ in range(3):
         ur = rng.normal(size=(3, s.n)) * np.abs(s.r).max()
         uv = rng.normal(size=(3, s.n)) * np.abs(s.v).max()
         um = rng.normal(size=s.n) * s.m
-        h = 1e-7
         fd = (loss(s.r + h * ur, s.v + h * uv, s.m + h * um) - loss(s.r - h * ur, s.v - h * uv, s.m - h * um)) / (2 * h)
         ad = float((dr * ur).sum() + (dv * uv).sum() + (dm * um).sum())
-        assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-12, (fd, ad)
+        assert abs(fd - ad) <= tol * abs(ad) + 1e-12, (fd, ad)

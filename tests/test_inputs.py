@@ -93,3 +93,28 @@ def test_loss_targets():
     idx, tgt = inputs.loss_targets(s)
     assert idx.shape == (64,) and np.all(np.diff(idx) > 0) and idx.min() >= 131
     assert tgt.shape == (3, 64) and np.abs(tgt - s.r[:, idx]).max() < 0.1
+
+
+def test_resolved_moons_variant():
+    """moon_omega_dt_max raises only the radii of moons whose orbit the step
+    does not resolve; every other draw is the same."""
+    base = inputs.solar_system(1031)
+    res = inputs.solar_system(1031, moon_omega_dt_max=0.5)
+    host_idx = slice(0, 31)
+    assert np.array_equal(base.r[:, host_idx], res.r[:, host_idx])
+    assert np.array_equal(base.r[:, 131:], res.r[:, 131:]) and np.array_equal(base.m, res.m)
+    # moon radius and rate around the nearest major body (its host)
+    def rates(s):
+        d = s.r[:, 31:131, None] - s.r[:, None, 1:31]
+        dist = np.linalg.norm(d, axis=0)
+        k = dist.argmin(axis=1)
+        R = dist[np.arange(100), k]
+        M = s.m[1:31][k] + s.m[31:131]
+        return R, np.sqrt(s.G * M / R**3) * inputs.DT_DAY
+    R0, w0 = rates(base)
+    R1, w1 = rates(res)
+    assert w0.max() > 1.0  # the plain draw has unresolved moons
+    assert w1.max() <= 0.5 * (1 + 1e-9)
+    kept = w0 <= 0.5
+    np.testing.assert_allclose(R1[kept], R0[kept], rtol=1e-12)
+    assert np.all(R1[~kept] > R0[~kept])

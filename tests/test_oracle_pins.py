@@ -422,10 +422,60 @@ def test_grad_openmp_identical():
     s = inputs.solar_system(131, seed=2)
     rng = np.random.default_rng(0)
     gr = rng.normal(size=(3, s.n))
-    a = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=False)
-    b = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=True)
+    a = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=False, magnitudes=True)
+    b = oracle.grad(s.G, s.dt, 3, s.r, s.v, s.m, gr, None, openmp=True, magnitudes=True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+# ---------------------------------------------------------------------------
+# Magnitude sums of the adjoint (the condition-free scale of each gradient
+# element): pinned by the cases where they are known exactly and by the
+# triangle inequality; the signed gradient of the same sweep is unchanged.
+# ---------------------------------------------------------------------------
+def test_grad_magnitudes_zero_steps():
+    """T = 0: no product with a nonzero adjoint, so the magnitudes are the
+    seeds' magnitudes and zero for the masses."""
+    s = inputs.solar_system(31, seed=4)
+    rng = np.random.default_rng(5)
+    gr, gv = rng.normal(size=(3, s.n)), rng.normal(size=(3, s.n))
+    g = oracle.grad(s.G, s.dt, 0, s.r, s.v, s.m, gr, gv, magnitudes=True)
+    assert np.array_equal(g[3], np.abs(gr)) and np.array_equal(g[4], np.abs(gv)) and np.all(g[5] == 0)
+
+
+def test_grad_magnitudes_equal_the_gradient_without_cancellation():
+    """Two bodies on the x axis moving along it, one step, seed dL/dv_T on
+    the x component of body 0 only: every term of every element has the same
+    sign (K_xx = -2/|d|^3 is the only entry that meets a nonzero adjoint, and
+    each mixed product m_q w_j - m_j w_q pairs terms of opposite sign), so the
+    magnitude sums equal the gradient's magnitudes.  A dropped or mis-signed
+    term in either sum breaks the equality."""
+    G, dt = 2.9591220828e-4, 0.1
+    r = np.array([[0.0, 1.3], [0.0, 0.0], [0.0, 0.0]])
+    v = np.array([[0.0, 0.002], [0.0, 0.0], [0.0, 0.0]])
+    m = np.array([1e-3, 3e-4])
+    gv = np.zeros((3, 2))
+    gv[0, 0] = 0.7
+    g = oracle.grad(G, dt, 1, r, v, m, np.zeros((3, 2)), gv, magnitudes=True)
+    for signed, mag in zip(g[:3], g[3:]):
+        np.testing.assert_allclose(mag, np.abs(signed), rtol=1e-14, atol=0.0)
+    assert np.all(g[3][0] > 0) and np.all(g[5] > 0)  # the sums are not trivially zero
+
+
+def test_grad_magnitudes_bound_the_gradient_and_keep_it():
+    """|grad| <= magnitude sum element by element (triangle inequality), on
+    a system whose terms do cancel; the signed outputs are bitwise those of
+    the sweep without magnitudes."""
+    s = inputs.solar_system(31, seed=3)
+    rng = np.random.default_rng(1)
+    gr, gv = rng.normal(size=(3, s.n)), rng.normal(size=(3, s.n))
+    g = oracle.grad(s.G, s.dt, 20, s.r, s.v, s.m, gr, gv, magnitudes=True)
+    plain = oracle.grad(s.G, s.dt, 20, s.r, s.v, s.m, gr, gv)
+    for a, b in zip(g[:3], plain):
+        assert np.array_equal(a, b)
+    ratios = [float((np.abs(a) / b).max()) for a, b in zip(g[:3], g[3:])]
+    assert max(ratios) <= 1.0 + 1e-12, ratios
+    assert max(float((b / np.abs(a)).max()) for a, b in zip(g[:3], g[3:])) > 10.0  # some elements do cancel
 
 
 # ---------------------------------------------------------------------------
