@@ -5,13 +5,14 @@ Workload (the paper's 10,425-body Solar-System model, Section 2, as seeded
 synthetic stand-in): N = 10,425 bodies (Sun, 30 major bodies, 100 moons,
 10,294 main-belt asteroids), dt = 0.1 day.  One benchmark "step" is one
 ``nbody_step(S)`` call advancing the system by S velocity-Verlet steps
-(default S = 100, i.e. 10 days); each Verlet step is an Eq. 1 force launch
-and a per-body Verlet launch (kick, drift, staging), chained with
-programmatic dependent launch and replayed from CUDA graphs.  The headline
-``value`` is the mixed-precision path; the FP64 path is measured the same way
-and reported under "fp64".  The roofline object describes the force kernel:
-its flops per launch over its mean event-timed duration (the same workload,
-each kernel launched alone by ``nbody_kernel_times``).
+(FP64: S = 10, i.e. one day; mixed: S = 100); each Verlet step is an Eq. 1
+force launch and a per-body Verlet launch (kick, drift, staging), chained
+with programmatic dependent launch and replayed from CUDA graphs.  The
+headline ``value`` is the FP64 path (the paper's arithmetic); the mixed path
+is measured the same way and reported under "mixed" with its speed-up.  Each
+roofline object describes that path's force kernel: its flops per launch
+over its mean event-timed duration (the same workload, each kernel launched
+alone by ``nbody_kernel_times``).
 
     interactions/s = N (N - 1) * S * K / (timed seconds)
 
@@ -56,7 +57,7 @@ PAPER_INTERACTIONS_PER_S = 7.9e7
 # the caches before each replay, so these are cold-L2 figures; in the timed
 # loop the state is L2-resident), keyed by a hash of the kernel sources they
 # were taken on (null once the sources change).
-NCU_TRAFFIC = {("e8f0865ec7652815", "mixed"): 368128, ("e8f0865ec7652815", "fp64"): 427776}
+NCU_TRAFFIC = {("620872dc1d17e15f", "mixed"): 1061376, ("620872dc1d17e15f", "fp64"): 422400}
 
 
 def kernel_hash() -> str:
@@ -78,7 +79,7 @@ def parse():
     ap.add_argument("--n", type=int, default=10425, help="bodies (10425 = the paper's model)")
     ap.add_argument("--inner", type=int, default=100, help="Verlet steps per benchmark step (mixed)")
     ap.add_argument("--inner-fp64", type=int, default=10, help="Verlet steps per benchmark step (FP64)")
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="time the FP64 path only (the headline)")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None, help="time one precision only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -231,14 +232,16 @@ def run_reference(args):
     per_step = N * (N - 1)
     import oracle as o
 
+    # One benchmark step = inner_fp64 Verlet steps, as the GPU arm's headline.
+    inner = args.inner_fp64
     r, v, a = s.r, s.v, None
     for _ in range(args.warmup):
-        r, v, a = o.verlet(s.G, s.dt, 1, r, v, s.m, a, openmp=True)
+        r, v, a = o.verlet(s.G, s.dt, inner, r, v, s.m, a, openmp=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r, v, a = o.verlet(s.G, s.dt, 1, r, v, s.m, a, openmp=True)
+        r, v, a = o.verlet(s.G, s.dt, inner, r, v, s.m, a, openmp=True)
     el = time.perf_counter() - t0
-    value = per_step * args.steps / el
+    value = per_step * inner * args.steps / el
     cores = oracle.threads(True)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -246,11 +249,12 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_INTERACTIONS_PER_S,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"solar_system_n{N}", "n_bodies": N, "dt_day": s.dt,
-                   "verlet_steps_per_step": 1, "precision": "fp64"},
+                   "verlet_steps_per_step": inner, "precision": "fp64",
+                   "parallelism": "host cores (OpenMP over target bodies)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"1 velocity-Verlet step of the N={N} system per benchmark step"},
+                         "sample": f"{inner} velocity-Verlet steps of the N={N} system per benchmark step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "verlet_steps_per_s": args.steps / el,
+        "verlet_steps_per_s": inner * args.steps / el,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -279,21 +283,28 @@ def timed_region(torch, b, stream, inner, steps, flush, dist, device):
     return sum(e0.elapsed_time(e1) for e0, e1 in evs), wall
 
 
-def roofline(r, prec, traffic):
+def roofline(r, prec, traffic, peaks=None):
     """ALU roofline of the force kernel (Eq. 1): FLOPS_PER_INTERACTION x
     N(N-1) per launch over its mean event-timed duration, against the derived
-    FP32 (mixed) or FP64 peak.  frac_step is the same flop count over the whole
-    timed step (force + Verlet kernels + launch gaps)."""
+    FP32 (mixed) or FP64 peak (and, with `peaks`, the FFMA / DFMA rates the
+    library's microbenchmark measured in the same run).  frac_step is the same
+    flop count over the whole timed step (force + Verlet kernels + launch
+    gaps)."""
     lanes = 128 if prec == "mixed" else 2
     kt = r["kernel_ms"]
-    return {"bound": "alu", "achieved": r["force_tflops"], "peak": PEAK_TFLOPS[prec], "unit": "TFLOP/s",
-            "frac": r["force_tflops"] / PEAK_TFLOPS[prec], "traffic": traffic,
-            "kernel": f"force_kernel<{prec}>", "force_ms": kt["force_ms"], "verlet_ms": kt["verlet_ms"],
-            "force_share": kt["force_ms"] / (kt["force_ms"] + kt["verlet_ms"]),
-            "frac_step": r["achieved_tflops"] / PEAK_TFLOPS[prec],
-            "peak_note": f"derived: 152 SMs x {lanes} {'FP32' if prec == 'mixed' else 'FP64'} FMA lanes x 2 flop "
-                         f"x 2070 MHz; {FLOPS_PER_INTERACTION} flop per interaction; achieved over the force "
-                         "kernel's mean event-timed launch duration"}
+    out = {"bound": "alu", "achieved": r["force_tflops"], "peak": PEAK_TFLOPS[prec], "unit": "TFLOP/s",
+           "frac": r["force_tflops"] / PEAK_TFLOPS[prec], "traffic": traffic,
+           "kernel": f"force_kernel<{prec}>", "force_ms": kt["force_ms"], "verlet_ms": kt["verlet_ms"],
+           "force_share": kt["force_ms"] / (kt["force_ms"] + kt["verlet_ms"]),
+           "frac_step": r["achieved_tflops"] / PEAK_TFLOPS[prec],
+           "peak_note": f"derived: 152 SMs x {lanes} {'FP32' if prec == 'mixed' else 'FP64'} FMA lanes x 2 flop "
+                        f"x 2070 MHz; {FLOPS_PER_INTERACTION} flop per interaction; achieved over the force "
+                        "kernel's mean event-timed launch duration"}
+    if peaks:
+        measured = peaks["fp32_tflops"] if prec == "mixed" else peaks["fp64_tflops"]
+        out["peak_measured_tflops"] = measured
+        out["frac_of_measured"] = r["force_tflops"] / measured
+    return out
 
 
 def run_ours(args):
@@ -315,8 +326,10 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
     results = {}
     tiles = {}
-    for prec, inner in (("mixed", args.inner), ("fp64", args.inner_fp64)):
-        if (prec == "fp64" and args.no_fp64) or (args.only and prec != args.only):
+    # FP64 first: the paper's arithmetic and the headline; the mixed path is
+    # reported beside it.
+    for prec, inner in (("fp64", args.inner_fp64), ("mixed", args.inner)):
+        if (prec == "mixed" and args.no_mixed) or (args.only and prec != args.only):
             continue
         with torch.cuda.stream(stream):
             b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, device=device)
@@ -330,20 +343,19 @@ def run_ours(args):
             for _ in range(args.warmup):
                 b.step(inner)
             b.sync()
-        clk = ClockSampler(local) if prec == "mixed" else None
-        if clk:
-            clk.__enter__()
+        clk = ClockSampler(local)
+        clk.__enter__()
         ev_ms, wall = timed_region(torch, b, stream, inner, args.steps, flush, dist, device)
-        if clk:
-            clk.__exit__(None, None, None)
-            results["clocks"] = clk.summary()
+        clk.__exit__(None, None, None)
         ev_s = max_over_ranks(ev_ms * 1e-3, dist, device)
         total = per_step * inner * args.steps * world
         results[prec] = {
             "value": total / ev_s, "ms_per_step": ev_s / args.steps * 1e3,
             "verlet_steps_per_s": inner * args.steps / ev_s, "wall_s": wall,
             "achieved_tflops": FLOPS_PER_INTERACTION * per_step * inner * args.steps / ev_s * 1e-12,
-            "inner": inner,
+            "inner": inner, "clocks": clk.summary(),
+            # one staging launch per nbody_step call, then a force and a Verlet launch per step
+            "gpu_launches": args.steps * (1 + 2 * inner),
         }
         # Roofline of the dominant kernel: the same workload, each kernel of
         # `inner` Verlet steps bracketed alone by events on this stream.
@@ -351,8 +363,8 @@ def run_ours(args):
             kt = b.kernel_times(inner)
         results[prec]["kernel_ms"] = kt
         results[prec]["force_tflops"] = FLOPS_PER_INTERACTION * per_step / (kt["force_ms"] * 1e-3) * 1e-12
-        if prec == "mixed" and not args.no_e2e:
-            results["e2e"] = e2e(torch, b, s, stream, inner, args, dist, device, world)
+        if not args.no_e2e:
+            results[prec]["e2e"] = e2e(torch, b, s, stream, inner, args, dist, device, world)
         b.close()
     extra = None
     if rank == 0 and world == 1 and not args.no_extras and not args.only:
@@ -361,57 +373,54 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(s, args.cpu_seconds)
     peaks = None
-    if rank == 0 and not args.only:
+    if rank == 0:
         p = nbody.peaks()  # measured instruction rates (1e9 lane-ops/s) on this GPU
         peaks = {"fp32_tflops": 2 * p["ffma"] * 1e-3, "fp64_tflops": 2 * p["dfma"] * 1e-3,
                  "mufu_rsqrt_f32_gops": p["rsqrt_f32"], "mufu_rsqrt_f64_gops": p["rsqrt_f64"],
                  "cvt_f32_f64_gops": p["cvt_f32_f64"], "ffma2_tflops": 2 * p["ffma2_lanes"] * 1e-3,
                  "sm_mhz_during_ffma": p["sm_mhz"]}
-    if rank == 0 and args.only and args.only not in results:
-        return 0
-    if rank == 0 and args.only == "fp64":
-        print(json.dumps({"metric": METRIC, "value": results["fp64"]["value"], "unit": UNIT,
-                          "ms_per_step": results["fp64"]["ms_per_step"], "precision": "fp64"}), flush=True)
+    if rank == 0 and args.only:
+        r = results[args.only]
+        print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                          "precision": args.only, "tiles": tiles.get(args.only),
+                          "roofline": roofline(r, args.only, None, peaks)}), flush=True)
         return 0
     if rank == 0:
-        m = results["mixed"]
+        f = results["fp64"]
         khash = kernel_hash()
-        traffic = NCU_TRAFFIC.get((khash, "mixed"))
         line = {
-            "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": m["value"] / PAPER_INTERACTIONS_PER_S,
+            "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": f["value"] / PAPER_INTERACTIONS_PER_S,
             "baseline_note": "vs the paper's production run (1e4-body model, 176 CPU processors, ~23 min for "
                              "1000 steps) = 7.9e7 interactions/s: context on other hardware",
-            "dtype": "f32+f64 (mixed: FP64 state and Verlet update, FP32 pair arithmetic)",
+            "dtype": "f64",
             "data": "synthetic (seeded Solar-System-shaped initial conditions)",
             "config": {"workload": f"solar_system_n{N}", "n_bodies": N, "dt_day": s.dt,
-                       "verlet_steps_per_step": args.inner, "precision": "mixed", "tiles": tiles.get("mixed"),
+                       "verlet_steps_per_step": f["inner"], "precision": "fp64", "tiles": tiles.get("fp64"),
                        "l2": "flushed between timed steps (256 MB write outside the events); the 1.3 MB state "
                              "stays L2-resident within a step by design",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "verlet_steps_per_s": m["verlet_steps_per_s"],
-            "roofline": roofline(m, "mixed", traffic),
-            "gpu_launches": args.steps * (1 + 2 * args.inner),
-            "clocks": results.get("clocks"),
+            "verlet_steps_per_s": f["verlet_steps_per_s"],
+            "roofline": roofline(f, "fp64", NCU_TRAFFIC.get((khash, "fp64")), peaks),
+            "gpu_launches": f["gpu_launches"],
+            "clocks": f["clocks"],
         }
+        if "e2e" in f:
+            line["e2e"] = f["e2e"]
+        if "mixed" in results:
+            m = results["mixed"]
+            line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
+                             "dtype": "f32+f64 (FP64 state and Verlet update, FP32 pair arithmetic)",
+                             "verlet_steps_per_step": m["inner"], "verlet_steps_per_s": m["verlet_steps_per_s"],
+                             "tiles": tiles.get("mixed"),
+                             "roofline": roofline(m, "mixed", NCU_TRAFFIC.get((khash, "mixed")), peaks),
+                             "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
+                             "mixed_speedup": m["value"] / f["value"]}
+            if "e2e" in m:
+                line["mixed"]["e2e"] = m["e2e"]
         if peaks:
-            line["roofline"]["peak_measured_tflops"] = peaks["fp32_tflops"]
-            line["roofline"]["frac_of_measured"] = m["force_tflops"] / peaks["fp32_tflops"]
             line["measured_peaks"] = peaks
-        if "fp64" in results:
-            f = results["fp64"]
-            line["fp64"] = {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"],
-                            "verlet_steps_per_step": f["inner"], "verlet_steps_per_s": f["verlet_steps_per_s"],
-                            "tiles": tiles.get("fp64"),
-                            "roofline": roofline(f, "fp64", NCU_TRAFFIC.get((khash, "fp64"))),
-                            "mixed_speedup": m["value"] / f["value"]}
-            if peaks:
-                line["fp64"]["roofline"]["peak_measured_tflops"] = peaks["fp64_tflops"]
-                line["fp64"]["roofline"]["frac_of_measured"] = f["force_tflops"] / peaks["fp64_tflops"]
-            line["gpu_launches"] += args.steps * (1 + 2 * f["inner"])
-        if "e2e" in results:
-            line["e2e"] = results["e2e"]
         if extra:
             line.update(extra)
         if cpu is not None:

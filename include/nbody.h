@@ -68,7 +68,11 @@ typedef enum {
   /* FP64 state and Verlet update (Eqs. 3-4); r_j - r_p formed from a
    * hi/lo float split of the FP64 positions (about as exact as the FP64
    * difference rounded to FP32); 1/|d|^3 and the m_j-weighted terms in
-   * FP32; per-body sums folded into FP64 every 64 terms. */
+   * FP32; per-body sums kept as float pairs, folded every 128 terms.
+   * Sources are kept in a spatial order; for a group of 64 sources whose
+   * distance to a warp's 32 targets exceeds 2e6 times their largest lo
+   * parts, the difference is taken from the hi parts alone, which moves each
+   * such term by at most 1e-6 relative (see nbody_reorder). */
   NBODY_MIXED = 1
 } nbody_precision;
 
@@ -94,6 +98,14 @@ typedef struct {
   int32_t ckpt_every; /* adjoint checkpoint interval in steps; 0 selects 100 */
   int32_t flags;      /* bitwise OR of NBODY_FLAG_* */
   int32_t integrator; /* nbody_integrator (0, the zero value, is Verlet) */
+  /* Path of a JSON file of autotuner results, or NULL (off).  nbody_init
+   * takes its work decomposition (nbody_tiles) from the entry for this
+   * context's precision, integrator, floor(log2(bodies)),
+   * floor(log2(systems)), SM count and kernel build, if there is one;
+   * nbody_autotune writes its winner there.  A missing, unreadable or
+   * malformed file, or a stale entry (other kernels), is ignored: the
+   * context starts from the built-in defaults.  The string is copied. */
+  const char *tune_cache;
 } nbody_opts;
 
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
@@ -162,9 +174,21 @@ nbody_status nbody_step(nbody_ctx *ctx, int64_t n_steps);
 nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
 
 /* Re-read the bound state after the caller changed x..vz or m: recompute
- * a = Eq. 1 at the current positions and re-take the nbody_grad snapshot.
- * Asynchronous (but validates positions synchronously, like nbody_init). */
+ * a = Eq. 1 at the current positions and re-take the nbody_grad snapshot;
+ * mixed precision also re-sorts the sources spatially (nbody_reorder), so
+ * the context then computes bitwise what a new one on this state would.
+ * Asynchronous (but reads the positions and validates them synchronously,
+ * like nbody_init). */
 nbody_status nbody_reset(nbody_ctx *ctx);
+
+/* Mixed precision: re-sort each system's sources into a spatial (Morton)
+ * order of the current positions.  nbody_init and nbody_reset sort; the
+ * order only decides how many source groups the force kernel finds far from
+ * a warp's targets (those take its hi-only path, see NBODY_MIXED) and the
+ * order of the sums, never what is summed.  As bodies move, groups spread
+ * and fewer are far: call this between steps of a long run.  No-op for FP64
+ * contexts.  Synchronous. */
+nbody_status nbody_reorder(nbody_ctx *ctx);
 
 /* Total energy of each system at the current state (Sections 2 and 4):
  *   E_s = sum_p (1/2) m_p |v_p|^2 - sum_{p<j} G m_p m_j / |r_j - r_p|,
@@ -199,7 +223,10 @@ nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
  * steps of the general (two-kernel) path, the one tiles shape, and keep the
  * fastest; a context whose nbody_step runs a single-launch kernel keeps
  * doing so.  The bound state is restored afterwards.  best (HOST, may be
- * NULL) receives the winner, best_ms its time per step.  Synchronous. */
+ * NULL) receives the winner, best_ms its time per step.  With a tune_cache
+ * (nbody_opts) the winner is also written there (replacing the entry with
+ * the same key); if that file cannot be written the call returns
+ * NBODY_EINVAL after keeping the winner.  Synchronous. */
 nbody_status nbody_autotune(nbody_ctx *ctx, int32_t probe_steps, nbody_tiles *best,
                             double *best_ms);
 
@@ -245,6 +272,41 @@ nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
  * nbody_accel in FP64 to rounding (the source order of the sum differs). */
 nbody_status nbody_accel_static(int64_t n, double G, const double *x, const double *y, const double *z,
                                 const double *m, double *ax, double *ay, double *az, void *cuda_stream);
+
+/* Row shards (Section 3's distributed method: each of `world` processes
+ * owns a block of bodies, sums Eq. 1 for them over every body, and all
+ * exchange the new positions after every step).  Turns a context of ONE
+ * system integrated with velocity Verlet into rank `rank` of `world`:
+ * every rank binds the same whole state; rank k owns bodies [k C, (k+1) C)
+ * (C = ceil(N / world) rounded up to even; the last chunks may be short or
+ * empty).  The source buffer becomes `world` chunks of C entries of 32 bytes
+ * (rank k's bodies in chunk k, the rest inert padding), and the current
+ * positions of all bodies are staged for the first step (the Eq. 3 drift),
+ * so every rank starts with the same complete buffer.  Synchronous.  EINVAL
+ * for several systems, RK4 or leapfrog, a context that is already a shard,
+ * or rank/world out of range.  A shard then steps only with
+ * nbody_shard_step; nbody_step, nbody_accel, nbody_reset, nbody_reorder,
+ * nbody_energy, nbody_grad, nbody_set_tiles, nbody_autotune and
+ * nbody_kernel_times return EINVAL (the bound state of other ranks' bodies
+ * is not kept up to date). */
+nbody_status nbody_shard(nbody_ctx *ctx, int32_t rank, int32_t world);
+
+/* One Verlet step of this rank's bodies: Eq. 1 for its bodies against every
+ * source of the current buffer, Eq. 4 and Eq. 3, and their next positions
+ * staged into this rank's chunk of the next buffer.  Before the next
+ * nbody_shard_step, every rank's chunk must be copied into every other
+ * rank's buffer (an all-gather; see nbody_shard_buffer).  Asynchronous on the
+ * context's stream. */
+nbody_status nbody_shard_step(nbody_ctx *ctx);
+
+/* The DEVICE buffer the next nbody_shard_step reads: `world` chunks of
+ * *chunk_bytes bytes (32 bytes per entry), chunk k starting at byte
+ * k * *chunk_bytes.  After nbody_shard_step this rank's chunk is current;
+ * an in-place all-gather of the chunks (e.g. ncclAllGather with send buffer
+ * = this rank's chunk, receive buffer = the whole buffer), ordered on the
+ * context's stream, completes it.  The buffer alternates between two
+ * allocations, so ask again after every step. */
+nbody_status nbody_shard_buffer(const nbody_ctx *ctx, void **stage, int64_t *chunk_bytes);
 
 /* Release the context and everything it owns.  NULL is a no-op. */
 void nbody_free(nbody_ctx *ctx);

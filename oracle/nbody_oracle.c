@@ -343,13 +343,15 @@ void oracle_vjp(int64_t n, double G, const double *x, const double *y,
  * The forward trajectory r_0..r_T is stored whole (no checkpointing).
  * dLdv_T may be NULL (zero).  Outputs are 3n (x block, y block, z block),
  * 3n and n doubles.
- * absr, absv, absm (all NULL, or 3n, 3n, n outputs): the same sweep run on
- * magnitudes -- every quantity replaced by a non-negative bound on the
- * magnitudes of the terms it is a sum of (seeds |dL/dr_T|, |dL/dv_T|; |dt|;
- * the magnitude form of the products in vjp_impl).  Each output element is
- * the sum of the magnitudes of all the elementary terms whose signed sum is
- * the gradient element: the scale against which a rounding error in that
- * element is judged when the terms cancel (condition number = abs / |grad|).
+ * absr, absv, absm (all NULL, or 3n, 3n, n outputs): the scale against
+ * which a rounding error in each gradient element is judged -- the sum of
+ * the magnitudes of everything the sweep adds into that element: for rho,
+ * |dL/dr_T| plus, at every product, the magnitudes of the terms of J^T alpha
+ * (vjp_impl's magnitude form with the sweep's own alpha); for g_m the
+ * magnitudes of the mass terms likewise; for nu, |dL/dv_T| plus, at every
+ * update nu += dt rho, |dt| times the bound on |rho| so far.  Each bounds
+ * the magnitude of its element (|grad| <= abs elementwise), and abs / |grad|
+ * is the element's condition number with respect to errors in the terms.
  * Returns 0, or -1 if memory could not be allocated. */
 int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
                 const double *y0, const double *z0, const double *vx0,
@@ -361,7 +363,7 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
   const int mag = absr != NULL && absv != NULL && absm != NULL;
   double *traj = (double *)malloc(sizeof(double) * 3 * N * (size_t)(T + 1));
   double *work = (double *)malloc(sizeof(double) * 9 * N + 8);
-  double *mw = mag ? (double *)malloc(sizeof(double) * 6 * N + 8) : NULL;
+  double *mw = mag ? (double *)malloc(sizeof(double) * 3 * N + 8) : NULL;
   if (!traj || !work || (mag && !mw)) {
     free(traj);
     free(work);
@@ -390,11 +392,11 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
       return -1;
     }
   }
-  /* reuse work as (nu, alpha, nu_next); magnitudes: R = absr, V = absv,
-   * A and the scratch copy of V in mw */
+  /* reuse work as (nu, alpha, nu_next); magnitudes: absr, absv, absm
+   * accumulate; A = |alpha| (scratch in mw) */
   double *nu = work, *al = work + 3 * N, *tmp = work + 6 * N;
   double *rho = dLdr0;
-  double *V = absv, *A = mw, *Vt = mw ? mw + 3 * N : NULL;
+  double *A = mw;
   const double adt = fabs(dt);
   memcpy(rho, dLdr_T, sizeof(double) * 3 * N);
   if (dLdv_T)
@@ -406,15 +408,14 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
   if (mag) {
     for (size_t k = 0; k < 3 * N; k++) {
       absr[k] = fabs(dLdr_T[k]);
-      V[k] = dLdv_T ? fabs(dLdv_T[k]) : 0.0;
-      A[k] = 0.0;
+      absv[k] = dLdv_T ? fabs(dLdv_T[k]) : 0.0;
     }
     memset(absm, 0, sizeof(double) * N);
   }
   for (int64_t i = T - 1; i >= 0; i--) {
     for (size_t k = 0; k < 3 * N; k++) al[k] += 0.5 * dt * nu[k];
     if (mag)
-      for (size_t k = 0; k < 3 * N; k++) A[k] += 0.5 * adt * V[k];
+      for (size_t k = 0; k < 3 * N; k++) A[k] = fabs(al[k]);
     const double *r = traj + 3 * N * (size_t)(i + 1);
     vjp_impl(n, G, r, r + N, r + 2 * N, m, al, al + N, al + 2 * N, rho,
              rho + N, rho + 2 * N, dLdm, A, A ? A + N : NULL,
@@ -425,14 +426,11 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
       al[k] = 0.5 * dt * nu[k] + 0.5 * dt * dt * rho[k];
     }
     memcpy(nu, tmp, sizeof(double) * 3 * N);
-    if (mag) {
-      for (size_t k = 0; k < 3 * N; k++) {
-        Vt[k] = V[k] + adt * absr[k];
-        A[k] = 0.5 * adt * V[k] + 0.5 * dt * dt * absr[k];
-      }
-      memcpy(V, Vt, sizeof(double) * 3 * N);
-    }
+    if (mag)
+      for (size_t k = 0; k < 3 * N; k++) absv[k] += adt * absr[k];
   }
+  if (mag)
+    for (size_t k = 0; k < 3 * N; k++) A[k] = fabs(al[k]);
   vjp_impl(n, G, traj, traj + N, traj + 2 * N, m, al, al + N, al + 2 * N,
            rho, rho + N, rho + 2 * N, dLdm, A, A ? A + N : NULL,
            A ? A + 2 * N : NULL, absr, absr ? absr + N : NULL,

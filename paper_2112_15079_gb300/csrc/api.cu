@@ -18,6 +18,13 @@
 
 #include "nbody.h"
 #include "nbody_internal.h"
+#include "tune_cache.h"
+
+// Hash of the kernel sources of this build (set by the build script): the
+// tune cache keys its entries with it.
+#ifndef NBODY_KERNEL_HASH
+#define NBODY_KERNEL_HASH "unknown"
+#endif
 
 using nb::Item;
 
@@ -35,6 +42,8 @@ struct Work {
   nb::Seg *segs = nullptr;
   int32_t *seg_off = nullptr;
   uint16_t *nsl = nullptr;  // [N] partial rows of each body
+  std::vector<uint16_t> nsl_rank;  // the plan's rows per block position (body order before any reordering)
+  std::vector<int64_t> plan_off, plan_soff;  // the target ranges it was planned for (positions, stage entries)
   double *partial = nullptr;
   int32_t *dyn_ctr = nullptr;  // [2] dynamic-chunk counter (self-resetting)
   int n_blks = 0, rows = 0, grid = 0, n_dyn = 0;
@@ -68,6 +77,7 @@ struct nbody_ctx {
   double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
   const double *m = nullptr;
   nbody_opts o{};
+  std::string tune_cache;  // copy of o.tune_cache ("" = off)
   cudaStream_t user_stream = nullptr;
   cudaStream_t stream = nullptr;  // where work runs (user stream, or private when user passed NULL)
   bool own_stream = false;
@@ -84,6 +94,20 @@ struct nbody_ctx {
   int64_t n_stage = 0;               // stage entries (mixed: systems padded to even length)
   std::vector<int64_t> soff;         // stage offset of each system
   int32_t *qidx = nullptr;           // [N] stage index of each body (mixed)
+  int32_t *perm = nullptr;           // [n_stage] body of each stage entry (mixed; padding: any body)
+  float4 *boxes = nullptr;           // mixed: [n_stage / 64 rounded up][2] source-group boxes of the next force launch
+  std::vector<int32_t> qidx_h;       // host copy of qidx (mixed)
+  // Targets and sources of the force launches: system s's targets are the
+  // block positions [tgt_off[s], tgt_off[s+1]) at stage entries from
+  // tgt_soff[s]; its sources are the stage entries [src_b[s], src_b[s] +
+  // src_n[s]).  Unsharded: the systems themselves.
+  std::vector<int64_t> tgt_off, tgt_soff, src_b, src_n;
+  // Row shard (nbody_shard): this rank completes bodies [sh_begin, sh_end);
+  // the stage holds sh_world chunks of sh_chunk entries (rank k's bodies at
+  // entries [k sh_chunk, ...), then inert padding).
+  int32_t sh_world = 0, sh_rank = 0;
+  int64_t sh_chunk = 0, sh_begin = 0, sh_end = 0;
+  int sh_cur = 0;  // the stage the next shard step reads
   double *R = nullptr;               // [3][N] mixed: FP64 positions of the staged step
   double *rk = nullptr;              // RK4: [3][3N] stage velocity V, sums AR and AV
   double *snap = nullptr;            // [6][N] r0, v0 for nbody_grad
@@ -180,6 +204,17 @@ bool tiles_valid(const nbody_tiles &t, int precision) {
          t.tj % 64 == 0 && t.jsplit >= 0 && t.jsplit <= 64 && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 32;
 }
 
+nb::TuneKey tune_key(const nbody_ctx *c) {
+  nb::TuneKey k;
+  k.precision = c->o.precision;
+  k.integrator = c->o.integrator;
+  k.n_log2 = nb::floor_log2(c->N);
+  k.systems_log2 = nb::floor_log2(c->n_sys);
+  k.sms = c->nsm;
+  k.kernels = NBODY_KERNEL_HASH;
+  return k;
+}
+
 nbody_tiles default_tiles(const nbody_ctx *c) {
   // The autotuner's picks on GB300: FP64 is bound by the FP64 pipe (~90% busy)
   // with three 128-thread CTAs per SM at every size; the mixed path takes two
@@ -204,6 +239,36 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
 
 void free_work(nbody_ctx *c, Work &w);
 
+// Rows per BODY from the plan's rows per block position: position r of
+// system s is stage entry soff[s] + (r - offsets[s]), which holds body
+// perm[...] -- so body p takes the rows of position offsets[s] + (qidx[p] -
+// soff[s]).  Without a reordered stage (FP64) the two coincide.
+nbody_status upload_nsl(nbody_ctx *c, Work &wk) {
+  if (!wk.nsl) return NBODY_OK;
+  std::vector<uint16_t> body(static_cast<size_t>(c->N), 0);  // bodies outside the plan's targets: 0 rows
+  const size_t n_sys = wk.plan_soff.size();
+  for (size_t s = 0; s < n_sys; ++s) {
+    const int64_t q0 = wk.plan_soff[s], n = wk.plan_off[s + 1] - wk.plan_off[s];
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t q = q0 + r;  // stage entry of block position plan_off[s] + r
+      const int64_t p = c->qidx_h.empty() ? q : -1;
+      if (p >= 0) body[p] = wk.nsl_rank[wk.plan_off[s] + r];
+    }
+  }
+  if (!c->qidx_h.empty()) {  // reordered stage: body p sits at entry qidx[p]
+    std::vector<int64_t> pos_of_entry(static_cast<size_t>(c->n_stage), -1);
+    for (size_t s = 0; s < n_sys; ++s)
+      for (int64_t r = 0; r < wk.plan_off[s + 1] - wk.plan_off[s]; ++r)
+        pos_of_entry[wk.plan_soff[s] + r] = wk.plan_off[s] + r;
+    for (int32_t p = 0; p < c->N; ++p) {
+      const int64_t r = pos_of_entry[c->qidx_h[p]];
+      if (r >= 0) body[p] = wk.nsl_rank[r];
+    }
+  }
+  NB_CUDA(c, cudaMemcpy(wk.nsl, body.data(), sizeof(uint16_t) * body.size(), cudaMemcpyHostToDevice));
+  return NBODY_OK;
+}
+
 // Build stream-K work tables (the plan is work_plan.h's) and upload them.
 // row_doubles: 8-byte words per body and partial row (3 force, 4 VJP).
 nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, int row_doubles) {
@@ -211,15 +276,20 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   if (occ < 1) return fail(c, NBODY_EINVAL, "tiles do not fit on an SM (threads %d, ipt %d, tj %d)", t.threads, t.ipt, t.tj);
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
   nb::WorkPlan plan;
-  const std::string why = nb::plan_work(c->offsets, c->soff, c->o.precision == NBODY_MIXED, t.threads, t.ipt,
-                                        t.jsplit, static_cast<int64_t>(c->nsm) * cps, plan);
+  const bool own_src = c->src_b.empty();
+  const std::string why = nb::plan_work(c->tgt_off, c->tgt_soff, c->o.precision == NBODY_MIXED, t.threads, t.ipt,
+                                        t.jsplit, static_cast<int64_t>(c->nsm) * cps, plan,
+                                        own_src ? nullptr : &c->src_b, own_src ? nullptr : &c->src_n);
   if (!why.empty()) return fail(c, NBODY_EINVAL, "%s", why.c_str());
+  wk.plan_off = c->tgt_off;
+  wk.plan_soff = c->tgt_soff;
   const std::vector<nb::Blk> &blks = plan.blks;
   const std::vector<nb::Seg> &segs = plan.segs;
   const std::vector<int32_t> &seg_off = plan.seg_off;
   const std::vector<uint16_t> &nsl = plan.nsl;
   const int rows = plan.rows;
   const int64_t G = plan.grid, D = plan.n_dyn;
+  wk.nsl_rank = nsl;
   wk.n_dyn = static_cast<int>(D);
   wk.n_blks = static_cast<int>(blks.size());
   wk.rows = rows;
@@ -231,17 +301,18 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.segs), sizeof(nb::Seg) * segs.size())) != NBODY_OK) return st;
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.seg_off), sizeof(int32_t) * seg_off.size())) != NBODY_OK)
       return st;
-    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * nsl.size())) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * static_cast<size_t>(c->N))) != NBODY_OK)
+      return st;
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial),
                      sizeof(double) * row_doubles * static_cast<size_t>(rows) * c->N)) != NBODY_OK)
       return st;
     NB_CUDA(c, cudaMemset(wk.dyn_ctr, 0, sizeof(int32_t) * 2));
+    // (nsl: one entry per body, those outside the planned targets 0)
     NB_CUDA(c, cudaMemcpy(wk.blks, blks.data(), sizeof(nb::Blk) * blks.size(), cudaMemcpyHostToDevice));
     NB_CUDA(c, cudaMemcpy(wk.segs, segs.data(), sizeof(nb::Seg) * segs.size(), cudaMemcpyHostToDevice));
     NB_CUDA(c, cudaMemcpy(wk.seg_off, seg_off.data(), sizeof(int32_t) * seg_off.size(), cudaMemcpyHostToDevice));
-    NB_CUDA(c, cudaMemcpy(wk.nsl, nsl.data(), sizeof(uint16_t) * nsl.size(), cudaMemcpyHostToDevice));
-    return NBODY_OK;
+    return upload_nsl(c, wk);
   };
   const nbody_status st = upload();
   if (st != NBODY_OK) free_work(c, wk);  // all or nothing: no half-built tables
@@ -311,6 +382,8 @@ nb::ForceArgs force_args(nbody_ctx *c, const void *cur) {
   nb::ForceArgs a{};
   a.cur = cur;
   a.partial = c->fw.partial;
+  a.perm = c->perm;
+  a.boxes = c->boxes;
   a.flags = c->flags;
   a.blks = c->fw.blks;
   a.segs = c->fw.segs;
@@ -337,6 +410,8 @@ nb::VerletArgs verlet_args(nbody_ctx *c, const State &s, const void *cur, void *
   a.qidx = c->qidx;
   a.flags = c->flags;
   a.N = c->N;
+  a.p_begin = c->sh_world > 0 ? static_cast<int32_t>(c->sh_begin) : 0;  // a row shard completes its own bodies
+  a.p_end = c->sh_world > 0 ? static_cast<int32_t>(c->sh_end) : c->N;
   a.mode = mode;
   a.release_early = c->fw.occ == 1 ? 1 : 0;
   a.dt = c->o.dt;
@@ -376,6 +451,7 @@ nb::RkArgs rk_args(nbody_ctx *c, const State &s, const void *cur, void *nxt, int
 nbody_status launch_one_step(nbody_ctx *c, const State &s, const void *cur, void *nxt, int mode, cudaStream_t st,
                              const cudaEvent_t *ev = nullptr) {
   const bool chained = ev == nullptr;
+  if (c->o.precision == NBODY_MIXED) NB_CUDA(c, nb::launch_boxes(cur, c->n_stage / 2, c->boxes, st, chained));
   if (ev) NB_CUDA(c, cudaEventRecord(ev[0], st));
   NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
                               force_args(c, cur), st, chained));
@@ -392,6 +468,7 @@ nbody_status launch_rk4_step(nbody_ctx *c, const State &s, cudaStream_t st) {
   for (int k = 0; k < 4; ++k) {
     const void *cur = c->stage[k & 1];
     void *nxt = c->stage[1 - (k & 1)];
+    if (c->o.precision == NBODY_MIXED) NB_CUDA(c, nb::launch_boxes(cur, c->n_stage / 2, c->boxes, st, true));
     NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
                                 force_args(c, cur), st, true));
     NB_CUDA(c, nb::launch_rk_stage(c->o.precision, rk_args(c, s, cur, nxt, 2 + k), st, true));
@@ -458,6 +535,84 @@ nbody_status check_flags(nbody_ctx *c, bool init_phase) {
   return NBODY_OK;
 }
 
+// Bit i of q moved to bit 3i (21 bits in, 63 out).
+uint64_t spread3(uint32_t q) {
+  uint64_t k = 0;
+  for (int i = 0; i < 21; ++i) k |= static_cast<uint64_t>((q >> i) & 1u) << (3 * i);
+  return k;
+}
+
+// Spatial order of each system's stage (mixed path): the bodies of a system
+// sorted by the Morton code of their position in the system's bounding box
+// (21 bits per axis; ties by body index), so that consecutive stage entries
+// -- a warp's targets, a tile's source groups -- sit near each other and far
+// groups take the force kernel's hi-only path.  Any order gives Eq. 1 to
+// rounding; the order only decides which pairs are far (and the order of
+// the sums).  Synchronous: reads the bound positions.  A system with a
+// non-finite coordinate keeps body order (staging then reports it).
+nbody_status spatial_order(nbody_ctx *c) {
+  if (c->o.precision != NBODY_MIXED) return NBODY_OK;
+  const size_t N = c->N, b = sizeof(double) * N;
+  std::vector<double> h(3 * N);
+  NB_CUDA(c, cudaMemcpyAsync(h.data(), c->x, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(h.data() + N, c->y, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(h.data() + 2 * N, c->z, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->qidx_h.assign(N, 0);
+  std::vector<int32_t> perm(static_cast<size_t>(c->n_stage), 0);
+  std::vector<std::pair<uint64_t, int32_t>> key;
+  // Ranges sorted independently: (first body, end body, first stage entry,
+  // end stage entry) -- each system, or each rank's chunk of a row shard.
+  struct Range {
+    int64_t b, e, q, qe;
+  };
+  std::vector<Range> ranges;
+  if (c->sh_world > 0) {
+    for (int64_t k = 0; k < c->sh_world; ++k)
+      ranges.push_back({std::min<int64_t>(k * c->sh_chunk, N), std::min<int64_t>((k + 1) * c->sh_chunk, N),
+                        k * c->sh_chunk, (k + 1) * c->sh_chunk});
+  } else {
+    for (int64_t s = 0; s < c->n_sys; ++s) ranges.push_back({c->offsets[s], c->offsets[s + 1], c->soff[s], c->soff[s + 1]});
+  }
+  for (const Range &rg : ranges) {
+    const int64_t b0 = rg.b, e0 = rg.e;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool finite = true;
+    for (int64_t p = b0; p < e0; ++p)
+      for (int k = 0; k < 3; ++k) {
+        const double v = h[k * N + p];
+        finite = finite && std::isfinite(v);
+        lo[k] = std::min(lo[k], v);
+        hi[k] = std::max(hi[k], v);
+      }
+    const double span = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]});
+    key.clear();
+    for (int64_t p = b0; p < e0; ++p) {
+      uint64_t code = 0;
+      if (finite && span > 0.0) {
+        const double scale = ((1u << 21) - 1) / span;
+        for (int k = 0; k < 3; ++k) {
+          const double t = std::floor((h[k * N + p] - lo[k]) * scale);
+          const uint32_t q = static_cast<uint32_t>(std::min(std::max(t, 0.0), double((1u << 21) - 1)));
+          code |= spread3(q) << k;
+        }
+      }
+      key.emplace_back(code, static_cast<int32_t>(p));
+    }
+    std::sort(key.begin(), key.end());
+    for (int64_t r = 0; r < e0 - b0; ++r) {
+      const int64_t slot = rg.q + r;
+      c->qidx_h[key[r].second] = static_cast<int32_t>(slot);
+      perm[slot] = key[r].second;
+    }
+    for (int64_t slot = rg.q + (e0 - b0); slot < rg.qe; ++slot) perm[slot] = static_cast<int32_t>(std::min<int64_t>(b0, N - 1));
+  }
+  NB_CUDA(c, cudaMemcpyAsync(c->qidx, c->qidx_h.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(c->perm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NBODY_OK;
+}
+
 nbody_status snapshot(nbody_ctx *c) {
   const size_t N = c->N, b = sizeof(double) * N;
   double *src[6] = {c->x, c->y, c->z, c->vx, c->vy, c->vz};
@@ -488,6 +643,8 @@ nbody_status alloc_scratch(nbody_ctx *c) {
     c->soff[s + 1] = c->soff[s] + (c->o.precision == NBODY_MIXED ? (ns + 1) / 2 * 2 : ns);
   }
   c->n_stage = c->soff[c->n_sys];
+  c->tgt_off = c->offsets;
+  c->tgt_soff.assign(c->soff.begin(), c->soff.end() - 1);
 #define NB_ALLOC(ptr, bytes) \
   if ((st = dalloc(c, reinterpret_cast<void **>(&(ptr)), (bytes))) != NBODY_OK) return st;
   NB_ALLOC(c->a, sizeof(double) * 3 * N);
@@ -496,11 +653,8 @@ nbody_status alloc_scratch(nbody_ctx *c) {
   if (c->o.precision == NBODY_MIXED) {
     NB_ALLOC(c->R, sizeof(double) * 3 * N);
     NB_ALLOC(c->qidx, sizeof(int32_t) * N);
-    std::vector<int32_t> q(N);
-    for (int64_t s = 0; s < c->n_sys; ++s)
-      for (int64_t p = c->offsets[s]; p < c->offsets[s + 1]; ++p)
-        q[p] = static_cast<int32_t>(c->soff[s] + (p - c->offsets[s]));
-    NB_CUDA(c, cudaMemcpy(c->qidx, q.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+    NB_ALLOC(c->perm, sizeof(int32_t) * static_cast<size_t>(c->n_stage));
+    NB_ALLOC(c->boxes, 2 * sizeof(float4) * static_cast<size_t>((c->n_stage / 2 + nb::kBoxPairs - 1) / nb::kBoxPairs));
     for (int b = 0; b < 2; ++b) NB_CUDA(c, nb::launch_pad_fill(c->stage[b], c->n_stage / 2, c->stream));
   }
   if (c->o.integrator == NBODY_RK4) NB_ALLOC(c->rk, sizeof(double) * 9 * N);
@@ -661,6 +815,8 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   c->N = static_cast<int32_t>(offsets[n_systems]);
   c->x = x; c->y = y; c->z = z; c->vx = vx; c->vy = vy; c->vz = vz; c->m = m;
   c->o = *o;
+  if (o->tune_cache) c->tune_cache = o->tune_cache;
+  c->o.tune_cache = nullptr;  // the context keeps its own copy
   if (c->o.ckpt_every == 0) c->o.ckpt_every = 100;
   c->user_stream = static_cast<cudaStream_t>(cuda_stream);
   // Optional host-side test hook: NBODY_INJECT_WAIT_STALL=k stalls one
@@ -709,7 +865,22 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   }
   nbody_status st = alloc_scratch(c);
   if (st != NBODY_OK) return bail(st);
-  if ((st = build_items(c, default_tiles(c))) != NBODY_OK) return bail(st);
+  if ((st = begin_work(c)) != NBODY_OK || (st = spatial_order(c)) != NBODY_OK) return bail(st);
+  // Tiles: the tune cache's entry for this context, if it has a usable one,
+  // else the defaults.
+  bool tiled = false;
+  nb::TuneEntry te;
+  if (!c->tune_cache.empty() && nb::tune_cache_lookup(c->tune_cache, tune_key(c), te)) {
+    nbody_tiles t{};
+    t.threads = te.threads;
+    t.ipt = te.ipt;
+    t.tj = te.tj;
+    t.jsplit = te.jsplit;
+    t.ctas_per_sm = te.ctas_per_sm;
+    tiled = tiles_valid(t, c->o.precision) && build_items(c, t) == NBODY_OK;
+    cudaGetLastError();
+  }
+  if (!tiled && (st = build_items(c, default_tiles(c))) != NBODY_OK) return bail(st);
   // One FP64 Verlet system: every step of a call in one launch, a cluster up
   // to kSmallClusterMax bodies, a cooperative grid up to the grid kernel's
   // limit (each faster than the general path there).
@@ -735,6 +906,7 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
 nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return NBODY_OK;
   nbody_status st;
@@ -823,6 +995,7 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
 nbody_status nbody_accel(nbody_ctx *c, double *ax, double *ay, double *az) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (!ax || !ay || !az) return fail(c, NBODY_EINVAL, "output pointer is NULL");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -836,12 +1009,35 @@ nbody_status nbody_accel(nbody_ctx *c, double *ax, double *ay, double *az) {
 nbody_status nbody_reset(nbody_ctx *c) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
+  // As nbody_init: the spatial order of the new positions (mixed), so a reset
+  // context computes bitwise what a new one would.
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if ((st = spatial_order(c)) != NBODY_OK || (st = upload_nsl(c, c->fw)) != NBODY_OK ||
+      (st = upload_nsl(c, c->adj.vj)) != NBODY_OK)
+    return st;
   return refresh(c);
+}
+
+nbody_status nbody_reorder(nbody_ctx *c) {
+  if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if ((st = spatial_order(c)) != NBODY_OK) return st;
+  if ((st = upload_nsl(c, c->fw)) != NBODY_OK) return st;
+  if ((st = upload_nsl(c, c->adj.vj)) != NBODY_OK) return st;
+  return end_work(c);
 }
 
 nbody_status nbody_energy(nbody_ctx *c, double *e_host) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (!e_host) return fail(c, NBODY_EINVAL, "e_host is NULL");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -884,6 +1080,7 @@ nbody_status nbody_get_tiles(const nbody_ctx *c, nbody_tiles *t) {
 nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (!t || !tiles_valid(*t, c->o.precision))
     return fail(c, NBODY_EINVAL, "invalid tiles (see nbody.h: supported threads/ipt pairs, tj 64..2048 step 64, jsplit 0..64, ctas_per_sm 1..32)");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -893,6 +1090,7 @@ nbody_status nbody_set_tiles(nbody_ctx *c, const nbody_tiles *t) {
 nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best, double *best_ms) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (probe_steps < 1) return fail(c, NBODY_EINVAL, "probe_steps must be >= 1");
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   // Tiles shape only the general path (and nbody_accel / nbody_grad): time
@@ -927,19 +1125,24 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   for (int th : {64, 128, 256, 384, 512, 768, 1024})
     for (int ip : {1, 2, 4})
       for (int tj : {128, 256, 512, 1024, 2048})
-        for (int cps : {1, 2, 3, 4}) {
+        for (int cps : {1, 2, 3, 4})
+          for (int js : {0, 1, 2, 4}) {
           if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
           // FP64 is bound by the FP64 pipe: only the barrier spacing (tj) and the warp count matter
           if (!mixed && tj < 512) continue;
           if (mixed && tj > 1024) continue;
           // at most 1024 threads per SM; the mixed path wants >= 512 threads or >= 1024 targets per SM
           if (th * cps > 1024 || (mixed && th * cps < 512 && th * cps * ip < 1024)) continue;
+          // Dynamic chunks (jsplit) add partial rows; they pay only where the
+          // cost per interaction varies between shares: the mixed path, whose
+          // far source groups cost 12 lane operations against 18 for near ones.
+          if (js > 0 && !mixed) continue;
           nbody_tiles t;
           t.threads = th;
           t.ipt = ip;
           t.tj = tj;
           t.ctas_per_sm = cps;
-          t.jsplit = 0;  // dynamic chunks measured slower on GB300 (more partial rows)
+          t.jsplit = js;
           cand.push_back(t);
         }
   cudaEvent_t e0, e1;
@@ -979,12 +1182,24 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   if ((st = check_flags(c, false)) != NBODY_OK) return st;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
+  if (!c->tune_cache.empty()) {
+    nb::TuneEntry te;
+    te.threads = win.threads;
+    te.ipt = win.ipt;
+    te.tj = win.tj;
+    te.jsplit = win.jsplit;
+    te.ctas_per_sm = win.ctas_per_sm;
+    te.ms_per_step = win_ms;
+    const std::string why = nb::tune_cache_store(c->tune_cache, tune_key(c), te);
+    if (!why.empty()) return fail(c, NBODY_EINVAL, "tune cache not written: %s", why.c_str());
+  }
   return NBODY_OK;
 }
 
 nbody_status nbody_kernel_times(nbody_ctx *c, int32_t n_steps, double *out) {
   if (!c || !out) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "nbody_kernel_times times Verlet steps only");
   if (n_steps < 1) return fail(c, NBODY_EINVAL, "n_steps must be >= 1");
   nbody_status st;
@@ -1031,6 +1246,7 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
                         double *dL_dv0, double *dL_dm) {
   if (!c) return NBODY_EINVAL;
   const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (n_steps < 0) return fail(c, NBODY_EINVAL, "n_steps must be >= 0");
   if (!dL_dr_T || !dL_dr0 || !dL_dv0 || !dL_dm) return fail(c, NBODY_EINVAL, "a gradient pointer is NULL");
   if (n_steps > (int64_t(1) << 31)) return fail(c, NBODY_EINVAL, "n_steps too large");
@@ -1084,6 +1300,7 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   NB_CUDA(c, nb::launch_adjoint_init(prec, ad, dL_dr_T, dL_dv_T, c->stream));
   nb::VjpArgs vj{};
   vj.w = A.w;
+  vj.perm = c->perm;
   vj.partial = A.vj.partial;
   vj.flags = c->flags;
   vj.blks = A.vj.blks;
@@ -1121,6 +1338,94 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   NB_CUDA(c, cudaMemcpyAsync(dL_dm, A.gm, b, cudaMemcpyDeviceToDevice, c->stream));
   if ((st = end_work(c)) != NBODY_OK) return st;
   return check_flags(c, false);
+}
+
+nbody_status nbody_shard(nbody_ctx *c, int32_t rank, int32_t world) {
+  if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
+  if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "the context is already a row shard");
+  if (world < 1 || rank < 0 || rank >= world) return fail(c, NBODY_EINVAL, "need 0 <= rank < world");
+  if (c->n_sys != 1) return fail(c, NBODY_EINVAL, "row shards take one system");
+  if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "row shards run velocity Verlet");
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int64_t N = c->N;
+  const int64_t C = ((N + world - 1) / world + 1) / 2 * 2;  // equal chunks, whole source pairs
+  const int64_t n_stage = C * world;
+  // Stages of world equal chunks: bodies of rank k at entries [k C, ...),
+  // the rest inert padding (every entry starts as padding; staging
+  // overwrites the real ones).
+  drop_graphs(c);
+  for (int b = 0; b < 2; ++b) {
+    dfree(c, c->stage[b]);
+    c->stage[b] = nullptr;
+  }
+  dfree(c, c->perm);
+  c->perm = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dalloc(c, &c->stage[b], 32 * static_cast<size_t>(n_stage))) != NBODY_OK) return st;
+    NB_CUDA(c, c->o.precision == NBODY_MIXED ? nb::launch_pad_fill(c->stage[b], n_stage / 2, c->stream)
+                                             : nb::launch_pad_fill_fp64(c->stage[b], n_stage, c->stream));
+  }
+  if (c->o.precision == NBODY_MIXED) {
+    dfree(c, c->boxes);
+    c->boxes = nullptr;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&c->perm), sizeof(int32_t) * static_cast<size_t>(n_stage))) !=
+            NBODY_OK ||
+        (st = dalloc(c, reinterpret_cast<void **>(&c->boxes),
+                     2 * sizeof(float4) * static_cast<size_t>((n_stage / 2 + nb::kBoxPairs - 1) / nb::kBoxPairs))) !=
+            NBODY_OK)
+      return st;
+  }
+  c->n_stage = n_stage;
+  c->soff = {0, n_stage};
+  c->sh_world = world;
+  c->sh_rank = rank;
+  c->sh_chunk = C;
+  c->sh_begin = std::min<int64_t>(rank * C, N);
+  c->sh_end = std::min<int64_t>(c->sh_begin + C, N);
+  c->sh_cur = 0;
+  c->small = c->grid = false;
+  // the adjoint's workspace is laid out for the old stage; shards take no gradient
+  free_work(c, c->adj.vj);
+  for (void *q : {static_cast<void *>(c->adj.rho), static_cast<void *>(c->adj.nu), static_cast<void *>(c->adj.gm),
+                  c->adj.w, static_cast<void *>(c->adj.shadow), static_cast<void *>(c->adj.ckpt), c->adj.store})
+    dfree(c, q);
+  c->adj = Adjoint{};
+  if ((st = spatial_order(c)) != NBODY_OK) return st;
+  // This rank's targets against every source of the system.
+  c->tgt_off = {c->sh_begin, c->sh_end};
+  c->tgt_soff = {c->sh_begin};
+  c->src_b = {0};
+  c->src_n = {n_stage};
+  if (c->sh_end > c->sh_begin && (st = build_items(c, c->tiles)) != NBODY_OK) return st;
+  // Every rank holds the whole state: stage the first step's Eq. 3 drift of
+  // every body, so the first shard step needs no exchange.
+  NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, bound_state(c), 1, 0), c->stream));
+  if ((st = end_work(c)) != NBODY_OK) return st;
+  return check_flags(c, false);
+}
+
+nbody_status nbody_shard_step(nbody_ctx *c) {
+  if (!c) return NBODY_EINVAL;
+  const DeviceGuard dg(c->dev);
+  if (c->sh_world == 0) return fail(c, NBODY_EINVAL, "not a row shard (see nbody_shard)");
+  nbody_status st;
+  if ((st = begin_work(c)) != NBODY_OK) return st;
+  const int k = c->sh_cur;
+  if (c->sh_end > c->sh_begin &&
+      (st = launch_one_step(c, bound_state(c), c->stage[k], c->stage[1 - k], nb::kModeStep, c->stream)) != NBODY_OK)
+    return st;
+  c->sh_cur = 1 - k;
+  return end_work(c);
+}
+
+nbody_status nbody_shard_buffer(const nbody_ctx *c, void **stage, int64_t *chunk_bytes) {
+  if (!c || !stage || !chunk_bytes || c->sh_world == 0) return NBODY_EINVAL;
+  *stage = c->stage[c->sh_cur];
+  *chunk_bytes = 32 * c->sh_chunk;
+  return NBODY_OK;
 }
 
 void nbody_free(nbody_ctx *c) {

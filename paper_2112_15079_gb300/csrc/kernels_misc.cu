@@ -53,6 +53,62 @@ size_t force_smem_bytes(int precision, int tj) {
 }
 
 // ---------------------------------------------------------------------------
+// Widened boxes of the mixed stage's source groups for the next force launch:
+// group g = stage pairs [kBoxPairs g, kBoxPairs (g + 1)), one warp per group,
+// lane l reading pair kBoxPairs g + l.  The box of the hi parts is widened on
+// every side by kFarKappa times the largest lo part (see step_kernel.cuh).
+// Padding sources (coordinate kPadCoord, mu = 0) stay out of the box; a group
+// of padding only gets an empty box (low corner +inf, high corner -inf),
+// which the far test finds far from every warp.
+// ---------------------------------------------------------------------------
+constexpr int kBoxWarps = 8;  // groups per CTA
+
+__global__ void __launch_bounds__(32 * kBoxWarps) box_kernel(const float4 *stage, int64_t n_pairs, float4 *boxes) {
+  grid_dependency_wait();  // the stage was written by the previous kernel
+  grid_dependency_launch();
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * kBoxWarps + threadIdx.x / 32;
+  const int64_t n_groups = (n_pairs + kBoxPairs - 1) / kBoxPairs;
+  if (g >= n_groups) return;  // warp-uniform
+  const int64_t b = g * kBoxPairs + (threadIdx.x & 31);
+  float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, lo[3] = {0.f, 0.f, 0.f};
+  if (b < n_pairs) {
+    // (xh0 xh1 yh0 yh1) (zh0 zh1 mu0 mu1) (xl0 xl1 yl0 yl1) (zl0 zl1 - -)
+    const float4 A = stage[4 * b], B = stage[4 * b + 1], C = stage[4 * b + 2], D = stage[4 * b + 3];
+    const float hx[2] = {A.x, A.y}, hy[2] = {A.z, A.w}, hz[2] = {B.x, B.y}, mu[2] = {B.z, B.w};
+    const float lx[2] = {C.x, C.y}, ly[2] = {C.z, C.w}, lz[2] = {D.x, D.y};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (hx[e] == kPadCoord && mu[e] == 0.f) continue;
+      mn[0] = fminf(mn[0], hx[e]);
+      mn[1] = fminf(mn[1], hy[e]);
+      mn[2] = fminf(mn[2], hz[e]);
+      mx[0] = fmaxf(mx[0], hx[e]);
+      mx[1] = fmaxf(mx[1], hy[e]);
+      mx[2] = fmaxf(mx[2], hz[e]);
+      lo[0] = fmaxf(lo[0], fabsf(lx[e]));
+      lo[1] = fmaxf(lo[1], fabsf(ly[e]));
+      lo[2] = fmaxf(lo[2], fabsf(lz[e]));
+    }
+  }
+  warp_box(mn[0], mn[1], mn[2], mx[0], mx[1], mx[2], lo[0], lo[1], lo[2], boxes + 2 * g);
+}
+
+cudaError_t launch_boxes(const void *stage, int64_t n_pairs, float4 *boxes, cudaStream_t s, bool chained) {
+  const int64_t n_groups = (n_pairs + kBoxPairs - 1) / kBoxPairs;
+  if (n_groups <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>((n_groups + kBoxWarps - 1) / kBoxWarps));
+  cfg.blockDim = dim3(32 * kBoxWarps);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, box_kernel, static_cast<const float4 *>(stage), n_pairs, boxes);
+}
+
+// ---------------------------------------------------------------------------
 // Completes a step for VerletShape<PREC>::kBodies consecutive bodies per CTA.
 //   Phase A (kLanes threads per body): a_new = the sum of the body's force
 //   partials in a fixed order.  Lane l takes rows l, l + kLanes, ... (TwoSum:
@@ -196,16 +252,16 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
   // spends 64 cycles on every warp instruction, so this is the latency).
   constexpr bool kSplit = PREC == 1;
   __shared__ T s_hi[3][NB], s_lo[3][NB];
-  const int p0 = blockIdx.x * NB;
+  const int p0 = a.p_begin + blockIdx.x * NB;  // bodies [p_begin, p_end) (a row shard, or all)
   const int b = threadIdx.x / L, lane = threadIdx.x % L;
   const int p = p0 + b;  // phase A body
-  const bool live = p < a.N;
+  const bool live = p < a.p_end;
   const size_t N = static_cast<size_t>(a.N);
   const int warp = threadIdx.x >> 5;
   const int k = kSplit ? (threadIdx.x & 31) : threadIdx.x;  // phase B body within the CTA
   const int q = p0 + k;
   const int comp = kSplit ? warp : 0;
-  const bool own = (kSplit ? warp < 3 : threadIdx.x < NB) && q < a.N;
+  const bool own = (kSplit ? warp < 3 : threadIdx.x < NB) && q < a.p_end;
   constexpr bool step = MODE != kModeForce;
   constexpr bool leap = MODE == kModeLeapfrog;
   // This thread's component arrays (mixed split; the FP64 path uses all three).
@@ -306,10 +362,10 @@ __global__ void __launch_bounds__(VerletShape<PREC>::kBlock) verlet_kernel(const
 }
 
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained) {
-  if (a.N <= 0) return cudaSuccess;
+  if (a.p_end <= a.p_begin) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   const int64_t nb = precision == 0 ? VerletShape<0>::kBodies : VerletShape<1>::kBodies;
-  cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.N) + nb - 1) / nb));
+  cfg.gridDim = dim3(static_cast<unsigned>((static_cast<int64_t>(a.p_end - a.p_begin) + nb - 1) / nb));
   cfg.blockDim = dim3(precision == 0 ? VerletShape<0>::kBlock : VerletShape<1>::kBlock);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -557,6 +613,20 @@ __global__ void pad_fill_kernel(float *stage, int64_t n_pairs) {
   if (i >= n_pairs * 16) return;
   const int f = static_cast<int>(i & 15);
   stage[i] = f < 6 ? kPadCoord : 0.f;
+}
+
+// Padding sources of the FP64 layout (row shards pad the stage to equal
+// chunks): (kPadCoord, kPadCoord, kPadCoord, mu = 0); the term of each is
+// exactly 0 against any real target.
+__global__ void pad_fill_fp64_kernel(double4_32a *stage, int64_t n) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) stage[i] = make_double4_32a(kPadCoord, kPadCoord, kPadCoord, 0.0);
+}
+
+cudaError_t launch_pad_fill_fp64(void *stage, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  pad_fill_fp64_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(static_cast<double4_32a *>(stage), n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s) {

@@ -160,6 +160,43 @@ __device__ __forceinline__ void interact_mixed(const float4 &hj, const float4 &l
 }
 
 // ---------------------------------------------------------------------------
+// Bounding boxes for the mixed force kernel's far test
+// ---------------------------------------------------------------------------
+
+// Warp-wide minimum / maximum of a float through the integer reduction unit:
+// ord() maps floats to unsigned integers in the same order.
+__device__ __forceinline__ unsigned ord(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ float warp_min(float v) { return unord(__reduce_min_sync(0xffffffffu, ord(v))); }
+__device__ __forceinline__ float warp_max(float v) { return unord(__reduce_max_sync(0xffffffffu, ord(v))); }
+
+// Widened box of one warp's hi coordinates (mn, mx over its lanes) with lo
+// parts up to (lx, ly, lz) per component: [mn - kappa l, mx + kappa l] per axis
+// with l = |(lx, ly, lz)|, written by lane 0 to box[0..1].
+__device__ __forceinline__ void warp_box(float mnx, float mny, float mnz, float mxx, float mxy, float mxz, float lx,
+                                         float ly, float lz, float4 *box) {
+  mnx = warp_min(mnx);
+  mny = warp_min(mny);
+  mnz = warp_min(mnz);
+  mxx = warp_max(mxx);
+  mxy = warp_max(mxy);
+  mxz = warp_max(mxz);
+  lx = warp_max(lx);
+  ly = warp_max(ly);
+  lz = warp_max(lz);
+  const float w = kFarKappa * sqrtf(fmaf(lz, lz, fmaf(ly, ly, lx * lx)));
+  if ((threadIdx.x & 31) == 0) {
+    box[0] = make_float4(mnx - w, mny - w, mnz - w, 0.f);
+    box[1] = make_float4(mxx + w, mxy + w, mxz + w, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Velocity Verlet (Eqs. 3-4), one body, one component.  The fused step
 // epilogue and the stand-alone pre-drift both call these, so a run split
 // into several nbody_step calls is bitwise identical to one call.

@@ -39,6 +39,7 @@ struct ForceArgs {
   double *partial;  // [rows][3][N]: doubles (FP64) or float pairs (mixed), 24 B per row and body
   const int32_t *perm;  // [stage entries] body of each stage entry (mixed, spatial order); NULL: the
                         // block's targets are bodies i0.. in order
+  const float4 *boxes;  // mixed: [groups][2] widened box of stage pairs [32 g, 32 g + 32) (box_kernel)
   unsigned *flags;
   const Blk *blks;
   const Seg *segs;
@@ -69,6 +70,7 @@ struct VerletArgs {
   const int32_t *qidx;  // [N] stage index of body p (mixed); NULL: p
   unsigned *flags;
   int32_t N;
+  int32_t p_begin, p_end;  // the bodies this launch completes: [p_begin, p_end) (all: 0, N)
   int32_t mode;
   int32_t release_early;  // 1: the next force grid may launch at once (it fits one CTA per SM)
   double dt, half_dt, half_dt2;
@@ -156,8 +158,14 @@ struct ReduceArgs {
 cudaError_t launch_prep(int precision, const PrepArgs &a, cudaStream_t s);
 // Mixed stages: fill n_pairs pair blocks with inert padding sources.
 cudaError_t launch_pad_fill(void *stage, int64_t n_pairs, cudaStream_t s);
+// FP64 stages: fill n entries with inert padding sources.
+cudaError_t launch_pad_fill_fp64(void *stage, int64_t n, cudaStream_t s);
 cudaError_t launch_force(int precision, int threads, int ipt, int grid, size_t smem, const ForceArgs &a,
                          cudaStream_t s, bool chained);
+// Mixed stages: the widened box of every group of kBoxPairs stage pairs
+// (boxes[2 g], boxes[2 g + 1]: low and high corner), read by the next force
+// launch.  `chained`: programmatic stream serialization, as the force launch.
+cudaError_t launch_boxes(const void *stage, int64_t n_pairs, float4 *boxes, cudaStream_t s, bool chained);
 cudaError_t launch_verlet(int precision, const VerletArgs &a, cudaStream_t s, bool chained);
 
 // Classical RK4 on y = (r, v), y' = (v, A(r)) (kernels_misc.cu).  rk_stage

@@ -155,6 +155,8 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   va.nsl = nsl;
   va.flags = flags;
   va.N = N;
+  va.p_begin = 0;
+  va.p_end = N;
   va.mode = nb::kModeForce;
   if (nb::launch_verlet(0, va, st, false) != cudaSuccess) return fail(NBODY_ECUDA, "sum launch failed");
 

@@ -29,6 +29,22 @@
 // .f32x2), halving the issued FP32 instructions.  Systems are padded to an
 // even length with inert sources (far away, massless: their term is 0).
 //
+// Mixed path, far source groups: the stage of each system is in a spatial
+// (Morton) order fixed by the host, and a warp's targets are consecutive
+// stage entries, so they sit close together.  The stage is cut into groups
+// of kBoxPairs pairs (64 sources); before each force launch box_kernel
+// computes each group's bounding box of the hi parts, widened on every side
+// by kFarKappa times the largest lo part of the group (as a vector), and
+// every warp keeps the same box for its targets.  Where the two widened boxes are
+// disjoint along some axis, every pair between them is at least kFarKappa
+// (lo_j + lo_p) apart, and the difference of the hi parts alone,
+// d' = hi_j - hi_p, moves the term mu_j d / |d|^3 by at most
+// 2 |lo_j - lo_p| / |d| <= kFarEps relative (the derivative of d / |d|^3 has
+// norm 2 / |d|^3): such a group takes the hi-only path, 12 FP32 lane
+// operations per interaction instead of 18.  A target's own source is never
+// in a far group (its box contains the target), so that path needs no self
+// test.
+//
 // Launch chaining: griddepcontrol.wait before the first read of data the
 // previous kernels wrote (staged sources), then griddepcontrol.
 // launch_dependents, so the Verlet kernel's launch overlaps our work; it
@@ -98,6 +114,26 @@ __device__ __forceinline__ void interact_pair(const ulonglong2 &v0, const ulongl
   az = fma2(f, dz, az);
 }
 
+// The far-group form of interact_pair: d = hi_j - hi_p only (the lo parts
+// are dropped; the caller has checked that this moves each term by at most
+// kFarEps relative), no self test.  v0 = (xh, yh), v1 = (zh, mu).
+__device__ __forceinline__ void interact_pair_hi(const ulonglong2 &v0, const ulonglong2 &v1, f2 nxh, f2 nyh, f2 nzh,
+                                                 f2 &ax, f2 &ay, f2 &az) {
+  const f2 dx = add2(v0.x, nxh);
+  const f2 dy = add2(v0.y, nyh);
+  const f2 dz = add2(v1.x, nzh);
+  f2 r2 = mul2(dx, dx);
+  r2 = fma2(dy, dy, r2);
+  r2 = fma2(dz, dz, r2);
+  float ra, rb;
+  upk(r2, ra, rb);
+  const f2 q = pk(rsqrt_approx(ra), rsqrt_approx(rb));
+  const f2 f = mul2(mul2(v1.y, q), mul2(q, q));
+  ax = fma2(f, dx, ax);
+  ay = fma2(f, dy, ay);
+  az = fma2(f, dz, az);
+}
+
 // Register budget: the mixed kernel wants many warps per SM (64 registers
 // at 1024 threads per SM for IPT 1, 85 for IPT 2 at 768, up to 255 for
 // IPT 4 at 256); the FP64 kernel
@@ -113,8 +149,11 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ int s_flag;  // bit 0: abort (a wait ran out)
+  // Mixed: the widened box of each warp's targets (low corner, high corner).
+  __shared__ __align__(16) float4 s_wbox[PREC == 1 ? 2 * (THREADS / 32) : 1];
 
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int tj = a.tj;  // sources per stage; both layouts take 32 bytes per source
   auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * tj * 32; };
 
@@ -159,16 +198,20 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     }
 
     // ---- targets into registers ---------------------------------------
+    // Target k of this thread: stage entry tq (the block's entries are
+    // consecutive), body pidx (the same index, or perm[tq] in a spatially
+    // ordered stage).
     int pidx[IPT], tq[IPT];
     bool valid[IPT];
     bool any_valid = false;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-      const int p = bk.i0 + tid + k * THREADS;
-      valid[k] = p < bk.i1;
+      const int r = tid + k * THREADS, cnt_b = bk.i1 - bk.i0;
+      valid[k] = r < cnt_b;
       any_valid |= valid[k];
-      pidx[k] = valid[k] ? p : bk.i1 - 1;  // duplicate a real target, result discarded
-      tq[k] = bk.q0 + (pidx[k] - bk.i0);
+      const int rr = valid[k] ? r : cnt_b - 1;  // duplicate a real target, result discarded
+      tq[k] = bk.q0 + rr;
+      pidx[k] = a.perm ? a.perm[tq[k]] : bk.i0 + rr;
     }
     const bool warp_busy = __any_sync(0xffffffffu, any_valid);  // warp-uniform
     // FP64 path: (acc, cmp) is a hi/lo pair fed once per tile with the tile's
@@ -201,6 +244,21 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         nyl[k] = pk(-e[kYl], -e[kYl]);
         nzl[k] = pk(-e[kZl], -e[kZl]);
       }
+    }
+    if constexpr (PREC == 1) {  // the widened box of this warp's targets
+      float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, lo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const float *e = static_cast<const float *>(a.cur) + pair_off(tq[k]);
+        const float h[3] = {e[kXh], e[kYh], e[kZh]}, l[3] = {e[kXl], e[kYl], e[kZl]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          mn[c] = fminf(mn[c], h[c]);
+          mx[c] = fmaxf(mx[c], h[c]);
+          lo[c] = fmaxf(lo[c], fabsf(l[c]));
+        }
+      }
+      warp_box(mn[0], mn[1], mn[2], mx[0], mx[1], mx[2], lo[0], lo[1], lo[2], &s_wbox[2 * warp]);
     }
     // Mixed path: the source pairs that may hold one of this warp's own
     // targets (for each k, the warp's 32 consecutive targets span <= 17
@@ -258,67 +316,10 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         }
       } else if (warp_busy) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(stage_ptr(s));  // 4 per pair block
-        const int npairs = cnt >> 1;
-        for (int g0 = 0; g0 < npairs; g0 += kFoldPairs) {
-          const int lim = min(kFoldPairs, npairs - g0);
-          const int P0 = (jt0 >> 1) + g0;  // stage pair index of the group's first pair
-          bool need_mask = false;
+        const int Pt = jt0 >> 1, Pe = (jt0 + cnt) >> 1;  // the tile's stage pairs [Pt, Pe)
+        auto fold = [&]() {  // the packed sub-sums into the float pairs
 #pragma unroll
-          for (int k = 0; k < IPT; ++k) need_mask |= mlo[k] < P0 + lim && mhi[k] >= P0;
-          // Pairs [b0, b1) of the group: unmasked, or with the self test.
-          // Both visit the pairs in ascending order and give the same terms
-          // for non-self pairs, so the split does not change the sum.
-          auto unmasked = [&](int b0, int b1) {
-            // (IPT 1 is capped at 64 registers: unrolling this rarer path
-            // would spill.)
-#pragma unroll(IPT == 1 ? 1 : 4)
-            for (int b = b0; b < b1; ++b) {
-              const ulonglong2 *pb = src + 4 * (g0 + b);
-              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
-#pragma unroll
-              for (int k = 0; k < IPT; ++k)
-                interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
-                                     pax[k], pay[k], paz[k]);
-            }
-          };
-          auto masked = [&](int b0, int b1) {
-            for (int b = b0; b < b1; ++b) {
-              const ulonglong2 *pb = src + 4 * (g0 + b);
-              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
-              const int P = P0 + b;
-#pragma unroll
-              for (int k = 0; k < IPT; ++k)
-                interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], 2 * P == tq[k],
-                                    2 * P + 1 == tq[k], pax[k], pay[k], paz[k]);
-            }
-          };
-          if (!need_mask && lim == kFoldPairs) {
-#pragma unroll 4
-            for (int b = 0; b < kFoldPairs; ++b) {
-              const ulonglong2 *pb = src + 4 * (g0 + b);
-              const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
-#pragma unroll
-              for (int k = 0; k < IPT; ++k)
-                interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
-                                     pax[k], pay[k], paz[k]);
-            }
-          } else {
-            // Only the pairs that may hold one of this warp's own targets
-            // (per k an ascending, warp-uniform range) take the self test.
-            int cur = 0;
-#pragma unroll
-            for (int k = 0; k < IPT; ++k) {
-              const int r0 = max(mlo[k] - P0, cur), r1 = min(mhi[k] - P0 + 1, lim);
-              if (r0 < r1) {
-                unmasked(cur, r0);
-                masked(r0, r1);
-                cur = r1;
-              }
-            }
-            unmasked(cur, lim);
-          }
-#pragma unroll
-          for (int k = 0; k < IPT; ++k) {  // fold the packed sub-sums into the float pairs
+          for (int k = 0; k < IPT; ++k) {
             float e, o;
             upk(pax[k], e, o);
             two_sum_acc(shx[k], slx[k], e + o);
@@ -328,7 +329,97 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
             two_sum_acc(shz[k], slz[k], e + o);
             pax[k] = pay[k] = paz[k] = 0ull;
           }
+        };
+        // Pairs [b0, b1) (stage pair indices): unmasked, with the self test,
+        // or hi-only (far groups).  All visit the pairs in ascending order.
+        auto unmasked = [&](int b0, int b1) {
+          // (IPT 1 is capped at 64 registers: unrolling this rarer path
+          // would spill.)
+#pragma unroll(IPT == 1 ? 1 : 4)
+          for (int b = b0; b < b1; ++b) {
+            const ulonglong2 *pb = src + 4 * (b - Pt);
+            const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k)
+              interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
+                                   pax[k], pay[k], paz[k]);
+          }
+        };
+        auto masked = [&](int b0, int b1) {
+          for (int b = b0; b < b1; ++b) {
+            const ulonglong2 *pb = src + 4 * (b - Pt);
+            const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k)
+              interact_pair<true>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], 2 * b == tq[k],
+                                  2 * b + 1 == tq[k], pax[k], pay[k], paz[k]);
+          }
+        };
+        int since_fold = 0;  // pairs in the packed sub-sums
+        // The tile in box groups (stage pairs [32 g, 32 g + 32), cut at the
+        // tile's ends): far groups take the hi-only path.
+        for (int P = Pt; P < Pe;) {
+          const int g = P / kBoxPairs;
+          const int P1 = min((g + 1) * kBoxPairs, Pe);
+          const float4 glo = a.boxes[2 * g], ghi = a.boxes[2 * g + 1];
+          const float4 wlo = s_wbox[2 * warp], whi = s_wbox[2 * warp + 1];
+          const bool far = glo.x > whi.x || glo.y > whi.y || glo.z > whi.z || wlo.x > ghi.x || wlo.y > ghi.y ||
+                           wlo.z > ghi.z;
+          if (far) {
+            if (P1 - P == kBoxPairs) {
+#pragma unroll 4
+              for (int b = P; b < P + kBoxPairs; ++b) {
+                const ulonglong2 *pb = src + 4 * (b - Pt);
+                const ulonglong2 v0 = pb[0], v1 = pb[1];
+#pragma unroll
+                for (int k = 0; k < IPT; ++k) interact_pair_hi(v0, v1, nxh[k], nyh[k], nzh[k], pax[k], pay[k], paz[k]);
+              }
+            } else {
+              for (int b = P; b < P1; ++b) {
+                const ulonglong2 *pb = src + 4 * (b - Pt);
+                const ulonglong2 v0 = pb[0], v1 = pb[1];
+#pragma unroll
+                for (int k = 0; k < IPT; ++k) interact_pair_hi(v0, v1, nxh[k], nyh[k], nzh[k], pax[k], pay[k], paz[k]);
+              }
+            }
+          } else {
+            bool need_mask = false;
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) need_mask |= mlo[k] < P1 && mhi[k] >= P;
+            if (!need_mask && P1 - P == kBoxPairs) {
+#pragma unroll 4
+              for (int b = P; b < P + kBoxPairs; ++b) {
+                const ulonglong2 *pb = src + 4 * (b - Pt);
+                const ulonglong2 v0 = pb[0], v1 = pb[1], v2 = pb[2], v3 = pb[3];
+#pragma unroll
+                for (int k = 0; k < IPT; ++k)
+                  interact_pair<false>(v0, v1, v2, v3, nxh[k], nyh[k], nzh[k], nxl[k], nyl[k], nzl[k], false, false,
+                                       pax[k], pay[k], paz[k]);
+              }
+            } else {
+              // Only the pairs that may hold one of this warp's own targets
+              // (per k an ascending, warp-uniform range) take the self test.
+              int cur = P;
+#pragma unroll
+              for (int k = 0; k < IPT; ++k) {
+                const int r0 = max(mlo[k], cur), r1 = min(mhi[k] + 1, P1);
+                if (r0 < r1) {
+                  unmasked(cur, r0);
+                  masked(r0, r1);
+                  cur = r1;
+                }
+              }
+              unmasked(cur, P1);
+            }
+          }
+          since_fold += P1 - P;
+          if (since_fold >= kFoldPairs) {
+            fold();
+            since_fold = 0;
+          }
+          P = P1;
         }
+        fold();
       }
 
       __syncthreads();  // every thread is done with stage s

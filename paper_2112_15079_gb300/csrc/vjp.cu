@@ -121,10 +121,11 @@ __global__ void __launch_bounds__(THREADS) vjp_kernel(const VjpArgs a) {
     const Seg sg = a.segs[si];
     const Blk bk = a.blks[sg.blk];
     const int q_end = bk.q0 + (bk.i1 - bk.i0);
-    const int p = bk.i0 + tid;
-    const bool valid = p < bk.i1;
-    const int pi = valid ? p : bk.i1 - 1;
-    const int tq = bk.q0 + (pi - bk.i0);
+    // target: stage entry tq (consecutive within the block), body p (the
+    // same index, or perm[tq] in a spatially ordered stage)
+    const bool valid = tid < bk.i1 - bk.i0;
+    const int tq = bk.q0 + (valid ? tid : bk.i1 - bk.i0 - 1);
+    const int p = a.perm ? a.perm[tq] : bk.i0 + (tq - bk.q0);
     // Mixed path: the stage pairs that may hold one of this warp's targets.
     const int mlo = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(tq))) >> 1;
     const int mhi = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(tq))) >> 1;

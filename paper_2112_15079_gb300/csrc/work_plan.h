@@ -48,12 +48,18 @@ struct WorkPlan {
   int64_t n_dyn = 0;             // dynamic chunks
 };
 
-// offsets: [n_sys + 1] body offsets of the systems; soff: [n_sys + 1] their
-// stage offsets (the mixed stage pads every system to an even length).
-// slots: SMs x resident CTAs per SM the launch may use.  Returns an empty
-// string on success, else the reason the plan cannot be made.
+// offsets: [n_sys + 1] body offsets of the systems' targets; soff: [n_sys + 1]
+// their stage offsets (the mixed stage pads every system to an even length).
+// By default each system's sources are its targets' stage entries; with
+// src_begin / src_count ([n_sys] each) system s takes the src_count[s]
+// stage entries from src_begin[s] instead (a row shard: a block of targets
+// against every source of the system).  slots: SMs x resident CTAs per SM
+// the launch may use.  Returns an empty string on success, else the reason
+// the plan cannot be made.
 inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vector<int64_t> &soff, bool mixed,
-                             int threads, int ipt, int jsplit, int64_t slots, WorkPlan &out) {
+                             int threads, int ipt, int jsplit, int64_t slots, WorkPlan &out,
+                             const std::vector<int64_t> *src_begin = nullptr,
+                             const std::vector<int64_t> *src_count = nullptr) {
   out = WorkPlan{};
   const int64_t n_sys = static_cast<int64_t>(offsets.size()) - 1;
   const int64_t B = static_cast<int64_t>(threads) * ipt;
@@ -63,7 +69,9 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
   int64_t W = 0;
   for (int64_t s = 0; s < n_sys; ++s) {
     const int64_t b = offsets[s], e = offsets[s + 1], ns = e - b;
-    const int64_t len = (ns + unit - 1) / unit;  // units of this system's (padded) source range
+    const int64_t sb = src_begin ? (*src_begin)[s] : soff[s];  // first source (stage entry)
+    const int64_t sn = src_count ? (*src_count)[s] : ns;       // sources
+    const int64_t len = (sn + unit - 1) / unit;  // units of this system's (padded) source range
     const int64_t nb_s = (ns + B - 1) / B;
     for (int64_t k = 0; k < nb_s; ++k) {
       const int64_t i0 = b + ns * k / nb_s, i1 = b + ns * (k + 1) / nb_s;
@@ -76,7 +84,7 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
       // warps with at least one target: thread t holds targets t + k*threads
       const int64_t busy = std::min<int64_t>(threads, i1 - i0);
       const int64_t w = (busy + 31) / 32;
-      bj0.push_back(soff[s]);
+      bj0.push_back(sb);
       bunits.push_back(len);
       bw.push_back(w);
       bstart.push_back(W);

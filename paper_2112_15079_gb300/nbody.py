@@ -35,7 +35,8 @@ INTEGRATORS = {"verlet": NBODY_VERLET, "rk4": NBODY_RK4, "leapfrog": NBODY_LEAPF
 
 class nbody_opts(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("integrator", ctypes.c_int32)]
+                ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("integrator", ctypes.c_int32),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class nbody_tiles(ctypes.Structure):
@@ -54,6 +55,7 @@ _SIGS = {
     "nbody_step": (_S, [_P, ctypes.c_int64]),
     "nbody_accel": (_S, [_P, _P, _P, _P]),
     "nbody_reset": (_S, [_P]),
+    "nbody_reorder": (_S, [_P]),
     "nbody_energy": (_S, [_P, ctypes.POINTER(ctypes.c_double)]),
     "nbody_grad": (_S, [_P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "nbody_sync": (_S, [_P]),
@@ -65,6 +67,9 @@ _SIGS = {
     "nbody_last_error": (ctypes.c_char_p, [_P]),
     "nbody_peaks": (_S, [ctypes.POINTER(ctypes.c_double)]),
     "nbody_accel_static": (_S, [ctypes.c_int64, ctypes.c_double] + [_P] * 8),
+    "nbody_shard": (_S, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "nbody_shard_step": (_S, [_P]),
+    "nbody_shard_buffer": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -127,7 +132,7 @@ class NBody:
 
     def __init__(self, r, v, m, offsets=None, *, G: float, dt: float, precision: str = "fp64",
                  ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None,
-                 integrator: str = "verlet"):
+                 integrator: str = "verlet", tune_cache: str | None = None):
         torch = _torch()
         device = torch.device(device if device is not None else "cuda")
         self.device = device
@@ -147,7 +152,8 @@ class NBody:
         self._stream = stream if stream is not None else torch.cuda.current_stream(device)
         opts = nbody_opts(G=self.G, dt=self.dt, precision=PRECISIONS[precision], ckpt_every=int(ckpt_every),
                           flags=(0 if graphs else NBODY_FLAG_NO_GRAPH) | (0 if small else NBODY_FLAG_NO_SMALL),
-                          integrator=INTEGRATORS[integrator])
+                          integrator=INTEGRATORS[integrator],
+                          tune_cache=None if tune_cache is None else os.fsencode(tune_cache))
         self._ctx = _P()
         s = self.state
         ptrs = [s[k].data_ptr() for k in range(6)] + [self.m.data_ptr()]
@@ -176,6 +182,11 @@ class NBody:
 
     def reset(self) -> None:
         check(nbody_reset(self._ctx), self._ctx)
+
+    def reorder(self) -> None:
+        """Mixed precision: re-sort the sources spatially at the current
+        positions (a performance hint for long runs; no-op in FP64)."""
+        check(nbody_reorder(self._ctx), self._ctx)
 
     def energy(self) -> np.ndarray:
         out = (ctypes.c_double * self.n_systems)()

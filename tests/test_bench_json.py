@@ -40,3 +40,14 @@ def test_traffic_figures_match_the_force_kernel_sources():
     assert (h, "mixed") in bench.NCU_TRAFFIC and (h, "fp64") in bench.NCU_TRAFFIC, (
         "the force kernel sources changed since the DRAM counters were taken: re-take them with ncu "
         "and update NCU_TRAFFIC")
+
+
+def test_roofline_against_measured_peaks():
+    n = 10425
+    r = {"force_tflops": 0.7, "achieved_tflops": 0.65,
+         "kernel_ms": {"force_ms": 3.1, "verlet_ms": 0.04, "step_ms": 3.2, "steps": 10}}
+    peaks = {"fp32_tflops": 77.4, "fp64_tflops": 1.05}
+    ro = bench.roofline(r, "fp64", None, peaks)
+    assert ro["peak_measured_tflops"] == 1.05 and ro["frac_of_measured"] == pytest.approx(0.7 / 1.05)
+    assert bench.roofline(r, "mixed", None, peaks)["frac_of_measured"] == pytest.approx(0.7 / 77.4)
+    assert "frac_of_measured" not in bench.roofline(r, "mixed", None)

@@ -806,3 +806,75 @@ def test_nondefault_stream(nb):
         out = b.state.clone()
     st.synchronize()
     assert torch.equal(out, ref.state)
+
+
+def _threshold_system(gap_over_threshold):
+    """Two clusters on the x axis near x = 3 AU (one binade, ulp 2^-22):
+    64 massless targets whose x = hi + 0.45 ulp, and 128 sources of mass
+    1e-3 whose x = hi - 0.45 ulp, at a gap (between the clusters' hi boxes)
+    of `gap_over_threshold` times the far threshold kappa (lo_w + lo_s),
+    kappa = 2 / 1e-6 + 1.  y, z are multiples of 2^-14 (no lo part), so the
+    lo parts the hi-only path drops are aligned with d: the worst case of
+    its bound, an error of about 2 |lo_j - lo_p| / |d| = 1e-6 at the
+    threshold.  Returns (system, indices of the targets, threshold)."""
+    ulp = 2.0 ** -22
+    lo = 0.45 * ulp
+    kappa = 2.0 / 1e-6 + 1.0
+    thr = kappa * (2 * lo)
+    grid = 2.0 ** -14 * np.arange(16)
+    yz = np.array([(a, b) for a in grid for b in grid])
+    x0 = np.float32(3.0)
+    xw = np.full(64, np.float64(x0)) + lo
+    gap = gap_over_threshold * thr
+    xs_hi = np.float64(np.float32(x0 + gap))
+    xs = np.full(128, xs_hi) - lo
+    r = np.zeros((3, 192))
+    r[0, :64], r[1, :64], r[2, :64] = xw, yz[:64, 0], yz[:64, 1]
+    r[0, 64:], r[1, 64:], r[2, 64:] = xs, yz[:128, 0], yz[:128, 1] + 2.0 ** -6
+    m = np.concatenate([np.zeros(64), np.full(128, 1e-3)])
+    return inputs.System(r=r, v=np.zeros_like(r), m=m), np.arange(64), thr
+
+
+@pytest.mark.parametrize("ratio", [0.8, 1.25, 3.0])
+def test_mixed_far_threshold_adversarial(nb, ratio):
+    """Targets and sources placed just inside (0.8) and just outside (1.25,
+    3) the distance beyond which the mixed kernel drops the lo parts, with
+    the dropped parts aligned with d (worst case).  Inside: the hi/lo path,
+    FP32-level error (<= 3e-7).  Outside: the hi-only path, whose error
+    bound is 1e-6 at the threshold and falls as 1 / distance; the measured
+    error must stay within that bound plus the FP32-level error, and (so the
+    case really exercises the far path) exceed the FP32 level just outside.
+    A threshold set too small would put pairs closer than it on the hi-only
+    path with errors above the bound."""
+    s, idx, thr = _threshold_system(ratio)
+    b = nb.NBody(s.r, s.v, s.m, G=1.0, dt=0.1, precision="mixed")
+    a = b.accel().cpu().numpy()[:, idx]
+    ref = oracle.accel(1.0, s.r, s.m)[:, idx]
+    err = np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    if ratio < 1.0:
+        assert err.max() <= 3e-7, err.max()
+    else:
+        assert err.max() <= 1e-6 / ratio + 3e-7, (ratio, err.max())
+        if ratio < 2.0:
+            assert err.max() > 4e-7, (ratio, err.max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reorder_keeps_parity(nb, precision):
+    """nbody_reorder between steps (a new spatial order of the sources in
+    the mixed path, a no-op in FP64) leaves the trajectory on the oracle's."""
+    s = inputs.solar_system(2131, seed=81, n_moons=0)
+    b = _make(nb, s, precision)
+    b.step(30)
+    b.reorder()
+    b.step(30)
+    r_ref, v_ref, _ = oracle.verlet(s.G, s.dt, 60, s.r, s.v, s.m, openmp=True)
+    tol = 1e-12 if precision == "fp64" else 1e-7
+    assert np.abs(b.r.cpu().numpy() - r_ref).max() <= tol * np.abs(r_ref).max()
+    a = b.accel().cpu().numpy()
+    r = b.r.cpu().numpy()
+    _check_accel(precision, a, oracle.accel(s.G, r, s.m, openmp=True), oracle.term_norm(s.G, r, s.m, openmp=True))
+    if precision == "fp64":  # no-op: bitwise the same as without
+        c = _make(nb, s, precision)
+        c.step(60)
+        assert np.array_equal(c.state.cpu().numpy(), b.state.cpu().numpy())
