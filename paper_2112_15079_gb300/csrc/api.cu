@@ -218,21 +218,28 @@ nb::TuneKey tune_key(const nbody_ctx *c) {
 nbody_tiles default_tiles(const nbody_ctx *c) {
   // The autotuner's picks on GB300: FP64 is bound by the FP64 pipe (~90% busy)
   // with three 128-thread CTAs per SM at every size; the mixed path takes two
-  // 512-thread CTAs per SM with one target per thread up to ~16k bodies (short
-  // shares, more warps) and one 1024-thread CTA per SM from 64k bodies on.
+  // 512-thread CTAs per SM with one target per thread up to ~32k bodies (short
+  // shares, more warps), and beyond one 512-thread CTA per SM with two
+  // targets per thread and 8 dynamic chunks per CTA: far and near source
+  // groups cost 12 and 18 lane operations per interaction, so static shares
+  // of equal length finish at different times (65,536 bodies: 1.86 ms against
+  // 1.98 ms with one target per thread and static shares only).
   nbody_tiles t{};
   t.jsplit = 0;  // static shares only (dynamic chunks add partial rows)
   t.tj = 1024;
-  t.ipt = 2;
   if (c->o.precision == NBODY_FP64) {
     t.threads = 128;
     t.ipt = 1;
     t.ctas_per_sm = 3;
-  } else {
+  } else if (c->N <= 32768) {
+    t.threads = 512;
     t.ipt = 1;
-    const bool small = c->N <= 32768;
-    t.threads = small ? 512 : 1024;
-    t.ctas_per_sm = small ? 2 : 1;
+    t.ctas_per_sm = 2;
+  } else {
+    t.threads = 512;
+    t.ipt = 2;
+    t.ctas_per_sm = 1;
+    t.jsplit = 8;
   }
   return t;
 }
@@ -1126,7 +1133,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
     for (int ip : {1, 2, 4})
       for (int tj : {128, 256, 512, 1024, 2048})
         for (int cps : {1, 2, 3, 4})
-          for (int js : {0, 1, 2, 4}) {
+          for (int js : {0, 1, 2, 4, 8, 16}) {
           if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
           // FP64 is bound by the FP64 pipe: only the barrier spacing (tj) and the warp count matter
           if (!mixed && tj < 512) continue;

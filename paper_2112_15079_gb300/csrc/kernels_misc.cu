@@ -48,8 +48,9 @@ bool force_config_supported(int precision, int threads, int ipt) {
 }
 
 size_t force_smem_bytes(int precision, int tj) {
-  (void)precision;  // both layouts take 32 bytes per staged source
-  return static_cast<size_t>(kStages) * tj * 32;
+  // 32 bytes per staged source in both layouts; the mixed stage also holds
+  // the boxes of the source groups its tile touches
+  return static_cast<size_t>(kStages) * (static_cast<size_t>(tj) * 32 + (precision == 1 ? (tj / 64 + 2) * 32 : 0));
 }
 
 // ---------------------------------------------------------------------------

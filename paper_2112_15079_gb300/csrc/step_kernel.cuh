@@ -149,13 +149,24 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ int s_flag;  // bit 0: abort (a wait ran out)
-  // Mixed: the widened box of each warp's targets (low corner, high corner).
+  // Mixed: the widened box of each warp's targets (low corner, high corner);
+  // per target, its negated lo parts (read by the near path only) and its
+  // running sums as float pairs (touched once per kFoldPairs pairs) -- kept
+  // in shared memory so the source loop has the registers for more pairs in
+  // flight.  Index [field][k * THREADS + tid].
   __shared__ __align__(16) float4 s_wbox[PREC == 1 ? 2 * (THREADS / 32) : 1];
+  constexpr int kT = PREC == 1 ? THREADS * IPT : 1;
+  __shared__ float s_tlo[3][kT];
+  __shared__ float s_sum[6][kT];  // x hi, x lo, y hi, y lo, z hi, z lo
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int tj = a.tj;  // sources per stage; both layouts take 32 bytes per source
-  auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * tj * 32; };
+  // Stage s: tj sources (32 bytes each), then (mixed) the boxes of the
+  // source groups the tile touches (at most tj / 64 + 2 groups, 32 bytes each).
+  const size_t stage_bytes = static_cast<size_t>(tj) * 32 + (PREC == 1 ? (tj / 64 + 2) * 32 : 0);
+  auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * stage_bytes; };
+  auto box_ptr = [&](int s) { return reinterpret_cast<const float4 *>(stage_ptr(s) + static_cast<size_t>(tj) * 32); };
 
   __shared__ int s_piece;
   if (tid == 0) {
@@ -188,10 +199,16 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     auto issue = [&](int t) {  // tid 0 only
       const int s = t % kStages;
       const int j = sg.s0 + t * tj;
-      const uint32_t bytes = static_cast<uint32_t>(min(tj, sg.s1 - j)) * 32u;
-      mbar_arrive_expect_tx(&bar[s], bytes);
+      const int n = min(tj, sg.s1 - j);
+      const uint32_t bytes = static_cast<uint32_t>(n) * 32u;
+      // mixed: the boxes of groups (j / 2) / 32 .. ((j + n) / 2 - 1) / 32, 32 bytes each
+      const int g0 = (j >> 1) / kBoxPairs, g1 = (((j + n) >> 1) - 1) / kBoxPairs;
+      const uint32_t bbytes = PREC == 1 ? static_cast<uint32_t>(g1 - g0 + 1) * 32u : 0u;
+      mbar_arrive_expect_tx(&bar[s], bytes + bbytes);
       bulk_g2s(stage_ptr(s), static_cast<const unsigned char *>(a.cur) + static_cast<size_t>(j) * 32, bytes,
                &bar[s]);
+      if (PREC == 1)
+        bulk_g2s(stage_ptr(s) + static_cast<size_t>(tj) * 32, a.boxes + 2 * static_cast<size_t>(g0), bbytes, &bar[s]);
     };
     if (tid == 0) {
       for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
@@ -223,12 +240,10 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     // kFoldPairs source pairs at a time through TwoSum, so the source loop
     // issues no FP64 instruction (GB300 runs FP64 and f32<->f64 conversions
     // at 1/64 of the FP32 rate).
-    f2 nxh[IPT], nyh[IPT], nzh[IPT], nxl[IPT], nyl[IPT], nzl[IPT], pax[IPT], pay[IPT], paz[IPT];
-    float shx[IPT], shy[IPT], shz[IPT], slx[IPT], sly[IPT], slz[IPT];
+    f2 nxh[IPT], nyh[IPT], nzh[IPT], pax[IPT], pay[IPT], paz[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       accx[k] = accy[k] = accz[k] = cmpx[k] = cmpy[k] = cmpz[k] = 0.0;
-      shx[k] = shy[k] = shz[k] = slx[k] = sly[k] = slz[k] = 0.f;
       pax[k] = pay[k] = paz[k] = 0ull;
       if (PREC == 0) {
         const double4_32a r = static_cast<const double4_32a *>(a.cur)[tq[k]];
@@ -240,9 +255,12 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         nxh[k] = pk(-e[kXh], -e[kXh]);
         nyh[k] = pk(-e[kYh], -e[kYh]);
         nzh[k] = pk(-e[kZh], -e[kZh]);
-        nxl[k] = pk(-e[kXl], -e[kXl]);
-        nyl[k] = pk(-e[kYl], -e[kYl]);
-        nzl[k] = pk(-e[kZl], -e[kZl]);
+        const int i = k * THREADS + tid;
+        s_tlo[0][i] = -e[kXl];
+        s_tlo[1][i] = -e[kYl];
+        s_tlo[2][i] = -e[kZl];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) s_sum[f][i] = 0.f;
       }
     }
     if constexpr (PREC == 1) {  // the widened box of this warp's targets
@@ -316,18 +334,34 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         }
       } else if (warp_busy) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(stage_ptr(s));  // 4 per pair block
+        const float4 *gbox = box_ptr(s);  // the boxes of groups Pt / kBoxPairs ..
         const int Pt = jt0 >> 1, Pe = (jt0 + cnt) >> 1;  // the tile's stage pairs [Pt, Pe)
+        const int gt = Pt / kBoxPairs;
         auto fold = [&]() {  // the packed sub-sums into the float pairs
 #pragma unroll
           for (int k = 0; k < IPT; ++k) {
-            float e, o;
-            upk(pax[k], e, o);
-            two_sum_acc(shx[k], slx[k], e + o);
-            upk(pay[k], e, o);
-            two_sum_acc(shy[k], sly[k], e + o);
-            upk(paz[k], e, o);
-            two_sum_acc(shz[k], slz[k], e + o);
+            const int i = k * THREADS + tid;
+            const f2 p3[3] = {pax[k], pay[k], paz[k]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float e, o, h = s_sum[2 * c][i], l = s_sum[2 * c + 1][i];
+              upk(p3[c], e, o);
+              two_sum_acc(h, l, e + o);
+              s_sum[2 * c][i] = h;
+              s_sum[2 * c + 1][i] = l;
+            }
             pax[k] = pay[k] = paz[k] = 0ull;
+          }
+        };
+        // Near groups read the targets' lo parts from shared memory.
+        f2 nxl[IPT], nyl[IPT], nzl[IPT];
+        auto load_lo = [&]() {
+#pragma unroll
+          for (int k = 0; k < IPT; ++k) {
+            const int i = k * THREADS + tid;
+            nxl[k] = pk(s_tlo[0][i], s_tlo[0][i]);
+            nyl[k] = pk(s_tlo[1][i], s_tlo[1][i]);
+            nzl[k] = pk(s_tlo[2][i], s_tlo[2][i]);
           }
         };
         // Pairs [b0, b1) (stage pair indices): unmasked, with the self test,
@@ -361,7 +395,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         for (int P = Pt; P < Pe;) {
           const int g = P / kBoxPairs;
           const int P1 = min((g + 1) * kBoxPairs, Pe);
-          const float4 glo = a.boxes[2 * g], ghi = a.boxes[2 * g + 1];
+          const float4 glo = gbox[2 * (g - gt)], ghi = gbox[2 * (g - gt) + 1];
           const float4 wlo = s_wbox[2 * warp], whi = s_wbox[2 * warp + 1];
           const bool far = glo.x > whi.x || glo.y > whi.y || glo.z > whi.z || wlo.x > ghi.x || wlo.y > ghi.y ||
                            wlo.z > ghi.z;
@@ -383,6 +417,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
               }
             }
           } else {
+            load_lo();
             bool need_mask = false;
 #pragma unroll
             for (int k = 0; k < IPT; ++k) need_mask |= mlo[k] < P1 && mhi[k] >= P;
@@ -456,9 +491,10 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         prow[2 * N + pidx[k]] = accz[k] + cmpz[k];
       } else {
         float2 *frow = reinterpret_cast<float2 *>(prow);
-        frow[pidx[k]] = make_float2(shx[k], slx[k]);
-        frow[N + pidx[k]] = make_float2(shy[k], sly[k]);
-        frow[2 * N + pidx[k]] = make_float2(shz[k], slz[k]);
+        const int i = k * THREADS + tid;
+        frow[pidx[k]] = make_float2(s_sum[0][i], s_sum[1][i]);
+        frow[N + pidx[k]] = make_float2(s_sum[2][i], s_sum[3][i]);
+        frow[2 * N + pidx[k]] = make_float2(s_sum[4][i], s_sum[5][i]);
       }
     }
   }
