@@ -69,6 +69,13 @@ namespace nb {
 void set_last_error(const char *msg) { g_init_error = msg; }
 }  // namespace nb
 
+// A widened box (the force kernel's far test widens the hi-part box by
+// kFarKappa times the largest lo part); empty: no real body inside.
+struct PlanBox {
+  float lo[3], hi[3];
+  bool empty;
+};
+
 struct nbody_ctx {
   int dev = 0, nsm = 0;
   int64_t n_sys = 0;
@@ -97,6 +104,11 @@ struct nbody_ctx {
   int32_t *perm = nullptr;           // [n_stage] body of each stage entry (mixed; padding: any body)
   float4 *boxes = nullptr;           // mixed: [n_stage / 64 rounded up][2] source-group boxes of the next force launch
   std::vector<int32_t> qidx_h;       // host copy of qidx (mixed)
+  // mixed, for planning (see chunk_costs): per stage entry its hi parts and
+  // the magnitudes of its lo parts ([n_stage][6]); per source group of
+  // 2 kBoxPairs entries its widened box
+  std::vector<float> ent;
+  std::vector<PlanBox> gbox;
   // Targets and sources of the force launches: system s's targets are the
   // block positions [tgt_off[s], tgt_off[s+1]) at stage entries from
   // tgt_soff[s]; its sources are the stage entries [src_b[s], src_b[s] +
@@ -276,6 +288,8 @@ nbody_status upload_nsl(nbody_ctx *c, Work &wk) {
   return NBODY_OK;
 }
 
+nb::ChunkCost chunk_costs(const nbody_ctx *c, const nbody_tiles &t);
+
 // Build stream-K work tables (the plan is work_plan.h's) and upload them.
 // row_doubles: 8-byte words per body and partial row (3 force, 4 VJP).
 nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, int row_doubles) {
@@ -284,9 +298,14 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   const int64_t cps = std::min<int64_t>(t.ctas_per_sm, occ);
   nb::WorkPlan plan;
   const bool own_src = c->src_b.empty();
+  // the mixed force kernel's pairs cost 12 or 18 operations (far or near
+  // groups): its shares are cut by cost
+  const bool by_cost = row_doubles == 3 && !c->gbox.empty();
+  const nb::ChunkCost cost = by_cost ? chunk_costs(c, t) : nb::ChunkCost{};
   const std::string why = nb::plan_work(c->tgt_off, c->tgt_soff, c->o.precision == NBODY_MIXED, t.threads, t.ipt,
                                         t.jsplit, static_cast<int64_t>(c->nsm) * cps, plan,
-                                        own_src ? nullptr : &c->src_b, own_src ? nullptr : &c->src_n);
+                                        own_src ? nullptr : &c->src_b, own_src ? nullptr : &c->src_n,
+                                        by_cost ? &cost : nullptr);
   if (!why.empty()) return fail(c, NBODY_EINVAL, "%s", why.c_str());
   wk.plan_off = c->tgt_off;
   wk.plan_soff = c->tgt_soff;
@@ -549,6 +568,124 @@ uint64_t spread3(uint32_t q) {
   return k;
 }
 
+// Planning data of the mixed stage, from the positions in body order h
+// ([3][N]) and the stage order perm: each entry's hi parts and lo-part
+// magnitudes, and each source group's widened box (as the box kernel makes
+// it: padding entries excluded).
+void plan_boxes(nbody_ctx *c, const std::vector<double> &h, const std::vector<int32_t> &perm) {
+  const size_t N = c->N;
+  const int64_t ns = c->n_stage, GS = 2 * nb::kBoxPairs;
+  c->ent.assign(static_cast<size_t>(6 * ns), 0.f);
+  std::vector<char> real(static_cast<size_t>(ns), 0);
+  for (int64_t q = 0; q < ns; ++q) {
+    const int32_t p = perm[q];
+    real[q] = c->qidx_h[p] == q;
+    for (int k = 0; k < 3; ++k) {
+      const double x = h[k * N + p];
+      const float hi = static_cast<float>(x);
+      c->ent[6 * q + k] = hi;
+      c->ent[6 * q + 3 + k] = std::fabs(static_cast<float>(x - static_cast<double>(hi)));
+    }
+  }
+  c->gbox.assign(static_cast<size_t>((ns + GS - 1) / GS), PlanBox{});
+  for (size_t g = 0; g < c->gbox.size(); ++g) {
+    PlanBox b{{INFINITY, INFINITY, INFINITY}, {-INFINITY, -INFINITY, -INFINITY}, true};
+    float l[3] = {0.f, 0.f, 0.f};
+    for (int64_t q = static_cast<int64_t>(g) * GS; q < std::min(ns, static_cast<int64_t>(g + 1) * GS); ++q) {
+      if (!real[q]) continue;
+      for (int k = 0; k < 3; ++k) {
+        b.lo[k] = std::min(b.lo[k], c->ent[6 * q + k]);
+        b.hi[k] = std::max(b.hi[k], c->ent[6 * q + k]);
+        l[k] = std::max(l[k], c->ent[6 * q + 3 + k]);
+      }
+      b.empty = false;
+    }
+    const float w = nb::kFarKappa * std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    for (int k = 0; k < 3; ++k) {
+      b.lo[k] -= w;
+      b.hi[k] += w;
+    }
+    c->gbox[g] = b;
+  }
+}
+
+// Planning cost of the mixed force launch per target block and chunk of the
+// block's sources.  Each busy warp of the block (lane l of warp w holds the
+// block's entries 32 (ipt w + k) + l, the last entry standing in past the
+// block's end, as in the kernel) gets the widened box of its targets;
+// against a source group whose box is disjoint from it (the kernel's far
+// test) a pair costs 12 FP32 lane operations per target, else 18.  A chunk's
+// weight per unit is that cost summed over the busy warps.  Chunks are one
+// source group (kBoxPairs units) unless that means more than about 2e7 box
+// tests; then several, and one group per chunk is tested.
+nb::ChunkCost chunk_costs(const nbody_ctx *c, const nbody_tiles &t) {
+  const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
+  const std::vector<nb::Blk> blks = nb::make_blocks(c->tgt_off, c->tgt_soff, B);
+  const int64_t n_sys = static_cast<int64_t>(c->tgt_off.size()) - 1;
+  struct Src {
+    int64_t sb, len;
+  };
+  std::vector<Src> src(blks.size());
+  int64_t tests = 0;
+  {
+    size_t k = 0;
+    for (int64_t s = 0; s < n_sys; ++s) {
+      const int64_t e = c->tgt_off[s + 1], ns = e - c->tgt_off[s];
+      const int64_t sb = c->src_b.empty() ? c->tgt_soff[s] : c->src_b[s];
+      const int64_t sn = c->src_n.empty() ? ns : c->src_n[s];
+      for (; k < blks.size() && blks[k].i0 < e; ++k) {
+        src[k] = {sb, (sn + 1) / 2};
+        const int64_t busy = (blks[k].i1 - blks[k].i0 + 32 * t.ipt - 1) / (32 * t.ipt);
+        tests += busy * ((src[k].len + nb::kBoxPairs - 1) / nb::kBoxPairs);
+      }
+    }
+  }
+  nb::ChunkCost cost;
+  const int64_t m = std::max<int64_t>(1, (tests + 19999999) / 20000000);
+  cost.chunk_units = nb::kBoxPairs * m;
+  cost.w.resize(blks.size());
+  std::vector<PlanBox> wb;
+  for (size_t k = 0; k < blks.size(); ++k) {
+    const nb::Blk &bk = blks[k];
+    const int64_t cnt = bk.i1 - bk.i0, nw = (cnt + 32 * t.ipt - 1) / (32 * t.ipt);
+    wb.assign(static_cast<size_t>(nw), PlanBox{});
+    for (int64_t w = 0; w < nw; ++w) {
+      PlanBox b{{INFINITY, INFINITY, INFINITY}, {-INFINITY, -INFINITY, -INFINITY}, false};
+      float l[3] = {0.f, 0.f, 0.f};
+      for (int64_t r = 32 * t.ipt * w; r < 32 * t.ipt * (w + 1); ++r) {
+        const int64_t q = bk.q0 + std::min(r, cnt - 1);
+        for (int d = 0; d < 3; ++d) {
+          b.lo[d] = std::min(b.lo[d], c->ent[6 * q + d]);
+          b.hi[d] = std::max(b.hi[d], c->ent[6 * q + d]);
+          l[d] = std::max(l[d], c->ent[6 * q + 3 + d]);
+        }
+      }
+      const float wd = nb::kFarKappa * std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+      for (int d = 0; d < 3; ++d) {
+        b.lo[d] -= wd;
+        b.hi[d] += wd;
+      }
+      wb[w] = b;
+    }
+    const int64_t len = src[k].len, nch = (len + cost.chunk_units - 1) / cost.chunk_units;
+    std::vector<int64_t> &wk = cost.w[k];
+    wk.assign(static_cast<size_t>(nch), 0);
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      const int64_t u0 = ch * cost.chunk_units, u1 = std::min(len, u0 + cost.chunk_units);
+      const int64_t g = (src[k].sb / 2 + (u0 + u1 - 1) / 2) / nb::kBoxPairs;  // the group at the chunk's middle
+      const PlanBox &gb = c->gbox[std::min<size_t>(static_cast<size_t>(g), c->gbox.size() - 1)];
+      int64_t sum = 0;
+      for (const PlanBox &b : wb) {
+        const bool far = gb.empty || gb.lo[0] > b.hi[0] || gb.lo[1] > b.hi[1] || gb.lo[2] > b.hi[2] ||
+                         b.lo[0] > gb.hi[0] || b.lo[1] > gb.hi[1] || b.lo[2] > gb.hi[2];
+        sum += far ? 12 : 18;
+      }
+      wk[ch] = sum;
+    }
+  }
+  return cost;
+}
+
 // Spatial order of each system's stage (mixed path): the bodies of a system
 // sorted by the Morton code of their position in the system's bounding box
 // (21 bits per axis; ties by body index), so that consecutive stage entries
@@ -614,6 +751,7 @@ nbody_status spatial_order(nbody_ctx *c) {
     }
     for (int64_t slot = rg.q + (e0 - b0); slot < rg.qe; ++slot) perm[slot] = static_cast<int32_t>(std::min<int64_t>(b0, N - 1));
   }
+  plan_boxes(c, h, perm);
   NB_CUDA(c, cudaMemcpyAsync(c->qidx, c->qidx_h.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
   NB_CUDA(c, cudaMemcpyAsync(c->perm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice, c->stream));
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1022,8 +1160,8 @@ nbody_status nbody_reset(nbody_ctx *c) {
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
-  if ((st = spatial_order(c)) != NBODY_OK || (st = upload_nsl(c, c->fw)) != NBODY_OK ||
-      (st = upload_nsl(c, c->adj.vj)) != NBODY_OK)
+  if ((st = spatial_order(c)) != NBODY_OK || (st = upload_nsl(c, c->adj.vj)) != NBODY_OK ||
+      (c->o.precision == NBODY_MIXED && (st = build_items(c, c->tiles)) != NBODY_OK))
     return st;
   return refresh(c);
 }
@@ -1036,7 +1174,8 @@ nbody_status nbody_reorder(nbody_ctx *c) {
   if ((st = begin_work(c)) != NBODY_OK) return st;
   NB_CUDA(c, cudaStreamSynchronize(c->stream));
   if ((st = spatial_order(c)) != NBODY_OK) return st;
-  if ((st = upload_nsl(c, c->fw)) != NBODY_OK) return st;
+  // the order moved bodies between stage entries, and the planning costs changed
+  if (c->o.precision == NBODY_MIXED && (st = build_items(c, c->tiles)) != NBODY_OK) return st;
   if ((st = upload_nsl(c, c->adj.vj)) != NBODY_OK) return st;
   return end_work(c);
 }
@@ -1132,7 +1271,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   for (int th : {64, 128, 256, 384, 512, 768, 1024})
     for (int ip : {1, 2, 4})
       for (int tj : {128, 256, 512, 1024, 2048})
-        for (int cps : {1, 2, 3, 4})
+        for (int cps : {1, 2, 3, 4, 6, 8})
           for (int js : {0, 1, 2, 4, 8, 16}) {
           if (!nb::force_config_supported(c->o.precision, th, ip)) continue;
           // FP64 is bound by the FP64 pipe: only the barrier spacing (tj) and the warp count matter

@@ -56,7 +56,7 @@ size_t force_smem_bytes(int precision, int tj) {
 // ---------------------------------------------------------------------------
 // Widened boxes of the mixed stage's source groups for the next force launch:
 // group g = stage pairs [kBoxPairs g, kBoxPairs (g + 1)), one warp per group,
-// lane l reading pair kBoxPairs g + l.  The box of the hi parts is widened on
+// lane l reading pairs kBoxPairs g + l + 32 i.  The box of the hi parts is widened on
 // every side by kFarKappa times the largest lo part (see step_kernel.cuh).
 // Padding sources (coordinate kPadCoord, mu = 0) stay out of the box; a group
 // of padding only gets an empty box (low corner +inf, high corner -inf),
@@ -70,9 +70,11 @@ __global__ void __launch_bounds__(32 * kBoxWarps) box_kernel(const float4 *stage
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kBoxWarps + threadIdx.x / 32;
   const int64_t n_groups = (n_pairs + kBoxPairs - 1) / kBoxPairs;
   if (g >= n_groups) return;  // warp-uniform
-  const int64_t b = g * kBoxPairs + (threadIdx.x & 31);
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, lo[3] = {0.f, 0.f, 0.f};
-  if (b < n_pairs) {
+#pragma unroll
+  for (int i = 0; i < kBoxPairs / 32; ++i) {
+    const int64_t b = g * kBoxPairs + (threadIdx.x & 31) + 32 * i;
+    if (b >= n_pairs) break;
     // (xh0 xh1 yh0 yh1) (zh0 zh1 mu0 mu1) (xl0 xl1 yl0 yl1) (zl0 zl1 - -)
     const float4 A = stage[4 * b], B = stage[4 * b + 1], C = stage[4 * b + 2], D = stage[4 * b + 3];
     const float hx[2] = {A.x, A.y}, hy[2] = {A.z, A.w}, hz[2] = {B.x, B.y}, mu[2] = {B.z, B.w};

@@ -223,8 +223,8 @@ constexpr int kStages = 2;          // shared-memory pipeline depth of the force
 constexpr int kFoldPairs = 64;      // mixed path: packed sub-sums of 64 source pairs folded into a float pair
 constexpr float kPadCoord = 1e15f;  // mixed padding source: far away and massless (term exactly 0)
 // Mixed force kernel: source groups of kBoxPairs pairs (64 sources) get a
-// bounding box per tile; a warp whose targets are far from a group's box
-// takes the hi-only path for it (see step_kernel.cuh).  kFarEps bounds the
+// bounding box before each force launch; a warp whose targets are far from a
+// group's box takes the hi-only path for it (see step_kernel.cuh).  kFarEps bounds the
 // relative error that dropping the lo parts adds to one term of Eq. 1;
 // kFarKappa = 2 / kFarEps + 1 is the separation, in units of the largest lo
 // parts, beyond which that bound holds.

@@ -16,9 +16,11 @@
 //
 // Sources stream through a kStages-deep shared-memory ring filled by 1-D bulk
 // copies (cp.async.bulk, completion on mbarriers) issued by one thread, `tj`
-// sources per stage.  Targets live in registers (IPT per thread, strided by
-// THREADS so their loads coalesce); warps without a valid target skip the
-// arithmetic.
+// sources per stage.  Targets live in registers, IPT per thread: warp w
+// holds the block's 32 IPT consecutive entries from 32 IPT w, lane l entry
+// 32 (IPT w + k) + l for k < IPT, so the loads coalesce and a warp's targets
+// sit together in the stage (on the mixed path, near each other in space);
+// warps without a valid target skip the arithmetic.
 //
 // FP64 path: sources as double4 (x, y, z, G m), one per body.
 // Mixed path: sources as pair blocks of 64 bytes holding two consecutive
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
     bool any_valid = false;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-      const int r = tid + k * THREADS, cnt_b = bk.i1 - bk.i0;
+      const int r = (warp * IPT + k) * 32 + lane, cnt_b = bk.i1 - bk.i0;
       valid[k] = r < cnt_b;
       any_valid |= valid[k];
       const int rr = valid[k] ? r : cnt_b - 1;  // duplicate a real target, result discarded

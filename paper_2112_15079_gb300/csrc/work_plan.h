@@ -7,7 +7,7 @@
 // most threads * ipt bodies).  The work line lists, block by block, the
 // sources of the block's system in units of `unit` sources (2 on the mixed
 // path, whose stage pairs sources; 1 on the FP64 path), each unit weighted by
-// the warps the block keeps busy.  Three quarters of the line (all of it when
+// the warps the block keeps busy (or by a cost model, below).  Three quarters of the line (all of it when
 // jsplit == 0) are cut into `grid` equal static shares, the rest into
 // grid * jsplit chunks handed out at run time.  A segment is the part of one
 // block inside one piece; its slot is its rank within the block, which fixes
@@ -56,22 +56,27 @@ struct WorkPlan {
 // against every source of the system).  slots: SMs x resident CTAs per SM
 // the launch may use.  Returns an empty string on success, else the reason
 // the plan cannot be made.
-inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vector<int64_t> &soff, bool mixed,
-                             int threads, int ipt, int jsplit, int64_t slots, WorkPlan &out,
-                             const std::vector<int64_t> *src_begin = nullptr,
-                             const std::vector<int64_t> *src_count = nullptr) {
-  out = WorkPlan{};
+//
+// cost (optional): the relative cost of each block's sources, piecewise
+// constant over chunks of cost->chunk_units units: cost->w[k][c] is the
+// weight of one unit of chunk c of block k (blocks as make_blocks returns
+// them).  Without it every unit of a block weighs the warps the block keeps
+// busy.  With it the line is cut into shares of equal cost, so on the mixed
+// path, where a (warp, source group) pair costs 12 or 18 lane operations per
+// interaction as the group is far or near, the shares still finish together.
+struct ChunkCost {
+  int64_t chunk_units = 1;
+  std::vector<std::vector<int64_t>> w;
+};
+
+// The target blocks of each system: at most B = threads * ipt consecutive
+// bodies, sizes balanced within the system; q0 = stage index of body i0.
+inline std::vector<Blk> make_blocks(const std::vector<int64_t> &offsets, const std::vector<int64_t> &soff,
+                                    int64_t B) {
+  std::vector<Blk> out;
   const int64_t n_sys = static_cast<int64_t>(offsets.size()) - 1;
-  const int64_t B = static_cast<int64_t>(threads) * ipt;
-  const int64_t unit = mixed ? 2 : 1;
-  if (n_sys < 1 || B < 1 || slots < 1) return "empty work";
-  std::vector<int64_t> bj0, bunits, bw, bstart;  // per block: first source, units, weight, line start
-  int64_t W = 0;
   for (int64_t s = 0; s < n_sys; ++s) {
     const int64_t b = offsets[s], e = offsets[s + 1], ns = e - b;
-    const int64_t sb = src_begin ? (*src_begin)[s] : soff[s];  // first source (stage entry)
-    const int64_t sn = src_count ? (*src_count)[s] : ns;       // sources
-    const int64_t len = (sn + unit - 1) / unit;  // units of this system's (padded) source range
     const int64_t nb_s = (ns + B - 1) / B;
     for (int64_t k = 0; k < nb_s; ++k) {
       const int64_t i0 = b + ns * k / nb_s, i1 = b + ns * (k + 1) / nb_s;
@@ -80,15 +85,58 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
       blk.i1 = static_cast<int32_t>(i1);
       blk.q0 = static_cast<int32_t>(soff[s] + (i0 - b));
       blk.nsplit = 0;
-      out.blks.push_back(blk);
-      // warps with at least one target: thread t holds targets t + k*threads
-      const int64_t busy = std::min<int64_t>(threads, i1 - i0);
-      const int64_t w = (busy + 31) / 32;
-      bj0.push_back(sb);
-      bunits.push_back(len);
-      bw.push_back(w);
-      bstart.push_back(W);
-      W += len * w;
+      out.push_back(blk);
+    }
+  }
+  return out;
+}
+
+inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vector<int64_t> &soff, bool mixed,
+                             int threads, int ipt, int jsplit, int64_t slots, WorkPlan &out,
+                             const std::vector<int64_t> *src_begin = nullptr,
+                             const std::vector<int64_t> *src_count = nullptr, const ChunkCost *cost = nullptr) {
+  out = WorkPlan{};
+  const int64_t n_sys = static_cast<int64_t>(offsets.size()) - 1;
+  const int64_t B = static_cast<int64_t>(threads) * ipt;
+  const int64_t unit = mixed ? 2 : 1;
+  if (n_sys < 1 || B < 1 || slots < 1) return "empty work";
+  out.blks = make_blocks(offsets, soff, B);
+  if (cost && cost->w.size() != out.blks.size()) return "cost model does not match the blocks";
+  // per block: first source, units, line start, line length; with a cost
+  // model also the line offset at the start of each chunk
+  std::vector<int64_t> bj0, bunits, bstart, blen;
+  std::vector<std::vector<int64_t>> pre;
+  int64_t W = 0;
+  {
+    size_t k = 0;
+    for (int64_t s = 0; s < n_sys; ++s) {
+      const int64_t b = offsets[s], e = offsets[s + 1], ns = e - b;
+      const int64_t sb = src_begin ? (*src_begin)[s] : soff[s];  // first source (stage entry)
+      const int64_t sn = src_count ? (*src_count)[s] : ns;       // sources
+      const int64_t len = (sn + unit - 1) / unit;  // units of this system's (padded) source range
+      for (; k < out.blks.size() && out.blks[k].i0 < e; ++k) {
+        const Blk &blk = out.blks[k];
+        int64_t L;
+        if (cost) {
+          const std::vector<int64_t> &w = cost->w[k];
+          const int64_t cu = cost->chunk_units, nch = (len + cu - 1) / cu;
+          if (static_cast<int64_t>(w.size()) != nch) return "cost model does not match the sources";
+          std::vector<int64_t> p(nch + 1, 0);
+          for (int64_t c = 0; c < nch; ++c)
+            p[c + 1] = p[c] + std::max<int64_t>(w[c], 1) * (std::min(len, (c + 1) * cu) - c * cu);
+          L = p[nch];
+          pre.push_back(std::move(p));
+        } else {
+          // warps with at least one target: warp w holds the block's targets
+          // [32 ipt w, 32 ipt (w + 1))
+          L = len * ((blk.i1 - blk.i0 + 32 * ipt - 1) / (32 * ipt));
+        }
+        bj0.push_back(sb);
+        bunits.push_back(len);
+        bstart.push_back(W);
+        blen.push_back(L);
+        W += L;
+      }
     }
   }
   int64_t units_total = 0;
@@ -114,16 +162,24 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
   const int64_t P = static_cast<int64_t>(cuts.size()) - 1;
   // Unit boundary of line position x inside block k (the same rounding for
   // both neighbours of a cut, so segments tile each block exactly).
-  auto cut = [&](size_t k, int64_t x) {
-    const int64_t off = std::min(std::max<int64_t>(x - bstart[k], 0), bunits[k] * bw[k]);
-    return (off + bw[k] / 2) / bw[k];
+  auto cut = [&](size_t k, int64_t x) -> int64_t {
+    const int64_t off = std::min(std::max<int64_t>(x - bstart[k], 0), blen[k]);
+    if (!cost) {
+      const int64_t bw = blen[k] / bunits[k];
+      return (off + bw / 2) / bw;
+    }
+    const std::vector<int64_t> &p = pre[k];
+    const int64_t c = std::max<int64_t>(0, (std::upper_bound(p.begin(), p.end(), off) - p.begin()) - 1);
+    if (c >= static_cast<int64_t>(p.size()) - 1) return bunits[k];
+    const int64_t w = std::max<int64_t>(cost->w[k][c], 1);
+    return std::min(bunits[k], c * cost->chunk_units + (off - p[c] + w / 2) / w);
   };
   out.seg_off.assign(P + 1, 0);
   size_t b = 0;
   for (int64_t g = 0; g < P; ++g) {
     const int64_t lo = cuts[g], hi = cuts[g + 1];
     out.seg_off[g] = static_cast<int32_t>(out.segs.size());
-    while (b < out.blks.size() && bstart[b] + bunits[b] * bw[b] <= lo) ++b;
+    while (b < out.blks.size() && bstart[b] + blen[b] <= lo) ++b;
     for (size_t k = b; k < out.blks.size() && bstart[k] < hi; ++k) {
       const int64_t u0 = cut(k, lo), u1 = cut(k, hi);
       if (u1 <= u0) continue;

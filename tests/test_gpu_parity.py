@@ -810,7 +810,7 @@ def test_nondefault_stream(nb):
 
 def _threshold_system(gap_over_threshold):
     """Two clusters on the x axis near x = 3 AU (one binade, ulp 2^-22):
-    64 massless targets whose x = hi + 0.45 ulp, and 128 sources of mass
+    64 massless targets whose x = hi + 0.45 ulp, and 256 sources of mass
     1e-3 whose x = hi - 0.45 ulp, at a gap (between the clusters' hi boxes)
     of `gap_over_threshold` times the far threshold kappa (lo_w + lo_s),
     kappa = 2 / 1e-6 + 1.  y, z are multiples of 2^-14 (no lo part), so the
@@ -827,11 +827,11 @@ def _threshold_system(gap_over_threshold):
     xw = np.full(64, np.float64(x0)) + lo
     gap = gap_over_threshold * thr
     xs_hi = np.float64(np.float32(x0 + gap))
-    xs = np.full(128, xs_hi) - lo
-    r = np.zeros((3, 192))
+    xs = np.full(256, xs_hi) - lo
+    r = np.zeros((3, 320))
     r[0, :64], r[1, :64], r[2, :64] = xw, yz[:64, 0], yz[:64, 1]
-    r[0, 64:], r[1, 64:], r[2, 64:] = xs, yz[:128, 0], yz[:128, 1] + 2.0 ** -6
-    m = np.concatenate([np.zeros(64), np.full(128, 1e-3)])
+    r[0, 64:], r[1, 64:], r[2, 64:] = xs, yz[:256, 0], yz[:256, 1] + 2.0 ** -6
+    m = np.concatenate([np.zeros(64), np.full(256, 1e-3)])
     return inputs.System(r=r, v=np.zeros_like(r), m=m), np.arange(64), thr
 
 

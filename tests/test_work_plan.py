@@ -38,15 +38,34 @@ def wp(tmp_path_factory):
     P = ctypes.c_void_p
     lib.wp_plan.restype = ctypes.c_int
     lib.wp_plan.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
+                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P,
+                            P, P, P, P, ctypes.c_int64, ctypes.c_int64]
     return lib
 
 
-def plan(wp, sizes, mixed, threads, ipt, jsplit, slots):
+def block_units(sizes, mixed, threads, ipt, src=None):
+    """Source units of each target block, in the planner's block order."""
+    unit = 2 if mixed else 1
+    B = threads * ipt
+    out = []
+    for s, n in enumerate(sizes):
+        sn = n if src is None else int(src[1][s])
+        out += [(sn + unit - 1) // unit] * ((n + B - 1) // B)
+    return out
+
+
+def plan(wp, sizes, mixed, threads, ipt, jsplit, slots, cost=None, src=None):
+    """cost: None or (chunk_units, [weights of each block's chunks])."""
     offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     padded = [(n + 1) // 2 * 2 if mixed else n for n in sizes]
     soff = np.concatenate([[0], np.cumsum(padded)]).astype(np.int64)
     n = int(offsets[-1])
+    cw = cw_off = None
+    if cost is not None:
+        cw = np.ascontiguousarray(np.concatenate([np.asarray(w, np.int64) for w in cost[1]]), dtype=np.int64)
+        cw_off = np.concatenate([[0], np.cumsum([len(w) for w in cost[1]])]).astype(np.int64)
+    sb = None if src is None else np.ascontiguousarray(src[0], dtype=np.int64)
+    sn = None if src is None else np.ascontiguousarray(src[1], dtype=np.int64)
     cap_b = sum((s + threads * ipt - 1) // (threads * ipt) for s in sizes)
     cap_p = slots * (jsplit + 1) + 1
     cap_s = cap_p + cap_b + 8
@@ -57,11 +76,15 @@ def plan(wp, sizes, mixed, threads, ipt, jsplit, slots):
     meta = np.zeros(5, np.int64)
     rc = wp.wp_plan(len(sizes), offsets.ctypes.data, soff.ctypes.data, int(mixed), threads, ipt, jsplit, slots,
                     cap_b, cap_s, cap_p, blks.ctypes.data, segs.ctypes.data, seg_off.ctypes.data,
-                    nsl.ctypes.data, meta.ctypes.data)
+                    nsl.ctypes.data, meta.ctypes.data, None if sb is None else sb.ctypes.data,
+                    None if sn is None else sn.ctypes.data, None if cw is None else cw.ctypes.data,
+                    None if cw is None else cw_off.ctypes.data, 0 if cost is None else len(cost[1]),
+                    1 if cost is None else int(cost[0]))
     assert rc == 0, rc
     nb_, ns_, grid, ndyn, rows = (int(x) for x in meta)
     return dict(offsets=offsets, soff=soff, blks=blks[:nb_], segs=segs[:ns_],
-                seg_off=seg_off[:grid + ndyn + 1], nsl=nsl, grid=grid, n_dyn=ndyn, rows=rows)
+                seg_off=seg_off[:grid + ndyn + 1], nsl=nsl, grid=grid, n_dyn=ndyn, rows=rows,
+                cost=cost, src=None if src is None else (sb, sn))
 
 
 def check(p, sizes, mixed, threads, ipt, jsplit, slots):
@@ -89,7 +112,11 @@ def check(p, sizes, mixed, threads, ipt, jsplit, slots):
         assert len(mine) == blk[3] >= 1
         mine = mine[np.argsort(mine[:, 3])]
         assert np.array_equal(mine[:, 3], np.arange(len(mine)))
-        assert mine[0, 1] == soff[s] and mine[-1, 2] == soff[s + 1]
+        if p["src"] is None:
+            assert mine[0, 1] == soff[s] and mine[-1, 2] == soff[s + 1]
+        else:  # explicit sources: [src_b, src_b + src_n rounded up to whole units)
+            sb, sn = int(p["src"][0][s]), int(p["src"][1][s])
+            assert mine[0, 1] == sb and mine[-1, 2] == sb + (sn + unit - 1) // unit * unit
         assert np.all(mine[1:, 1] == mine[:-1, 2]) and np.all(mine[:, 2] > mine[:, 1])
         if mixed:
             assert np.all(mine[:, 1] % 2 == 0) and np.all(mine[:, 2] % 2 == 0)
@@ -108,16 +135,33 @@ def check(p, sizes, mixed, threads, ipt, jsplit, slots):
         assert np.all(p["nsl"][blk[0]:blk[1]] == blk[3])
     assert p["rows"] == blks[:, 3].max()
     # static shares: equal weighted length up to one unit's rounding per segment
-    w = [(min(threads, blk[1] - blk[0]) + 31) // 32 for blk in blks]
-    W = sum(((soff[sys_of_blk[b] + 1] - soff[sys_of_blk[b]]) // unit) * w[b] for b in range(len(blks)))
+    def src_units(s):
+        if p["src"] is None:
+            return (soff[s + 1] - soff[s]) // unit
+        return (int(p["src"][1][s]) + unit - 1) // unit
+
+    # per block: the weight of each of its source units
+    if p["cost"] is None:
+        uw = [np.full(src_units(sys_of_blk[b]), (blk[1] - blk[0] + 32 * ipt - 1) // (32 * ipt), np.int64)
+              for b, blk in enumerate(blks)]
+    else:  # chunk c of block b weighs cost[1][b][c] per unit
+        cu = p["cost"][0]
+        uw = [np.maximum(np.repeat(np.asarray(p["cost"][1][b], np.int64), cu)[:src_units(sys_of_blk[b])], 1)
+              for b in range(len(blks))]
+    upre = [np.concatenate([[0], np.cumsum(w)]) for w in uw]
+    W = sum(int(x[-1]) for x in upre)
     Ws = W - W // 4 if p["n_dyn"] > 0 else W
-    wmax = max(w)
+    wmax = max(int(w.max()) for w in uw)
     for g in range(p["grid"]):
-        share = sum((sg[2] - sg[1]) // unit * w[sg[0]] for sg in segs[so[g]:so[g + 1]])
+        share = 0
+        for sg in segs[so[g]:so[g + 1]]:
+            s0 = int(p["src"][0][sys_of_blk[sg[0]]]) if p["src"] is not None else int(soff[sys_of_blk[sg[0]]])
+            u0, u1 = (int(sg[1]) - s0) // unit, (int(sg[2]) - s0) // unit
+            share += int(upre[sg[0]][u1] - upre[sg[0]][u0])
         nseg = so[g + 1] - so[g]
         assert abs(share - Ws / p["grid"]) <= wmax * (nseg + 1), (g, share, Ws / p["grid"])
     # minimum piece length
-    units = [(soff[sys_of_blk[b] + 1] - soff[sys_of_blk[b]]) // unit for b in range(len(blks))]
+    units = [src_units(sys_of_blk[b]) for b in range(len(blks))]
     umax = max(units)
     c = 0.5 if mixed else (1.0 if umax < 800 else 2.0 if umax < 2000 else 3.0)
     umin = max(1, math.ceil(c * math.sqrt(umax)))
@@ -155,3 +199,54 @@ def test_benchmark_and_small_system_plans(wp):
     p = plan(wp, [1], True, 512, 1, 4, 304)
     check(p, [1], True, 512, 1, 4, 304)
     assert p["grid"] == 1 and p["rows"] == 1
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_cost_weighted_plans(wp, mixed):
+    """A cost model per block and chunk of sources (the mixed path's far/near
+    estimate): the invariants hold and the static shares are equal in cost,
+    so a costlier block gets more, shorter shares, and a costlier chunk
+    shorter segments."""
+    rng = np.random.default_rng(17 + mixed)
+    for _ in range(60):
+        n_sys = int(rng.integers(1, 4))
+        sizes = [int(x) for x in rng.choice([31, 131, 700, 1531, 5003, 12000], n_sys)]
+        threads, ipt = [(128, 1), (256, 1), (512, 1), (256, 2)][int(rng.integers(0, 4))]
+        jsplit = int(rng.choice([0, 2, 8]))
+        slots = int(rng.choice([7, 152, 304]))
+        cu = int(rng.choice([1, 32, 96]))
+        w = [rng.integers(96, 289, size=(u + cu - 1) // cu) for u in block_units(sizes, mixed, threads, ipt)]
+        p = plan(wp, sizes, mixed, threads, ipt, jsplit, slots, cost=(cu, w))
+        check(p, sizes, mixed, threads, ipt, jsplit, slots)
+    # two blocks, one three times as costly: it gets about three times the shares
+    sizes = [2048]
+    units = block_units(sizes, True, 1024, 1)
+    p = plan(wp, sizes, True, 1024, 1, 0, 152, cost=(32, [[100] * ((units[0] + 31) // 32), [300] * ((units[1] + 31) // 32)]))
+    check(p, sizes, True, 1024, 1, 0, 152)
+    per_blk = [int((p["segs"][:, 0] == b).sum()) for b in range(2)]
+    assert 2.5 <= per_blk[1] / per_blk[0] <= 3.5, per_blk
+    # one block whose second half of sources costs twice the first: segments
+    # in the costly half are half as long
+    sizes = [1024]
+    units = block_units(sizes, True, 1024, 1)[0]  # 512 units, 16 chunks of 32
+    p = plan(wp, sizes, True, 1024, 1, 0, 48, cost=(32, [[100] * 8 + [200] * 8]))
+    check(p, sizes, True, 1024, 1, 0, 48)
+    lens = (p["segs"][:, 2] - p["segs"][:, 1]) // 2
+    first = lens[p["segs"][:, 2] <= units]  # segments inside the cheap half (units 0..256)
+    last = lens[p["segs"][:, 1] >= units]   # inside the costly half
+    assert len(first) and len(last)
+    assert 1.6 <= first.mean() / last.mean() <= 2.4, (first.mean(), last.mean())
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_row_shard_plans(wp, mixed):
+    """Row shards: one rank's targets (its block of bodies) against every
+    source entry of the stage (world chunks of C entries): each block's
+    segments tile the whole source range, and the shares stay balanced."""
+    for n, world, rank in ((1001, 2, 1), (10425, 3, 0), (10425, 3, 2), (5, 4, 1)):
+        c = ((n + world - 1) // world + 1) // 2 * 2
+        b, e = min(rank * c, n), min(rank * c + c, n)
+        if e <= b:
+            continue
+        p = plan(wp, [e - b], mixed, 256, 1, 0, 152, src=([0], [world * c]))
+        check(p, [e - b], mixed, 256, 1, 0, 152)
