@@ -7,11 +7,13 @@
 // most threads * ipt bodies).  The work line lists, block by block, the
 // sources of the block's system in units of `unit` sources (2 on the mixed
 // path, whose stage pairs sources; 1 on the FP64 path), each unit weighted by
-// the warps the block keeps busy (or by a cost model, below).  Three quarters of the line (all of it when
-// jsplit == 0) are cut into `grid` equal static shares, the rest into
-// grid * jsplit chunks handed out at run time.  A segment is the part of one
-// block inside one piece; its slot is its rank within the block, which fixes
-// the partial row it writes and its place in the summation order.
+// the warps the block keeps busy (or by a cost model, below).  The first
+// three quarters of every block's line (all of it when jsplit == 0), block
+// after block, are cut into `grid` equal static shares; the last quarters,
+// block after block, into grid * jsplit chunks handed out at run time.  A
+// segment is the part of one block inside one piece; its slot is its rank
+// within the block, which fixes the partial row it writes and its place in
+// the summation order.
 #pragma once
 
 #include <algorithm>
@@ -102,9 +104,9 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
   if (n_sys < 1 || B < 1 || slots < 1) return "empty work";
   out.blks = make_blocks(offsets, soff, B);
   if (cost && cost->w.size() != out.blks.size()) return "cost model does not match the blocks";
-  // per block: first source, units, line start, line length; with a cost
+  // per block: first source, units, line length; with a cost
   // model also the line offset at the start of each chunk
-  std::vector<int64_t> bj0, bunits, bstart, blen;
+  std::vector<int64_t> bj0, bunits, blen;
   std::vector<std::vector<int64_t>> pre;
   int64_t W = 0;
   {
@@ -133,7 +135,6 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
         }
         bj0.push_back(sb);
         bunits.push_back(len);
-        bstart.push_back(W);
         blen.push_back(L);
         W += L;
       }
@@ -155,15 +156,10 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
   const int64_t umin = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(cmin * std::sqrt(static_cast<double>(umax)))));
   const int64_t G = std::max<int64_t>(1, std::min<int64_t>(units_total / umin, slots));
   const int64_t D = std::min<int64_t>(static_cast<int64_t>(jsplit) * G, std::max<int64_t>(units_total - G, 0));
-  const int64_t Ws = D > 0 ? W - W / 4 : W;
-  std::vector<int64_t> cuts;  // piece boundaries on the line
-  for (int64_t g = 0; g <= G; ++g) cuts.push_back(Ws * g / G);
-  for (int64_t d = 1; d <= D; ++d) cuts.push_back(Ws + (W - Ws) * d / D);
-  const int64_t P = static_cast<int64_t>(cuts.size()) - 1;
-  // Unit boundary of line position x inside block k (the same rounding for
+  // Unit boundary of position x of block k's line (the same rounding for
   // both neighbours of a cut, so segments tile each block exactly).
   auto cut = [&](size_t k, int64_t x) -> int64_t {
-    const int64_t off = std::min(std::max<int64_t>(x - bstart[k], 0), blen[k]);
+    const int64_t off = std::min(std::max<int64_t>(x, 0), blen[k]);
     if (!cost) {
       const int64_t bw = blen[k] / bunits[k];
       return (off + bw / 2) / bw;
@@ -174,20 +170,46 @@ inline std::string plan_work(const std::vector<int64_t> &offsets, const std::vec
     const int64_t w = std::max<int64_t>(cost->w[k][c], 1);
     return std::min(bunits[k], c * cost->chunk_units + (off - p[c] + w / 2) / w);
   };
+  // The static line: the first three quarters of every block's line (all of
+  // it without dynamic chunks), block after block; then the dynamic line:
+  // the remaining quarter of every block's line.  So every block gets a
+  // share of the dynamic chunks, and its bodies about as many partial rows
+  // as any other block's.
+  struct Span {
+    size_t k;
+    int64_t a, b;  // positions [a, b) of block k's line
+  };
+  std::vector<Span> spans;
+  for (size_t k = 0; k < out.blks.size(); ++k) spans.push_back({k, 0, D > 0 ? blen[k] - blen[k] / 4 : blen[k]});
+  int64_t Ws = 0;
+  for (const Span &sp : spans) Ws += sp.b - sp.a;
+  if (D > 0)
+    for (size_t k = 0; k < out.blks.size(); ++k) spans.push_back({k, blen[k] - blen[k] / 4, blen[k]});
+  std::vector<int64_t> cuts;  // piece boundaries on the concatenated line
+  for (int64_t g = 0; g <= G; ++g) cuts.push_back(Ws * g / G);
+  for (int64_t d = 1; d <= D; ++d) cuts.push_back(Ws + (W - Ws) * d / D);
+  const int64_t P = static_cast<int64_t>(cuts.size()) - 1;
   out.seg_off.assign(P + 1, 0);
-  size_t b = 0;
+  size_t i = 0;
+  int64_t at = 0;  // line position of span i
   for (int64_t g = 0; g < P; ++g) {
     const int64_t lo = cuts[g], hi = cuts[g + 1];
     out.seg_off[g] = static_cast<int32_t>(out.segs.size());
-    while (b < out.blks.size() && bstart[b] + blen[b] <= lo) ++b;
-    for (size_t k = b; k < out.blks.size() && bstart[k] < hi; ++k) {
-      const int64_t u0 = cut(k, lo), u1 = cut(k, hi);
+    while (i < spans.size() && at + (spans[i].b - spans[i].a) <= lo) {
+      at += spans[i].b - spans[i].a;
+      ++i;
+    }
+    int64_t at_j = at;
+    for (size_t j = i; j < spans.size() && at_j < hi; at_j += spans[j].b - spans[j].a, ++j) {
+      const Span &sp = spans[j];
+      const int64_t x0 = sp.a + std::max<int64_t>(lo - at_j, 0), x1 = sp.a + std::min(hi - at_j, sp.b - sp.a);
+      const int64_t u0 = cut(sp.k, x0), u1 = cut(sp.k, x1);
       if (u1 <= u0) continue;
       Seg sg;
-      sg.blk = static_cast<int32_t>(k);
-      sg.s0 = static_cast<int32_t>(bj0[k] + u0 * unit);
-      sg.s1 = static_cast<int32_t>(bj0[k] + std::min(u1 * unit, bunits[k] * unit));
-      sg.slot = out.blks[k].nsplit++;
+      sg.blk = static_cast<int32_t>(sp.k);
+      sg.s0 = static_cast<int32_t>(bj0[sp.k] + u0 * unit);
+      sg.s1 = static_cast<int32_t>(bj0[sp.k] + std::min(u1 * unit, bunits[sp.k] * unit));
+      sg.slot = out.blks[sp.k].nsplit++;
       out.segs.push_back(sg);
     }
   }

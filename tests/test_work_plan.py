@@ -68,7 +68,7 @@ def plan(wp, sizes, mixed, threads, ipt, jsplit, slots, cost=None, src=None):
     sn = None if src is None else np.ascontiguousarray(src[1], dtype=np.int64)
     cap_b = sum((s + threads * ipt - 1) // (threads * ipt) for s in sizes)
     cap_p = slots * (jsplit + 1) + 1
-    cap_s = cap_p + cap_b + 8
+    cap_s = cap_p + 2 * cap_b + 8
     blks = np.zeros((cap_b, 4), np.int32)
     segs = np.zeros((cap_s, 4), np.int32)
     seg_off = np.zeros(cap_p + 1, np.int32)
