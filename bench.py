@@ -57,7 +57,7 @@ PAPER_INTERACTIONS_PER_S = 7.9e7
 # the caches before each replay, so these are cold-L2 figures; in the timed
 # loop the state is L2-resident), keyed by a hash of the kernel sources they
 # were taken on (null once the sources change).
-NCU_TRAFFIC = {("86a3c26dc30cc3fa", "mixed"): 1057536, ("86a3c26dc30cc3fa", "fp64"): 422400}
+NCU_TRAFFIC = {("2923e595f3a6a2f1", "mixed"): 1058304, ("2923e595f3a6a2f1", "fp64"): 422144}
 
 
 def kernel_hash() -> str:
@@ -358,8 +358,9 @@ def run_ours(args):
             "verlet_steps_per_s": inner * args.steps / ev_s, "wall_s": wall,
             "achieved_tflops": FLOPS_PER_INTERACTION * per_step * inner * args.steps / ev_s * 1e-12,
             "inner": inner, "clocks": clk.summary(),
-            # one staging launch per nbody_step call, then a force and a Verlet launch per step
-            "gpu_launches": args.steps * (1 + 2 * inner),
+            # one staging launch per nbody_step call, then per Verlet step the
+            # force and Verlet launches (mixed: and the source-box launch first)
+            "gpu_launches": args.steps * (1 + (3 if prec == "mixed" else 2) * inner),
         }
         # Roofline of the dominant kernel: the same workload, each kernel of
         # `inner` Verlet steps bracketed alone by events on this stream.
@@ -370,12 +371,6 @@ def run_ours(args):
         if not args.no_e2e:
             results[prec]["e2e"] = e2e(torch, b, s, stream, inner, args, dist, device, world)
         b.close()
-    extra = None
-    if rank == 0 and world == 1 and not args.no_extras and not args.only:
-        extra = extras(torch, nbody, inputs, stream, device, args)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle(s, args.cpu_seconds)
     peaks = None
     if rank == 0:
         p = nbody.peaks()  # measured instruction rates (1e9 lane-ops/s) on this GPU
@@ -383,6 +378,12 @@ def run_ours(args):
                  "mufu_rsqrt_f32_gops": p["rsqrt_f32"], "mufu_rsqrt_f64_gops": p["rsqrt_f64"],
                  "cvt_f32_f64_gops": p["cvt_f32_f64"], "ffma2_tflops": 2 * p["ffma2_lanes"] * 1e-3,
                  "sm_mhz_during_ffma": p["sm_mhz"]}
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extras and not args.only:
+        extra = extras(torch, nbody, inputs, stream, device, args, peaks)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(s, args.cpu_seconds)
     if rank == 0 and args.only:
         r = results[args.only]
         print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
@@ -545,7 +546,7 @@ def timed(torch, stream, fn, reps=1):
     return e0.elapsed_time(e1) * 1e-3
 
 
-def extras(torch, nbody, inputs, stream, device, args):
+def extras(torch, nbody, inputs, stream, device, args, peaks=None):
     """Adjoint cost, the 31-body model, a 521-body FP64 system, RK4, the uneven
     ensemble, N = 1M in both precisions, and (optionally) the full N sweep and
     the dt sweep."""
@@ -652,13 +653,13 @@ def extras(torch, nbody, inputs, stream, device, args):
             for key in ("fp64", "mixed", "fp64_rk4", "mixed_rk4", "fp64_leapfrog", "mixed_leapfrog"):
                 b2[key + "_order"] = float(np.log2(a[key] / b2[key]))
         out["dt_sweep"] = {"bodies": sd.n, "days": 73.0, "max_rel_energy_drift": rows}
-    # N sweep.  By default only N = 1,048,576 (the metric's second size, mixed
-    # and FP64, the library's default tiles: tuning there would cost minutes);
-    # --sweep adds 16,384 / 65,536 (autotuned) and 262,144 (their winner).
-    # FP64 at 1M bodies is one ~31 s step.
+    # N sweep.  By default N = 65,536 and 1,048,576 (the metric's second size),
+    # mixed and FP64, the library's default tiles (tuning at 1M would cost
+    # minutes); --sweep adds 16,384 and 65,536 autotuned, and 262,144 with
+    # their winner.  FP64 at 1M bodies is one ~31 s step.
     if not args.no_extras:
         tuned = {}
-        for n in ((16384, 65536, 262144, 1048576) if args.sweep else (1048576,)):
+        for n in ((16384, 65536, 262144, 1048576) if args.sweep else (65536, 1048576)):
             sn = inputs.solar_system(n)
             row = {}
             for prec in ("mixed", "fp64"):
@@ -666,7 +667,7 @@ def extras(torch, nbody, inputs, stream, device, args):
                     continue
                 with torch.cuda.stream(stream):
                     b = nbody.NBody(sn.r, sn.v, sn.m, G=sn.G, dt=sn.dt, precision=prec, device=device)
-                    if n <= 65536:
+                    if n <= 65536 and args.sweep:
                         tuned[prec] = b.autotune(probe_steps=4 if prec == "mixed" else 1)[0]
                     elif prec in tuned:
                         b.tiles = tuned[prec]
@@ -679,6 +680,9 @@ def extras(torch, nbody, inputs, stream, device, args):
                 row[prec] = {"interactions_per_s": per, "ms_per_step": t / k * 1e3,
                              "roofline_frac": per * FLOPS_PER_INTERACTION * 1e-12 / PEAK_TFLOPS[prec],
                              "tiles": b.tiles}
+                if peaks:  # the whole step (force, Verlet, boxes) against the measured peak
+                    measured = peaks["fp32_tflops"] if prec == "mixed" else peaks["fp64_tflops"]
+                    row[prec]["frac_of_measured"] = per * FLOPS_PER_INTERACTION * 1e-12 / measured
                 b.close()
             out.setdefault("sweep", {})[str(n)] = row
     return out

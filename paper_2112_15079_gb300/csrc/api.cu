@@ -232,10 +232,10 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
   // with three 128-thread CTAs per SM at every size; the mixed path takes two
   // 512-thread CTAs per SM with one target per thread up to ~32k bodies (short
   // shares, more warps), and beyond one 512-thread CTA per SM with two
-  // targets per thread and 8 dynamic chunks per CTA: far and near source
-  // groups cost 12 and 18 lane operations per interaction, so static shares
-  // of equal length finish at different times (65,536 bodies: 1.86 ms against
-  // 1.98 ms with one target per thread and static shares only).
+  // targets per thread and dynamic chunks: the shares are planned by the
+  // host's far/near cost estimate, but run-time differences between SMs
+  // remain (65,536 bodies: 1.81 ms with 8 chunks per CTA against 1.92 ms
+  // with static shares only; 262,144: 27.3 ms with 16 against 27.7 with 8).
   nbody_tiles t{};
   t.jsplit = 0;  // static shares only (dynamic chunks add partial rows)
   t.tj = 1024;
@@ -251,7 +251,7 @@ nbody_tiles default_tiles(const nbody_ctx *c) {
     t.threads = 512;
     t.ipt = 2;
     t.ctas_per_sm = 1;
-    t.jsplit = 8;
+    t.jsplit = c->N <= 131072 ? 8 : 16;
   }
   return t;
 }
