@@ -220,9 +220,10 @@ nbody_status nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *t);
 nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
 
 /* Time each candidate decomposition on the bound state for `probe_steps`
- * steps of the general (two-kernel) path, the one tiles shape, and keep the
- * fastest; a context whose nbody_step runs a single-launch kernel keeps
- * doing so.  The bound state is restored afterwards.  best (HOST, may be
+ * steps of the general (two-kernel) path, the one tiles shape, then the six
+ * fastest again three times each over 4 x probe_steps steps, and keep the
+ * one with the best time; a context whose nbody_step runs a single-launch
+ * kernel keeps doing so.  The bound state is restored afterwards.  best (HOST, may be
  * NULL) receives the winner, best_ms its time per step.  With a tune_cache
  * (nbody_opts) the winner is also written there (replacing the entry with
  * the same key); if that file cannot be written the call returns

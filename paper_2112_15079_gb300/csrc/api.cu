@@ -49,6 +49,7 @@ struct Work {
   int n_blks = 0, rows = 0, grid = 0, n_dyn = 0;
   int occ = 0;  // CTAs of the kernel that fit on one SM
   size_t smem = 0;
+  int stages = nb::kStages;  // force kernel: ring depth
 };
 
 // Adjoint workspace, allocated by the first nbody_grad and kept.
@@ -360,13 +361,29 @@ void free_work(nbody_ctx *c, Work &w) {
 // and tables, which stay a matching pair.
 nbody_status build_items(nbody_ctx *c, const nbody_tiles &t) {
   drop_graphs(c);
-  const size_t smem = nb::force_smem_bytes(c->o.precision, t.tj);
-  NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, smem));
-  const int occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, smem);
+  // The deepest ring (kMaxStages down to kStages tiles) at which the CTAs
+  // per SM the tiles ask for still fit: a deeper ring lets the warps of a
+  // CTA drift further apart and the next segment's tiles load earlier.
+  // A ring above the per-CTA shared-memory limit is refused by the runtime
+  // (invalid argument): the next shallower one is tried.
+  int stages = nb::kStages, occ = 0;
+  size_t smem = 0;
+  for (int k = nb::kMaxStages; k >= nb::kStages; --k) {
+    smem = nb::force_smem_bytes(c->o.precision, t.tj, k);
+    if (k > nb::kStages && nb::force_set_smem(c->o.precision, t.threads, t.ipt, smem) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (k == nb::kStages) NB_CUDA(c, nb::force_set_smem(c->o.precision, t.threads, t.ipt, smem));
+    occ = nb::force_max_ctas_per_sm(c->o.precision, t.threads, t.ipt, smem);
+    stages = k;
+    if (occ >= t.ctas_per_sm) break;
+  }
   Work nw;
   const nbody_status st = build_work(c, nw, t, occ, 3);
   if (st != NBODY_OK) return st;  // (the shared-memory limit was only raised)
   nw.smem = smem;
+  nw.stages = stages;
   free_work(c, c->fw);
   c->fw = nw;
   c->tiles = t;
@@ -418,6 +435,7 @@ nb::ForceArgs force_args(nbody_ctx *c, const void *cur) {
   a.n_dyn = c->fw.n_dyn;
   a.N = c->N;
   a.tj = c->tiles.tj;
+  a.stages = c->fw.stages;
   return a;
 }
 
@@ -618,6 +636,9 @@ void plan_boxes(nbody_ctx *c, const std::vector<double> &h, const std::vector<in
 // weight per unit is that cost summed over the busy warps.  Chunks are one
 // source group (kBoxPairs units) unless that means more than about 2e7 box
 // tests; then several, and one group per chunk is tested.
+// Relative cost of a (warp, source pair) step on the far and the near path.
+constexpr int64_t kCostFar = 12, kCostNear = 18;
+
 nb::ChunkCost chunk_costs(const nbody_ctx *c, const nbody_tiles &t) {
   const int64_t B = static_cast<int64_t>(t.threads) * t.ipt;
   const std::vector<nb::Blk> blks = nb::make_blocks(c->tgt_off, c->tgt_soff, B);
@@ -678,7 +699,7 @@ nb::ChunkCost chunk_costs(const nbody_ctx *c, const nbody_tiles &t) {
       for (const PlanBox &b : wb) {
         const bool far = gb.empty || gb.lo[0] > b.hi[0] || gb.lo[1] > b.hi[1] || gb.lo[2] > b.hi[2] ||
                          b.lo[0] > gb.hi[0] || b.lo[1] > gb.hi[1] || b.lo[2] > gb.hi[2];
-        sum += far ? 12 : 18;
+        sum += far ? kCostFar : kCostNear;
       }
       wk[ch] = sum;
     }
@@ -1294,26 +1315,45 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
   cudaEvent_t e0, e1;
   NB_CUDA(c, cudaEventCreate(&e0));
   NB_CUDA(c, cudaEventCreate(&e1));
-  nbody_tiles win = c->tiles;
-  double win_ms = 1e300;
-  for (const nbody_tiles &t : cand) {
-    if ((st = build_items(c, t)) != NBODY_OK) break;
-    // Warm-up with the timed step count, so the timed call replays a cached
-    // graph instead of capturing one while the GPU waits.
-    if ((st = nbody_step(c, probe_steps)) != NBODY_OK) break;
+  // One timing: build t, a warm-up call with the timed step count (so the
+  // timed call replays a cached graph instead of capturing one while the GPU
+  // waits), the timed call, and the state restored.  ms per step, or < 0.
+  auto time_tiles = [&](const nbody_tiles &t, int32_t steps) -> double {
+    if ((st = build_items(c, t)) != NBODY_OK) return -1.0;
+    if ((st = nbody_step(c, steps)) != NBODY_OK) return -1.0;
     cudaEventRecord(e0, c->stream);
-    if ((st = nbody_step(c, probe_steps)) != NBODY_OK) break;
+    if ((st = nbody_step(c, steps)) != NBODY_OK) return -1.0;
     cudaEventRecord(e1, c->stream);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       st = fail(c, NBODY_ECUDA, "autotune timing failed");
-      break;
+      return -1.0;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if ((st = restore()) != NBODY_OK) break;
-    if (ms / probe_steps < win_ms) {
-      win_ms = ms / probe_steps;
-      win = t;
+    if ((st = restore()) != NBODY_OK) return -1.0;
+    return static_cast<double>(ms) / steps;
+  };
+  // Round 1: every candidate once.  Round 2: the fastest few again, three
+  // times each over 4x the steps, keeping each one's best: single short
+  // probes of candidates a few percent apart pick the wrong one too often.
+  std::vector<std::pair<double, size_t>> r1;
+  for (size_t i = 0; i < cand.size() && st == NBODY_OK; ++i) {
+    const double ms = time_tiles(cand[i], probe_steps);
+    if (ms >= 0.0) r1.emplace_back(ms, i);
+  }
+  std::sort(r1.begin(), r1.end());
+  nbody_tiles win = c->tiles;
+  double win_ms = 1e300;
+  const int32_t steps2 = probe_steps > (1 << 28) ? probe_steps : 4 * probe_steps;
+  for (size_t r = 0; r < r1.size() && r < 6 && st == NBODY_OK; ++r) {
+    double best_t = 1e300;
+    for (int rep = 0; rep < 3 && st == NBODY_OK; ++rep) {
+      const double ms = time_tiles(cand[r1[r].second], steps2);
+      if (ms >= 0.0) best_t = std::min(best_t, ms);
+    }
+    if (best_t < win_ms) {
+      win_ms = best_t;
+      win = cand[r1[r].second];
     }
   }
   cudaEventDestroy(e0);

@@ -47,10 +47,10 @@ bool force_config_supported(int precision, int threads, int ipt) {
   return precision == 0 ? force_fp64_supported(threads, ipt) : force_mixed_supported(threads, ipt);
 }
 
-size_t force_smem_bytes(int precision, int tj) {
+size_t force_smem_bytes(int precision, int tj, int stages) {
   // 32 bytes per staged source in both layouts; the mixed stage also holds
   // the boxes of the source groups its tile touches
-  return static_cast<size_t>(kStages) * (static_cast<size_t>(tj) * 32 + (precision == 1 ? (tj / 64 + 2) * 32 : 0));
+  return static_cast<size_t>(stages) * (static_cast<size_t>(tj) * 32 + (precision == 1 ? (tj / 64 + 2) * 32 : 0));
 }
 
 // ---------------------------------------------------------------------------

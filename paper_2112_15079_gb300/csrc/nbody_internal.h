@@ -48,6 +48,7 @@ struct ForceArgs {
   int32_t n_dyn;
   int32_t N;
   int32_t tj;
+  int32_t stages;  // ring depth, kStages..kMaxStages (force_stages)
 };
 
 enum Mode : int32_t {
@@ -199,7 +200,7 @@ cudaError_t launch_rk_prep(int precision, const RkArgs &a, cudaStream_t s);
 cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem);  // raise the dynamic smem limit
 int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 bool force_config_supported(int precision, int threads, int ipt);
-size_t force_smem_bytes(int precision, int tj);
+size_t force_smem_bytes(int precision, int tj, int stages);  // dynamic smem of a ring of `stages` tiles
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);
@@ -219,7 +220,8 @@ cudaError_t launch_adjoint(int precision, const AdjArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_init(int precision, const AdjArgs &a, const double *dr, const double *dv, cudaStream_t s);
 void set_last_error(const char *msg);  // message returned by nbody_last_error(NULL) on this thread
 
-constexpr int kStages = 2;          // shared-memory pipeline depth of the force kernels
+constexpr int kStages = 2;          // shared-memory pipeline depth of the VJP kernels (and the force kernels' least)
+constexpr int kMaxStages = 4;       // the force kernels' deepest ring (ForceArgs::stages)
 constexpr int kFoldPairs = 64;      // mixed path: packed sub-sums of 64 source pairs folded into a float pair
 constexpr float kPadCoord = 1e15f;  // mixed padding source: far away and massless (term exactly 0)
 // Mixed force kernel: source groups of kBoxPairs pairs (64 sources) get a

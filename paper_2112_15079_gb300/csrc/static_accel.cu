@@ -147,7 +147,8 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   fa.n_dyn = 0;
   fa.N = N;
   fa.tj = kTj;
-  if (nb::launch_force(0, kThreads, 1, n_blocks, nb::force_smem_bytes(0, kTj), fa, st, false) != cudaSuccess)
+  fa.stages = nb::kStages;
+  if (nb::launch_force(0, kThreads, 1, n_blocks, nb::force_smem_bytes(0, kTj, nb::kStages), fa, st, false) != cudaSuccess)
     return fail(NBODY_ECUDA, "force launch failed");
   nb::VerletArgs va{};
   va.ax = ax; va.ay = ay; va.az = az;

@@ -14,13 +14,19 @@
 // order, so results do not depend on scheduling).  No CTA ever waits for
 // another.
 //
-// Sources stream through a kStages-deep shared-memory ring filled by 1-D bulk
-// copies (cp.async.bulk, completion on mbarriers) issued by one thread, `tj`
-// sources per stage.  Targets live in registers, IPT per thread: warp w
-// holds the block's 32 IPT consecutive entries from 32 IPT w, lane l entry
-// 32 (IPT w + k) + l for k < IPT, so the loads coalesce and a warp's targets
-// sit together in the stage (on the mixed path, near each other in space);
-// warps without a valid target skip the arithmetic.
+// Sources stream through a ring of 2-4 shared-memory stages (as deep as the
+// CTAs per SM allow) filled by 1-D bulk copies (cp.async.bulk) that thread
+// 0 issues, `tj` sources per stage.  Each stage has two mbarriers: `full`
+// completes when its tile has landed, `empty` when every warp has released
+// it.  The tiles of all the CTA's segments and pieces form one sequence, each
+// stage carrying a small header (segment, source range), so the next
+// segment's tiles load while the current one finishes and the warps never
+// meet at a CTA-wide barrier inside the loop.  Targets live in registers,
+// IPT per thread: warp w holds the block's 32 IPT consecutive entries from
+// 32 IPT w, lane l entry 32 (IPT w + k) + l for k < IPT, so the loads
+// coalesce and a warp's targets sit together in the stage (on the mixed
+// path, near each other in space); warps without a valid target skip the
+// arithmetic.
 //
 // FP64 path: sources as double4 (x, y, z, G m), one per body.
 // Mixed path: sources as pair blocks of 64 bytes holding two consecutive
@@ -149,13 +155,22 @@ struct MinBlocks {
 template <int PREC, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value)) force_kernel(const ForceArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ int s_flag;  // bit 0: abort (a wait ran out)
+  // Ring of a.stages stages: full[s] completes when tile data (or the end
+  // marker) is in stage s, empty[s] when every warp has released it.
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+  // Tile in stage s: (segment, first source, sources); segment -1 = no more work.
+  __shared__ int4 s_hdr[kMaxStages];
+  __shared__ int s_flag;              // bit 0: abort (a wait ran out)
+  // The producer's cursor (thread 0 only): the next tile to issue.
+  __shared__ struct {
+    int piece, si, se, t, nt, s0, s1, issued, state;  // state: 0 issuing, 1 end marker out, 2 stopped
+  } s_pc;
   // Mixed: the widened box of each warp's targets (low corner, high corner);
   // per target, its negated lo parts (read by the near path only) and its
   // running sums as float pairs (touched once per kFoldPairs pairs) -- kept
   // in shared memory so the source loop has the registers for more pairs in
-  // flight.  Index [field][k * THREADS + tid].
+  // flight.  Index [field][k * THREADS + tid].  All of it belongs to one
+  // warp (or thread), so no CTA-wide barrier guards it.
   __shared__ __align__(16) float4 s_wbox[PREC == 1 ? 2 * (THREADS / 32) : 1];
   constexpr int kT = PREC == 1 ? THREADS * IPT : 1;
   __shared__ float s_tlo[3][kT];
@@ -164,64 +179,160 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int tj = a.tj;  // sources per stage; both layouts take 32 bytes per source
+  const int K = a.stages;
   // Stage s: tj sources (32 bytes each), then (mixed) the boxes of the
   // source groups the tile touches (at most tj / 64 + 2 groups, 32 bytes each).
   const size_t stage_bytes = static_cast<size_t>(tj) * 32 + (PREC == 1 ? (tj / 64 + 2) * 32 : 0);
   auto stage_ptr = [&](int s) { return smem + static_cast<size_t>(s) * stage_bytes; };
   auto box_ptr = [&](int s) { return reinterpret_cast<const float4 *>(stage_ptr(s) + static_cast<size_t>(tj) * 32); };
+  const size_t N = static_cast<size_t>(a.N);
+  const int n_static = static_cast<int>(gridDim.x);
 
-  __shared__ int s_piece;
+  // ---- producer (thread 0) ---------------------------------------------
+  // The work of this CTA is its static piece (blockIdx.x), then dynamic
+  // pieces pulled from the counter while any is left; each piece is a run
+  // of segments, each segment a run of tiles.  seek() moves the cursor to
+  // the first tile of segment si or, past the piece's end, of the next
+  // piece that has a segment (piece -1: none left).
+  auto seek = [&]() {
+    while (s_pc.si >= s_pc.se) {
+      const int next = n_static + atomicAdd(a.dyn_ctr, 1);
+      if (next >= n_static + a.n_dyn) {
+        s_pc.piece = -1;
+        return;
+      }
+      s_pc.piece = next;
+      s_pc.si = a.seg_off[next];
+      s_pc.se = a.seg_off[next + 1];
+    }
+    const Seg sg = a.segs[s_pc.si];
+    s_pc.s0 = sg.s0;
+    s_pc.s1 = sg.s1;
+    s_pc.t = 0;
+    s_pc.nt = (sg.s1 - sg.s0 + tj - 1) / tj;
+  };
+  // Issue tiles while the ring has room: at most K tiles ahead of tile c
+  // (the next one warp 0 consumes), each into a stage every warp has
+  // released.  A stage still held is left for a later call, except for
+  // tile c itself, which must be out before anyone waits for it: for that
+  // one the wait is (bounded) blocking.  Other warps never wait for warp 0
+  // beyond that: the tiles before c were issued when warp 0 reached them.
+  auto pump = [&](int c) {
+    while (s_pc.state == 0 && s_pc.issued < c + K) {
+      const int u = s_pc.issued, s = u % K, n = u / K;
+      if (n > 0) {  // stage s last held tile u - K: released by every warp?
+        const uint32_t par = static_cast<uint32_t>(n - 1) & 1u;
+        if (u == c) {
+          if (!mbar_wait(&empty[s], par)) {
+            s_pc.state = 2;
+            atomicOr(&s_flag, 1);
+            return;
+          }
+        } else if (!mbar_test_wait(&empty[s], par)) {
+          return;
+        }
+      }
+      if (s_pc.piece < 0) {  // no more work: the end marker
+        s_hdr[s] = make_int4(-1, 0, 0, 0);
+        mbar_arrive(&full[s]);
+        s_pc.state = 1;
+        s_pc.issued = u + 1;
+        return;
+      }
+      const int j = s_pc.s0 + s_pc.t * tj;
+      const int nb = min(tj, s_pc.s1 - j);
+      s_hdr[s] = make_int4(s_pc.si, j, nb, 0);
+      const uint32_t bytes = static_cast<uint32_t>(nb) * 32u;
+      // mixed: the boxes of groups (j / 2) / 32 .. ((j + nb) / 2 - 1) / 32, 32 bytes each
+      const int g0 = (j >> 1) / kBoxPairs, g1 = (((j + nb) >> 1) - 1) / kBoxPairs;
+      const uint32_t bbytes = PREC == 1 ? static_cast<uint32_t>(g1 - g0 + 1) * 32u : 0u;
+      mbar_arrive_expect_tx(&full[s], bytes + bbytes);
+      bulk_g2s(stage_ptr(s), static_cast<const unsigned char *>(a.cur) + static_cast<size_t>(j) * 32, bytes,
+               &full[s]);
+      if (PREC == 1)
+        bulk_g2s(stage_ptr(s) + static_cast<size_t>(tj) * 32, a.boxes + 2 * static_cast<size_t>(g0), bbytes,
+                 &full[s]);
+      s_pc.issued = u + 1;
+      if (++s_pc.t == s_pc.nt) {
+        ++s_pc.si;
+        seek();
+      }
+    }
+  };
+
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < K; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], THREADS / 32);
+      s_hdr[s] = make_int4(-1, 0, 0, 0);
+    }
     mbar_init_fence();
     s_flag = 0;
   }
   grid_dependency_wait();    // staged sources of this step are complete (and the
                              // previous Verlet kernel has finished)
   grid_dependency_launch();  // so the Verlet kernel may start launching
+  if (tid == 0) {
+    s_pc.piece = blockIdx.x;
+    s_pc.si = a.seg_off[blockIdx.x];
+    s_pc.se = a.seg_off[blockIdx.x + 1];
+    s_pc.issued = 0;
+    s_pc.state = 0;
+    seek();
+    pump(0);  // the first tiles go out before the targets are loaded
+  }
   __syncthreads();
 
-  uint32_t phase = 0;  // bit s: parity of the next completion of stage s
+  // ---- consumers (every warp): tiles in issue order ---------------------
+  // A warp sets up a segment's targets when its first tile arrives and
+  // writes their partial sums when the next segment's first tile (or the
+  // end marker) arrives; between tiles it only releases the stage, so warps
+  // drift apart by up to K tiles instead of meeting at a barrier per tile.
   bool aborted = false;
-  const size_t N = static_cast<size_t>(a.N);
-  const int n_static = static_cast<int>(gridDim.x);
-  int piece = blockIdx.x;
+  int cur = -1;  // segment in progress
+  int q0 = 0, q_end = 0;  // stage indices of its block's targets: [q0, q_end)
+  int pidx[IPT], tq[IPT];
+  bool valid[IPT];
+  bool warp_busy = false;
+  // FP64 path: (acc, cmp) is a hi/lo pair fed once per tile with the tile's
+  // FP64 sub-sum through TwoSum.
+  double accx[IPT], accy[IPT], accz[IPT], cmpx[IPT], cmpy[IPT], cmpz[IPT];
+  double px[IPT], py[IPT], pz[IPT];
+  // Mixed path: packed partial sums (even / odd sources) and the running
+  // sums as unevaluated float pairs (hi + lo), fed one packed sub-sum of
+  // kFoldPairs source pairs at a time through TwoSum, so the source loop
+  // issues no FP64 instruction (GB300 runs FP64 and f32<->f64 conversions
+  // at 1/64 of the FP32 rate).
+  f2 nxh[IPT], nyh[IPT], nzh[IPT], pax[IPT], pay[IPT], paz[IPT];
+  int mlo[IPT], mhi[IPT];
 
-  while (!aborted) {
-  const int seg_begin = a.seg_off[piece], seg_end = a.seg_off[piece + 1];
-  for (int si = seg_begin; si < seg_end && !aborted; ++si) {
-    const Seg sg = a.segs[si];
-    const Blk bk = a.blks[sg.blk];
-    const int q_end = bk.q0 + (bk.i1 - bk.i0);  // stage indices of the block's targets: [q0, q_end)
-
-    // The first source tiles go out before the targets are loaded, so their
-    // copy overlaps the target loads.  The ring is free: every tile of the
-    // previous segment was consumed before the last __syncthreads.
-    const int ntiles = (sg.s1 - sg.s0 + tj - 1) / tj;
-    auto issue = [&](int t) {  // tid 0 only
-      const int s = t % kStages;
-      const int j = sg.s0 + t * tj;
-      const int n = min(tj, sg.s1 - j);
-      const uint32_t bytes = static_cast<uint32_t>(n) * 32u;
-      // mixed: the boxes of groups (j / 2) / 32 .. ((j + n) / 2 - 1) / 32, 32 bytes each
-      const int g0 = (j >> 1) / kBoxPairs, g1 = (((j + n) >> 1) - 1) / kBoxPairs;
-      const uint32_t bbytes = PREC == 1 ? static_cast<uint32_t>(g1 - g0 + 1) * 32u : 0u;
-      mbar_arrive_expect_tx(&bar[s], bytes + bbytes);
-      bulk_g2s(stage_ptr(s), static_cast<const unsigned char *>(a.cur) + static_cast<size_t>(j) * 32, bytes,
-               &bar[s]);
-      if (PREC == 1)
-        bulk_g2s(stage_ptr(s) + static_cast<size_t>(tj) * 32, a.boxes + 2 * static_cast<size_t>(g0), bbytes, &bar[s]);
-    };
-    if (tid == 0) {
-      for (int t = 0; t < kStages && t < ntiles; ++t) issue(t);
+  // The partial sums of segment `cur`, row `slot`.
+  auto flush = [&]() {
+    double *prow = a.partial + static_cast<size_t>(a.segs[cur].slot) * 3 * N;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      if (!valid[k]) continue;
+      if (PREC == 0) {
+        prow[pidx[k]] = accx[k] + cmpx[k];
+        prow[N + pidx[k]] = accy[k] + cmpy[k];
+        prow[2 * N + pidx[k]] = accz[k] + cmpz[k];
+      } else {
+        float2 *frow = reinterpret_cast<float2 *>(prow);
+        const int i = k * THREADS + tid;
+        frow[pidx[k]] = make_float2(s_sum[0][i], s_sum[1][i]);
+        frow[N + pidx[k]] = make_float2(s_sum[2][i], s_sum[3][i]);
+        frow[2 * N + pidx[k]] = make_float2(s_sum[4][i], s_sum[5][i]);
+      }
     }
+  };
 
-    // ---- targets into registers ---------------------------------------
-    // Target k of this thread: stage entry tq (the block's entries are
-    // consecutive), body pidx (the same index, or perm[tq] in a spatially
-    // ordered stage).
-    int pidx[IPT], tq[IPT];
-    bool valid[IPT];
+  // The targets of segment `cur` (this warp's share of its block): target k
+  // of this thread is stage entry tq (the block's entries are consecutive),
+  // body pidx (the same index, or perm[tq] in a spatially ordered stage).
+  auto setup = [&]() {
+    const Blk bk = a.blks[a.segs[cur].blk];
+    q0 = bk.q0;
+    q_end = bk.q0 + (bk.i1 - bk.i0);
     bool any_valid = false;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
@@ -232,17 +343,7 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
       tq[k] = bk.q0 + rr;
       pidx[k] = a.perm ? a.perm[tq[k]] : bk.i0 + rr;
     }
-    const bool warp_busy = __any_sync(0xffffffffu, any_valid);  // warp-uniform
-    // FP64 path: (acc, cmp) is a hi/lo pair fed once per tile with the tile's
-    // FP64 sub-sum through TwoSum.
-    double accx[IPT], accy[IPT], accz[IPT], cmpx[IPT], cmpy[IPT], cmpz[IPT];
-    double px[IPT], py[IPT], pz[IPT];
-    // Mixed path: packed partial sums (even / odd sources) and the running
-    // sums as unevaluated float pairs (hi + lo), fed one packed sub-sum of
-    // kFoldPairs source pairs at a time through TwoSum, so the source loop
-    // issues no FP64 instruction (GB300 runs FP64 and f32<->f64 conversions
-    // at 1/64 of the FP32 rate).
-    f2 nxh[IPT], nyh[IPT], nzh[IPT], pax[IPT], pay[IPT], paz[IPT];
+    warp_busy = __any_sync(0xffffffffu, any_valid);  // warp-uniform
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       accx[k] = accy[k] = accz[k] = cmpx[k] = cmpy[k] = cmpz[k] = 0.0;
@@ -272,34 +373,49 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         const float *e = static_cast<const float *>(a.cur) + pair_off(tq[k]);
         const float h[3] = {e[kXh], e[kYh], e[kZh]}, l[3] = {e[kXl], e[kYl], e[kZl]};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          mn[c] = fminf(mn[c], h[c]);
-          mx[c] = fmaxf(mx[c], h[c]);
-          lo[c] = fmaxf(lo[c], fabsf(l[c]));
+        for (int d = 0; d < 3; ++d) {
+          mn[d] = fminf(mn[d], h[d]);
+          mx[d] = fmaxf(mx[d], h[d]);
+          lo[d] = fmaxf(lo[d], fabsf(l[d]));
         }
       }
       warp_box(mn[0], mn[1], mn[2], mx[0], mx[1], mx[2], lo[0], lo[1], lo[2], &s_wbox[2 * warp]);
+      __syncwarp();  // lane 0 wrote the box the whole warp reads
     }
     // Mixed path: the source pairs that may hold one of this warp's own
     // targets (for each k, the warp's 32 consecutive targets span <= 17
     // pairs).  Only those pairs take the masked path.
-    int mlo[IPT], mhi[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       mlo[k] = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
       mhi[k] = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(tq[k]))) >> 1;
     }
+  };
 
-    // ---- source loop over [s0, s1) in tiles of tj ---------------------
-    for (int t = 0; t < ntiles; ++t) {
-      const int s = t % kStages;
-      if (!mbar_wait(&bar[s], (phase >> s) & 1u)) atomicOr(&s_flag, 1);
-      phase ^= 1u << s;
-      const int jt0 = sg.s0 + t * tj;
-      const int cnt = min(tj, sg.s1 - jt0);
+  int ct = 0;               // tiles this warp has consumed
+  int s = 0;                // their stage: ct mod K
+  uint32_t par = 0;         // and the parity of that stage's next phase: (ct / K) mod 2
+  for (;; ++ct) {
+    if (tid == 0) pump(ct);
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], par));
+    if (!ok) {  // a wait ran out: this warp winds down (the others run out on theirs)
+      if (lane == 0) atomicOr(&s_flag, 1);
+      aborted = true;
+      break;
+    }
+    const int4 h = s_hdr[s];
+    if (h.x < 0) break;  // no more work
+    if (h.x != cur) {
+      if (cur >= 0) flush();
+      cur = h.x;
+      setup();
+    }
+    {
+      const int jt0 = h.y, cnt = h.z;  // the tile's sources [jt0, jt0 + cnt)
 
       if (warp_busy && PREC == 0) {
-        const bool diag = jt0 < q_end && jt0 + cnt > bk.q0;  // tile may contain a target itself
+        const bool diag = jt0 < q_end && jt0 + cnt > q0;  // tile may contain a target itself
         const double4_32a *src = reinterpret_cast<const double4_32a *>(stage_ptr(s));
         double tx[IPT], ty[IPT], tz[IPT];
 #pragma unroll
@@ -459,58 +575,25 @@ __global__ void __launch_bounds__(THREADS, (MinBlocks<PREC, THREADS, IPT>::value
         fold();
       }
 
-      __syncthreads();  // every thread is done with stage s
-      if (s_flag & 1) {
-        aborted = true;
-        // Drain the copies this CTA may still have in flight (bounded): tile t
-        // itself (its wait may be the one that ran out; parity before the flip)
-        // and the tiles issued ahead of it.  Then leave.
-        if (tid == 0) {
-          mbar_wait(&bar[s], ((phase >> s) & 1u) ^ 1u);
-          for (int u = t + 1; u < ntiles && u < t + kStages; ++u) {
-            const int su = u % kStages;
-            mbar_wait(&bar[su], (phase >> su) & 1u);
-            phase ^= 1u << su;
-          }
-        }
-        break;
-      }
-      if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
     }
-    if (aborted) {
-      if (tid == 0) atomicOr(a.flags, kFlagTimeout);
-      break;
-    }
-
-    // ---- this segment's partial sums, row `slot` ---------------------
-    double *prow = a.partial + static_cast<size_t>(sg.slot) * 3 * N;
-#pragma unroll
-    for (int k = 0; k < IPT; ++k) {
-      if (!valid[k]) continue;
-      if (PREC == 0) {
-        prow[pidx[k]] = accx[k] + cmpx[k];
-        prow[N + pidx[k]] = accy[k] + cmpy[k];
-        prow[2 * N + pidx[k]] = accz[k] + cmpz[k];
-      } else {
-        float2 *frow = reinterpret_cast<float2 *>(prow);
-        const int i = k * THREADS + tid;
-        frow[pidx[k]] = make_float2(s_sum[0][i], s_sum[1][i]);
-        frow[N + pidx[k]] = make_float2(s_sum[2][i], s_sum[3][i]);
-        frow[2 * N + pidx[k]] = make_float2(s_sum[4][i], s_sum[5][i]);
-      }
+    __syncwarp();  // every lane is done with stage s
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (++s == K) {
+      s = 0;
+      par ^= 1u;
     }
   }
-  // next piece: a dynamic chunk, while any is left
-  __syncthreads();
-  if (tid == 0) s_piece = n_static + atomicAdd(a.dyn_ctr, 1);
-  __syncthreads();
-  piece = s_piece;
-  if (piece >= n_static + a.n_dyn) break;
-  }
+  if (!aborted && cur >= 0) flush();
 
+  // No copy into this CTA's shared memory may outlive it: thread 0 waits
+  // (bounded) for every tile it issued from the one warp 0 stopped at (after
+  // the end marker there is none; after a wait that ran out, at most K).
+  if (tid == 0)
+    for (int u = ct; u < s_pc.issued; ++u) mbar_wait(&full[u % K], static_cast<uint32_t>(u / K) & 1u);
+  __syncthreads();
   // The last CTA out resets the chunk counter for the next launch.
-  __syncthreads();
   if (tid == 0) {
+    if (s_flag & 1) atomicOr(a.flags, kFlagTimeout);
     __threadfence();
     if (atomicAdd(a.dyn_ctr + 1, 1) == n_static - 1) {
       atomicExch(a.dyn_ctr, 0);
