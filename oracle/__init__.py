@@ -16,6 +16,8 @@ Functions (all FP64 numpy arrays, structure-of-arrays):
 * ``rk4``        -- classical fourth-order Runge-Kutta steps on (r, v), the
                     higher-order method Section 2 names.
 * ``leapfrog``   -- drift-kick-drift leapfrog steps (Section 2).
+* ``respa``      -- close-encounter handling: impulse multiple time stepping
+                    with close pairs sub-cycled (an extension beyond Section 2).
 * ``energy``     -- total energy (kinetic, potential), the accuracy criterion
                     of Sections 2 and 4.
 * ``vjp``        -- vector-Jacobian product of Eq. 1 w.r.t. positions and masses.
@@ -91,6 +93,9 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
             lib.oracle_grad.argtypes = ([_I64, ctypes.c_double, ctypes.c_double, _I64]
                                         + [_D] * 15)
             lib.oracle_grad.restype = ctypes.c_int
+            lib.oracle_respa.argtypes = ([_I64, ctypes.c_double, ctypes.c_double, _I64, ctypes.c_double,
+                                          ctypes.c_double] + [_D] * 10 + [ctypes.POINTER(_I64)] * 2)
+            lib.oracle_respa.restype = ctypes.c_int
             lib.oracle_openmp_threads.argtypes = []
             lib.oracle_openmp_threads.restype = ctypes.c_int
             _LIBS[openmp] = lib
@@ -199,6 +204,30 @@ def rk4(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: np.n
     if rc != 0:
         raise MemoryError("oracle_rk4: allocation failed")
     return r, v, a
+
+
+def respa(G: float, dt: float, n_steps: int, r: np.ndarray, v: np.ndarray, m: np.ndarray,
+          theta_c: float, theta_s: float, openmp: bool = False):
+    """Close-encounter handling: n_steps impulse multiple-time-step steps
+    (close pairs, w dt > theta_c, sub-cycled per cluster with
+    k = ceil(w_max dt / theta_s) velocity-Verlet sub-steps on their own
+    forces; the rest of Eq. 1 as half kicks of dt).  Returns (r, v, a,
+    n_close_pairs, k_max); a = Eq. 1 at the final positions."""
+    r = _f64(r).copy()
+    v = _f64(v).copy()
+    m = _f64(m)
+    n = m.shape[0]
+    a = np.zeros((3, n))
+    npairs = _I64(0)
+    kmax = _I64(0)
+    rc = _lib(openmp).oracle_respa(n, G, dt, int(n_steps), float(theta_c), float(theta_s),
+                                   _c(r[0]), _c(r[1]), _c(r[2]), _c(v[0]), _c(v[1]), _c(v[2]), _c(m),
+                                   _c(a[0]), _c(a[1]), _c(a[2]), ctypes.byref(npairs), ctypes.byref(kmax))
+    if rc == -2:
+        raise ValueError("a close pair would need more than 1e6 sub-steps per step")
+    if rc != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return r, v, a, int(npairs.value), int(kmax.value)
 
 
 def energy(G: float, r: np.ndarray, v: np.ndarray, m: np.ndarray):

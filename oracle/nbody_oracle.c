@@ -442,6 +442,201 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
   return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Close-encounter handling: impulse multiple time stepping of close pairs.
+ *
+ * An extension beyond Section 2's method, for bodies whose two-body orbit
+ * the fixed step cannot follow (a moon with a period below a few dt is
+ * unstable under Eqs. 3-4 at any precision).  It is the reversible impulse
+ * multiple-time-step scheme of Tuckerman, Berne and Martyna (J. Chem. Phys.
+ * 97, 1990, 1992) with the force split by pairs:
+ *
+ *   close pair (p, j), p < j:  G (m_p + m_j) dt^2 > theta_c^2 d^3,
+ *     d = |r_j - r_p| at the positions the run starts from, i.e. the pair's
+ *     two-body angular frequency w = sqrt(G (m_p + m_j) / d^3) has
+ *     w dt > theta_c;
+ *   cluster: a connected set of bodies joined by close pairs;
+ *   sub-steps of a cluster: k = max over its pairs of ceil(w dt / theta_s);
+ *   A_near(r)_p = sum over the close pairs (p, j), j ascending, of
+ *     G m_j (r_j - r_p) / |r_j - r_p|^3;   A_far = A - A_near (A = Eq. 1).
+ *
+ * One step of dt:
+ *   v <- v + dt/2 A_far(r)                                   every body
+ *   r <- r + dt v                                            bodies in no cluster
+ *   k times, h = dt / k:  v <- v + h/2 A_near(r); r <- r + h v;
+ *                         v <- v + h/2 A_near(r)             each cluster
+ *   v <- v + dt/2 A_far(r)                                   every body
+ * Without close pairs this is velocity Verlet in its kick-drift-kick form,
+ * algebraically Eqs. 3-4.  The pairs and sub-step counts are fixed when the
+ * run starts.  On return (ax, ay, az) = A(r) (Eq. 1) at the final positions;
+ * *n_pairs and *k_max (either may be NULL) report the close pairs and the
+ * largest sub-step count.  Returns 0; -1 if scratch could not be allocated;
+ * -2 if a cluster would need more than 1e6 sub-steps per step.
+ * ---------------------------------------------------------------------- */
+static int64_t uf_find(int64_t *parent, int64_t i) {
+  while (parent[i] != i) {
+    parent[i] = parent[parent[i]];
+    i = parent[i];
+  }
+  return i;
+}
+
+/* A_near for the bodies listed in idx[0..cnt) (their close partners given as
+ * the CSR lists nb_off / nb_j, j ascending). */
+static void near_accel(double G, const double *x, const double *y,
+                       const double *z, const double *m, const int64_t *idx,
+                       int64_t cnt, const int64_t *nb_off, const int64_t *nb_j,
+                       double *anx, double *any, double *anz) {
+  for (int64_t k = 0; k < cnt; k++) {
+    const int64_t p = idx[k];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t e = nb_off[p]; e < nb_off[p + 1]; e++) {
+      const int64_t j = nb_j[e];
+      const double dx = x[j] - x[p];
+      const double dy = y[j] - y[p];
+      const double dz = z[j] - z[p];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double f = G * m[j] * (1.0 / (r2 * sqrt(r2))); /* as in Eq. 1 above */
+      sx += f * dx;
+      sy += f * dy;
+      sz += f * dz;
+    }
+    anx[p] = sx;
+    any[p] = sy;
+    anz[p] = sz;
+  }
+}
+
+int oracle_respa(int64_t n, double G, double dt, int64_t n_steps,
+                 double theta_c, double theta_s, double *x, double *y,
+                 double *z, double *vx, double *vy, double *vz,
+                 const double *m, double *ax, double *ay, double *az,
+                 int64_t *n_pairs, int64_t *k_max) {
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * nn);
+  int64_t *deg = (int64_t *)calloc(nn + 1, sizeof(int64_t));
+  double *wmax = (double *)calloc(nn, sizeof(double));
+  double *scratch = (double *)malloc(sizeof(double) * 6 * nn);
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * nn);
+  int64_t *kc = (int64_t *)malloc(sizeof(int64_t) * nn);
+  if (!parent || !deg || !wmax || !scratch || !order || !kc) {
+    free(parent); free(deg); free(wmax); free(scratch); free(order); free(kc);
+    return -1;
+  }
+  double *anx = scratch, *any = scratch + n, *anz = scratch + 2 * n;
+  double *fx = scratch + 3 * n, *fy = scratch + 4 * n, *fz = scratch + 5 * n;
+  /* close pairs, by brute force over all p < j */
+  int64_t pairs = 0;
+  for (int64_t p = 0; p < n; p++) parent[p] = p;
+  for (int64_t p = 0; p < n; p++)
+    for (int64_t j = p + 1; j < n; j++) {
+      const double dx = x[j] - x[p], dy = y[j] - y[p], dz = z[j] - z[p];
+      const double d2 = dx * dx + dy * dy + dz * dz;
+      const double d3 = d2 * sqrt(d2);
+      if (G * (m[p] + m[j]) * (dt * dt) > theta_c * theta_c * d3) {
+        pairs++;
+        deg[p + 1]++;
+        deg[j + 1]++;
+        parent[uf_find(parent, p)] = uf_find(parent, j);
+      }
+    }
+  for (int64_t p = 0; p < n; p++) deg[p + 1] += deg[p];
+  int64_t *nb_j = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * pairs > 0 ? 2 * pairs : 1));
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * nn);
+  if (!nb_j || !fill) {
+    free(parent); free(deg); free(wmax); free(scratch); free(order); free(kc);
+    free(nb_j); free(fill);
+    return -1;
+  }
+  for (int64_t p = 0; p < n; p++) fill[p] = deg[p];
+  for (int64_t p = 0; p < n; p++) /* partners in ascending order */
+    for (int64_t j = 0; j < n; j++) {
+      if (j == p) continue;
+      /* the same test as above, on the pair taken as (lower, higher) index */
+      const int64_t lo = p < j ? p : j, hi = p < j ? j : p;
+      const double dx = x[hi] - x[lo], dy = y[hi] - y[lo], dz = z[hi] - z[lo];
+      const double d2 = dx * dx + dy * dy + dz * dz;
+      const double d3 = d2 * sqrt(d2);
+      if (G * (m[lo] + m[hi]) * (dt * dt) > theta_c * theta_c * d3) {
+        nb_j[fill[p]++] = j;
+        const double w = sqrt(G * (m[lo] + m[hi]) / d3);
+        if (w > wmax[p]) wmax[p] = w;
+      }
+    }
+  /* sub-steps per cluster: the largest w dt / theta_s over its pairs */
+  int64_t kmx = 0;
+  for (int64_t p = 0; p < n; p++) kc[p] = 0;
+  for (int64_t p = 0; p < n; p++) {
+    if (deg[p + 1] == deg[p]) continue;
+    const int64_t root = uf_find(parent, p);
+    const double kd = ceil(wmax[p] * dt / theta_s);
+    if (kd > 1e6) {
+      free(parent); free(deg); free(wmax); free(scratch); free(order); free(kc);
+      free(nb_j); free(fill);
+      return -2;
+    }
+    const int64_t k = kd < 1.0 ? 1 : (int64_t)kd;
+    if (k > kc[root]) kc[root] = k;
+  }
+  for (int64_t p = 0; p < n; p++)
+    if (kc[p] > kmx) kmx = kc[p];
+  if (n_pairs) *n_pairs = pairs;
+  if (k_max) *k_max = kmx;
+  /* the bodies of each cluster, grouped (order[] lists cluster members by
+     root; a cluster is the run of equal roots) */
+  int64_t cnt = 0;
+  for (int64_t root = 0; root < n; root++) {
+    if (kc[root] == 0) continue;
+    for (int64_t p = 0; p < n; p++)
+      if (deg[p + 1] > deg[p] && uf_find(parent, p) == root) order[cnt++] = p;
+  }
+  double *r[3] = {x, y, z}, *v[3] = {vx, vy, vz}, *a[3] = {ax, ay, az};
+  double *an[3] = {anx, any, anz}, *f[3] = {fx, fy, fz};
+  for (int64_t p = 0; p < n; p++) anx[p] = any[p] = anz[p] = 0.0;
+  oracle_accel(n, G, x, y, z, m, ax, ay, az);
+  near_accel(G, x, y, z, m, order, cnt, deg, nb_j, anx, any, anz);
+  const double hd = 0.5 * dt;
+  for (int64_t step = 0; step < n_steps; step++) {
+    for (int c = 0; c < 3; c++) /* v <- v + dt/2 A_far(r) */
+      for (int64_t p = 0; p < n; p++) {
+        f[c][p] = a[c][p] - an[c][p];
+        v[c][p] = v[c][p] + hd * f[c][p];
+      }
+    for (int c = 0; c < 3; c++) /* bodies in no cluster drift a full step */
+      for (int64_t p = 0; p < n; p++)
+        if (deg[p + 1] == deg[p]) r[c][p] = r[c][p] + dt * v[c][p];
+    for (int64_t i0 = 0; i0 < cnt;) { /* each cluster: k sub-steps */
+      const int64_t root = uf_find(parent, order[i0]);
+      int64_t i1 = i0;
+      while (i1 < cnt && uf_find(parent, order[i1]) == root) i1++;
+      const int64_t k = kc[root];
+      const double h = dt / (double)k, hh = 0.5 * h;
+      for (int64_t sub = 0; sub < k; sub++) {
+        near_accel(G, x, y, z, m, order + i0, i1 - i0, deg, nb_j, anx, any, anz);
+        for (int64_t q = i0; q < i1; q++) {
+          const int64_t p = order[q];
+          for (int c = 0; c < 3; c++) {
+            v[c][p] = v[c][p] + hh * an[c][p];
+            r[c][p] = r[c][p] + h * v[c][p];
+          }
+        }
+        near_accel(G, x, y, z, m, order + i0, i1 - i0, deg, nb_j, anx, any, anz);
+        for (int64_t q = i0; q < i1; q++) {
+          const int64_t p = order[q];
+          for (int c = 0; c < 3; c++) v[c][p] = v[c][p] + hh * an[c][p];
+        }
+      }
+      i0 = i1;
+    }
+    oracle_accel(n, G, x, y, z, m, ax, ay, az); /* Eq. 1 at the new r */
+    for (int c = 0; c < 3; c++) /* v <- v + dt/2 A_far(r) */
+      for (int64_t p = 0; p < n; p++) v[c][p] = v[c][p] + hd * (a[c][p] - an[c][p]);
+  }
+  free(parent); free(deg); free(wmax); free(scratch); free(order); free(kc);
+  free(nb_j); free(fill);
+  return 0;
+}
+
 /* 1 when built with OpenMP, else 0; and the thread count it would use. */
 int oracle_openmp_threads(void) {
 #ifdef _OPENMP
