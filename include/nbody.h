@@ -106,6 +106,25 @@ typedef struct {
    * malformed file, or a stale entry (other kernels), is ignored: the
    * context starts from the built-in defaults.  The string is copied. */
   const char *tune_cache;
+  /* Close-encounter handling, for bodies whose two-body orbit the step
+   * cannot follow (a moon with a period below a few dt is unstable under
+   * Eqs. 3-4 at any precision).  An extension beyond Section 2's method:
+   * impulse multiple time stepping (Tuckerman, Berne and Martyna, J. Chem.
+   * Phys. 97, 1990, 1992) with the force split by pairs.  0 = off.  Else a
+   * pair of bodies of one system is close if its two-body angular frequency
+   * w = sqrt(G (m_p + m_j) / d^3), at the positions nbody_init (or
+   * nbody_reset) sees, has w |dt| > close_omega_dt; bodies joined by close
+   * pairs form clusters.  A step then is: v += dt/2 (A - A_near); each
+   * cluster takes k = ceil(max w |dt| / substep_omega_dt) velocity-Verlet
+   * sub-steps of dt/k on the forces of its close pairs (A_near), FP64,
+   * every other body drifts r += dt v; v += dt/2 (A - A_near) at the new
+   * positions (A = Eq. 1 in the context's precision).  Without close pairs
+   * this is velocity Verlet.  Verlet integrator only; nbody_grad,
+   * nbody_kernel_times and nbody_shard return EINVAL; at most 256 bodies
+   * and 1024 pairs per cluster and 1e6 sub-steps per step, else nbody_init
+   * returns EINVAL. */
+  double close_omega_dt;
+  double substep_omega_dt; /* w h per sub-step, > 0 when close_omega_dt > 0 (e.g. 0.05) */
 } nbody_opts;
 
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
@@ -180,6 +199,12 @@ nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
  * Asynchronous (but reads the positions and validates them synchronously,
  * like nbody_init). */
 nbody_status nbody_reset(nbody_ctx *ctx);
+
+/* Close-encounter handling (nbody_opts.close_omega_dt): the close pairs,
+ * clusters, cluster members and the largest sub-step count of the current
+ * set (all 0 when off).  Any output pointer may be NULL; HOST memory. */
+nbody_status nbody_close_info(const nbody_ctx *ctx, int64_t *n_pairs, int32_t *n_clusters, int32_t *n_members,
+                              int32_t *k_max);
 
 /* Mixed precision: re-sort each system's sources into a spatial (Morton)
  * order of the current positions.  nbody_init and nbody_reset sort; the

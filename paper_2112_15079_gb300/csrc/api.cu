@@ -18,6 +18,7 @@
 
 #include "nbody.h"
 #include "nbody_internal.h"
+#include "close_pairs.h"
 #include "tune_cache.h"
 
 // Hash of the kernel sources of this build (set by the build script): the
@@ -119,6 +120,13 @@ struct nbody_ctx {
   // the stage holds sh_world chunks of sh_chunk entries (rank k's bodies at
   // entries [k sh_chunk, ...), then inert padding).
   int32_t sh_world = 0, sh_rank = 0;
+  // Close-encounter handling (nbody_opts.close_omega_dt > 0): the clusters
+  // of close pairs (host copy and device tables), and per member a_near and
+  // the sub-cycle velocity ([3][members]).
+  bool close_on = false;
+  nb::CloseSet close;
+  int32_t *close_tab = nullptr;
+  double *close_an = nullptr, *close_vh = nullptr;
   int64_t sh_chunk = 0, sh_begin = 0, sh_end = 0;
   int sh_cur = 0;  // the stage the next shard step reads
   double *R = nullptr;               // [3][N] mixed: FP64 positions of the staged step
@@ -421,6 +429,84 @@ nb::PrepArgs prep_args(nbody_ctx *c, const State &s, int drift, int check, void 
   return p;
 }
 
+int n_clusters(const nbody_ctx *c) { return static_cast<int>(c->close.cl_k.size()); }
+
+// Arguments of the cluster kernel writing the stage `nxt`; complete: first
+// finish the step the Verlet kernel just closed.
+nb::CloseArgs close_args(nbody_ctx *c, const State &s, void *nxt, int complete) {
+  const size_t N = c->N;
+  const nb::CloseSet &cs = c->close;
+  nb::CloseArgs a{};
+  a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
+  a.ax = s.ax; a.ay = s.ay; a.az = s.az;
+  a.m = c->m;
+  a.an = c->close_an;
+  a.vh = c->close_vh;
+  int32_t *t = c->close_tab;  // cl_off, cl_k, mem_body, pr_off, pr_a, pr_b, mp_off, mp_pair
+  a.cl_off = t;
+  a.cl_k = (t += cs.cl_off.size());
+  a.mem_body = (t += cs.cl_k.size());
+  a.pr_off = (t += cs.mem_body.size());
+  a.pr_a = (t += cs.pr_off.size());
+  a.pr_b = (t += cs.pr_a.size());
+  a.mp_off = (t += cs.pr_b.size());
+  a.mp_pair = (t += cs.mp_off.size());
+  a.stage = nxt;
+  a.qidx = c->qidx;
+  a.Rx = c->R;
+  a.Ry = c->R ? c->R + N : nullptr;
+  a.Rz = c->R ? c->R + 2 * N : nullptr;
+  a.flags = c->flags;
+  a.n_mem = static_cast<int32_t>(cs.mem_body.size());
+  a.complete = complete;
+  a.precision = c->o.precision;
+  a.G = c->o.G;
+  a.dt = c->o.dt;
+  a.half_dt = 0.5 * c->o.dt;
+  return a;
+}
+
+// The close pairs and clusters of the bound positions (close_pairs.h), on
+// the host, and their device tables.  Synchronous.
+nbody_status build_close(nbody_ctx *c) {
+  const size_t N = c->N, b = sizeof(double) * N;
+  std::vector<double> h(4 * N);
+  NB_CUDA(c, cudaMemcpyAsync(h.data(), c->x, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(h.data() + N, c->y, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(h.data() + 2 * N, c->z, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaMemcpyAsync(h.data() + 3 * N, c->m, b, cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(c, cudaStreamSynchronize(c->stream));
+  nb::CloseSet cs;
+  const std::string why = nb::find_close_set(c->n_sys, c->offsets.data(), h.data(), h.data() + N, h.data() + 2 * N,
+                                             h.data() + 3 * N, c->o.G, c->o.dt, c->o.close_omega_dt,
+                                             c->o.substep_omega_dt, cs);
+  if (!why.empty()) return fail(c, NBODY_EINVAL, "%s", why.c_str());
+  for (size_t k = 0; k + 1 < cs.cl_off.size(); ++k) {
+    if (cs.cl_off[k + 1] - cs.cl_off[k] > nb::kCloseThreads || cs.pr_off[k + 1] - cs.pr_off[k] > nb::kCloseMaxPairs)
+      return fail(c, NBODY_EINVAL, "a cluster of close pairs has more than %d bodies or %d pairs", nb::kCloseThreads,
+                  nb::kCloseMaxPairs);
+  }
+  dfree(c, c->close_tab);
+  dfree(c, c->close_an);
+  dfree(c, c->close_vh);
+  c->close_tab = nullptr;
+  c->close_an = c->close_vh = nullptr;
+  std::vector<int32_t> tab;
+  for (const std::vector<int32_t> *v : {&cs.cl_off, &cs.cl_k, &cs.mem_body, &cs.pr_off, &cs.pr_a, &cs.pr_b,
+                                        &cs.mp_off, &cs.mp_pair})
+    tab.insert(tab.end(), v->begin(), v->end());
+  const size_t nm = cs.mem_body.size();
+  nbody_status st;
+  if ((st = dalloc(c, reinterpret_cast<void **>(&c->close_tab), sizeof(int32_t) * tab.size())) != NBODY_OK ||
+      (st = dalloc(c, reinterpret_cast<void **>(&c->close_an), sizeof(double) * 3 * nm)) != NBODY_OK ||
+      (st = dalloc(c, reinterpret_cast<void **>(&c->close_vh), sizeof(double) * 3 * nm)) != NBODY_OK)
+    return st;
+  NB_CUDA(c, cudaMemcpy(c->close_tab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice));
+  c->close = std::move(cs);
+  drop_graphs(c);  // graphs hold the previous tables' launches
+  return NBODY_OK;
+}
+
 nb::ForceArgs force_args(nbody_ctx *c, const void *cur) {
   nb::ForceArgs a{};
   a.cur = cur;
@@ -528,6 +614,9 @@ nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) 
             : launch_one_step(c, s, c->stage[i & 1], c->stage[1 - (i & 1)],
                               c->o.integrator == NBODY_LEAPFROG ? nb::kModeLeapfrog : nb::kModeStep, st);
     if (r != NBODY_OK) return r;
+    // close pairs: finish this step for the cluster members and sub-cycle
+    // them into the next stage
+    if (c->close_on) NB_CUDA(c, nb::launch_close(close_args(c, s, c->stage[1 - (i & 1)], 1), n_clusters(c), st, true));
   }
   return NBODY_OK;
 }
@@ -973,6 +1062,14 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL)) return fail(nullptr, NBODY_EINVAL, "unknown flags");
   if (o->integrator != NBODY_VERLET && o->integrator != NBODY_RK4 && o->integrator != NBODY_LEAPFROG)
     return fail(nullptr, NBODY_EINVAL, "unknown integrator %d", o->integrator);
+  if (!(o->close_omega_dt >= 0.0) || !std::isfinite(o->close_omega_dt))
+    return fail(nullptr, NBODY_EINVAL, "close_omega_dt must be finite and >= 0");
+  if (o->close_omega_dt > 0.0) {
+    if (!(o->substep_omega_dt > 0.0) || !std::isfinite(o->substep_omega_dt))
+      return fail(nullptr, NBODY_EINVAL, "substep_omega_dt must be finite and > 0 with close_omega_dt > 0");
+    if (o->integrator != NBODY_VERLET)
+      return fail(nullptr, NBODY_EINVAL, "close-encounter handling runs with the Verlet integrator only");
+  }
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;
   if (!c) return fail(nullptr, NBODY_ENOMEM, "host allocation failed");
@@ -1050,8 +1147,10 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   // One FP64 Verlet system: every step of a call in one launch, a cluster up
   // to kSmallClusterMax bodies, a cooperative grid up to the grid kernel's
   // limit (each faster than the general path there).
+  c->close_on = c->o.close_omega_dt > 0.0;
+  if (c->close_on && (st = build_close(c)) != NBODY_OK) return bail(st);
   const bool single = c->n_sys == 1 && c->o.precision == NBODY_FP64 && c->o.integrator == NBODY_VERLET &&
-                      !(c->o.flags & NBODY_FLAG_NO_SMALL);
+                      !(c->o.flags & NBODY_FLAG_NO_SMALL) && !c->close_on;
   c->small = single && c->N <= std::min(kSmallClusterMax, nb::small_max_bodies());
   if (c->small && nb::small_prepare() != cudaSuccess) {  // no 16-CTA clusters here: the next path
     cudaGetLastError();
@@ -1133,6 +1232,8 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
     NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 2, 0), c->stream));
   else  // Eq. 3 drift of the first step
     NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
+  if (c->close_on)  // the cluster members' first step starts from the state
+    NB_CUDA(c, nb::launch_close(close_args(c, s, c->stage[0], 0), n_clusters(c), c->stream, true));
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   NB_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
   if ((c->o.flags & NBODY_FLAG_NO_GRAPH) || cs != cudaStreamCaptureStatusNone) {
@@ -1184,7 +1285,18 @@ nbody_status nbody_reset(nbody_ctx *c) {
   if ((st = spatial_order(c)) != NBODY_OK || (st = upload_nsl(c, c->adj.vj)) != NBODY_OK ||
       (c->o.precision == NBODY_MIXED && (st = build_items(c, c->tiles)) != NBODY_OK))
     return st;
+  if (c->close_on && (st = build_close(c)) != NBODY_OK) return st;  // the pairs of the new positions
   return refresh(c);
+}
+
+nbody_status nbody_close_info(const nbody_ctx *c, int64_t *n_pairs, int32_t *n_clusters, int32_t *n_members,
+                              int32_t *k_max) {
+  if (!c) return NBODY_EINVAL;
+  if (n_pairs) *n_pairs = c->close.n_pairs;
+  if (n_clusters) *n_clusters = static_cast<int32_t>(c->close.cl_k.size());
+  if (n_members) *n_members = static_cast<int32_t>(c->close.mem_body.size());
+  if (k_max) *k_max = c->close.k_max;
+  return NBODY_OK;
 }
 
 nbody_status nbody_reorder(nbody_ctx *c) {
@@ -1387,6 +1499,7 @@ nbody_status nbody_kernel_times(nbody_ctx *c, int32_t n_steps, double *out) {
   const DeviceGuard dg(c->dev);
   if (c->sh_world > 0) return fail(c, NBODY_EINVAL, "a row shard steps with nbody_shard_step");
   if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "nbody_kernel_times times Verlet steps only");
+  if (c->close_on) return fail(c, NBODY_EINVAL, "nbody_kernel_times times plain Verlet steps (no close pairs)");
   if (n_steps < 1) return fail(c, NBODY_EINVAL, "n_steps must be >= 1");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -1437,6 +1550,7 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   if (!dL_dr_T || !dL_dr0 || !dL_dv0 || !dL_dm) return fail(c, NBODY_EINVAL, "a gradient pointer is NULL");
   if (n_steps > (int64_t(1) << 31)) return fail(c, NBODY_EINVAL, "n_steps too large");
   if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "the adjoint covers Verlet (Eqs. 3-4) only");
+  if (c->close_on) return fail(c, NBODY_EINVAL, "the adjoint covers plain Verlet (no close pairs)");
   nbody_status st;
   if ((st = ensure_adjoint(c, n_steps)) != NBODY_OK) return st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
@@ -1533,6 +1647,7 @@ nbody_status nbody_shard(nbody_ctx *c, int32_t rank, int32_t world) {
   if (world < 1 || rank < 0 || rank >= world) return fail(c, NBODY_EINVAL, "need 0 <= rank < world");
   if (c->n_sys != 1) return fail(c, NBODY_EINVAL, "row shards take one system");
   if (c->o.integrator != NBODY_VERLET) return fail(c, NBODY_EINVAL, "row shards run velocity Verlet");
+  if (c->close_on) return fail(c, NBODY_EINVAL, "row shards run plain Verlet (no close pairs)");
   nbody_status st;
   if ((st = begin_work(c)) != NBODY_OK) return st;
   NB_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -138,6 +138,27 @@ struct PrepArgs {
   double G, dt, half_dt2;
 };
 
+// Close-encounter handling (close.cu): clusters of close pairs sub-cycled in
+// FP64 after each step's Verlet kernel.  Members and pairs as CloseSet in
+// close_pairs.h (global member / pair indices).
+constexpr int kCloseThreads = 256;    // members per cluster at most (one thread each)
+constexpr int kCloseMaxPairs = 1024;  // pairs per cluster at most
+struct CloseArgs {
+  double *x, *y, *z, *vx, *vy, *vz;  // state (v written in complete mode)
+  const double *ax, *ay, *az;        // Eq. 1 at the state positions
+  const double *m;
+  double *an, *vh;                   // [3][n_mem]: a_near and the sub-cycle velocity of each member
+  const int32_t *cl_off, *cl_k, *mem_body, *pr_off, *pr_a, *pr_b, *mp_off, *mp_pair;
+  void *stage;                       // the next force launch's sources (FP64 double4 / mixed pair blocks)
+  const int32_t *qidx;               // mixed: stage entry of each body
+  double *Rx, *Ry, *Rz;              // mixed: FP64 staged positions
+  unsigned *flags;
+  int32_t n_mem;
+  int32_t complete;                  // 1: first finish the step the Verlet kernel closed
+  int32_t precision;
+  double G, dt, half_dt;
+};
+
 struct EnergyArgs {
   const double *x, *y, *z, *vx, *vy, *vz, *m;
   double *e_kin, *e_pot;  // per body
@@ -201,6 +222,7 @@ cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem);  /
 int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 bool force_config_supported(int precision, int threads, int ipt);
 size_t force_smem_bytes(int precision, int tj, int stages);  // dynamic smem of a ring of `stages` tiles
+cudaError_t launch_close(const CloseArgs &a, int n_clusters, cudaStream_t s, bool chained);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);

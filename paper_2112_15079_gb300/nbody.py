@@ -36,7 +36,8 @@ INTEGRATORS = {"verlet": NBODY_VERLET, "rk4": NBODY_RK4, "leapfrog": NBODY_LEAPF
 class nbody_opts(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("integrator", ctypes.c_int32),
-                ("tune_cache", ctypes.c_char_p)]
+                ("tune_cache", ctypes.c_char_p), ("close_omega_dt", ctypes.c_double),
+                ("substep_omega_dt", ctypes.c_double)]
 
 
 class nbody_tiles(ctypes.Structure):
@@ -56,6 +57,7 @@ _SIGS = {
     "nbody_accel": (_S, [_P, _P, _P, _P]),
     "nbody_reset": (_S, [_P]),
     "nbody_reorder": (_S, [_P]),
+    "nbody_close_info": (_S, [_P, ctypes.POINTER(ctypes.c_int64)] + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "nbody_energy": (_S, [_P, ctypes.POINTER(ctypes.c_double)]),
     "nbody_grad": (_S, [_P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "nbody_sync": (_S, [_P]),
@@ -132,7 +134,8 @@ class NBody:
 
     def __init__(self, r, v, m, offsets=None, *, G: float, dt: float, precision: str = "fp64",
                  ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None,
-                 integrator: str = "verlet", tune_cache: str | None = None):
+                 integrator: str = "verlet", tune_cache: str | None = None, close_omega_dt: float = 0.0,
+                 substep_omega_dt: float = 0.05):
         torch = _torch()
         device = torch.device(device if device is not None else "cuda")
         self.device = device
@@ -153,7 +156,8 @@ class NBody:
         opts = nbody_opts(G=self.G, dt=self.dt, precision=PRECISIONS[precision], ckpt_every=int(ckpt_every),
                           flags=(0 if graphs else NBODY_FLAG_NO_GRAPH) | (0 if small else NBODY_FLAG_NO_SMALL),
                           integrator=INTEGRATORS[integrator],
-                          tune_cache=None if tune_cache is None else os.fsencode(tune_cache))
+                          tune_cache=None if tune_cache is None else os.fsencode(tune_cache),
+                          close_omega_dt=float(close_omega_dt), substep_omega_dt=float(substep_omega_dt))
         self._ctx = _P()
         s = self.state
         ptrs = [s[k].data_ptr() for k in range(6)] + [self.m.data_ptr()]
@@ -182,6 +186,15 @@ class NBody:
 
     def reset(self) -> None:
         check(nbody_reset(self._ctx), self._ctx)
+
+    def close_info(self) -> dict:
+        """Close-encounter handling: close pairs, clusters, cluster members
+        and the largest sub-step count per step (all 0 when off)."""
+        npairs = ctypes.c_int64()
+        ncl, nmem, kmax = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(nbody_close_info(self._ctx, ctypes.byref(npairs), ctypes.byref(ncl), ctypes.byref(nmem),
+                               ctypes.byref(kmax)), self._ctx)
+        return {"pairs": npairs.value, "clusters": ncl.value, "members": nmem.value, "k_max": kmax.value}
 
     def reorder(self) -> None:
         """Mixed precision: re-sort the sources spatially at the current
