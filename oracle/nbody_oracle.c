@@ -458,7 +458,10 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
  *   cluster: a connected set of bodies joined by close pairs;
  *   sub-steps of a cluster: k = max over its pairs of ceil(w dt / theta_s);
  *   A_near(r)_p = sum over the close pairs (p, j), j ascending, of
- *     G m_j (r_j - r_p) / |r_j - r_p|^3;   A_far = A - A_near (A = Eq. 1).
+ *     G m_j (r_j - r_p) / |r_j - r_p|^3;
+ *   A_far(r)_p = the same sum over every other j != p (Eq. 1 without p's
+ *     close partners), summed directly rather than as A - A_near, so a
+ *     moon's far force does not inherit the rounding of its host's pull.
  *
  * One step of dt:
  *   v <- v + dt/2 A_far(r)                                   every body
@@ -466,6 +469,7 @@ int oracle_grad(int64_t n, double G, double dt, int64_t T, const double *x0,
  *   k times, h = dt / k:  v <- v + h/2 A_near(r); r <- r + h v;
  *                         v <- v + h/2 A_near(r)             each cluster
  *   v <- v + dt/2 A_far(r)                                   every body
+ * (A_far = A for a body with no close pair.)
  * Without close pairs this is velocity Verlet in its kick-drift-kick form,
  * algebraically Eqs. 3-4.  The pairs and sub-step counts are fixed when the
  * run starts.  On return (ax, ay, az) = A(r) (Eq. 1) at the final positions;
@@ -504,6 +508,37 @@ static void near_accel(double G, const double *x, const double *y,
     anx[p] = sx;
     any[p] = sy;
     anz[p] = sz;
+  }
+}
+
+/* A_far for the bodies idx[0..cnt): Eq. 1 over every j != p that is not one
+ * of p's close partners (nb_j[nb_off[p] .. nb_off[p+1]), ascending), j
+ * ascending, Neumaier-compensated as accel_rows. */
+static void far_accel(int64_t n, double G, const double *x, const double *y,
+                      const double *z, const double *m, const int64_t *idx,
+                      int64_t cnt, const int64_t *nb_off, const int64_t *nb_j,
+                      double *fx, double *fy, double *fz) {
+  for (int64_t k = 0; k < cnt; k++) {
+    const int64_t p = idx[k];
+    double sx = 0.0, sy = 0.0, sz = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+    int64_t e = nb_off[p];
+    for (int64_t j = 0; j < n; j++) {
+      if (j == p) continue;
+      while (e < nb_off[p + 1] && nb_j[e] < j) e++;
+      if (e < nb_off[p + 1] && nb_j[e] == j) continue; /* a close partner */
+      const double dx = x[j] - x[p];
+      const double dy = y[j] - y[p];
+      const double dz = z[j] - z[p];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double s = 1.0 / (r2 * sqrt(r2));
+      const double f = G * m[j] * s;
+      neumaier_add(&sx, &cx, f * dx);
+      neumaier_add(&sy, &cy, f * dy);
+      neumaier_add(&sz, &cz, f * dz);
+    }
+    fx[p] = sx + cx;
+    fy[p] = sy + cy;
+    fz[p] = sz + cz;
   }
 }
 
@@ -592,16 +627,15 @@ int oracle_respa(int64_t n, double G, double dt, int64_t n_steps,
   }
   double *r[3] = {x, y, z}, *v[3] = {vx, vy, vz}, *a[3] = {ax, ay, az};
   double *an[3] = {anx, any, anz}, *f[3] = {fx, fy, fz};
-  for (int64_t p = 0; p < n; p++) anx[p] = any[p] = anz[p] = 0.0;
+  /* F = A_far: Eq. 1 for bodies in no cluster, the direct far sum for the rest */
   oracle_accel(n, G, x, y, z, m, ax, ay, az);
-  near_accel(G, x, y, z, m, order, cnt, deg, nb_j, anx, any, anz);
+  for (int c = 0; c < 3; c++)
+    for (int64_t p = 0; p < n; p++) f[c][p] = a[c][p];
+  far_accel(n, G, x, y, z, m, order, cnt, deg, nb_j, fx, fy, fz);
   const double hd = 0.5 * dt;
   for (int64_t step = 0; step < n_steps; step++) {
     for (int c = 0; c < 3; c++) /* v <- v + dt/2 A_far(r) */
-      for (int64_t p = 0; p < n; p++) {
-        f[c][p] = a[c][p] - an[c][p];
-        v[c][p] = v[c][p] + hd * f[c][p];
-      }
+      for (int64_t p = 0; p < n; p++) v[c][p] = v[c][p] + hd * f[c][p];
     for (int c = 0; c < 3; c++) /* bodies in no cluster drift a full step */
       for (int64_t p = 0; p < n; p++)
         if (deg[p + 1] == deg[p]) r[c][p] = r[c][p] + dt * v[c][p];
@@ -629,8 +663,11 @@ int oracle_respa(int64_t n, double G, double dt, int64_t n_steps,
       i0 = i1;
     }
     oracle_accel(n, G, x, y, z, m, ax, ay, az); /* Eq. 1 at the new r */
+    for (int c = 0; c < 3; c++)
+      for (int64_t p = 0; p < n; p++) f[c][p] = a[c][p];
+    far_accel(n, G, x, y, z, m, order, cnt, deg, nb_j, fx, fy, fz);
     for (int c = 0; c < 3; c++) /* v <- v + dt/2 A_far(r) */
-      for (int64_t p = 0; p < n; p++) v[c][p] = v[c][p] + hd * (a[c][p] - an[c][p]);
+      for (int64_t p = 0; p < n; p++) v[c][p] = v[c][p] + hd * f[c][p];
   }
   free(parent); free(deg); free(wmax); free(scratch); free(order); free(kc);
   free(nb_j); free(fill);
