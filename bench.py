@@ -30,6 +30,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -611,6 +612,36 @@ def extras(torch, nbody, inputs, stream, device, args, peaks=None):
                                            "interactions_per_s": 4 * s.n * (s.n - 1) * k / t,
                                            "force_evaluations_per_step": 4}
         b.close()
+    # Close-encounter handling on the 10,425-body model (its moons as drawn:
+    # 13 have w dt > 2): cost per step, and how far the fast moons' distances
+    # to their hosts move over 365 steps, with and without it.
+    G, dt = s.G, s.dt
+    fast = []
+    for p in range(31, 131):  # the moons: each against the major bodies
+        for j in range(31):
+            d = np.linalg.norm(s.r[:, p] - s.r[:, j])
+            if math.sqrt(G * (s.m[p] + s.m[j]) / d ** 3) * dt > 2.0:
+                fast.append((j, p, d))
+    for prec, k in (("fp64", 20), ("mixed", 200)):
+        row = {}
+        for tc in (0.5, 0.0):
+            with torch.cuda.stream(stream):
+                b = nbody.NBody(s.r, s.v, s.m, G=G, dt=dt, precision=prec, close_omega_dt=tc, substep_omega_dt=0.05,
+                                device=device)
+                info = b.close_info()
+                b.step(2)
+                t = timed(torch, stream, lambda: b.step(k))
+                b.step(365 - 2 - k)
+                b.sync()
+                rr = b.state[0:3].cpu().numpy()
+            dev = max(abs(np.linalg.norm(rr[:, p] - rr[:, j]) / d0 - 1.0) for j, p, d0 in fast)
+            key = "close" if tc > 0 else "plain_verlet"
+            row[key] = {"ms_per_step": t / k * 1e3, "fast_moons_max_rel_distance_change_365_steps": dev}
+            if tc > 0:
+                row[key].update(close_pairs=info["pairs"], clusters=info["clusters"], k_max=info["k_max"],
+                                close_omega_dt=tc, substep_omega_dt=0.05)
+            b.close()
+        out.setdefault("close_encounters", {"fast_moons": len(fast)})[prec] = row
     # uneven ensemble, mixed, one context
     ens = inputs.ensemble(args.ensemble_systems)
     off, r, v, m = inputs.concat(ens)

@@ -114,15 +114,17 @@ typedef struct {
    * pair of bodies of one system is close if its two-body angular frequency
    * w = sqrt(G (m_p + m_j) / d^3), at the positions nbody_init (or
    * nbody_reset) sees, has w |dt| > close_omega_dt; bodies joined by close
-   * pairs form clusters.  A step then is: v += dt/2 (A - A_near); each
-   * cluster takes k = ceil(max w |dt| / substep_omega_dt) velocity-Verlet
-   * sub-steps of dt/k on the forces of its close pairs (A_near), FP64,
-   * every other body drifts r += dt v; v += dt/2 (A - A_near) at the new
-   * positions (A = Eq. 1 in the context's precision).  Without close pairs
-   * this is velocity Verlet.  Verlet integrator only; nbody_grad,
-   * nbody_kernel_times and nbody_shard return EINVAL; at most 256 bodies
-   * and 1024 pairs per cluster and 1e6 sub-steps per step, else nbody_init
-   * returns EINVAL. */
+   * pairs form clusters.  A step then is: v += dt/2 A_far; each cluster
+   * takes k = ceil(max w |dt| / substep_omega_dt) velocity-Verlet sub-steps
+   * of dt/k on the forces of its close pairs (A_near), FP64, every other
+   * body drifts r += dt v; v += dt/2 A_far at the new positions.  A_far is
+   * Eq. 1 in the context's precision for a body with no close pair, and for
+   * a cluster member the FP64 sum over every body of its system but itself
+   * and its close partners.  Without close pairs this is velocity Verlet.
+   * Verlet integrator only; nbody_grad, nbody_kernel_times and nbody_shard
+   * return EINVAL; at most 256 bodies and 1024 pairs per cluster, 64 close
+   * partners per body and 1e6 sub-steps per step, else nbody_init returns
+   * EINVAL. */
   double close_omega_dt;
   double substep_omega_dt; /* w h per sub-step, > 0 when close_omega_dt > 0 (e.g. 0.05) */
 } nbody_opts;

@@ -125,8 +125,9 @@ struct nbody_ctx {
   // the sub-cycle velocity ([3][members]).
   bool close_on = false;
   nb::CloseSet close;
+  std::vector<int32_t> fc_mem, fc_j0, fc_j1, mch_off;  // the members' far-force chunks (CloseArgs)
   int32_t *close_tab = nullptr;
-  double *close_an = nullptr, *close_vh = nullptr;
+  double *close_an = nullptr, *close_vh = nullptr, *close_far = nullptr;
   int64_t sh_chunk = 0, sh_begin = 0, sh_end = 0;
   int sh_cur = 0;  // the stage the next shard step reads
   double *R = nullptr;               // [3][N] mixed: FP64 positions of the staged step
@@ -438,11 +439,12 @@ nb::CloseArgs close_args(nbody_ctx *c, const State &s, void *nxt, int complete) 
   const nb::CloseSet &cs = c->close;
   nb::CloseArgs a{};
   a.x = s.x; a.y = s.y; a.z = s.z; a.vx = s.vx; a.vy = s.vy; a.vz = s.vz;
-  a.ax = s.ax; a.ay = s.ay; a.az = s.az;
   a.m = c->m;
   a.an = c->close_an;
   a.vh = c->close_vh;
-  int32_t *t = c->close_tab;  // cl_off, cl_k, mem_body, pr_off, pr_a, pr_b, mp_off, mp_pair
+  a.far_part = c->close_far;
+  // close_tab: cl_off, cl_k, mem_body, pr_off, pr_a, pr_b, mp_off, mp_pair, fc_mem, fc_j0, fc_j1, mch_off
+  int32_t *t = c->close_tab;
   a.cl_off = t;
   a.cl_k = (t += cs.cl_off.size());
   a.mem_body = (t += cs.cl_k.size());
@@ -451,6 +453,11 @@ nb::CloseArgs close_args(nbody_ctx *c, const State &s, void *nxt, int complete) 
   a.pr_b = (t += cs.pr_a.size());
   a.mp_off = (t += cs.pr_b.size());
   a.mp_pair = (t += cs.mp_off.size());
+  a.fc_mem = (t += cs.mp_pair.size());
+  a.fc_j0 = (t += c->fc_mem.size());
+  a.fc_j1 = (t += c->fc_j0.size());
+  a.mch_off = (t += c->fc_j1.size());
+  a.n_chunks = static_cast<int32_t>(c->fc_mem.size());
   a.stage = nxt;
   a.qidx = c->qidx;
   a.Rx = c->R;
@@ -486,21 +493,42 @@ nbody_status build_close(nbody_ctx *c) {
       return fail(c, NBODY_EINVAL, "a cluster of close pairs has more than %d bodies or %d pairs", nb::kCloseThreads,
                   nb::kCloseMaxPairs);
   }
+  const size_t nm = cs.mem_body.size();
+  for (size_t i = 0; i < nm; ++i)
+    if (cs.mp_off[i + 1] - cs.mp_off[i] > nb::kFarPartners)
+      return fail(c, NBODY_EINVAL, "a body has more than %d close partners", nb::kFarPartners);
+  // far-force chunks: each member's system in kFarChunk sources
+  std::vector<int32_t> fc_mem, fc_j0, fc_j1, mch_off{0};
+  for (size_t i = 0; i < nm; ++i) {
+    const int64_t p = cs.mem_body[i];
+    const int64_t sys = std::upper_bound(c->offsets.begin(), c->offsets.end(), p) - c->offsets.begin() - 1;
+    for (int64_t j = c->offsets[sys]; j < c->offsets[sys + 1]; j += nb::kFarChunk) {
+      fc_mem.push_back(static_cast<int32_t>(i));
+      fc_j0.push_back(static_cast<int32_t>(j));
+      fc_j1.push_back(static_cast<int32_t>(std::min<int64_t>(j + nb::kFarChunk, c->offsets[sys + 1])));
+    }
+    mch_off.push_back(static_cast<int32_t>(fc_mem.size()));
+  }
   dfree(c, c->close_tab);
   dfree(c, c->close_an);
   dfree(c, c->close_vh);
+  dfree(c, c->close_far);
   c->close_tab = nullptr;
-  c->close_an = c->close_vh = nullptr;
+  c->close_an = c->close_vh = c->close_far = nullptr;
   std::vector<int32_t> tab;
   for (const std::vector<int32_t> *v : {&cs.cl_off, &cs.cl_k, &cs.mem_body, &cs.pr_off, &cs.pr_a, &cs.pr_b,
-                                        &cs.mp_off, &cs.mp_pair})
+                                        &cs.mp_off, &cs.mp_pair, &fc_mem, &fc_j0, &fc_j1, &mch_off})
     tab.insert(tab.end(), v->begin(), v->end());
-  const size_t nm = cs.mem_body.size();
   nbody_status st;
   if ((st = dalloc(c, reinterpret_cast<void **>(&c->close_tab), sizeof(int32_t) * tab.size())) != NBODY_OK ||
       (st = dalloc(c, reinterpret_cast<void **>(&c->close_an), sizeof(double) * 3 * nm)) != NBODY_OK ||
-      (st = dalloc(c, reinterpret_cast<void **>(&c->close_vh), sizeof(double) * 3 * nm)) != NBODY_OK)
+      (st = dalloc(c, reinterpret_cast<void **>(&c->close_vh), sizeof(double) * 3 * nm)) != NBODY_OK ||
+      (st = dalloc(c, reinterpret_cast<void **>(&c->close_far), sizeof(double) * 3 * fc_mem.size())) != NBODY_OK)
     return st;
+  c->fc_mem = std::move(fc_mem);
+  c->fc_j0 = std::move(fc_j0);
+  c->fc_j1 = std::move(fc_j1);
+  c->mch_off = std::move(mch_off);
   NB_CUDA(c, cudaMemcpy(c->close_tab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice));
   c->close = std::move(cs);
   drop_graphs(c);  // graphs hold the previous tables' launches
@@ -616,7 +644,11 @@ nbody_status launch_steps(nbody_ctx *c, const State &s, int n, cudaStream_t st) 
     if (r != NBODY_OK) return r;
     // close pairs: finish this step for the cluster members and sub-cycle
     // them into the next stage
-    if (c->close_on) NB_CUDA(c, nb::launch_close(close_args(c, s, c->stage[1 - (i & 1)], 1), n_clusters(c), st, true));
+    if (c->close_on) {
+      const nb::CloseArgs ca = close_args(c, s, c->stage[1 - (i & 1)], 1);
+      NB_CUDA(c, nb::launch_close_far(ca, st, true));
+      NB_CUDA(c, nb::launch_close(ca, n_clusters(c), st, true));
+    }
   }
   return NBODY_OK;
 }
@@ -1232,8 +1264,11 @@ nbody_status nbody_step(nbody_ctx *c, int64_t n_steps) {
     NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 2, 0), c->stream));
   else  // Eq. 3 drift of the first step
     NB_CUDA(c, nb::launch_prep(c->o.precision, prep_args(c, s, 1, 0), c->stream));
-  if (c->close_on)  // the cluster members' first step starts from the state
-    NB_CUDA(c, nb::launch_close(close_args(c, s, c->stage[0], 0), n_clusters(c), c->stream, true));
+  if (c->close_on) {  // the cluster members' first step starts from the state
+    const nb::CloseArgs ca = close_args(c, s, c->stage[0], 0);
+    NB_CUDA(c, nb::launch_close_far(ca, c->stream, true));
+    NB_CUDA(c, nb::launch_close(ca, n_clusters(c), c->stream, true));
+  }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   NB_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
   if ((c->o.flags & NBODY_FLAG_NO_GRAPH) || cs != cudaStreamCaptureStatusNone) {

@@ -143,12 +143,18 @@ struct PrepArgs {
 // close_pairs.h (global member / pair indices).
 constexpr int kCloseThreads = 256;    // members per cluster at most (one thread each)
 constexpr int kCloseMaxPairs = 1024;  // pairs per cluster at most
+constexpr int kFarChunk = 4096;       // sources per CTA of the members' far-force kernel
+constexpr int kFarPartners = 64;      // close partners of one body at most
 struct CloseArgs {
   double *x, *y, *z, *vx, *vy, *vz;  // state (v written in complete mode)
-  const double *ax, *ay, *az;        // Eq. 1 at the state positions
   const double *m;
   double *an, *vh;                   // [3][n_mem]: a_near and the sub-cycle velocity of each member
+  double *far_part;                  // [3][n_chunks]: the members' far force, one chunk of sources each
   const int32_t *cl_off, *cl_k, *mem_body, *pr_off, *pr_a, *pr_b, *mp_off, *mp_pair;
+  // far-force chunks: chunk g sums member fc_mem[g]'s sources [fc_j0[g], fc_j1[g]);
+  // member i's chunks are mch_off[i] .. mch_off[i + 1]
+  const int32_t *fc_mem, *fc_j0, *fc_j1, *mch_off;
+  int32_t n_chunks;
   void *stage;                       // the next force launch's sources (FP64 double4 / mixed pair blocks)
   const int32_t *qidx;               // mixed: stage entry of each body
   double *Rx, *Ry, *Rz;              // mixed: FP64 staged positions
@@ -223,6 +229,7 @@ int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 bool force_config_supported(int precision, int threads, int ipt);
 size_t force_smem_bytes(int precision, int tj, int stages);  // dynamic smem of a ring of `stages` tiles
 cudaError_t launch_close(const CloseArgs &a, int n_clusters, cudaStream_t s, bool chained);
+cudaError_t launch_close_far(const CloseArgs &a, cudaStream_t s, bool chained);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);
 cudaError_t launch_energy_reduce(const ReduceArgs &a, cudaStream_t s);
 cudaError_t run_peaks(double *out);
