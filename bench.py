@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="also time N = 16,384 / 65,536 / 262,144 / 1,048,576")
     ap.add_argument("--dt-sweep", action="store_true",
                     help="also report the maximum energy drift against dt (FP64 and mixed, no moons)")
+    ap.add_argument("--close", type=float, default=0.0, metavar="THETA_C",
+                    help="with --only: time the path with close-encounter handling (close_omega_dt = THETA_C, "
+                         "substep_omega_dt = 0.05); no roofline (nbody_kernel_times covers plain Verlet)")
     ap.add_argument("--shard", action="store_true",
                     help="row shards instead of replicas: under torchrun every rank steps its own bodies of ONE "
                          "system (FP64, or --only mixed) and an all-gather per Verlet step exchanges the staged "
@@ -337,7 +340,8 @@ def run_ours(args):
         if (prec == "mixed" and args.no_mixed) or (args.only and prec != args.only):
             continue
         with torch.cuda.stream(stream):
-            b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, device=device)
+            b = nbody.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision=prec, device=device,
+                            close_omega_dt=args.close if args.only else 0.0, substep_omega_dt=0.05)
             forced = args.tiles_fp64 if (prec == "fp64" and args.tiles_fp64) else args.tiles
             if forced:
                 b.tiles = json.loads(forced)
@@ -365,6 +369,10 @@ def run_ours(args):
         }
         # Roofline of the dominant kernel: the same workload, each kernel of
         # `inner` Verlet steps bracketed alone by events on this stream.
+        if args.only and args.close > 0:
+            results[prec]["close"] = b.close_info()
+            b.close()
+            continue
         with torch.cuda.stream(stream):
             kt = b.kernel_times(inner)
         results[prec]["kernel_ms"] = kt
@@ -387,9 +395,13 @@ def run_ours(args):
         cpu = time_oracle(s, args.cpu_seconds)
     if rank == 0 and args.only:
         r = results[args.only]
-        print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
-                          "precision": args.only, "tiles": tiles.get(args.only),
-                          "roofline": roofline(r, args.only, None, peaks)}), flush=True)
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                "precision": args.only, "tiles": tiles.get(args.only)}
+        if "close" in r:
+            line["close_encounters"] = dict(r["close"], close_omega_dt=args.close, substep_omega_dt=0.05)
+        else:
+            line["roofline"] = roofline(r, args.only, None, peaks)
+        print(json.dumps(line), flush=True)
         return 0
     if rank == 0:
         f = results["fp64"]
