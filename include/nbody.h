@@ -136,6 +136,14 @@ typedef struct {
  * 8- or 16-CTA cluster up to 96 bodies, of a cooperative grid beyond,
  * unless this flag is set). */
 #define NBODY_FLAG_NO_SMALL 2
+/* FP64: use the force kernel that evaluates every ordered pair (p, j) on its
+ * own, instead of the default one that evaluates each pair once and applies
+ * it to both bodies (a_p += mu_j |d|^-3 d, a_j -= mu_p |d|^-3 d: Eq. 1 to
+ * rounding, 20 FP64 operations per two interactions instead of 32).  The
+ * default is used for systems of at most 65,536 bodies that are not row
+ * shards, when the systems hold at least 1.5 pairs of 64-body blocks per SM
+ * (about 1,200 bodies in one system; below that the other kernel is faster). */
+#define NBODY_FLAG_NO_SYM 4
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work
  * of a step -- every target block (at most threads * ipt bodies of one
@@ -202,6 +210,10 @@ nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
  * like nbody_init). */
 nbody_status nbody_reset(nbody_ctx *ctx);
 
+/* 1 in *on if the context's force launches evaluate each pair once (the FP64
+ * default, see NBODY_FLAG_NO_SYM), else 0.  HOST pointer. */
+nbody_status nbody_pair_once(const nbody_ctx *ctx, int32_t *on);
+
 /* Close-encounter handling (nbody_opts.close_omega_dt): the close pairs,
  * clusters, cluster members and the largest sub-step count of the current
  * set (all 0 when off).  Any output pointer may be NULL; HOST memory. */
@@ -250,7 +262,9 @@ nbody_status nbody_set_tiles(nbody_ctx *ctx, const nbody_tiles *t);
  * steps of the general (two-kernel) path, the one tiles shape, then the six
  * fastest again three times each over 4 x probe_steps steps, and keep the
  * one with the best time; a context whose nbody_step runs a single-launch
- * kernel keeps doing so.  The bound state is restored afterwards.  best (HOST, may be
+ * kernel keeps doing so.  (An FP64 context on the pair-once kernel, see
+ * NBODY_FLAG_NO_SYM, has no decomposition to choose: its current tiles are
+ * timed and kept.)  The bound state is restored afterwards.  best (HOST, may be
  * NULL) receives the winner, best_ms its time per step.  With a tune_cache
  * (nbody_opts) the winner is also written there (replacing the entry with
  * the same key); if that file cannot be written the call returns

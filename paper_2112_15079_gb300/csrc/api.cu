@@ -51,6 +51,9 @@ struct Work {
   int occ = 0;  // CTAs of the kernel that fit on one SM
   size_t smem = 0;
   int stages = nb::kStages;  // force kernel: ring depth
+  // FP64 force kernel with each pair once (sym.cu): block-pair items
+  int4 *sym_pairs = nullptr;
+  int n_sym = 0;
 };
 
 // Adjoint workspace, allocated by the first nbody_grad and kept.
@@ -355,7 +358,76 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   return st;
 }
 
+// The FP64 force kernel evaluates each pair once (sym.cu) when every system
+// has at most kSymMaxBodies bodies (its partial rows are [blocks][3][N]),
+// there are at least 1.5 block pairs per SM (with fewer, one CTA carries a
+// system's whole sum and the stream-K kernel is faster: measured on GB300,
+// 1,031 bodies / 153 pairs 60.8 against 55.3 us per step, 1,283 bodies /
+// 231 pairs 62.5 against 96.2), the context is not a row shard, and
+// NBODY_FLAG_NO_SYM is not set.
+bool sym_eligible(const nbody_ctx *c) {
+  if (c->o.precision != NBODY_FP64 || c->sh_world > 0 || (c->o.flags & NBODY_FLAG_NO_SYM)) return false;
+  int64_t pairs = 0;
+  for (int64_t s = 0; s < c->n_sys; ++s) {
+    const int64_t ns = c->offsets[s + 1] - c->offsets[s];
+    if (ns > nb::kSymMaxBodies) return false;
+    const int64_t nb = (ns + nb::kSymBlock - 1) / nb::kSymBlock;
+    pairs += nb * (nb + 1) / 2;
+  }
+  return 2 * pairs >= 3 * static_cast<int64_t>(c->nsm);
+}
+
+// Work tables of the pair-once FP64 kernel: the block pairs (I, J), I <= J,
+// of every system, off-diagonal items first; each body has one partial row
+// per block of its system.
+nbody_status build_sym_work(nbody_ctx *c, Work &wk) {
+  free_work(c, wk);
+  std::vector<int4> off_diag, diag;
+  int64_t rows = 1;
+  std::vector<uint16_t> nsl(static_cast<size_t>(c->N), 0);
+  for (int64_t s = 0; s < c->n_sys; ++s) {
+    const int64_t b = c->offsets[s], ns = c->offsets[s + 1] - b;
+    const int nb = static_cast<int>((ns + nb::kSymBlock - 1) / nb::kSymBlock);
+    rows = std::max<int64_t>(rows, nb);
+    for (int64_t p = b; p < b + ns; ++p) nsl[p] = static_cast<uint16_t>(nb);
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J)
+        (I == J ? diag : off_diag).push_back(make_int4(static_cast<int>(b), static_cast<int>(ns), I, J));
+  }
+  std::vector<int4> pairs = std::move(off_diag);
+  pairs.insert(pairs.end(), diag.begin(), diag.end());
+  const int occ = nb::force_sym_ctas_per_sm();
+  if (occ < 1) return fail(c, NBODY_ECUDA, "the pair-once FP64 kernel does not fit on an SM");
+  wk.nsl_rank = nsl;
+  wk.plan_off = c->tgt_off;
+  wk.plan_soff = c->tgt_soff;
+  wk.n_sym = static_cast<int>(pairs.size());
+  wk.rows = static_cast<int>(rows);
+  wk.grid = static_cast<int>(std::min<int64_t>(pairs.size(), static_cast<int64_t>(c->nsm) * occ));
+  wk.occ = occ;
+  wk.n_dyn = 0;
+  auto upload = [&]() -> nbody_status {
+    nbody_status st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.sym_pairs), sizeof(int4) * pairs.size())) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * static_cast<size_t>(c->N))) != NBODY_OK)
+      return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
+        NBODY_OK)
+      return st;
+    NB_CUDA(c, cudaMemset(wk.dyn_ctr, 0, sizeof(int32_t) * 2));
+    NB_CUDA(c, cudaMemcpy(wk.sym_pairs, pairs.data(), sizeof(int4) * pairs.size(), cudaMemcpyHostToDevice));
+    return upload_nsl(c, wk);
+  };
+  const nbody_status st = upload();
+  if (st != NBODY_OK) free_work(c, wk);
+  return st;
+}
+
 void free_work(nbody_ctx *c, Work &w) {
+  dfree(c, w.sym_pairs);
+  w.sym_pairs = nullptr;
+  w.n_sym = 0;
   dfree(c, w.blks);
   dfree(c, w.segs);
   dfree(c, w.seg_off);
@@ -370,6 +442,15 @@ void free_work(nbody_ctx *c, Work &w) {
 // and tables, which stay a matching pair.
 nbody_status build_items(nbody_ctx *c, const nbody_tiles &t) {
   drop_graphs(c);
+  if (sym_eligible(c)) {  // the tiles stay the context's, for nbody_get_tiles; this kernel has none
+    Work nw;
+    const nbody_status st = build_sym_work(c, nw);
+    if (st != NBODY_OK) return st;
+    free_work(c, c->fw);
+    c->fw = nw;
+    c->tiles = t;
+    return NBODY_OK;
+  }
   // The deepest ring (kMaxStages down to kStages tiles) at which the CTAs
   // per SM the tiles ask for still fit: a deeper ring lets the warps of a
   // CTA drift further apart and the next segment's tiles load earlier.
@@ -601,6 +682,24 @@ nb::RkArgs rk_args(nbody_ctx *c, const State &s, const void *cur, void *nxt, int
   return a;
 }
 
+// The force launch of one step from the staged sources `cur`.
+nbody_status launch_force_kernel(nbody_ctx *c, const void *cur, cudaStream_t st, bool chained) {
+  if (c->fw.sym_pairs) {
+    nb::SymArgs a{};
+    a.cur = static_cast<const double4_32a *>(cur);
+    a.partial = c->fw.partial;
+    a.pairs = c->fw.sym_pairs;
+    a.n_pairs = c->fw.n_sym;
+    a.ctr = c->fw.dyn_ctr;
+    a.N = c->N;
+    NB_CUDA(c, nb::launch_force_sym(a, c->fw.grid, st, chained));
+    return NBODY_OK;
+  }
+  NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
+                              force_args(c, cur), st, chained));
+  return NBODY_OK;
+}
+
 // One Verlet step (or, kModeForce, only a = Eq. 1) from the staged sources
 // `cur`, staging the next positions into `nxt`: the force kernel, then the
 // per-body Verlet kernel, chained.
@@ -611,8 +710,8 @@ nbody_status launch_one_step(nbody_ctx *c, const State &s, const void *cur, void
   const bool chained = ev == nullptr;
   if (c->o.precision == NBODY_MIXED) NB_CUDA(c, nb::launch_boxes(cur, c->n_stage / 2, c->boxes, st, chained));
   if (ev) NB_CUDA(c, cudaEventRecord(ev[0], st));
-  NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
-                              force_args(c, cur), st, chained));
+  nbody_status fs;
+  if ((fs = launch_force_kernel(c, cur, st, chained)) != NBODY_OK) return fs;
   if (ev) NB_CUDA(c, cudaEventRecord(ev[1], st));
   NB_CUDA(c, nb::launch_verlet(c->o.precision, verlet_args(c, s, cur, nxt, mode), st, chained));
   if (ev) NB_CUDA(c, cudaEventRecord(ev[2], st));
@@ -627,8 +726,8 @@ nbody_status launch_rk4_step(nbody_ctx *c, const State &s, cudaStream_t st) {
     const void *cur = c->stage[k & 1];
     void *nxt = c->stage[1 - (k & 1)];
     if (c->o.precision == NBODY_MIXED) NB_CUDA(c, nb::launch_boxes(cur, c->n_stage / 2, c->boxes, st, true));
-    NB_CUDA(c, nb::launch_force(c->o.precision, c->tiles.threads, c->tiles.ipt, c->fw.grid, c->fw.smem,
-                                force_args(c, cur), st, true));
+    nbody_status fs;
+    if ((fs = launch_force_kernel(c, cur, st, true)) != NBODY_OK) return fs;
     NB_CUDA(c, nb::launch_rk_stage(c->o.precision, rk_args(c, s, cur, nxt, 2 + k), st, true));
   }
   return NBODY_OK;
@@ -1091,7 +1190,8 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
   if (o->precision != NBODY_FP64 && o->precision != NBODY_MIXED)
     return fail(nullptr, NBODY_EINVAL, "unknown precision %d", o->precision);
   if (o->ckpt_every < 0) return fail(nullptr, NBODY_EINVAL, "ckpt_every must be >= 0");
-  if (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL)) return fail(nullptr, NBODY_EINVAL, "unknown flags");
+  if (o->flags & ~(NBODY_FLAG_NO_GRAPH | NBODY_FLAG_NO_SMALL | NBODY_FLAG_NO_SYM))
+    return fail(nullptr, NBODY_EINVAL, "unknown flags");
   if (o->integrator != NBODY_VERLET && o->integrator != NBODY_RK4 && o->integrator != NBODY_LEAPFROG)
     return fail(nullptr, NBODY_EINVAL, "unknown integrator %d", o->integrator);
   if (!(o->close_omega_dt >= 0.0) || !std::isfinite(o->close_omega_dt))
@@ -1324,6 +1424,12 @@ nbody_status nbody_reset(nbody_ctx *c) {
   return refresh(c);
 }
 
+nbody_status nbody_pair_once(const nbody_ctx *c, int32_t *on) {
+  if (!c || !on) return NBODY_EINVAL;
+  *on = c->fw.sym_pairs != nullptr ? 1 : 0;
+  return NBODY_OK;
+}
+
 nbody_status nbody_close_info(const nbody_ctx *c, int64_t *n_pairs, int32_t *n_clusters, int32_t *n_members,
                               int32_t *k_max) {
   if (!c) return NBODY_EINVAL;
@@ -1459,6 +1565,8 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
           t.jsplit = js;
           cand.push_back(t);
         }
+  // the pair-once FP64 kernel has no tiles to choose: time the current ones only
+  if (sym_eligible(c)) cand.assign(1, c->tiles);
   cudaEvent_t e0, e1;
   NB_CUDA(c, cudaEventCreate(&e0));
   NB_CUDA(c, cudaEventCreate(&e1));

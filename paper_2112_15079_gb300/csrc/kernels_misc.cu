@@ -147,7 +147,9 @@ __device__ __forceinline__ void pair_add(T &hi, T &lo, T vhi, T vlo) {
 
 // Phase A of the per-body kernels: body p's force partials (rows 0..rows-1)
 // summed in a fixed order by L = VerletShape<PREC>::kLanes threads; the sum,
-// an unevaluated (hi, lo) pair per component, ends in lane 0.
+// an unevaluated (hi, lo) pair per component, ends in lane 0.  FP64 adds
+// each group of U rows plainly before it enters the pair (see below); the
+// mixed path feeds every row through the pair.
 template <int PREC, typename T>
 __device__ __forceinline__ void sum_partial_rows(const double *partial, int rows, size_t N, int p, int lane, T &sx,
                                                  T &ex, T &sy, T &ey, T &sz, T &ez) {
@@ -174,12 +176,31 @@ __device__ __forceinline__ void sum_partial_rows(const double *partial, int rows
         vz_[u] = __ldg(row + 2 * N + p);
       }
     }
+    if constexpr (PREC == 0) {
+      // FP64: the (up to) U loaded rows added plainly in row order, then the
+      // group sum into the (hi, lo) pair: one TwoSum per U rows (the
+      // pair-once kernel leaves a row per 64-body block, ~160 per body at
+      // N = 10,425; each row is a sum of at most 128 terms).
+      E gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (c0 + u * L < rows) {
-        add(sx, ex, vx_[u]);
-        add(sy, ey, vy_[u]);
-        add(sz, ez, vz_[u]);
+      for (int u = 0; u < U; ++u) {
+        if (c0 + u * L < rows) {
+          gx += vx_[u];
+          gy += vy_[u];
+          gz += vz_[u];
+        }
+      }
+      add(sx, ex, gx);
+      add(sy, ey, gy);
+      add(sz, ez, gz);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c0 + u * L < rows) {
+          add(sx, ex, vx_[u]);
+          add(sy, ey, vy_[u]);
+          add(sz, ez, vz_[u]);
+        }
       }
     }
   }

@@ -138,6 +138,20 @@ struct PrepArgs {
   double G, dt, half_dt2;
 };
 
+// FP64 force kernel with each pair once (sym.cu): work items are block
+// pairs (I, J), I <= J, of kSymBlock bodies of one system.
+constexpr int kSymBlock = 64;
+constexpr int kSymThreads = 64;        // two warps: one 32-body tile of block I each
+constexpr int kSymMaxBodies = 65536;   // per system (the partial rows are [blocks][3][N])
+struct SymArgs {
+  const double4_32a *cur;  // staged sources (x, y, z, G m) per body
+  double *partial;         // [blocks][3][N]: row J of a body of block I holds block J's pull
+  const int4 *pairs;       // (first body of the system, its bodies, I, J)
+  int32_t n_pairs;
+  int32_t *ctr;            // [2]: next item, CTAs done (the last one resets both)
+  int32_t N;
+};
+
 // Close-encounter handling (close.cu): clusters of close pairs sub-cycled in
 // FP64 after each step's Verlet kernel.  Members and pairs as CloseSet in
 // close_pairs.h (global member / pair indices).
@@ -228,6 +242,8 @@ cudaError_t force_set_smem(int precision, int threads, int ipt, size_t smem);  /
 int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 bool force_config_supported(int precision, int threads, int ipt);
 size_t force_smem_bytes(int precision, int tj, int stages);  // dynamic smem of a ring of `stages` tiles
+cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool chained);
+int force_sym_ctas_per_sm();
 cudaError_t launch_close(const CloseArgs &a, int n_clusters, cudaStream_t s, bool chained);
 cudaError_t launch_close_far(const CloseArgs &a, cudaStream_t s, bool chained);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);

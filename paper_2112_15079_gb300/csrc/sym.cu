@@ -1,0 +1,175 @@
+// Eq. 1 force kernel of the FP64 path, each pair once (Newton's third law).
+//
+// The FP64 pipe bounds this path, and one interaction of Eq. 1 takes 16 FP64
+// operations (3 differences, 3 for |d|^2, 6 for |d|^-3 from the MUFU seed and
+// its series, the product with mu_j, 3 accumulations).  The pair (p, j) and
+// its reaction share the first 12 of them: evaluating each unordered pair
+// once and accumulating both terms -- a_p += mu_j |d|^-3 d and
+// a_j -= mu_p |d|^-3 d -- takes 20 operations for two interactions.
+//
+// Decomposition: each system's bodies are cut into blocks of 64 (two warp
+// tiles of 32); the work items are the block pairs (I, J), I <= J, handed
+// out by a counter (off-diagonal pairs first, the cheaper diagonal ones
+// last).  A CTA of two warps takes an item: warp w keeps the 32 bodies of
+// tile w of block I in registers and, for each tile t of block J, loads its
+// 32 bodies as the "sources" and rotates them (positions, masses and their
+// reaction sums) once around the warp with shuffles: after 32 steps every
+// source has met every target once and its reaction sum is back in its own
+// lane, with no FP64 reduction.  A tile paired with itself (diagonal items)
+// rotates 16 steps (the 16th for the target side only: lanes L and L + 16
+// meet twice).  The two warps' reaction sums for a J tile are added in a
+// fixed order in shared memory.
+//
+// Output: block I's sums go to partial row J of its bodies, block J's to row
+// I (a diagonal item adds both into row I); the Verlet kernel adds a body's
+// rows 0 .. blocks-1 in order, so the result does not depend on which CTA
+// took which item.
+#include "nbody_dev.cuh"
+
+namespace nb {
+
+namespace {
+
+__device__ __forceinline__ double4_32a sym_load(const double4_32a *cur, int64_t sb, int il, int ns, double pad) {
+  if (il < ns) return cur[sb + il];
+  // outside the system: inert (massless, far away, distinct per lane)
+  return make_double4_32a(pad, 0.0, 0.0, 0.0);
+}
+
+__device__ __forceinline__ void sym_pair(double xi, double yi, double zi, double mi, double xj, double yj, double zj,
+                                         double mj, double &ax, double &ay, double &az, double &bx, double &by,
+                                         double &bz, bool react) {
+  const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+  const double s3 = inv_r3(fma(dz, dz, fma(dy, dy, dx * dx)));
+  const double fi = mj * s3;
+  ax = fma(fi, dx, ax);
+  ay = fma(fi, dy, ay);
+  az = fma(fi, dz, az);
+  if (react) {
+    const double fj = mi * s3;
+    bx = fma(-fj, dx, bx);
+    by = fma(-fj, dy, by);
+    bz = fma(-fj, dz, bz);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kSymThreads) force_sym_kernel(const SymArgs a) {
+  __shared__ double s_b[2][2][3][32];  // reaction sums [warp][J tile][component][lane]
+  __shared__ int s_item;
+  grid_dependency_wait();    // staged sources of this step are complete
+  grid_dependency_launch();  // the Verlet kernel may start launching
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const size_t N = static_cast<size_t>(a.N);
+  for (;;) {
+    __syncthreads();  // the previous item's shared sums are consumed
+    if (tid == 0) s_item = atomicAdd(a.ctr, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.n_pairs) break;
+    const int4 pr = a.pairs[item];  // (first body of the system, its bodies, block I, block J)
+    const int64_t sb = pr.x;
+    const int ns = pr.y, I = pr.z, J = pr.w;
+    const double4_32a pi = sym_load(a.cur, sb, I * kSymBlock + w * 32 + lane, ns, 1e15 * (lane + 1));
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int t = 0; t < 2; ++t) {
+      double bx = 0.0, by = 0.0, bz = 0.0;
+      if (I == J && t < w) {  // tile pair (w, t) is (t, w), done by warp t
+      } else {
+        const double4_32a pj0 = sym_load(a.cur, sb, J * kSymBlock + t * 32 + lane, ns, 1e15 * (lane + 1) + 5e14);
+        double xj = pj0.x, yj = pj0.y, zj = pj0.z, mj = pj0.w;
+        auto rotate = [&]() {
+          const int src = (lane + 1) & 31;
+          xj = __shfl_sync(0xffffffffu, xj, src);
+          yj = __shfl_sync(0xffffffffu, yj, src);
+          zj = __shfl_sync(0xffffffffu, zj, src);
+          mj = __shfl_sync(0xffffffffu, mj, src);
+          bx = __shfl_sync(0xffffffffu, bx, src);
+          by = __shfl_sync(0xffffffffu, by, src);
+          bz = __shfl_sync(0xffffffffu, bz, src);
+        };
+        if (I == J && t == w) {  // a tile with itself: offsets 1..15 both ways, 16 one way
+#pragma unroll 4
+          for (int k = 1; k <= 16; ++k) {
+            rotate();
+            sym_pair(pi.x, pi.y, pi.z, pi.w, xj, yj, zj, mj, ax, ay, az, bx, by, bz, k < 16);
+          }
+          // lane L holds the sums of lane L + 16: hand them back
+          const int back = (lane + 16) & 31;
+          bx = __shfl_sync(0xffffffffu, bx, back);
+          by = __shfl_sync(0xffffffffu, by, back);
+          bz = __shfl_sync(0xffffffffu, bz, back);
+        } else {
+#pragma unroll 4
+          for (int k = 0; k < 32; ++k) {
+            sym_pair(pi.x, pi.y, pi.z, pi.w, xj, yj, zj, mj, ax, ay, az, bx, by, bz, true);
+            rotate();
+          }
+        }
+      }
+      s_b[w][t][0][lane] = bx;
+      s_b[w][t][1][lane] = by;
+      s_b[w][t][2][lane] = bz;
+    }
+    __syncthreads();
+    // thread (w, lane): body J*64 + tid of block J (reaction sums of both
+    // warps, warp 0 first) and body I*64 + tid of block I (its own sums)
+    const int jl = J * kSymBlock + tid, il = I * kSymBlock + tid;
+    double rj[3];
+    for (int d = 0; d < 3; ++d) rj[d] = s_b[0][w][d][lane] + s_b[1][w][d][lane];
+    if (I == J) {
+      if (il < ns) {
+        double *row = a.partial + static_cast<size_t>(I) * 3 * N;
+        row[sb + il] = ax + rj[0];
+        row[N + sb + il] = ay + rj[1];
+        row[2 * N + sb + il] = az + rj[2];
+      }
+    } else {
+      if (il < ns) {
+        double *row = a.partial + static_cast<size_t>(J) * 3 * N;
+        row[sb + il] = ax;
+        row[N + sb + il] = ay;
+        row[2 * N + sb + il] = az;
+      }
+      if (jl < ns) {
+        double *row = a.partial + static_cast<size_t>(I) * 3 * N;
+        row[sb + jl] = rj[0];
+        row[N + sb + jl] = rj[1];
+        row[2 * N + sb + jl] = rj[2];
+      }
+    }
+  }
+  // The last CTA out resets the item counter for the next launch.
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.ctr + 1, 1) == static_cast<int>(gridDim.x) - 1) {
+      atomicExch(a.ctr, 0);
+      atomicExch(a.ctr + 1, 0);
+    }
+  }
+}
+
+cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool chained) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kSymThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, force_sym_kernel, a);
+}
+
+int force_sym_ctas_per_sm() {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_sym_kernel, kSymThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
+}  // namespace nb

@@ -27,6 +27,7 @@ NBODY_OK, NBODY_EINVAL, NBODY_ENOMEM, NBODY_ECUDA, NBODY_ENONFINITE, NBODY_ETIME
 NBODY_FP64, NBODY_MIXED = 0, 1
 NBODY_FLAG_NO_GRAPH = 1
 NBODY_FLAG_NO_SMALL = 2
+NBODY_FLAG_NO_SYM = 4
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT"}
 PRECISIONS = {"fp64": NBODY_FP64, "mixed": NBODY_MIXED}
 NBODY_VERLET, NBODY_RK4, NBODY_LEAPFROG = 0, 1, 2
@@ -57,6 +58,7 @@ _SIGS = {
     "nbody_accel": (_S, [_P, _P, _P, _P]),
     "nbody_reset": (_S, [_P]),
     "nbody_reorder": (_S, [_P]),
+    "nbody_pair_once": (_S, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "nbody_close_info": (_S, [_P, ctypes.POINTER(ctypes.c_int64)] + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "nbody_energy": (_S, [_P, ctypes.POINTER(ctypes.c_double)]),
     "nbody_grad": (_S, [_P, ctypes.c_int64, _P, _P, _P, _P, _P]),
@@ -135,7 +137,7 @@ class NBody:
     def __init__(self, r, v, m, offsets=None, *, G: float, dt: float, precision: str = "fp64",
                  ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None,
                  integrator: str = "verlet", tune_cache: str | None = None, close_omega_dt: float = 0.0,
-                 substep_omega_dt: float = 0.05):
+                 substep_omega_dt: float = 0.05, pair_once: bool = True):
         torch = _torch()
         device = torch.device(device if device is not None else "cuda")
         self.device = device
@@ -154,7 +156,8 @@ class NBody:
         self.G, self.dt, self.precision, self.integrator = float(G), float(dt), precision, integrator
         self._stream = stream if stream is not None else torch.cuda.current_stream(device)
         opts = nbody_opts(G=self.G, dt=self.dt, precision=PRECISIONS[precision], ckpt_every=int(ckpt_every),
-                          flags=(0 if graphs else NBODY_FLAG_NO_GRAPH) | (0 if small else NBODY_FLAG_NO_SMALL),
+                          flags=(0 if graphs else NBODY_FLAG_NO_GRAPH) | (0 if small else NBODY_FLAG_NO_SMALL)
+                          | (0 if pair_once else NBODY_FLAG_NO_SYM),
                           integrator=INTEGRATORS[integrator],
                           tune_cache=None if tune_cache is None else os.fsencode(tune_cache),
                           close_omega_dt=float(close_omega_dt), substep_omega_dt=float(substep_omega_dt))
@@ -186,6 +189,14 @@ class NBody:
 
     def reset(self) -> None:
         check(nbody_reset(self._ctx), self._ctx)
+
+    @property
+    def pair_once(self) -> bool:
+        """Whether the force launches evaluate each pair once (the FP64
+        default for systems of at most 65,536 bodies)."""
+        on = ctypes.c_int32()
+        check(nbody_pair_once(self._ctx, ctypes.byref(on)), self._ctx)
+        return bool(on.value)
 
     def close_info(self) -> dict:
         """Close-encounter handling: close pairs, clusters, cluster members
