@@ -171,3 +171,48 @@ def test_entry_points_without_close_pairs_refuse_them(nb):
     with pytest.raises(nb.NBodyError):
         b.kernel_times(2)
     b.close()
+
+
+def test_batched_systems_are_handled_each_on_its_own(nb):
+    """Two 131-body systems in one context: the close pairs never cross
+    systems, and each system's trajectory equals the oracle's run alone."""
+    s1 = inputs.solar_system(131)
+    s2 = inputs.solar_system(131, seed=inputs.BASE_SEED + 7)
+    off, r, v, m = inputs.concat([s1, s2])
+    for precision in ("fp64", "mixed"):
+        b = nb.NBody(r, v, m, off, G=s1.G, dt=s1.dt, precision=precision, close_omega_dt=TC, substep_omega_dt=TS)
+        info = b.close_info()
+        b.step(20)
+        b.sync()
+        st = b.state.cpu().numpy()
+        b.close()
+        pairs = 0
+        for k, sy in enumerate((s1, s2)):
+            ro, _, _, npairs, _ = oracle.respa(sy.G, sy.dt, 20, sy.r, sy.v, sy.m, TC, TS)
+            pairs += npairs
+            assert np.abs(st[:3, off[k]:off[k + 1]] - ro).max() <= 1e-8
+        assert info["pairs"] == pairs
+
+
+def test_reset_rebuilds_the_close_set(nb):
+    """After nbody_reset to another state the context steps bitwise like a
+    new one built on that state (the close pairs of the new positions)."""
+    s1 = inputs.solar_system(131)
+    s2 = inputs.solar_system(131, seed=inputs.BASE_SEED + 3)
+    import torch
+    b = nb.NBody(s1.r, s1.v, s1.m, G=s1.G, dt=s1.dt, precision="fp64", close_omega_dt=TC, substep_omega_dt=TS)
+    b.step(5)
+    b.state[0:3].copy_(torch.as_tensor(s2.r))
+    b.state[3:6].copy_(torch.as_tensor(s2.v))
+    b.m.copy_(torch.as_tensor(s2.m))
+    b.reset()
+    info = b.close_info()
+    b.step(10)
+    b.sync()
+    c = nb.NBody(s2.r, s2.v, s2.m, G=s2.G, dt=s2.dt, precision="fp64", close_omega_dt=TC, substep_omega_dt=TS)
+    assert c.close_info() == info
+    c.step(10)
+    c.sync()
+    assert np.array_equal(b.state.cpu().numpy(), c.state.cpu().numpy())
+    b.close()
+    c.close()
