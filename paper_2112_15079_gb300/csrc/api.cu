@@ -377,10 +377,10 @@ bool sym_eligible(const nbody_ctx *c) {
   return 2 * pairs >= 3 * static_cast<int64_t>(c->nsm);
 }
 
-// Work tables of the pair-once FP64 kernel: the block pairs (I, J), I <= J,
+// Work tables of the pair-once FP64 kernels: the block pairs (I, J), I <= J,
 // of every system, off-diagonal items first; each body has one partial row
-// per block of its system.
-nbody_status build_sym_work(nbody_ctx *c, Work &wk) {
+// per block of its system (row_doubles values each: 3 force, 4 VJP).
+nbody_status build_sym_work(nbody_ctx *c, Work &wk, int row_doubles = 3) {
   free_work(c, wk);
   std::vector<int4> off_diag, diag;
   int64_t rows = 1;
@@ -412,8 +412,8 @@ nbody_status build_sym_work(nbody_ctx *c, Work &wk) {
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.nsl), sizeof(uint16_t) * static_cast<size_t>(c->N))) != NBODY_OK)
       return st;
     if ((st = dalloc(c, reinterpret_cast<void **>(&wk.dyn_ctr), sizeof(int32_t) * 2)) != NBODY_OK) return st;
-    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial), sizeof(double) * 3 * static_cast<size_t>(rows) * c->N)) !=
-        NBODY_OK)
+    if ((st = dalloc(c, reinterpret_cast<void **>(&wk.partial),
+                     sizeof(double) * row_doubles * static_cast<size_t>(rows) * c->N)) != NBODY_OK)
       return st;
     NB_CUDA(c, cudaMemset(wk.dyn_ctr, 0, sizeof(int32_t) * 2));
     NB_CUDA(c, cudaMemcpy(wk.sym_pairs, pairs.data(), sizeof(int4) * pairs.size(), cudaMemcpyHostToDevice));
@@ -1107,11 +1107,15 @@ nbody_status ensure_adjoint(nbody_ctx *c, int64_t n_steps) {
     t.tj = kVjpTile;
     t.jsplit = 0;
     t.ctas_per_sm = 32;
-    const size_t smem = nb::vjp_smem_bytes(prec, t.tj);
-    int occ = 0;
-    NB_CUDA(c, nb::vjp_prepare(prec, smem, &occ));
-    if ((st = build_work(c, A.vj, t, occ, 4)) != NBODY_OK) return st;
-    A.vj.smem = smem;
+    if (sym_eligible(c)) {  // FP64: the VJP evaluates each pair once too
+      if ((st = build_sym_work(c, A.vj, 4)) != NBODY_OK) return st;
+    } else {
+      const size_t smem = nb::vjp_smem_bytes(prec, t.tj);
+      int occ = 0;
+      NB_CUDA(c, nb::vjp_prepare(prec, smem, &occ));
+      if ((st = build_work(c, A.vj, t, occ, 4)) != NBODY_OK) return st;
+      A.vj.smem = smem;
+    }
     const size_t wbytes = (prec == NBODY_FP64 ? 32 : 16) * static_cast<size_t>(c->n_stage);
     if ((st = dalloc(c, reinterpret_cast<void **>(&A.rho), sizeof(double) * 3 * N)) != NBODY_OK) return st;
     if ((st = dalloc(c, reinterpret_cast<void **>(&A.nu), sizeof(double) * 3 * N)) != NBODY_OK) return st;
@@ -1752,9 +1756,21 @@ nbody_status nbody_grad(nbody_ctx *c, int64_t n_steps, const double *dL_dr_T, co
   vj.N = c->N;
   vj.tj = kVjpTile;
   auto product = [&](const void *pos, int mode) -> nbody_status {
-    vj.pos = pos;
-    vj.stall = ++c->wait_seq == c->stall_at ? 1 : 0;
-    NB_CUDA(c, nb::launch_vjp(prec, A.vj.grid, A.vj.smem, vj, c->stream));
+    if (A.vj.sym_pairs) {  // pair-once (FP64): no bounded wait to stall
+      nb::VjpSymArgs vs{};
+      vs.pos = static_cast<const double4_32a *>(pos);
+      vs.w = static_cast<const double4_32a *>(A.w);
+      vs.partial = A.vj.partial;
+      vs.pairs = A.vj.sym_pairs;
+      vs.n_pairs = A.vj.n_sym;
+      vs.ctr = A.vj.dyn_ctr;
+      vs.N = c->N;
+      NB_CUDA(c, nb::launch_vjp_sym(vs, A.vj.grid, c->stream));
+    } else {
+      vj.pos = pos;
+      vj.stall = ++c->wait_seq == c->stall_at ? 1 : 0;
+      NB_CUDA(c, nb::launch_vjp(prec, A.vj.grid, A.vj.smem, vj, c->stream));
+    }
     ad.mode = mode;
     NB_CUDA(c, nb::launch_adjoint(prec, ad, c->stream));
     return NBODY_OK;

@@ -152,6 +152,18 @@ struct SymArgs {
   int32_t N;
 };
 
+// The adjoint's VJP with each pair once (FP64, sym.cu): the same items,
+// rows of 4 values per body (J^T w and the mass sum).
+struct VjpSymArgs {
+  const double4_32a *pos;  // positions staged by the forward pass (x, y, z, G m)
+  const double4_32a *w;    // w per body (x, y, z, -)
+  double *partial;         // [blocks][4][N]
+  const int4 *pairs;
+  int32_t n_pairs;
+  int32_t *ctr;
+  int32_t N;
+};
+
 // Close-encounter handling (close.cu): clusters of close pairs sub-cycled in
 // FP64 after each step's Verlet kernel.  Members and pairs as CloseSet in
 // close_pairs.h (global member / pair indices).
@@ -243,6 +255,7 @@ int force_max_ctas_per_sm(int precision, int threads, int ipt, size_t smem);
 bool force_config_supported(int precision, int threads, int ipt);
 size_t force_smem_bytes(int precision, int tj, int stages);  // dynamic smem of a ring of `stages` tiles
 cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool chained);
+cudaError_t launch_vjp_sym(const VjpSymArgs &a, int grid, cudaStream_t s);
 int force_sym_ctas_per_sm();
 cudaError_t launch_close(const CloseArgs &a, int n_clusters, cudaStream_t s, bool chained);
 cudaError_t launch_close_far(const CloseArgs &a, cudaStream_t s, bool chained);

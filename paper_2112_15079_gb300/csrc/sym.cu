@@ -150,6 +150,130 @@ __global__ void __launch_bounds__(kSymThreads) force_sym_kernel(const SymArgs a)
   }
 }
 
+// The adjoint's vector-Jacobian product of Eq. 1 (see vjp.cu), each pair
+// once.  For the pair (q, j), d = r_j - r_q, s3 = |d|^-3, s5 = |d|^-5 and
+// u = mu_q w_j - mu_j w_q, the q term s3 u - 3 s5 (d.u) d changes sign
+// under q <-> j (K(d) is even in d, u is odd), and the mass terms are
+// s3 (w_j . d) for q and -s3 (w_q . d) for j.  Rows hold 4 values per body
+// (the three components and the mass sum), block I's sums in row J, block
+// J's in row I, as in force_sym_kernel.
+__global__ void __launch_bounds__(kSymThreads) vjp_sym_kernel(const VjpSymArgs a) {
+  __shared__ double s_b[2][2][4][32];  // reaction sums [warp][J tile][component][lane]
+  __shared__ int s_item;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const size_t N = static_cast<size_t>(a.N);
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(a.ctr, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.n_pairs) break;
+    const int4 pr = a.pairs[item];
+    const int64_t sb = pr.x;
+    const int ns = pr.y, I = pr.z, J = pr.w;
+    const int iq = I * kSymBlock + w * 32 + lane;
+    const double4_32a pq = sym_load(a.pos, sb, iq, ns, 1e15 * (lane + 1));
+    const double4_32a wq = iq < ns ? a.w[sb + iq] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = 0; t < 2; ++t) {
+      double b[4] = {0.0, 0.0, 0.0, 0.0};
+      if (!(I == J && t < w)) {  // tile pair (w, t) with t < w of a diagonal item is (t, w), warp t's
+        const int ij = J * kSymBlock + t * 32 + lane;
+        const double4_32a pj0 = sym_load(a.pos, sb, ij, ns, 1e15 * (lane + 1) + 5e14);
+        const double4_32a wj0 = ij < ns ? a.w[sb + ij] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        double xj = pj0.x, yj = pj0.y, zj = pj0.z, mj = pj0.w, wjx = wj0.x, wjy = wj0.y, wjz = wj0.z;
+        auto rotate = [&]() {
+          const int src = (lane + 1) & 31;
+          xj = __shfl_sync(0xffffffffu, xj, src);
+          yj = __shfl_sync(0xffffffffu, yj, src);
+          zj = __shfl_sync(0xffffffffu, zj, src);
+          mj = __shfl_sync(0xffffffffu, mj, src);
+          wjx = __shfl_sync(0xffffffffu, wjx, src);
+          wjy = __shfl_sync(0xffffffffu, wjy, src);
+          wjz = __shfl_sync(0xffffffffu, wjz, src);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) b[c] = __shfl_sync(0xffffffffu, b[c], src);
+        };
+        auto pair = [&](bool react) {
+          const double dx = xj - pq.x, dy = yj - pq.y, dz = zj - pq.z;
+          const double y = inv_r1(fma(dz, dz, fma(dy, dy, dx * dx)));
+          const double y2 = y * y;
+          const double s3 = y * y2;
+          const double s5 = s3 * y2;
+          const double ux = fma(-mj, wq.x, pq.w * wjx);
+          const double uy = fma(-mj, wq.y, pq.w * wjy);
+          const double uz = fma(-mj, wq.z, pq.w * wjz);
+          const double t3 = 3.0 * s5 * fma(dz, uz, fma(dy, uy, dx * ux));
+          const double tx = fma(-t3, dx, s3 * ux), ty = fma(-t3, dy, s3 * uy), tz = fma(-t3, dz, s3 * uz);
+          acc[0] += tx;
+          acc[1] += ty;
+          acc[2] += tz;
+          acc[3] = fma(s3, fma(wjz, dz, fma(wjy, dy, wjx * dx)), acc[3]);
+          if (react) {
+            b[0] -= tx;
+            b[1] -= ty;
+            b[2] -= tz;
+            b[3] = fma(-s3, fma(wq.z, dz, fma(wq.y, dy, wq.x * dx)), b[3]);
+          }
+        };
+        if (I == J && t == w) {
+#pragma unroll 2
+          for (int k = 1; k <= 16; ++k) {
+            rotate();
+            pair(k < 16);
+          }
+          const int back = (lane + 16) & 31;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) b[c] = __shfl_sync(0xffffffffu, b[c], back);
+        } else {
+#pragma unroll 2
+          for (int k = 0; k < 32; ++k) {
+            pair(true);
+            rotate();
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s_b[w][t][c][lane] = b[c];
+    }
+    __syncthreads();
+    const int jl = J * kSymBlock + tid, il = I * kSymBlock + tid;
+    double rj[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) rj[c] = s_b[0][w][c][lane] + s_b[1][w][c][lane];
+    if (I == J) {
+      if (il < ns) {
+        double *row = a.partial + static_cast<size_t>(I) * 4 * N;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) row[c * N + sb + il] = acc[c] + rj[c];
+      }
+    } else {
+      if (il < ns) {
+        double *row = a.partial + static_cast<size_t>(J) * 4 * N;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) row[c * N + sb + il] = acc[c];
+      }
+      if (jl < ns) {
+        double *row = a.partial + static_cast<size_t>(I) * 4 * N;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) row[c * N + sb + jl] = rj[c];
+      }
+    }
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.ctr + 1, 1) == static_cast<int>(gridDim.x) - 1) {
+      atomicExch(a.ctr, 0);
+      atomicExch(a.ctr + 1, 0);
+    }
+  }
+}
+
+cudaError_t launch_vjp_sym(const VjpSymArgs &a, int grid, cudaStream_t s) {
+  vjp_sym_kernel<<<grid, kSymThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool chained) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

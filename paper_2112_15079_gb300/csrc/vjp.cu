@@ -302,12 +302,19 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjArgs a) {
   const int rows = a.nsl[p];
   double s[4], e[4];
   if (PREC == 0) {
+    // rows in groups of 8, added plainly in row order, each group sum then
+    // through TwoSum (the pair-once VJP leaves a row per 64-body block)
 #pragma unroll
     for (int c = 0; c < 4; ++c) s[c] = e[c] = 0.0;
-    for (int r = 0; r < rows; ++r) {
-      const double *row = a.partial + static_cast<size_t>(r) * 4 * N;
+    for (int r0 = 0; r0 < rows; r0 += 8) {
+      double g[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int r = r0; r < min(rows, r0 + 8); ++r) {
+        const double *row = a.partial + static_cast<size_t>(r) * 4 * N;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) two_sum_acc(s[c], e[c], row[c * N + p]);
+        for (int c = 0; c < 4; ++c) g[c] += row[c * N + p];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) two_sum_acc(s[c], e[c], g[c]);
     }
   } else {
     float fs[4] = {0.f, 0.f, 0.f, 0.f}, fe[4] = {0.f, 0.f, 0.f, 0.f};
