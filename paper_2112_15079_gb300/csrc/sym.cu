@@ -75,8 +75,7 @@ __global__ void __launch_bounds__(kSymThreads) force_sym_kernel(const SymArgs a)
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int t = 0; t < 2; ++t) {
       double bx = 0.0, by = 0.0, bz = 0.0;
-      if (I == J && t < w) {  // tile pair (w, t) is (t, w), done by warp t
-      } else {
+      if (!(I == J && t < w)) {  // tile pair (w, t) with t < w of a diagonal item is (t, w), warp t's
         const double4_32a pj0 = sym_load(a.cur, sb, J * kSymBlock + t * 32 + lane, ns, 1e15 * (lane + 1) + 5e14);
         double xj = pj0.x, yj = pj0.y, zj = pj0.z, mj = pj0.w;
         auto rotate = [&]() {
