@@ -372,6 +372,7 @@ def run_ours(args):
         total = per_step * inner * args.steps * world
         results[prec] = {
             "pair_once": b.pair_once,
+            "pair_once_block": b.pair_once_block,
             "value": total / ev_s, "ms_per_step": ev_s / args.steps * 1e3,
             "verlet_steps_per_s": inner * args.steps / ev_s, "wall_s": wall,
             "achieved_tflops": FLOPS_PER_INTERACTION * per_step * inner * args.steps / ev_s * 1e-12,
@@ -714,15 +715,14 @@ def extras(torch, nbody, inputs, stream, device, args, peaks=None):
     # N sweep.  By default N = 65,536 and 1,048,576 (the metric's second size),
     # mixed and FP64, the library's default tiles (tuning at 1M would cost
     # minutes); --sweep adds 16,384 and 65,536 autotuned, and 262,144 with
-    # their winner.  FP64 at 1M bodies is one ~31 s step.
+    # their winner.  FP64 above 65,536 bodies runs the wide-block pair-once
+    # kernel (one step each: about 1.3 s at 262,144 and 20 s at 1M bodies).
     if not args.no_extras:
         tuned = {}
         for n in ((16384, 65536, 262144, 1048576) if args.sweep else (65536, 1048576)):
             sn = inputs.solar_system(n)
             row = {}
             for prec in ("mixed", "fp64"):
-                if prec == "fp64" and n == 262144:
-                    continue
                 with torch.cuda.stream(stream):
                     b = nbody.NBody(sn.r, sn.v, sn.m, G=sn.G, dt=sn.dt, precision=prec, device=device)
                     if n <= 65536 and args.sweep:
@@ -737,7 +737,7 @@ def extras(torch, nbody, inputs, stream, device, args, peaks=None):
                 per = n * (n - 1) * k / t
                 row[prec] = {"interactions_per_s": per, "ms_per_step": t / k * 1e3,
                              "roofline_frac": per * FLOPS_PER_INTERACTION * 1e-12 / PEAK_TFLOPS[prec],
-                             "tiles": b.tiles}
+                             "tiles": b.tiles, "pair_once_block": b.pair_once_block}
                 if peaks:  # the whole step (force, Verlet, boxes) against the measured peak
                     measured = peaks["fp32_tflops"] if prec == "mixed" else peaks["fp64_tflops"]
                     row[prec]["frac_of_measured"] = per * FLOPS_PER_INTERACTION * 1e-12 / measured

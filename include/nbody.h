@@ -127,6 +127,19 @@ typedef struct {
    * EINVAL. */
   double close_omega_dt;
   double substep_omega_dt; /* w h per sub-step, > 0 when close_omega_dt > 0 (e.g. 0.05) */
+  /* Bodies per block of the FP64 force kernel that evaluates each pair once
+   * (NBODY_FLAG_NO_SYM), 0 = automatic.  A body keeps one partial sum (24 B)
+   * per block of its system.  Automatic: 64 when every system has at most
+   * 65,536 bodies; above, the narrowest of 256 .. 4,096 (powers of two)
+   * whose partial sums take at most 2 GiB, else 4,096 if they take at most
+   * 16 GiB (else every ordered pair is evaluated); and only when the systems
+   * hold at least 1.5 block pairs per SM.  Otherwise 64 or a power of two
+   * from 256 to 4,096, used whatever the systems' sizes (for FP64 contexts
+   * that are not row shards), if the partial sums take at most 16 GiB and
+   * 65,535 blocks per system, else nbody_init returns EINVAL.  Blocks above
+   * 64 bodies apply to the force only; nbody_grad's VJP then evaluates
+   * every ordered pair. */
+  int32_t pair_once_block;
 } nbody_opts;
 
 /* Launch nbody_step's kernels directly instead of replaying CUDA graphs. */
@@ -140,9 +153,10 @@ typedef struct {
  * own, instead of the default one that evaluates each pair once and applies
  * it to both bodies (a_p += mu_j |d|^-3 d, a_j -= mu_p |d|^-3 d: Eq. 1 to
  * rounding, 20 FP64 operations per two interactions instead of 32).  The
- * default is used for systems of at most 65,536 bodies that are not row
- * shards, when the systems hold at least 1.5 pairs of 64-body blocks per SM
- * (about 1,200 bodies in one system; below that the other kernel is faster). */
+ * default is used for contexts that are not row shards, when the systems
+ * hold at least 1.5 block pairs per SM (64-body blocks: about 1,200 bodies
+ * in one system; below that the other kernel is faster) and the partial
+ * sums fit (nbody_opts.pair_once_block). */
 #define NBODY_FLAG_NO_SYM 4
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work
@@ -210,7 +224,8 @@ nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
  * like nbody_init). */
 nbody_status nbody_reset(nbody_ctx *ctx);
 
-/* 1 in *on if the context's force launches evaluate each pair once (the FP64
+/* The bodies per block (64 .. 4,096, see nbody_opts.pair_once_block) in *on
+ * if the context's force launches evaluate each pair once (the FP64
  * default, see NBODY_FLAG_NO_SYM), else 0.  HOST pointer. */
 nbody_status nbody_pair_once(const nbody_ctx *ctx, int32_t *on);
 

@@ -54,6 +54,7 @@ struct Work {
   // FP64 force kernel with each pair once (sym.cu): block-pair items
   int4 *sym_pairs = nullptr;
   int n_sym = 0;
+  int sym_tiles = 0;  // 32-body tiles per block (2: 64-body blocks)
 };
 
 // Adjoint workspace, allocated by the first nbody_grad and kept.
@@ -358,36 +359,60 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   return st;
 }
 
-// The FP64 force kernel evaluates each pair once (sym.cu) when every system
-// has at most kSymMaxBodies bodies (its partial rows are [blocks][3][N]),
-// there are at least 1.5 block pairs per SM (with fewer, one CTA carries a
-// system's whole sum and the stream-K kernel is faster: measured on GB300,
-// 1,031 bodies / 153 pairs 60.8 against 55.3 us per step, 1,283 bodies /
-// 231 pairs 62.5 against 96.2), the context is not a row shard, and
-// NBODY_FLAG_NO_SYM is not set.
-bool sym_eligible(const nbody_ctx *c) {
-  if (c->o.precision != NBODY_FP64 || c->sh_world > 0 || (c->o.flags & NBODY_FLAG_NO_SYM)) return false;
+// Bodies per block of the pair-once FP64 force kernels (sym.cu) for this
+// context, or 0 where the every-ordered-pair kernel runs: mixed precision,
+// row shards and NBODY_FLAG_NO_SYM.  A body has one partial row (24 B) per
+// block of its system.  With nbody_opts.pair_once_block = 0 the blocks are
+// 64 bodies when every system has at most kSymMaxBodies (rows <= 1.6 GB at
+// 65,536), else the narrowest wide block (256 .. 4,096 bodies) whose rows
+// fit in kSymRowBudget, else 4,096 bodies if the rows fit in kSymRowLimit;
+// and the default applies only when the systems hold at least 1.5 block
+// pairs per SM (with fewer, one CTA carries a system's whole sum and the
+// stream-K kernel is faster: measured on GB300, 1,031 bodies / 153 pairs
+// 60.8 against 55.3 us per step, 1,283 bodies / 231 pairs 62.5 against
+// 96.2).  A requested block size is used as asked if its rows fit in
+// kSymRowLimit (checked at nbody_init).
+constexpr int64_t kSymRowBudget = int64_t(2) << 30;
+constexpr int64_t kSymRowLimit = int64_t(16) << 30;
+
+int64_t sym_row_bytes(const nbody_ctx *c, int64_t B) {
+  int64_t rows = 1;
+  for (int64_t s = 0; s < c->n_sys; ++s) rows = std::max(rows, (c->offsets[s + 1] - c->offsets[s] + B - 1) / B);
+  return rows * 3 * static_cast<int64_t>(sizeof(double)) * static_cast<int64_t>(c->N);
+}
+
+int sym_block(const nbody_ctx *c) {
+  if (c->o.precision != NBODY_FP64 || c->sh_world > 0 || (c->o.flags & NBODY_FLAG_NO_SYM)) return 0;
+  if (c->o.pair_once_block > 0) return c->o.pair_once_block;
+  int64_t nmax = 0;
+  for (int64_t s = 0; s < c->n_sys; ++s) nmax = std::max(nmax, c->offsets[s + 1] - c->offsets[s]);
+  int64_t B = nb::kSymBlock;
+  if (nmax > nb::kSymMaxBodies) {
+    B = 32 * nb::kSymWideMinTiles;
+    while (B < 32 * nb::kSymWideMaxTiles && sym_row_bytes(c, B) > kSymRowBudget) B *= 2;
+    if (sym_row_bytes(c, B) > kSymRowLimit) return 0;
+  }
   int64_t pairs = 0;
   for (int64_t s = 0; s < c->n_sys; ++s) {
-    const int64_t ns = c->offsets[s + 1] - c->offsets[s];
-    if (ns > nb::kSymMaxBodies) return false;
-    const int64_t nb = (ns + nb::kSymBlock - 1) / nb::kSymBlock;
+    const int64_t nb = (c->offsets[s + 1] - c->offsets[s] + B - 1) / B;
     pairs += nb * (nb + 1) / 2;
   }
-  return 2 * pairs >= 3 * static_cast<int64_t>(c->nsm);
+  return 2 * pairs >= 3 * static_cast<int64_t>(c->nsm) ? static_cast<int>(B) : 0;
 }
 
 // Work tables of the pair-once FP64 kernels: the block pairs (I, J), I <= J,
-// of every system, off-diagonal items first; each body has one partial row
-// per block of its system (row_doubles values each: 3 force, 4 VJP).
-nbody_status build_sym_work(nbody_ctx *c, Work &wk, int row_doubles = 3) {
+// of every system, off-diagonal items first, blocks of B bodies (64, or
+// wide: force only); each body has one partial row per block of its system
+// (row_doubles values each: 3 force, 4 VJP).
+nbody_status build_sym_work(nbody_ctx *c, Work &wk, int row_doubles, int B) {
   free_work(c, wk);
+  if (B != nb::kSymBlock && row_doubles != 3) return fail(c, NBODY_EINVAL, "wide pair-once blocks are force-only");
   std::vector<int4> off_diag, diag;
   int64_t rows = 1;
   std::vector<uint16_t> nsl(static_cast<size_t>(c->N), 0);
   for (int64_t s = 0; s < c->n_sys; ++s) {
     const int64_t b = c->offsets[s], ns = c->offsets[s + 1] - b;
-    const int nb = static_cast<int>((ns + nb::kSymBlock - 1) / nb::kSymBlock);
+    const int nb = static_cast<int>((ns + B - 1) / B);
     rows = std::max<int64_t>(rows, nb);
     for (int64_t p = b; p < b + ns; ++p) nsl[p] = static_cast<uint16_t>(nb);
     for (int I = 0; I < nb; ++I)
@@ -396,12 +421,15 @@ nbody_status build_sym_work(nbody_ctx *c, Work &wk, int row_doubles = 3) {
   }
   std::vector<int4> pairs = std::move(off_diag);
   pairs.insert(pairs.end(), diag.begin(), diag.end());
-  const int occ = nb::force_sym_ctas_per_sm();
+  if (rows > 65535 || pairs.size() > static_cast<size_t>(INT32_MAX))
+    return fail(c, NBODY_EINVAL, "too many pair-once blocks (%lld in a system)", static_cast<long long>(rows));
+  const int occ = nb::force_sym_ctas_per_sm(B / 32);
   if (occ < 1) return fail(c, NBODY_ECUDA, "the pair-once FP64 kernel does not fit on an SM");
   wk.nsl_rank = nsl;
   wk.plan_off = c->tgt_off;
   wk.plan_soff = c->tgt_soff;
   wk.n_sym = static_cast<int>(pairs.size());
+  wk.sym_tiles = B / 32;
   wk.rows = static_cast<int>(rows);
   wk.grid = static_cast<int>(std::min<int64_t>(pairs.size(), static_cast<int64_t>(c->nsm) * occ));
   wk.occ = occ;
@@ -442,9 +470,9 @@ void free_work(nbody_ctx *c, Work &w) {
 // and tables, which stay a matching pair.
 nbody_status build_items(nbody_ctx *c, const nbody_tiles &t) {
   drop_graphs(c);
-  if (sym_eligible(c)) {  // the tiles stay the context's, for nbody_get_tiles; this kernel has none
+  if (const int B = sym_block(c)) {  // the tiles stay the context's, for nbody_get_tiles; this kernel has none
     Work nw;
-    const nbody_status st = build_sym_work(c, nw);
+    const nbody_status st = build_sym_work(c, nw, 3, B);
     if (st != NBODY_OK) return st;
     free_work(c, c->fw);
     c->fw = nw;
@@ -692,6 +720,7 @@ nbody_status launch_force_kernel(nbody_ctx *c, const void *cur, cudaStream_t st,
     a.n_pairs = c->fw.n_sym;
     a.ctr = c->fw.dyn_ctr;
     a.N = c->N;
+    a.tiles = c->fw.sym_tiles;
     NB_CUDA(c, nb::launch_force_sym(a, c->fw.grid, st, chained));
     return NBODY_OK;
   }
@@ -1107,8 +1136,8 @@ nbody_status ensure_adjoint(nbody_ctx *c, int64_t n_steps) {
     t.tj = kVjpTile;
     t.jsplit = 0;
     t.ctas_per_sm = 32;
-    if (sym_eligible(c)) {  // FP64: the VJP evaluates each pair once too
-      if ((st = build_sym_work(c, A.vj, 4)) != NBODY_OK) return st;
+    if (sym_block(c) == nb::kSymBlock) {  // FP64: the VJP evaluates each pair once too (64-body blocks)
+      if ((st = build_sym_work(c, A.vj, 4, nb::kSymBlock)) != NBODY_OK) return st;
     } else {
       const size_t smem = nb::vjp_smem_bytes(prec, t.tj);
       int occ = 0;
@@ -1205,6 +1234,16 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
       return fail(nullptr, NBODY_EINVAL, "substep_omega_dt must be finite and > 0 with close_omega_dt > 0");
     if (o->integrator != NBODY_VERLET)
       return fail(nullptr, NBODY_EINVAL, "close-encounter handling runs with the Verlet integrator only");
+  }
+  if (const int B = o->pair_once_block) {
+    if (B != nb::kSymBlock && !(B >= 32 * nb::kSymWideMinTiles && B <= 32 * nb::kSymWideMaxTiles && (B & (B - 1)) == 0))
+      return fail(nullptr, NBODY_EINVAL, "pair_once_block must be 0, 64 or a power of two from %d to %d",
+                  32 * nb::kSymWideMinTiles, 32 * nb::kSymWideMaxTiles);
+    int64_t rows = 1;
+    for (int64_t s = 0; s < n_systems; ++s) rows = std::max(rows, (offsets[s + 1] - offsets[s] + B - 1) / B);
+    if (rows > 65535 || rows * 3 * static_cast<int64_t>(sizeof(double)) * offsets[n_systems] > kSymRowLimit)
+      return fail(nullptr, NBODY_EINVAL, "pair_once_block %d: the partial rows would exceed %lld bytes", B,
+                  static_cast<long long>(kSymRowLimit));
   }
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;
@@ -1430,7 +1469,7 @@ nbody_status nbody_reset(nbody_ctx *c) {
 
 nbody_status nbody_pair_once(const nbody_ctx *c, int32_t *on) {
   if (!c || !on) return NBODY_EINVAL;
-  *on = c->fw.sym_pairs != nullptr ? 1 : 0;
+  *on = c->fw.sym_pairs != nullptr ? 32 * c->fw.sym_tiles : 0;
   return NBODY_OK;
 }
 
@@ -1570,7 +1609,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
           cand.push_back(t);
         }
   // the pair-once FP64 kernel has no tiles to choose: time the current ones only
-  if (sym_eligible(c)) cand.assign(1, c->tiles);
+  if (sym_block(c)) cand.assign(1, c->tiles);
   cudaEvent_t e0, e1;
   NB_CUDA(c, cudaEventCreate(&e0));
   NB_CUDA(c, cudaEventCreate(&e1));

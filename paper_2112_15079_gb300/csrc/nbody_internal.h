@@ -142,7 +142,12 @@ struct PrepArgs {
 // pairs (I, J), I <= J, of kSymBlock bodies of one system.
 constexpr int kSymBlock = 64;
 constexpr int kSymThreads = 64;        // two warps: one 32-body tile of block I each
-constexpr int kSymMaxBodies = 65536;   // per system (the partial rows are [blocks][3][N])
+constexpr int kSymMaxBodies = 65536;   // per system, by default (the partial rows are [blocks][3][N])
+// Wide blocks of 32 T bodies (force_sym_wide_kernel) above that: T tiles.
+constexpr int kSymWideWarps = 4;
+constexpr int kSymWideThreads = 32 * kSymWideWarps;
+constexpr int kSymWideMinTiles = 8;    // 256 bodies
+constexpr int kSymWideMaxTiles = 128;  // 4,096 bodies (96 KB of shared sums)
 struct SymArgs {
   const double4_32a *cur;  // staged sources (x, y, z, G m) per body
   double *partial;         // [blocks][3][N]: row J of a body of block I holds block J's pull
@@ -150,6 +155,7 @@ struct SymArgs {
   int32_t n_pairs;
   int32_t *ctr;            // [2]: next item, CTAs done (the last one resets both)
   int32_t N;
+  int32_t tiles;           // 32-body tiles per block: 2 (64-body blocks, force_sym_kernel) or wide
 };
 
 // The adjoint's VJP with each pair once (FP64, sym.cu): the same items,
@@ -256,7 +262,8 @@ bool force_config_supported(int precision, int threads, int ipt);
 size_t force_smem_bytes(int precision, int tj, int stages);  // dynamic smem of a ring of `stages` tiles
 cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool chained);
 cudaError_t launch_vjp_sym(const VjpSymArgs &a, int grid, cudaStream_t s);
-int force_sym_ctas_per_sm();
+int force_sym_ctas_per_sm(int tiles);   // resident CTAs per SM (raises the wide kernel's smem limit)
+size_t force_sym_smem_bytes(int tiles);
 cudaError_t launch_close(const CloseArgs &a, int n_clusters, cudaStream_t s, bool chained);
 cudaError_t launch_close_far(const CloseArgs &a, cudaStream_t s, bool chained);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);

@@ -149,6 +149,128 @@ __global__ void __launch_bounds__(kSymThreads) force_sym_kernel(const SymArgs a)
   }
 }
 
+// Wide blocks, for systems whose 64-body blocks would need too many partial
+// rows (one per block): blocks of B = 32 T bodies (T tiles, a power of two,
+// kSymWideMinTiles .. kSymWideMaxTiles), so a body has one row per B bodies
+// of its system.  A CTA of kSymWideWarps warps takes an item (I, J).  In
+// round r warp w holds tile p = r W + w of block I in registers; in phase
+// t = 0 .. T-1 it rotates tile q = (p + t) mod T of block J past it, as
+// force_sym_kernel does, and adds the tile's reaction sums into block J's
+// sums in shared memory.  A CTA barrier closes each phase, and within a
+// phase the warps' q differ, so each tile's shared sums take their terms in
+// phase order, whichever warp runs first.  Block I's sums of a tile are
+// added per tile pair, in phase order.  Off-diagonal items: block I's sums
+// go to row J, block J's shared sums to row I.  A diagonal item takes the
+// tile pairs q >= p only (q == p as the 16-step half rotation); each warp
+// adds its tile's own sums into the shared sums after its round, and the
+// total goes to row I.  Tiles past the end of the system are skipped.
+__global__ void __launch_bounds__(kSymWideThreads) force_sym_wide_kernel(const SymArgs a) {
+  extern __shared__ double s_acc[];  // [3][32 T]: block J's reaction sums of the item
+  __shared__ int s_item;
+  grid_dependency_wait();    // staged sources of this step are complete
+  grid_dependency_launch();  // the Verlet kernel may start launching
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int T = a.tiles, BT = 32 * T;
+  const size_t N = static_cast<size_t>(a.N);
+  for (;;) {
+    __syncthreads();  // the previous item's shared sums are consumed
+    if (tid == 0) s_item = atomicAdd(a.ctr, 1);
+    for (int k = tid; k < 3 * BT; k += kSymWideThreads) s_acc[k] = 0.0;
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.n_pairs) break;
+    const int4 pr = a.pairs[item];  // (first body of the system, its bodies, block I, block J)
+    const int64_t sb = pr.x;
+    const int ns = pr.y, I = pr.z, J = pr.w;
+    const bool diag = I == J;
+    const int i0 = I * BT, j0 = J * BT;  // first body of each block within the system
+    for (int r = 0; r < T; r += kSymWideWarps) {
+      const int p = r + w;
+      const bool p_live = i0 + p * 32 < ns;  // warp-uniform
+      const double4_32a pi = sym_load(a.cur, sb, i0 + p * 32 + lane, ns, 1e15 * (lane + 1));
+      double ax = 0.0, ay = 0.0, az = 0.0;
+      // the next phase's J tile, loaded a phase ahead
+      int q = p;
+      double4_32a pn = sym_load(a.cur, sb, j0 + q * 32 + lane, ns, 1e15 * (lane + 1) + 5e14);
+      for (int t = 0; t < T; ++t) {
+        const double4_32a pj0 = pn;
+        const int qn = (p + t + 1) & (T - 1);
+        if (t + 1 < T) pn = sym_load(a.cur, sb, j0 + qn * 32 + lane, ns, 1e15 * (lane + 1) + 5e14);
+        if (p_live && j0 + q * 32 < ns && !(diag && q < p)) {  // (q < p on a diagonal item: tile q's warp's pair)
+          double xj = pj0.x, yj = pj0.y, zj = pj0.z, mj = pj0.w;
+          double tx = 0.0, ty = 0.0, tz = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
+          auto rotate = [&]() {
+            const int src = (lane + 1) & 31;
+            xj = __shfl_sync(0xffffffffu, xj, src);
+            yj = __shfl_sync(0xffffffffu, yj, src);
+            zj = __shfl_sync(0xffffffffu, zj, src);
+            mj = __shfl_sync(0xffffffffu, mj, src);
+            bx = __shfl_sync(0xffffffffu, bx, src);
+            by = __shfl_sync(0xffffffffu, by, src);
+            bz = __shfl_sync(0xffffffffu, bz, src);
+          };
+          if (diag && q == p) {  // a tile with itself: offsets 1..15 both ways, 16 one way
+#pragma unroll 4
+            for (int k = 1; k <= 16; ++k) {
+              rotate();
+              sym_pair(pi.x, pi.y, pi.z, pi.w, xj, yj, zj, mj, tx, ty, tz, bx, by, bz, k < 16);
+            }
+            const int back = (lane + 16) & 31;
+            bx = __shfl_sync(0xffffffffu, bx, back);
+            by = __shfl_sync(0xffffffffu, by, back);
+            bz = __shfl_sync(0xffffffffu, bz, back);
+          } else {
+#pragma unroll 4
+            for (int k = 0; k < 32; ++k) {
+              sym_pair(pi.x, pi.y, pi.z, pi.w, xj, yj, zj, mj, tx, ty, tz, bx, by, bz, true);
+              rotate();
+            }
+          }
+          ax += tx;
+          ay += ty;
+          az += tz;
+          double *acc = s_acc + q * 32 + lane;
+          acc[0] += bx;
+          acc[BT] += by;
+          acc[2 * BT] += bz;
+        }
+        q = qn;
+        __syncthreads();  // phase done: the J tiles change hands
+      }
+      if (p_live) {
+        const int il = i0 + p * 32 + lane;
+        if (diag) {  // tile p's own sums join its shared sums (no warp takes tile p until the next barrier)
+          double *acc = s_acc + p * 32 + lane;
+          acc[0] += ax;
+          acc[BT] += ay;
+          acc[2 * BT] += az;
+        } else if (il < ns) {
+          double *row = a.partial + static_cast<size_t>(J) * 3 * N;
+          row[sb + il] = ax;
+          row[N + sb + il] = ay;
+          row[2 * N + sb + il] = az;
+        }
+      }
+    }
+    __syncthreads();
+    // block J's sums (on a diagonal item, the block's whole sums) to row I
+    double *row = a.partial + static_cast<size_t>(I) * 3 * N;
+    for (int k = tid; k < BT && j0 + k < ns; k += kSymWideThreads) {
+      row[sb + j0 + k] = s_acc[k];
+      row[N + sb + j0 + k] = s_acc[BT + k];
+      row[2 * N + sb + j0 + k] = s_acc[2 * BT + k];
+    }
+  }
+  // The last CTA out resets the item counter for the next launch.
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.ctr + 1, 1) == static_cast<int>(gridDim.x) - 1) {
+      atomicExch(a.ctr, 0);
+      atomicExch(a.ctr + 1, 0);
+    }
+  }
+}
+
 // The adjoint's vector-Jacobian product of Eq. 1 (see vjp.cu), each pair
 // once.  For the pair (q, j), d = r_j - r_q, s3 = |d|^-3, s5 = |d|^-5 and
 // u = mu_q w_j - mu_j w_q, the q term s3 u - 3 s5 (d.u) d changes sign
@@ -273,22 +395,38 @@ cudaError_t launch_vjp_sym(const VjpSymArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t force_sym_smem_bytes(int tiles) {
+  return tiles == 2 ? 0 : sizeof(double) * 3 * 32 * static_cast<size_t>(tiles);
+}
+
 cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool chained) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kSymThreads);
+  cfg.blockDim = dim3(a.tiles == 2 ? kSymThreads : kSymWideThreads);
+  cfg.dynamicSmemBytes = force_sym_smem_bytes(a.tiles);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, force_sym_kernel, a);
+  if (a.tiles == 2) return cudaLaunchKernelEx(&cfg, force_sym_kernel, a);
+  return cudaLaunchKernelEx(&cfg, force_sym_wide_kernel, a);
 }
 
-int force_sym_ctas_per_sm() {
+int force_sym_ctas_per_sm(int tiles) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_sym_kernel, kSymThreads, 0) != cudaSuccess) {
+  cudaError_t e;
+  if (tiles == 2) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_sym_kernel, kSymThreads, 0);
+  } else {
+    const size_t smem = force_sym_smem_bytes(tiles);
+    e = cudaFuncSetAttribute(force_sym_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(force_sym_smem_bytes(kSymWideMaxTiles)));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_sym_wide_kernel, kSymWideThreads, smem);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

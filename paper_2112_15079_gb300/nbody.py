@@ -38,7 +38,7 @@ class nbody_opts(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("integrator", ctypes.c_int32),
                 ("tune_cache", ctypes.c_char_p), ("close_omega_dt", ctypes.c_double),
-                ("substep_omega_dt", ctypes.c_double)]
+                ("substep_omega_dt", ctypes.c_double), ("pair_once_block", ctypes.c_int32)]
 
 
 class nbody_tiles(ctypes.Structure):
@@ -137,7 +137,7 @@ class NBody:
     def __init__(self, r, v, m, offsets=None, *, G: float, dt: float, precision: str = "fp64",
                  ckpt_every: int = 0, graphs: bool = True, small: bool = True, device=None, stream=None,
                  integrator: str = "verlet", tune_cache: str | None = None, close_omega_dt: float = 0.0,
-                 substep_omega_dt: float = 0.05, pair_once: bool = True):
+                 substep_omega_dt: float = 0.05, pair_once: bool = True, pair_once_block: int = 0):
         torch = _torch()
         device = torch.device(device if device is not None else "cuda")
         self.device = device
@@ -160,7 +160,8 @@ class NBody:
                           | (0 if pair_once else NBODY_FLAG_NO_SYM),
                           integrator=INTEGRATORS[integrator],
                           tune_cache=None if tune_cache is None else os.fsencode(tune_cache),
-                          close_omega_dt=float(close_omega_dt), substep_omega_dt=float(substep_omega_dt))
+                          close_omega_dt=float(close_omega_dt), substep_omega_dt=float(substep_omega_dt),
+                          pair_once_block=int(pair_once_block))
         self._ctx = _P()
         s = self.state
         ptrs = [s[k].data_ptr() for k in range(6)] + [self.m.data_ptr()]
@@ -193,10 +194,16 @@ class NBody:
     @property
     def pair_once(self) -> bool:
         """Whether the force launches evaluate each pair once (the FP64
-        default for systems of at most 65,536 bodies)."""
+        default, see ``pair_once_block``)."""
+        return self.pair_once_block > 0
+
+    @property
+    def pair_once_block(self) -> int:
+        """Bodies per block of the pair-once force kernel (64 .. 4,096), or
+        0 when the force launches evaluate every ordered pair."""
         on = ctypes.c_int32()
         check(nbody_pair_once(self._ctx, ctypes.byref(on)), self._ctx)
-        return bool(on.value)
+        return int(on.value)
 
     def close_info(self) -> dict:
         """Close-encounter handling: close pairs, clusters, cluster members

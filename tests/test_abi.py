@@ -65,3 +65,20 @@ def test_errors_without_context_are_reported():
     assert nbody.nbody_step(None, 1) == nbody.NBODY_EINVAL
     assert nbody.nbody_sync(None) == nbody.NBODY_EINVAL
     nbody.nbody_free(None)
+
+
+def test_pair_once_block_is_validated():
+    """nbody_opts.pair_once_block: 0, 64 or a power of two from 256 to 4,096,
+    with partial sums of at most 16 GiB and 65,535 blocks per system; checked
+    before any CUDA call (the state pointers are never read)."""
+    from paper_2112_15079_gb300 import nbody
+    buf = (ctypes.c_double * 4)()
+    ptrs = [ctypes.cast(buf, ctypes.c_void_p)] * 7
+    for block, n, msg in [(128, 2, b"power of two"), (8192, 2, b"power of two"), (300, 2, b"power of two"),
+                          (-1, 2, b"power of two"), (256, 1 << 30, b"exceed")]:
+        ctx = ctypes.c_void_p()
+        off = (ctypes.c_int64 * 2)(0, n)
+        opts = nbody.nbody_opts(G=1.0, dt=0.1, precision=0, pair_once_block=block)
+        st = nbody.nbody_init(ctypes.byref(ctx), 1, off, *ptrs, ctypes.byref(opts), None)
+        assert st == nbody.NBODY_EINVAL, block
+        assert msg in nbody.nbody_last_error(None), (block, nbody.nbody_last_error(None))

@@ -1,8 +1,9 @@
-"""GPU parity of the FP64 force kernel that evaluates each pair once
+"""GPU parity of the FP64 force kernels that evaluate each pair once
 (sym.cu: a_p += mu_j |d|^-3 d and a_j -= mu_p |d|^-3 d from one evaluation,
-block pairs of 64 bodies, warp-rotated source tiles), against the oracle's
-Eq. 1 and against the stream-K kernel that evaluates every ordered pair
-(NBODY_FLAG_NO_SYM).
+block pairs of 64 bodies, warp-rotated source tiles; and the wide-block
+kernel, blocks of 256 .. 4,096 bodies whose reaction sums stay in shared
+memory), against the oracle's Eq. 1 and against the stream-K kernel that
+evaluates every ordered pair (NBODY_FLAG_NO_SYM).
 
 Gate: the FP64 bound, max_p |a_p - a_ref| / |a_ref| <= 1e-13 (measured
 ~1e-15: each pair is the same FP64 term as in the other kernel, and a body's
@@ -14,7 +15,17 @@ sampled rows), and 48 systems of 100-700 bodies in one context (block pairs
 never cross systems).  Trajectories: 10 steps of the 2,131-body model equal
 the oracle's Verlet to 1e-12 AU (its unresolved moons make longer runs
 diverge at the rounding level, as for the other kernel); a run is bitwise
-the same across split calls and without graphs."""
+the same across split calls and without graphs.
+
+Wide blocks (nbody_opts.pair_once_block): every body at 1,283 and 10,425
+bodies with blocks of 256, 512 and 4,096 (ragged last blocks, tiles past
+the end of a system, a single diagonal item), an exact 4,096-body block,
+48 small systems in blocks of 256, the automatic choice above 65,536
+bodies (65,537: 256; 262,144: 1,024; sampled rows), and a 10-step
+trajectory that is bitwise the same across split calls and without
+graphs.  Same gate: a body's sum is at most 32 terms per tile pair, the
+tile pairs of a block pair added in a fixed order (at most 128), the rows
+added as above."""
 import numpy as np
 import pytest
 
@@ -35,10 +46,10 @@ def nb():
     return nbody
 
 
-def _accel(nb, r, v, m, offsets=None, pair_once=True):
+def _accel(nb, r, v, m, offsets=None, pair_once=True, block=0):
     b = nb.NBody(r, v, m, offsets, G=inputs.G_AU_DAY, dt=inputs.DT_DAY, precision="fp64", small=False,
-                 pair_once=pair_once)
-    used = b.pair_once
+                 pair_once=pair_once, pair_once_block=block)
+    used = b.pair_once_block
     a = b.accel().cpu().numpy()
     b.close()
     return a, used
@@ -52,7 +63,7 @@ def _rel(a, ref):
 def test_every_body_matches_the_oracle(nb, n):
     s = inputs.solar_system(n)
     a, used = _accel(nb, s.r, s.v, s.m)
-    assert used
+    assert used == 64
     ref = oracle.accel(s.G, s.r, s.m, openmp=True)
     assert _rel(a, ref) <= 1e-13
     a2, used2 = _accel(nb, s.r, s.v, s.m, pair_once=False)
@@ -109,3 +120,77 @@ def test_small_systems_keep_the_stream_k_kernel(nb):
     b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="mixed")
     assert not b.pair_once
     b.close()
+
+
+@pytest.mark.parametrize("n,block", [(1283, 256), (1283, 512), (4096, 4096), (10425, 256), (10425, 4096)])
+def test_wide_blocks_every_body(nb, n, block):
+    s = inputs.solar_system(n)
+    a, used = _accel(nb, s.r, s.v, s.m, block=block)
+    assert used == block
+    ref = oracle.accel(s.G, s.r, s.m, openmp=True)
+    assert _rel(a, ref) <= 1e-13
+
+
+def test_wide_blocks_many_small_systems(nb):
+    rng = np.random.default_rng(12)
+    systems = [inputs.solar_system(int(k), seed=inputs.BASE_SEED + 100 + i, n_moons=20)
+               for i, k in enumerate(rng.integers(100, 701, size=48))]
+    off, r, v, m = inputs.concat(systems)
+    a, used = _accel(nb, r, v, m, off, block=256)
+    assert used == 256
+    for i, sy in enumerate(systems):
+        ref = oracle.accel(sy.G, sy.r, sy.m)
+        assert _rel(a[:, off[i]:off[i + 1]], ref) <= 1e-13, i
+
+
+@pytest.mark.parametrize("n,block", [(65537, 256), (262144, 1024)])
+def test_wide_blocks_chosen_above_65536_bodies(nb, n, block):
+    s = inputs.solar_system(n, seed=33)
+    a, used = _accel(nb, s.r, s.v, s.m)
+    assert used == block  # the narrowest block whose partial rows take at most 2 GiB
+    rows = np.unique(np.concatenate([np.arange(0, 131), np.arange(n - 100, n),
+                                     np.random.default_rng(4).integers(0, n, 200)]))
+    ref = oracle.accel_rows(s.G, s.r, s.m, rows, openmp=True)
+    assert _rel(a[:, rows], ref) <= 1e-13
+
+
+def test_wide_blocks_trajectory_and_bitwise_repeatability(nb):
+    s = inputs.solar_system(2131)
+    b1 = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64", small=False, pair_once_block=512)
+    assert b1.pair_once_block == 512
+    b1.step(10)
+    b2 = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64", small=False, graphs=False,
+                  pair_once_block=512)
+    b2.step(3)
+    b2.step(7)
+    b1.sync()
+    b2.sync()
+    s1, s2 = b1.state.cpu().numpy(), b2.state.cpu().numpy()
+    assert np.array_equal(s1, s2)
+    r_ref, v_ref, _ = oracle.verlet(s.G, s.dt, 10, s.r, s.v, s.m, oracle.accel(s.G, s.r, s.m, openmp=True),
+                                    openmp=True)
+    assert np.abs(s1[:3] - r_ref).max() <= 1e-12
+    b1.close()
+    b2.close()
+
+
+def test_wide_blocks_force_only(nb):
+    """Blocks above 64 bodies apply to the force: nbody_grad's VJP evaluates
+    every ordered pair; the gradient meets the adjoint tests' per-element
+    FP64 gate against the oracle's."""
+    torch = pytest.importorskip("torch")
+    from test_gpu_adjoint import check_grad
+    s = inputs.solar_system(2131, seed=61, n_moons=0)
+    T = 12
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(np.arange(31, s.n), 16, replace=False))
+    rT, vT, _ = oracle.verlet(s.G, s.dt, T, s.r, s.v, s.m, openmp=True)
+    gr = np.zeros((3, s.n))
+    gr[:, idx] = 2 * (rT[:, idx] - s.r[:, idx])
+    ref = oracle.grad(s.G, s.dt, T, s.r, s.v, s.m, gr, np.zeros_like(gr), openmp=True, magnitudes=True)
+    b = nb.NBody(s.r, s.v, s.m, G=s.G, dt=s.dt, precision="fp64", small=False, ckpt_every=5,
+                 pair_once_block=256)
+    assert b.pair_once_block == 256
+    got = [t.cpu().numpy() for t in b.grad(T, torch.tensor(gr))]
+    b.close()
+    check_grad("fp64", got, ref)
