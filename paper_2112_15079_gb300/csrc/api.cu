@@ -359,54 +359,81 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   return st;
 }
 
-// Bodies per block of the pair-once FP64 force kernels (sym.cu) for this
-// context, or 0 where the every-ordered-pair kernel runs: mixed precision,
-// row shards and NBODY_FLAG_NO_SYM.  A body has one partial row (24 B) per
-// block of its system.  With nbody_opts.pair_once_block = 0 the blocks are
-// 64 bodies when every system has at most kSymMaxBodies (rows <= 1.6 GB at
-// 65,536), else the narrowest wide block (256 .. 4,096 bodies) whose rows
-// fit in kSymRowBudget, else 4,096 bodies if the rows fit in kSymRowLimit;
-// and the default applies only when the systems hold at least 1.5 block
-// pairs per SM (with fewer, one CTA carries a system's whole sum and the
-// stream-K kernel is faster: measured on GB300, 1,031 bodies / 153 pairs
-// 60.8 against 55.3 us per step, 1,283 bodies / 231 pairs 62.5 against
-// 96.2).  A requested block size is used as asked if its rows fit in
-// kSymRowLimit (checked at nbody_init).
+// Bodies (FP64) or stage entries (mixed) per block of the pair-once force
+// kernels (sym.cu, sym_mixed.cu) for this context, or 0 where the
+// every-ordered-pair kernel runs: row shards and NBODY_FLAG_NO_SYM.  A body
+// has one partial row (24 B) per block of its system.  With
+// nbody_opts.pair_once_block = 0:
+//   FP64: 64 when every system has at most kSymMaxBodies (rows <= 1.6 GB at
+//   65,536), else the narrowest wide block (256 .. 4,096 bodies) whose rows
+//   fit in kSymRowBudget, else 4,096 if they fit in kSymRowLimit; used when
+//   the systems hold at least 1.5 block pairs per SM (with fewer, one CTA
+//   carries a system's whole sum and the stream-K kernel is faster:
+//   measured on GB300, 1,031 bodies / 153 pairs 60.8 against 55.3 us per
+//   step, 1,283 bodies / 231 pairs 62.5 against 96.2).
+//   Mixed: for a largest system of at least kMsymMinBodies (measured on
+//   GB300: 65,536 bodies 1.68 against 1.82 ms per step, 1,048,576 bodies
+//   405 against 430 ms; 10,425 bodies 77 against 68 us, where the block
+//   pairs fill the SMs unevenly and the per-body kernel reads 82 rows), the
+//   narrowest block (128 .. 2,048 entries) that leaves the largest system
+//   at most kMsymMaxRows rows per body (the per-body kernel reads them every
+//   step), if the rows fit in kSymRowLimit and the block pairs give at
+//   least 8 warps per SM (each warp holds 128 targets).
+// A requested block size is used as asked if its rows fit in kSymRowLimit
+// (checked at nbody_init).
 constexpr int64_t kSymRowBudget = int64_t(2) << 30;
 constexpr int64_t kSymRowLimit = int64_t(16) << 30;
+constexpr int64_t kMsymMaxRows = 128;
+constexpr int64_t kMsymMinBodies = 65536;
 
-int64_t sym_row_bytes(const nbody_ctx *c, int64_t B) {
+int64_t sym_rows(const nbody_ctx *c, int64_t B) {
   int64_t rows = 1;
   for (int64_t s = 0; s < c->n_sys; ++s) rows = std::max(rows, (c->offsets[s + 1] - c->offsets[s] + B - 1) / B);
-  return rows * 3 * static_cast<int64_t>(sizeof(double)) * static_cast<int64_t>(c->N);
+  return rows;
+}
+
+int64_t sym_row_bytes(const nbody_ctx *c, int64_t B) {
+  return sym_rows(c, B) * 3 * static_cast<int64_t>(sizeof(double)) * static_cast<int64_t>(c->N);
 }
 
 int sym_block(const nbody_ctx *c) {
-  if (c->o.precision != NBODY_FP64 || c->sh_world > 0 || (c->o.flags & NBODY_FLAG_NO_SYM)) return 0;
+  if (c->sh_world > 0 || (c->o.flags & NBODY_FLAG_NO_SYM)) return 0;
   if (c->o.pair_once_block > 0) return c->o.pair_once_block;
   int64_t nmax = 0;
   for (int64_t s = 0; s < c->n_sys; ++s) nmax = std::max(nmax, c->offsets[s + 1] - c->offsets[s]);
+  auto pairs_of = [&](int64_t B) {
+    int64_t pairs = 0;
+    for (int64_t s = 0; s < c->n_sys; ++s) {
+      const int64_t nb = (c->offsets[s + 1] - c->offsets[s] + B - 1) / B;
+      pairs += nb * (nb + 1) / 2;
+    }
+    return pairs;
+  };
+  if (c->o.precision == NBODY_MIXED) {
+    if (nmax < kMsymMinBodies) return 0;
+    int64_t B = 32 * nb::kMsymMinTiles;
+    while (B < 32 * nb::kMsymMaxTiles && sym_rows(c, B) > kMsymMaxRows) B *= 2;
+    if (sym_row_bytes(c, B) > kSymRowLimit) return 0;
+    return pairs_of(B) * (B / 128) >= 8 * static_cast<int64_t>(c->nsm) ? static_cast<int>(B) : 0;
+  }
   int64_t B = nb::kSymBlock;
   if (nmax > nb::kSymMaxBodies) {
     B = 32 * nb::kSymWideMinTiles;
     while (B < 32 * nb::kSymWideMaxTiles && sym_row_bytes(c, B) > kSymRowBudget) B *= 2;
     if (sym_row_bytes(c, B) > kSymRowLimit) return 0;
   }
-  int64_t pairs = 0;
-  for (int64_t s = 0; s < c->n_sys; ++s) {
-    const int64_t nb = (c->offsets[s + 1] - c->offsets[s] + B - 1) / B;
-    pairs += nb * (nb + 1) / 2;
-  }
-  return 2 * pairs >= 3 * static_cast<int64_t>(c->nsm) ? static_cast<int>(B) : 0;
+  return 2 * pairs_of(B) >= 3 * static_cast<int64_t>(c->nsm) ? static_cast<int>(B) : 0;
 }
 
-// Work tables of the pair-once FP64 kernels: the block pairs (I, J), I <= J,
-// of every system, off-diagonal items first, blocks of B bodies (64, or
-// wide: force only); each body has one partial row per block of its system
-// (row_doubles values each: 3 force, 4 VJP).
+// Work tables of the pair-once kernels: the block pairs (I, J), I <= J, of
+// every system, off-diagonal items first, blocks of B bodies (FP64: 64, or
+// wide: force only) or stage entries (mixed, force only); each body has one
+// partial row per block of its system (row_doubles values each: 3 force,
+// 4 VJP).  An item is (first stage entry of the system, its bodies, I, J).
 nbody_status build_sym_work(nbody_ctx *c, Work &wk, int row_doubles, int B) {
   free_work(c, wk);
   if (B != nb::kSymBlock && row_doubles != 3) return fail(c, NBODY_EINVAL, "wide pair-once blocks are force-only");
+  const bool mixed = c->o.precision == NBODY_MIXED;
   std::vector<int4> off_diag, diag;
   int64_t rows = 1;
   std::vector<uint16_t> nsl(static_cast<size_t>(c->N), 0);
@@ -417,13 +444,13 @@ nbody_status build_sym_work(nbody_ctx *c, Work &wk, int row_doubles, int B) {
     for (int64_t p = b; p < b + ns; ++p) nsl[p] = static_cast<uint16_t>(nb);
     for (int I = 0; I < nb; ++I)
       for (int J = I; J < nb; ++J)
-        (I == J ? diag : off_diag).push_back(make_int4(static_cast<int>(b), static_cast<int>(ns), I, J));
+        (I == J ? diag : off_diag).push_back(make_int4(static_cast<int>(c->soff[s]), static_cast<int>(ns), I, J));
   }
   std::vector<int4> pairs = std::move(off_diag);
   pairs.insert(pairs.end(), diag.begin(), diag.end());
   if (rows > 65535 || pairs.size() > static_cast<size_t>(INT32_MAX))
     return fail(c, NBODY_EINVAL, "too many pair-once blocks (%lld in a system)", static_cast<long long>(rows));
-  const int occ = nb::force_sym_ctas_per_sm(B / 32);
+  const int occ = mixed ? nb::force_msym_ctas_per_sm(B / 32, B / 128) : nb::force_sym_ctas_per_sm(B / 32);
   if (occ < 1) return fail(c, NBODY_ECUDA, "the pair-once FP64 kernel does not fit on an SM");
   wk.nsl_rank = nsl;
   wk.plan_off = c->tgt_off;
@@ -721,6 +748,21 @@ nbody_status launch_force_kernel(nbody_ctx *c, const void *cur, cudaStream_t st,
     a.ctr = c->fw.dyn_ctr;
     a.N = c->N;
     a.tiles = c->fw.sym_tiles;
+    if (c->o.precision == NBODY_MIXED) {
+      nb::MsymArgs m{};
+      m.cur = static_cast<const float *>(cur);
+      m.boxes = c->boxes;
+      m.partial = c->fw.partial;
+      m.pairs = c->fw.sym_pairs;
+      m.perm = c->perm;
+      m.n_pairs = c->fw.n_sym;
+      m.ctr = c->fw.dyn_ctr;
+      m.N = static_cast<int32_t>(c->N);
+      m.tiles = c->fw.sym_tiles;
+      m.warps = c->fw.sym_tiles / 4;
+      NB_CUDA(c, nb::launch_force_msym(m, c->fw.grid, st, chained));
+      return NBODY_OK;
+    }
     NB_CUDA(c, nb::launch_force_sym(a, c->fw.grid, st, chained));
     return NBODY_OK;
   }
@@ -1236,9 +1278,15 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
       return fail(nullptr, NBODY_EINVAL, "close-encounter handling runs with the Verlet integrator only");
   }
   if (const int B = o->pair_once_block) {
-    if (B != nb::kSymBlock && !(B >= 32 * nb::kSymWideMinTiles && B <= 32 * nb::kSymWideMaxTiles && (B & (B - 1)) == 0))
+    const bool pow2 = B > 0 && (B & (B - 1)) == 0;
+    if (o->precision == NBODY_MIXED) {
+      if (!(pow2 && B >= 32 * nb::kMsymMinTiles && B <= 32 * nb::kMsymMaxTiles))
+        return fail(nullptr, NBODY_EINVAL, "pair_once_block (mixed) must be 0 or a power of two from %d to %d",
+                    32 * nb::kMsymMinTiles, 32 * nb::kMsymMaxTiles);
+    } else if (B != nb::kSymBlock && !(pow2 && B >= 32 * nb::kSymWideMinTiles && B <= 32 * nb::kSymWideMaxTiles)) {
       return fail(nullptr, NBODY_EINVAL, "pair_once_block must be 0, 64 or a power of two from %d to %d",
                   32 * nb::kSymWideMinTiles, 32 * nb::kSymWideMaxTiles);
+    }
     int64_t rows = 1;
     for (int64_t s = 0; s < n_systems; ++s) rows = std::max(rows, (offsets[s + 1] - offsets[s] + B - 1) / B);
     if (rows > 65535 || rows * 3 * static_cast<int64_t>(sizeof(double)) * offsets[n_systems] > kSymRowLimit)

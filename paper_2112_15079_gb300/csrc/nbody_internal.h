@@ -158,6 +158,25 @@ struct SymArgs {
   int32_t tiles;           // 32-body tiles per block: 2 (64-body blocks, force_sym_kernel) or wide
 };
 
+// Mixed force kernel with each pair once (sym_mixed.cu): block pairs (I, J),
+// I <= J, of 32 T stage entries of one system; a CTA of W = T / 4 warps per
+// item.
+constexpr int kMsymMinTiles = 4;   // 128 entries: one warp's four target tiles
+constexpr int kMsymMaxTiles = 64;  // 2,048 entries
+constexpr int kMsymMaxWarps = kMsymMaxTiles / 4;
+struct MsymArgs {
+  const float *cur;        // mixed stage (pair blocks of two entries)
+  const float4 *boxes;     // [groups][2] widened boxes of the stage groups (box_kernel)
+  double *partial;         // [blocks][3][N] float pairs: row J of a body of block I holds block J's pull
+  const int4 *pairs;       // (first stage entry of the system, its bodies, I, J)
+  const int32_t *perm;     // [stage entries] body of each entry
+  int32_t n_pairs;
+  int32_t *ctr;            // [2]: next item, CTAs done (the last one resets both)
+  int32_t N;
+  int32_t tiles;           // T: 32-entry tiles per block, kMsymMinTiles .. kMsymMaxTiles (a power of two)
+  int32_t warps;           // W = T / 4 warps per CTA
+};
+
 // The adjoint's VJP with each pair once (FP64, sym.cu): the same items,
 // rows of 4 values per body (J^T w and the mass sum).
 struct VjpSymArgs {
@@ -264,6 +283,9 @@ cudaError_t launch_force_sym(const SymArgs &a, int grid, cudaStream_t s, bool ch
 cudaError_t launch_vjp_sym(const VjpSymArgs &a, int grid, cudaStream_t s);
 int force_sym_ctas_per_sm(int tiles);   // resident CTAs per SM (raises the wide kernel's smem limit)
 size_t force_sym_smem_bytes(int tiles);
+cudaError_t launch_force_msym(const MsymArgs &a, int grid, cudaStream_t s, bool chained);
+int force_msym_ctas_per_sm(int tiles, int warps);  // resident CTAs per SM (raises the smem limit)
+size_t force_msym_smem_bytes(int tiles, int warps);
 cudaError_t launch_close(const CloseArgs &a, int n_clusters, cudaStream_t s, bool chained);
 cudaError_t launch_close_far(const CloseArgs &a, cudaStream_t s, bool chained);
 cudaError_t launch_energy(const EnergyArgs &a, cudaStream_t s);

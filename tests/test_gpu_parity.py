@@ -35,8 +35,9 @@ def nb():
     return nbody
 
 
-def _make(nb, s, precision, tiles=None, graphs=True, offsets=None, small=True):
-    b = nb.NBody(s.r, s.v, s.m, offsets, G=s.G, dt=s.dt, precision=precision, graphs=graphs, small=small)
+def _make(nb, s, precision, tiles=None, graphs=True, offsets=None, small=True, pair_once=True):
+    b = nb.NBody(s.r, s.v, s.m, offsets, G=s.G, dt=s.dt, precision=precision, graphs=graphs, small=small,
+                 pair_once=pair_once)
     if tiles:
         t = b.tiles
         t.update(tiles)
@@ -94,13 +95,16 @@ def test_initial_accel_vs_oracle(nb, precision, tiles, n):
     _check_accel(precision, a, ref, oracle.term_norm(s.G, s.r, s.m, openmp=True))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_full_size_10425_accel_every_body(nb, precision, record_property):
-    """The 10,425-body Solar-System-shaped model, all bodies, default tiles.
-    The mixed gate's exclusions are reported (no body of this model has
-    T_p / |a_p| > 1e3: the Sun's pull dominates every sum)."""
+@pytest.mark.parametrize("precision,pair_once", [("fp64", True), ("fp64", False), ("mixed", False)])
+def test_full_size_10425_accel_every_body(nb, precision, pair_once, record_property):
+    """The 10,425-body Solar-System-shaped model, all bodies, default tiles
+    (FP64: with the pair-once kernel, the default, and with the every-
+    ordered-pair kernel; mixed: the every-ordered-pair kernel, its default at
+    this size).  The mixed gate's exclusions are reported (no body of this
+    model has T_p / |a_p| > 1e3: the Sun's pull dominates every sum)."""
     s = inputs.solar_system(10425)
-    b = _make(nb, s, precision)
+    b = _make(nb, s, precision, pair_once=pair_once)
+    assert b.pair_once == pair_once
     a = b.accel().cpu().numpy()
     ref = oracle.accel(s.G, s.r, s.m, openmp=True)
     rep = _check_accel(precision, a, ref, oracle.term_norm(s.G, s.r, s.m, openmp=True))
