@@ -13,28 +13,29 @@
 // handed out by a counter.  A CTA of W = T / 4 warps takes an item: warp p
 // holds block I's entries [128 p, 128 p + 128) in registers, four per lane
 // (slot a: entry 128 p + 32 a + lane).  Block J is cut into chunks of 64
-// entries; in phase t the warp takes chunk c = (2 p + t) mod (T / 2), two
-// entries per lane (slot h: entry 64 c + 32 h + lane, packed in one f32x2
-// register pair), and rotates them around the warp with shuffles: in 32
-// steps every source meets every target once, eight pairs per lane and
-// step, the two sources of a lane in one packed instruction.  The chunk's
-// 2 KB of stage pair blocks are copied (cp.async) into the warp's shared
-// memory a phase ahead.  The sources' reaction sums rotate with them; a
-// CTA barrier closes each phase, and within a phase the warps' chunks
-// differ, so each chunk belongs to one warp and its sums in shared memory
-// take their terms in phase order.
+// entries; in phase t the warp takes chunk c = (2 p + t) mod (T / 2).  The
+// chunk's 32 stage pair blocks (two entries each, 64 B) are copied
+// (cp.async) into the warp's shared memory a phase ahead, the four 16-byte
+// pieces of each block into four arrays, so that at step k lane l reads
+// pair block (l + k) mod 32 without bank conflicts, its two entries already
+// packed as f32x2 operands: in 32 steps every source meets every target
+// once, eight pairs per lane and step, the two sources of a lane in one
+// packed instruction.  The sources' reaction sums rotate around the warp
+// with shuffles, one lane per step; a CTA barrier closes each phase, and
+// within a phase the warps' chunks differ, so each chunk belongs to one
+// warp and its sums in shared memory take their terms in phase order.
 //
 // Sums, all float pairs (hi, lo) fed through TwoSum: a target's packed
 // per-slot sums every two phases (64 terms per half), a source's reaction
-// sums twice per phase (after 16 steps, when the sources that started in
-// lane l sit in lane l - 16, and at the end; 64 terms per half).
+// sums twice per phase (after 16 steps, when the sums of the sources of pair
+// block l sit in lane l - 16, and at the end; 64 terms per half).
 // Off-diagonal items: block I's sums go to row J of its bodies, block J's to
-// row I.  Diagonal items (I == J) take the 32-entry tile pairs (i, j) with
-// i <= j once, i == j as the half rotation (offsets 1..16 for the target,
-// 1..15 for the reaction), by weights on the two chunks that meet the
-// warp's own tiles; each warp adds its targets' sums into the block's
-// shared sums after the last phase, and the total goes to row I.  Entries past
-// the end of a system's stage are inert (massless, far away, distinct).
+// row I.  Diagonal items (I == J) take each pair (target entry e, source
+// entry f) with e < f, by weights on the two chunks that meet the warp's
+// own entries (the others are wholly above or below them); each warp adds
+// its targets' sums into the block's shared sums after the last phase, and
+// the total goes to row I.  Entries past the end of a system's stage are
+// inert (massless, far away, distinct).
 //
 // Far test: a chunk takes the hi-only difference when the union of the
 // widened boxes (box_kernel) of the 64-entry stage groups holding the
@@ -46,14 +47,17 @@ namespace nb {
 
 namespace {
 
-// Per-warp shared scratch: the targets' negated lo parts (duplicated in both
-// halves, read by the near path) and their running float-pair sums.
+// Per-warp shared scratch: two chunk buffers, the targets' negated lo parts
+// (duplicated in both halves, read by the near path) and their running
+// float-pair sums.
 struct MsymWarp {
-  float chunk[32 * 16];  // the next chunk's 32 stage pair blocks (cp.async, a phase ahead)
-  f2 tlo[4][3][32];      // [slot a][component][lane]
-  f2 clo[3][32];         // the chunk's lo parts [component][home lane] (slots packed), for the near path
-  float sum[4][6][32];   // [slot a][x hi, x lo, y hi, y lo, z hi, z lo][lane]
-  float4 box[2];         // the union of the widened boxes of the targets' groups
+  // [buffer][piece][pair block]: the 16-byte pieces (xh0 xh1 yh0 yh1),
+  // (zh0 zh1 mu0 mu1), (xl0 xl1 yl0 yl1), (zl0 zl1 - -) of a chunk's pair blocks
+  float4 src[2][4][32];
+  f2 tlo[4][3][32];     // [slot a][component][lane]
+  f2 tmu[4][32];        // MU_SMEM: the targets' mu (duplicated) [slot a][lane]
+  float sum[4][6][32];  // [slot a][x hi, x lo, y hi, y lo, z hi, z lo][lane]
+  float4 box[2];        // the union of the widened boxes of the targets' groups
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -102,64 +106,42 @@ __device__ __forceinline__ float4 msym_lo(const float *cur, int s0, int e, int n
   return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Entry u (0..63) of a staged chunk whose first entry is local entry jb:
-// hi and mu into h, lo into l (inert past the system's nst entries).
-__device__ __forceinline__ void chunk_entry(const float *chunk, int jb, int u, int nst, float4 &h, float4 &l) {
-  if (jb + u < nst) {
-    const float *q = chunk + pair_off(u);
-    h = make_float4(q[kXh], q[kYh], q[kZh], q[kMu]);
-    l = make_float4(q[kXl], q[kYl], q[kZl], 0.f);
-  } else {
-    const float x = 2.f * kPadCoord + 1e12f * static_cast<float>(jb + u - nst);
-    h = make_float4(x, x, x, 0.f);
-    l = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-// Diagonal items: the class of the tile pair (target tile it, source tile
-// jt), 2 bits: tile pairs i < j in full (1), i == j as the half rotation
-// (2), i > j not at all (0: that pair is the warp holding tile j's).
-__device__ __forceinline__ int diag_class(int it, int jt) { return it < jt ? 1 : it == jt ? 2 : 0; }
-
-// The target weight and the reaction weight of a pair of class cls at
-// rotation offset k (half rotation: offsets 1..16 for the target, 1..15 for
-// the reaction).
-__device__ __forceinline__ void diag_weights(int cls, int k, float &wt, float &wr) {
-  wt = (cls == 1 || (cls == 2 && k >= 1 && k <= 16)) ? 1.f : 0.f;
-  wr = (cls == 1 || (cls == 2 && k >= 1 && k <= 15)) ? 1.f : 0.f;
-}
-
-// One chunk: 32 rotation steps of the lane's two packed sources past its
-// four targets.  Reaction sums fold into the chunk's shared sums s_j (local
-// chunk entry jc + 32 h + lane) half way and at the end.  NEAR: the sources'
-// lo parts come from ws.clo (at step k the lane holds the sources of lane
-// lane + k).  MASKED: diagonal weights, from the class of the tile pair of
-// target slot a and source slot h in bits 2 (2 a + h) of codes.
-template <bool NEAR, bool MASKED>
-__device__ __forceinline__ void msym_chunk(f2 sx, f2 sy, f2 sz, f2 sm, const f2 (&nxh)[4],
-                                           const f2 (&nyh)[4], const f2 (&nzh)[4], const f2 (&tmu)[4],
-                                           const MsymWarp &ws, int lane, int codes, f2 (&ax)[4],
-                                           f2 (&ay)[4], f2 (&az)[4], float *s_j, int BT, int jc) {
+// One chunk: 32 rotation steps of the chunk's sources past the lane's four
+// targets; at step k lane l takes the two entries of pair block
+// (l + k) mod 32 from the chunk buffer cb.  Reaction sums fold into the
+// chunk's shared sums s_j (local chunk entries jc + 2 m + h for pair block
+// m) half way and at the end.  MASKED (a diagonal item): a pair counts only
+// if the target's entry, et0 + 32 a, precedes the source's, jc + 2 m + h.
+// MU_SMEM: the targets' mu come from ws.tmu instead of registers.
+template <bool NEAR, bool MASKED, bool MU_SMEM>
+__device__ __forceinline__ void msym_chunk(const float4 (*cb)[32], const f2 (&nxh)[4], const f2 (&nyh)[4],
+                                           const f2 (&nzh)[4], const f2 (&tmu)[4], const MsymWarp &ws, int lane,
+                                           int et0, f2 (&ax)[4], f2 (&ay)[4], f2 (&az)[4], float *s_j, int BT,
+                                           int jc) {
   f2 bx = 0ull, by = 0ull, bz = 0ull;
-  // the reaction sums held here belong to the sources that started in lane `home`
-  auto fold = [&](int home) {
+  // the reaction sums held here belong to the sources of pair block m
+  auto fold = [&](int m) {
     const f2 b[3] = {bx, by, bz};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       float b0, b1;
       upk(b[d], b0, b1);
-      const int e0 = jc + home, e1 = jc + 32 + home;
+      const int e0 = jc + 2 * m;
       two_sum_acc(s_j[(2 * d) * BT + e0], s_j[(2 * d + 1) * BT + e0], -b0);
-      two_sum_acc(s_j[(2 * d) * BT + e1], s_j[(2 * d + 1) * BT + e1], -b1);
+      two_sum_acc(s_j[(2 * d) * BT + e0 + 1], s_j[(2 * d + 1) * BT + e0 + 1], -b1);
     }
   };
   auto step = [&](int k) {
+    const int m = (lane + k) & 31;
+    const float4 A = cb[0][m], B = cb[1][m];
+    const f2 sx = pk(A.x, A.y), sy = pk(A.z, A.w), sz = pk(B.x, B.y), sm = pk(B.z, B.w);
     f2 sxl = 0ull, syl = 0ull, szl = 0ull;
     if (NEAR) {
-      const int hl = (lane + k) & 31;
-      sxl = ws.clo[0][hl];
-      syl = ws.clo[1][hl];
-      szl = ws.clo[2][hl];
+      const float4 C = cb[2][m];
+      const float2 D = *reinterpret_cast<const float2 *>(&cb[3][m]);  // (zl0, zl1)
+      sxl = pk(C.x, C.y);
+      syl = pk(C.z, C.w);
+      szl = pk(D.x, D.y);
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -174,19 +156,21 @@ __device__ __forceinline__ void msym_chunk(f2 sx, f2 sy, f2 sz, f2 sm, const f2 
       r2 = fma2(dz, dz, r2);
       float ra, rb;
       upk(r2, ra, rb);
-      float wt0 = 1.f, wr0 = 1.f, wt1 = 1.f, wr1 = 1.f;
+      float w0 = 1.f, w1 = 1.f;
       if (MASKED) {
-        diag_weights((codes >> (4 * a)) & 3, k, wt0, wr0);
-        diag_weights((codes >> (4 * a + 2)) & 3, k, wt1, wr1);
-        ra = (wt0 != 0.f || wr0 != 0.f) ? ra : 1.f;  // a target with itself: r2 = 0
-        rb = (wt1 != 0.f || wr1 != 0.f) ? rb : 1.f;
+        const int et = et0 + 32 * a, es = jc + 2 * m;
+        w0 = et < es ? 1.f : 0.f;
+        w1 = et < es + 1 ? 1.f : 0.f;
+        ra = w0 != 0.f ? ra : 1.f;  // (a target with itself: r2 = 0)
+        rb = w1 != 0.f ? rb : 1.f;
       }
       const f2 q = pk(rsqrt_approx(ra), rsqrt_approx(rb));
       const f2 q3 = mul2(mul2(q, q), q);
-      f2 fi = mul2(sm, q3), fj = mul2(tmu[a], q3);
+      f2 fi = mul2(sm, q3), fj = mul2(MU_SMEM ? ws.tmu[a][lane] : tmu[a], q3);
       if (MASKED) {
-        fi = mul2(fi, pk(wt0, wt1));
-        fj = mul2(fj, pk(wr0, wr1));
+        const f2 wgt = pk(w0, w1);
+        fi = mul2(fi, wgt);
+        fj = mul2(fj, wgt);
       }
       ax[a] = fma2(fi, dx, ax[a]);
       ay[a] = fma2(fi, dy, ay[a]);
@@ -195,11 +179,7 @@ __device__ __forceinline__ void msym_chunk(f2 sx, f2 sy, f2 sz, f2 sm, const f2 
       by = fma2(fj, dy, by);
       bz = fma2(fj, dz, bz);
     }
-    const int src = (lane + 1) & 31;
-    sx = __shfl_sync(0xffffffffu, sx, src);
-    sy = __shfl_sync(0xffffffffu, sy, src);
-    sz = __shfl_sync(0xffffffffu, sz, src);
-    sm = __shfl_sync(0xffffffffu, sm, src);
+    const int src = (lane + 1) & 31;  // the sums follow their sources to the next lane's step
     bx = __shfl_sync(0xffffffffu, bx, src);
     by = __shfl_sync(0xffffffffu, by, src);
     bz = __shfl_sync(0xffffffffu, bz, src);
@@ -215,6 +195,11 @@ __device__ __forceinline__ void msym_chunk(f2 sx, f2 sy, f2 sz, f2 sm, const f2 
 
 }  // namespace
 
+// MU_SMEM: the targets' mu in shared memory, which frees 8 registers in the
+// rotation loop (measured on GB300: faster with 2,048-entry blocks, 16-warp
+// CTAs: 1,048,576 bodies 395 against 403 ms per step; slower with 512-entry
+// blocks: 65,536 bodies 1.71 against 1.64 ms).
+template <bool MU_SMEM>
 __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const MsymArgs a) {
   extern __shared__ __align__(16) unsigned char msym_smem[];
   __shared__ int s_item;
@@ -243,16 +228,26 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
       const int p = w;               // one round: W = T / 4 warps cover block I
       const int ib = i0 + 128 * p;   // this warp's targets: local entries [ib, ib + 128)
       const bool p_live = ib < nst;  // warp-uniform
-      // copy chunk cc's stage pair blocks (those inside the system) into ws.chunk
-      auto stage_chunk = [&](int cc) {
+      // chunk cc into buffer bb: lane l copies pair block l (its four
+      // pieces) if it lies inside the system, else writes two inert entries
+      auto stage_chunk = [&](int cc, int bb) {
         const int jb = j0 + 64 * cc;
-        const int npb = min(32, (nst - jb) / 2);
-        const float *src = cur + static_cast<size_t>((s0 + jb) >> 1) * 16;
-        for (int q = lane; q < 4 * npb; q += 32) cp_async16(&ws.chunk[4 * q], src + 4 * q);
+        const int e0 = jb + 2 * lane;  // the block's first local entry
+        if (e0 < nst) {
+          const float4 *src = reinterpret_cast<const float4 *>(cur) + static_cast<size_t>((s0 + e0) >> 1) * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cp_async16(&ws.src[bb][q][lane], src + q);
+        } else {
+          const float x0 = 2.f * kPadCoord + 1e12f * static_cast<float>(e0 - nst), x1 = x0 + 1e12f;
+          ws.src[bb][0][lane] = make_float4(x0, x1, x0, x1);
+          ws.src[bb][1][lane] = make_float4(x0, x1, 0.f, 0.f);
+          ws.src[bb][2][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+          ws.src[bb][3][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         cp_async_commit();
       };
       int c = (2 * p) % NC;
-      if (p_live) stage_chunk(c);
+      if (p_live) stage_chunk(c, 0);
       f2 nxh[4], nyh[4], nzh[4], tmu[4], ax[4], ay[4], az[4];
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
@@ -262,6 +257,7 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
         nyh[s] = pk(-h.y, -h.y);
         nzh[s] = pk(-h.z, -h.z);
         tmu[s] = pk(h.w, h.w);
+        ws.tmu[s][lane] = tmu[s];
         ws.tlo[s][0][lane] = pk(-l.x, -l.x);
         ws.tlo[s][1][lane] = pk(-l.y, -l.y);
         ws.tlo[s][2][lane] = pk(-l.z, -l.z);
@@ -295,30 +291,21 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
         const bool masked = diag && 2 * cc <= 4 * p + 3;
         if (p_live) {
           cp_async_wait_all();
-          __syncwarp();  // every lane's copies have landed
-          float4 h0, l0, h1, l1;
-          chunk_entry(ws.chunk, jb, lane, nst, h0, l0);
-          chunk_entry(ws.chunk, jb, 32 + lane, nst, h1, l1);
-          ws.clo[0][lane] = pk(l0.x, l1.x);
-          ws.clo[1][lane] = pk(l0.y, l1.y);
-          ws.clo[2][lane] = pk(l0.z, l1.z);
-          __syncwarp();  // the chunk is read: the next one may land over it
-          if (t + 1 < NC) stage_chunk(c);
+          __syncwarp();  // every lane's copies (and inert entries) are in buffer t & 1
+          // the next chunk into the other buffer, read last in the previous phase
+          if (t + 1 < NC) stage_chunk(c, (t + 1) & 1);
           if (jb < nst && !skip) {
             float4 jlo, jhi;
             box_union(a.boxes, s0 + jb, s0 + min(jb + 64, nst), jlo, jhi);
             const bool far = boxes_apart(ws.box[0], ws.box[1], jlo, jhi);
-            const f2 sx = pk(h0.x, h1.x), sy = pk(h0.y, h1.y), sz = pk(h0.z, h1.z), sm = pk(h0.w, h1.w);
-            const int jc = 64 * cc;
+            const float4(*cb)[32] = ws.src[t & 1];
+            const int jc = 64 * cc, et0 = 128 * p + lane;
             if (far && !masked)
-              msym_chunk<false, false>(sx, sy, sz, sm, nxh, nyh, nzh, tmu, ws, lane, 0, ax, ay, az, s_j, BT, jc);
-            else if (masked) {
-              int codes = 0;
-              for (int u = 0; u < 8; ++u) codes |= diag_class(4 * p + (u >> 1), 2 * cc + (u & 1)) << (2 * u);
-              msym_chunk<true, true>(sx, sy, sz, sm, nxh, nyh, nzh, tmu, ws, lane, codes, ax, ay, az, s_j, BT, jc);
-            } else {
-              msym_chunk<true, false>(sx, sy, sz, sm, nxh, nyh, nzh, tmu, ws, lane, 0, ax, ay, az, s_j, BT, jc);
-            }
+              msym_chunk<false, false, MU_SMEM>(cb, nxh, nyh, nzh, tmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
+            else if (masked)
+              msym_chunk<true, true, MU_SMEM>(cb, nxh, nyh, nzh, tmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
+            else
+              msym_chunk<true, false, MU_SMEM>(cb, nxh, nyh, nzh, tmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
           }
         }
         if ((t & 1) || t + 1 == NC) fold_targets();
@@ -365,6 +352,10 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
   }
 }
 
+namespace {
+bool msym_mu_smem(int tiles) { return tiles == kMsymMaxTiles; }
+}  // namespace
+
 size_t force_msym_smem_bytes(int tiles, int warps) {
   return static_cast<size_t>(warps) * sizeof(MsymWarp) + sizeof(float) * 6 * 32 * static_cast<size_t>(tiles);
 }
@@ -380,16 +371,20 @@ cudaError_t launch_force_msym(const MsymArgs &a, int grid, cudaStream_t s, bool 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, force_msym_kernel, a);
+  if (msym_mu_smem(a.tiles)) return cudaLaunchKernelEx(&cfg, force_msym_kernel<true>, a);
+  return cudaLaunchKernelEx(&cfg, force_msym_kernel<false>, a);
 }
 
 int force_msym_ctas_per_sm(int tiles, int warps) {
   int occ = 0;
-  cudaError_t e = cudaFuncSetAttribute(force_msym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(force_msym_smem_bytes(kMsymMaxTiles, kMsymMaxWarps)));
+  const int max_smem = static_cast<int>(force_msym_smem_bytes(kMsymMaxTiles, kMsymMaxWarps));
+  cudaError_t e = cudaFuncSetAttribute(force_msym_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_msym_kernel, 32 * warps,
-                                                      force_msym_smem_bytes(tiles, warps));
+    e = cudaFuncSetAttribute(force_msym_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, msym_mu_smem(tiles) ? force_msym_kernel<true>
+                                                                               : force_msym_kernel<false>,
+                                                      32 * warps, force_msym_smem_bytes(tiles, warps));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
