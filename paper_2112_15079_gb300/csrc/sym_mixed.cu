@@ -55,7 +55,6 @@ struct MsymWarp {
   // (zh0 zh1 mu0 mu1), (xl0 xl1 yl0 yl1), (zl0 zl1 - -) of a chunk's pair blocks
   float4 src[2][4][32];
   f2 tlo[4][3][32];     // [slot a][component][lane]
-  f2 tmu[4][32];        // MU_SMEM: the targets' mu (duplicated) [slot a][lane]
   float sum[4][6][32];  // [slot a][x hi, x lo, y hi, y lo, z hi, z lo][lane]
   float4 box[2];        // the union of the widened boxes of the targets' groups
 };
@@ -112,10 +111,12 @@ __device__ __forceinline__ float4 msym_lo(const float *cur, int s0, int e, int n
 // chunk's shared sums s_j (local chunk entries jc + 2 m + h for pair block
 // m) half way and at the end.  MASKED (a diagonal item): a pair counts only
 // if the target's entry, et0 + 32 a, precedes the source's, jc + 2 m + h.
-// MU_SMEM: the targets' mu come from ws.tmu instead of registers.
+// MU_SMEM: the targets' mu come from wmu ([slot a][lane], shared memory)
+// instead of registers.
 template <bool NEAR, bool MASKED, bool MU_SMEM>
 __device__ __forceinline__ void msym_chunk(const float4 (*cb)[32], const f2 (&nxh)[4], const f2 (&nyh)[4],
-                                           const f2 (&nzh)[4], const f2 (&tmu)[4], const MsymWarp &ws, int lane,
+                                           const f2 (&nzh)[4], const f2 (&tmu)[4], const f2 (*wmu)[32],
+                                           const MsymWarp &ws, int lane,
                                            int et0, f2 (&ax)[4], f2 (&ay)[4], f2 (&az)[4], float *s_j, int BT,
                                            int jc) {
   f2 bx = 0ull, by = 0ull, bz = 0ull;
@@ -166,7 +167,7 @@ __device__ __forceinline__ void msym_chunk(const float4 (*cb)[32], const f2 (&nx
       }
       const f2 q = pk(rsqrt_approx(ra), rsqrt_approx(rb));
       const f2 q3 = mul2(mul2(q, q), q);
-      f2 fi = mul2(sm, q3), fj = mul2(MU_SMEM ? ws.tmu[a][lane] : tmu[a], q3);
+      f2 fi = mul2(sm, q3), fj = mul2(MU_SMEM ? wmu[a][lane] : tmu[a], q3);
       if (MASKED) {
         const f2 wgt = pk(w0, w1);
         fi = mul2(fi, wgt);
@@ -210,6 +211,8 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
   MsymWarp &ws = reinterpret_cast<MsymWarp *>(msym_smem)[w];
   // block J's sums of the item: [x hi, x lo, y hi, y lo, z hi, z lo][BT]
   float *s_j = reinterpret_cast<float *>(msym_smem + static_cast<size_t>(W) * sizeof(MsymWarp));
+  // MU_SMEM: this warp's targets' mu, after the sums
+  f2 (*wmu)[32] = reinterpret_cast<f2 (*)[32]>(s_j + 6 * BT) + 4 * w;
   const size_t N = static_cast<size_t>(a.N);
   const float *cur = a.cur;
   for (;;) {
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
         nyh[s] = pk(-h.y, -h.y);
         nzh[s] = pk(-h.z, -h.z);
         tmu[s] = pk(h.w, h.w);
-        ws.tmu[s][lane] = tmu[s];
+        if (MU_SMEM) wmu[s][lane] = tmu[s];
         ws.tlo[s][0][lane] = pk(-l.x, -l.x);
         ws.tlo[s][1][lane] = pk(-l.y, -l.y);
         ws.tlo[s][2][lane] = pk(-l.z, -l.z);
@@ -301,11 +304,11 @@ __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const
             const float4(*cb)[32] = ws.src[t & 1];
             const int jc = 64 * cc, et0 = 128 * p + lane;
             if (far && !masked)
-              msym_chunk<false, false, MU_SMEM>(cb, nxh, nyh, nzh, tmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
+              msym_chunk<false, false, MU_SMEM>(cb, nxh, nyh, nzh, tmu, wmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
             else if (masked)
-              msym_chunk<true, true, MU_SMEM>(cb, nxh, nyh, nzh, tmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
+              msym_chunk<true, true, MU_SMEM>(cb, nxh, nyh, nzh, tmu, wmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
             else
-              msym_chunk<true, false, MU_SMEM>(cb, nxh, nyh, nzh, tmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
+              msym_chunk<true, false, MU_SMEM>(cb, nxh, nyh, nzh, tmu, wmu, ws, lane, et0, ax, ay, az, s_j, BT, jc);
           }
         }
         if ((t & 1) || t + 1 == NC) fold_targets();
@@ -357,7 +360,8 @@ bool msym_mu_smem(int tiles) { return tiles == kMsymMaxTiles; }
 }  // namespace
 
 size_t force_msym_smem_bytes(int tiles, int warps) {
-  return static_cast<size_t>(warps) * sizeof(MsymWarp) + sizeof(float) * 6 * 32 * static_cast<size_t>(tiles);
+  return static_cast<size_t>(warps) * sizeof(MsymWarp) + sizeof(float) * 6 * 32 * static_cast<size_t>(tiles) +
+         (msym_mu_smem(tiles) ? sizeof(f2) * 4 * 32 * static_cast<size_t>(warps) : 0);
 }
 
 cudaError_t launch_force_msym(const MsymArgs &a, int grid, cudaStream_t s, bool chained) {
