@@ -304,8 +304,8 @@ nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
 #define NBODY_STATIC_MAX_BODIES 65536
 
 /* All-pairs gravitational accelerations of ONE system, FP64, without
- * allocating device memory.  The paper has no counterpart: this is a
- * deployment variant of the force kernel.  Some callers cannot allocate: a host that reserves all device
+ * allocating device memory: a deployment variant of the force kernel.
+ * Some callers cannot allocate: a host that reserves all device
  * memory at start-up and forbids allocation afterwards (a real-time loop, a
  * service with a fixed memory budget), or a component running while another
  * allocator owns the device memory, where one more cudaMalloc may fail or
@@ -318,10 +318,11 @@ nbody_status nbody_kernel_times(nbody_ctx *ctx, int32_t n_steps, double *out);
  *   x, y, z, m   DEVICE arrays of n doubles (positions, masses >= 0).
  *   ax, ay, az   DEVICE arrays of n doubles, written with a_p.
  *   cuda_stream  stream to run on (NULL: legacy default stream).
- * Synchronous: returns after the results are written.  EINVAL for coincident
- * bodies or non-finite input.  Messages: nbody_last_error(NULL).
- * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Synchronous: returns after the results are written, so it cannot be
+ * captured into a CUDA graph: on a stream that is capturing it returns
+ * NBODY_EINVAL before any work.  EINVAL for coincident bodies or non-finite
+ * input.  Messages: nbody_last_error(NULL).  The first call on a device looks
+ * up the device address of the array (cudaGetSymbolAddress).
  * All calls on a device share the array and it keeps the last call's
  * contents; each call re-stages its inputs and clears its counters, but calls
  * that overlap on the GPU (other streams or host threads) race on the array

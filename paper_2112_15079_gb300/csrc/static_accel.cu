@@ -89,6 +89,12 @@ extern "C" nbody_status nbody_accel_static(int64_t n, double G, const double *x,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(NBODY_ECUDA, "no usable CUDA device");
+  // The call ends with a copy to pageable host memory and a synchronize,
+  // which a stream capture cannot hold: refuse before touching the stream.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap) != cudaSuccess)
+    return fail(NBODY_ECUDA, "cudaStreamIsCapturing failed");
+  if (cap != cudaStreamCaptureStatusNone) return fail(NBODY_EINVAL, "the stream is being captured into a graph");
   void *base = nullptr;
   {
     // First call on this device: find the device address of the array (the

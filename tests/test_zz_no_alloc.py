@@ -122,3 +122,26 @@ def test_static_accel_rejects_sizes_beyond_the_limit(nb):
     assert st == nb.NBODY_EINVAL
     assert b"NBODY_STATIC_MAX_BODIES" in nb.nbody_last_error(None)
     assert nb.nbody_accel_static(0, 1.0, p, p, p, p, p, p, p, None) == nb.NBODY_EINVAL
+
+
+def test_static_accel_refuses_a_capturing_stream(nb):
+    """The call ends with a synchronous copy, which a stream capture cannot
+    hold: on a capturing stream it returns EINVAL before any work, the
+    capture completes, and the next plain call works."""
+    torch = pytest.importorskip("torch")
+    s = inputs.solar_system(131, seed=75)
+    r, m, out = _buffers(torch, s)
+    _call(nb, s, r, m, out)  # warm: the device address of the array is known
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=side):
+        out.mul_(1.0)
+        st = nb.nbody_accel_static(s.n, s.G, r[0].data_ptr(), r[1].data_ptr(), r[2].data_ptr(), m.data_ptr(),
+                                   out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), side.cuda_stream)
+    assert st == nb.NBODY_EINVAL
+    assert b"captured" in nb.nbody_last_error(None)
+    g.replay()
+    torch.cuda.synchronize()
+    _call(nb, s, r, m, out)
+    want = oracle.accel(s.G, s.r, s.m)
+    assert _rel(out.cpu().numpy(), want).max() <= FP64_TOL
