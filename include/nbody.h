@@ -127,18 +127,26 @@ typedef struct {
    * EINVAL. */
   double close_omega_dt;
   double substep_omega_dt; /* w h per sub-step, > 0 when close_omega_dt > 0 (e.g. 0.05) */
-  /* Bodies per block of the FP64 force kernel that evaluates each pair once
-   * (NBODY_FLAG_NO_SYM), 0 = automatic.  A body keeps one partial sum (24 B)
-   * per block of its system.  Automatic: 64 when every system has at most
-   * 65,536 bodies; above, the narrowest of 256 .. 4,096 (powers of two)
-   * whose partial sums take at most 2 GiB, else 4,096 if they take at most
-   * 16 GiB (else every ordered pair is evaluated); and only when the systems
-   * hold at least 1.5 block pairs per SM.  Otherwise 64 or a power of two
-   * from 256 to 4,096, used whatever the systems' sizes (for FP64 contexts
-   * that are not row shards), if the partial sums take at most 16 GiB and
-   * 65,535 blocks per system, else nbody_init returns EINVAL.  Blocks above
-   * 64 bodies apply to the force only; nbody_grad's VJP then evaluates
-   * every ordered pair. */
+  /* Block size of the force kernels that evaluate each pair once (see
+   * NBODY_FLAG_NO_SYM), 0 = automatic.  A body keeps one partial sum (24 B)
+   * per block of its system.
+   *   FP64, bodies per block.  Automatic: 64 when every system has at most
+   *   65,536 bodies; above, the narrowest of 256 .. 4,096 (powers of two)
+   *   whose partial sums take at most 2 GiB, else 4,096 if they take at most
+   *   16 GiB (else every ordered pair is evaluated); and only when the
+   *   systems hold at least 1.5 block pairs per SM.  Or set: 64, or a power
+   *   of two from 256 to 4,096.  Blocks above 64 apply to the force only:
+   *   nbody_grad's VJP then evaluates every ordered pair.
+   *   Mixed, stage entries per block (the stage holds each system's bodies
+   *   in a spatial order).  Automatic: for a largest system of at least
+   *   65,536 bodies, the narrowest of 128 .. 2,048 that leaves it at most 128
+   *   partial sums per body, if the block pairs keep 8 warps per SM busy and
+   *   the sums take at most 16 GiB (else, and below 65,536 bodies, every
+   *   ordered pair is evaluated).  Or set: a power of two from 128 to 2,048.
+   *   Force only (nbody_grad's VJP evaluates every ordered pair).
+   * A set size is used whatever the systems' sizes (for contexts that are
+   * not row shards) if the partial sums take at most 16 GiB and 65,535 blocks
+   * per system, else nbody_init returns EINVAL. */
   int32_t pair_once_block;
 } nbody_opts;
 
@@ -149,14 +157,15 @@ typedef struct {
  * 8- or 16-CTA cluster up to 96 bodies, of a cooperative grid beyond,
  * unless this flag is set). */
 #define NBODY_FLAG_NO_SMALL 2
-/* FP64: use the force kernel that evaluates every ordered pair (p, j) on its
+/* Use the force kernel that evaluates every ordered pair (p, j) on its
  * own, instead of the default one that evaluates each pair once and applies
  * it to both bodies (a_p += mu_j |d|^-3 d, a_j -= mu_p |d|^-3 d: Eq. 1 to
- * rounding, 20 FP64 operations per two interactions instead of 32).  The
- * default is used for contexts that are not row shards, when the systems
- * hold at least 1.5 block pairs per SM (64-body blocks: about 1,200 bodies
- * in one system; below that the other kernel is faster) and the partial
- * sums fit (nbody_opts.pair_once_block). */
+ * rounding, 20 FP64 operations per two interactions instead of 32; mixed:
+ * 16 FP32 operations per two interactions of a far pair instead of 24).
+ * FP64 uses it for contexts that are not row shards, when the systems hold
+ * at least 1.5 block pairs per SM (64-body blocks: about 1,200 bodies in one
+ * system; below that the other kernel is faster) and the partial sums fit;
+ * mixed for systems of at least 65,536 bodies (nbody_opts.pair_once_block). */
 #define NBODY_FLAG_NO_SYM 4
 
 /* Work decomposition of the force kernels (see nbody_set_tiles).  The work
@@ -224,9 +233,10 @@ nbody_status nbody_accel(nbody_ctx *ctx, double *ax, double *ay, double *az);
  * like nbody_init). */
 nbody_status nbody_reset(nbody_ctx *ctx);
 
-/* The bodies per block (64 .. 4,096, see nbody_opts.pair_once_block) in *on
- * if the context's force launches evaluate each pair once (the FP64
- * default, see NBODY_FLAG_NO_SYM), else 0.  HOST pointer. */
+/* The block size (FP64 bodies, 64 .. 4,096; mixed stage entries, 128 ..
+ * 2,048; see nbody_opts.pair_once_block) in *on if the context's force
+ * launches evaluate each pair once (see NBODY_FLAG_NO_SYM), else 0.  HOST
+ * pointer. */
 nbody_status nbody_pair_once(const nbody_ctx *ctx, int32_t *on);
 
 /* Close-encounter handling (nbody_opts.close_omega_dt): the close pairs,

@@ -68,17 +68,21 @@ def test_errors_without_context_are_reported():
 
 
 def test_pair_once_block_is_validated():
-    """nbody_opts.pair_once_block: 0, 64 or a power of two from 256 to 4,096,
-    with partial sums of at most 16 GiB and 65,535 blocks per system; checked
-    before any CUDA call (the state pointers are never read)."""
+    """nbody_opts.pair_once_block: FP64 0, 64 or a power of two from 256 to
+    4,096, mixed 0 or a power of two from 128 to 2,048, with partial sums of
+    at most 16 GiB and 65,535 blocks per system; checked before any CUDA call
+    (the state pointers are never read)."""
     from paper_2112_15079_gb300 import nbody
     buf = (ctypes.c_double * 4)()
     ptrs = [ctypes.cast(buf, ctypes.c_void_p)] * 7
-    for block, n, msg in [(128, 2, b"power of two"), (8192, 2, b"power of two"), (300, 2, b"power of two"),
-                          (-1, 2, b"power of two"), (256, 1 << 30, b"exceed")]:
+    cases = [(0, 128, 2, b"power of two"), (0, 8192, 2, b"power of two"), (0, 300, 2, b"power of two"),
+             (0, -1, 2, b"power of two"), (0, 256, 1 << 30, b"exceed"),
+             # mixed: 128 .. 2,048 stage entries (no 64-entry blocks)
+             (1, 64, 2, b"(mixed)"), (1, 4096, 2, b"(mixed)"), (1, 96, 2, b"(mixed)"), (1, 128, 1 << 30, b"exceed")]
+    for prec, block, n, msg in cases:
         ctx = ctypes.c_void_p()
         off = (ctypes.c_int64 * 2)(0, n)
-        opts = nbody.nbody_opts(G=1.0, dt=0.1, precision=0, pair_once_block=block)
+        opts = nbody.nbody_opts(G=1.0, dt=0.1, precision=prec, pair_once_block=block)
         st = nbody.nbody_init(ctypes.byref(ctx), 1, off, *ptrs, ctypes.byref(opts), None)
-        assert st == nbody.NBODY_EINVAL, block
-        assert msg in nbody.nbody_last_error(None), (block, nbody.nbody_last_error(None))
+        assert st == nbody.NBODY_EINVAL, (prec, block)
+        assert msg in nbody.nbody_last_error(None), (prec, block, nbody.nbody_last_error(None))
