@@ -193,14 +193,15 @@ class NBody:
 
     @property
     def pair_once(self) -> bool:
-        """Whether the force launches evaluate each pair once (the FP64
-        default, see ``pair_once_block``)."""
+        """Whether the force launches evaluate each pair once (FP64 from ~1,200
+        bodies, mixed from 65,536; see ``pair_once_block``)."""
         return self.pair_once_block > 0
 
     @property
     def pair_once_block(self) -> int:
-        """Bodies per block of the pair-once force kernel (64 .. 4,096), or
-        0 when the force launches evaluate every ordered pair."""
+        """Block size of the pair-once force kernel (FP64 bodies, 64 ..
+        4,096; mixed stage entries, 128 .. 2,048), or 0 when the force
+        launches evaluate every ordered pair."""
         on = ctypes.c_int32()
         check(nbody_pair_once(self._ctx, ctypes.byref(on)), self._ctx)
         return int(on.value)
