@@ -197,9 +197,10 @@ __device__ __forceinline__ void msym_chunk(const float4 (*cb)[32], const f2 (&nx
 }  // namespace
 
 // MU_SMEM: the targets' mu in shared memory, which frees 8 registers in the
-// rotation loop (measured on GB300: faster with 2,048-entry blocks, 16-warp
-// CTAs: 1,048,576 bodies 395 against 403 ms per step; slower with 512-entry
-// blocks: 65,536 bodies 1.71 against 1.64 ms).
+// rotation loop.  Used with 2,048-entry blocks (16-warp CTAs, one per SM),
+// where it measured faster on GB300 (1,048,576 bodies: 395 against 403 ms
+// per step); with 512-entry blocks its 4 KB per CTA cost an SM its fourth
+// CTA (65,536 bodies: 1.71 against 1.64 ms), so they keep mu in registers.
 template <bool MU_SMEM>
 __global__ void __launch_bounds__(32 * kMsymMaxWarps, 1) force_msym_kernel(const MsymArgs a) {
   extern __shared__ __align__(16) unsigned char msym_smem[];
