@@ -372,9 +372,9 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
 //   measured on GB300, 1,031 bodies / 153 pairs 60.8 against 55.3 us per
 //   step, 1,283 bodies / 231 pairs 62.5 against 96.2).
 //   Mixed: for a largest system of at least kMsymMinBodies (measured on
-//   GB300: 65,536 bodies 1.68 against 1.82 ms per step, 1,048,576 bodies
-//   405 against 430 ms; 10,425 bodies 77 against 68 us, where the block
-//   pairs fill the SMs unevenly and the per-body kernel reads 82 rows), the
+//   GB300: 65,536 bodies 1.63 against 1.82 ms per step, 1,048,576 bodies
+//   395 against 430 ms; 10,425 bodies 75 against 68 us, where the
+//   per-body kernel reads 82 rows per body and does not overlap), the
 //   narrowest block (128 .. 2,048 entries) that leaves the largest system
 //   at most kMsymMaxRows rows per body (the per-body kernel reads them every
 //   step), if the rows fit in kSymRowLimit and the block pairs give at
