@@ -359,70 +359,14 @@ nbody_status build_work(nbody_ctx *c, Work &wk, const nbody_tiles &t, int occ, i
   return st;
 }
 
-// Bodies (FP64) or stage entries (mixed) per block of the pair-once force
-// kernels (sym.cu, sym_mixed.cu) for this context, or 0 where the
-// every-ordered-pair kernel runs: row shards and NBODY_FLAG_NO_SYM.  A body
-// has one partial row (24 B) per block of its system.  With
-// nbody_opts.pair_once_block = 0:
-//   FP64: 64 when every system has at most kSymMaxBodies (rows <= 1.6 GB at
-//   65,536), else the narrowest wide block (256 .. 4,096 bodies) whose rows
-//   fit in kSymRowBudget, else 4,096 if they fit in kSymRowLimit; used when
-//   the systems hold at least 1.5 block pairs per SM (with fewer, one CTA
-//   carries a system's whole sum and the stream-K kernel is faster:
-//   measured on GB300, 1,031 bodies / 153 pairs 60.8 against 55.3 us per
-//   step, 1,283 bodies / 231 pairs 62.5 against 96.2).
-//   Mixed: for a largest system of at least kMsymMinBodies (measured on
-//   GB300: 65,536 bodies 1.63 against 1.82 ms per step, 1,048,576 bodies
-//   395 against 430 ms; 10,425 bodies 75 against 68 us, where the
-//   per-body kernel reads 82 rows per body and does not overlap), the
-//   narrowest block (128 .. 2,048 entries) that leaves the largest system
-//   at most kMsymMaxRows rows per body (the per-body kernel reads them every
-//   step), if the rows fit in kSymRowLimit and the block pairs give at
-//   least 8 warps per SM (each warp holds 128 targets).
-// A requested block size is used as asked if its rows fit in kSymRowLimit
-// (checked at nbody_init).
-constexpr int64_t kSymRowBudget = int64_t(2) << 30;
-constexpr int64_t kSymRowLimit = int64_t(16) << 30;
-constexpr int64_t kMsymMaxRows = 128;
-constexpr int64_t kMsymMinBodies = 65536;
-
-int64_t sym_rows(const nbody_ctx *c, int64_t B) {
-  int64_t rows = 1;
-  for (int64_t s = 0; s < c->n_sys; ++s) rows = std::max(rows, (c->offsets[s + 1] - c->offsets[s] + B - 1) / B);
-  return rows;
-}
-
-int64_t sym_row_bytes(const nbody_ctx *c, int64_t B) {
-  return sym_rows(c, B) * 3 * static_cast<int64_t>(sizeof(double)) * static_cast<int64_t>(c->N);
-}
-
+// Block size of the pair-once force kernels for this context
+// (pair_once_plan.h), or 0 where the every-ordered-pair kernel runs: row
+// shards, NBODY_FLAG_NO_SYM, and the cases pair_once_block turns down.
 int sym_block(const nbody_ctx *c) {
   if (c->sh_world > 0 || (c->o.flags & NBODY_FLAG_NO_SYM)) return 0;
-  if (c->o.pair_once_block > 0) return c->o.pair_once_block;
-  int64_t nmax = 0;
-  for (int64_t s = 0; s < c->n_sys; ++s) nmax = std::max(nmax, c->offsets[s + 1] - c->offsets[s]);
-  auto pairs_of = [&](int64_t B) {
-    int64_t pairs = 0;
-    for (int64_t s = 0; s < c->n_sys; ++s) {
-      const int64_t nb = (c->offsets[s + 1] - c->offsets[s] + B - 1) / B;
-      pairs += nb * (nb + 1) / 2;
-    }
-    return pairs;
-  };
-  if (c->o.precision == NBODY_MIXED) {
-    if (nmax < kMsymMinBodies) return 0;
-    int64_t B = 32 * nb::kMsymMinTiles;
-    while (B < 32 * nb::kMsymMaxTiles && sym_rows(c, B) > kMsymMaxRows) B *= 2;
-    if (sym_row_bytes(c, B) > kSymRowLimit) return 0;
-    return pairs_of(B) * (B / 128) >= 8 * static_cast<int64_t>(c->nsm) ? static_cast<int>(B) : 0;
-  }
-  int64_t B = nb::kSymBlock;
-  if (nmax > nb::kSymMaxBodies) {
-    B = 32 * nb::kSymWideMinTiles;
-    while (B < 32 * nb::kSymWideMaxTiles && sym_row_bytes(c, B) > kSymRowBudget) B *= 2;
-    if (sym_row_bytes(c, B) > kSymRowLimit) return 0;
-  }
-  return 2 * pairs_of(B) >= 3 * static_cast<int64_t>(c->nsm) ? static_cast<int>(B) : 0;
+  std::vector<int64_t> sizes(static_cast<size_t>(c->n_sys));
+  for (int64_t s = 0; s < c->n_sys; ++s) sizes[s] = c->offsets[s + 1] - c->offsets[s];
+  return nb::pair_once_block(sizes, c->o.precision == NBODY_MIXED, c->nsm, c->o.pair_once_block);
 }
 
 // Work tables of the pair-once kernels: the block pairs (I, J), I <= J, of
@@ -1289,9 +1233,9 @@ nbody_status nbody_init(nbody_ctx **out, int64_t n_systems, const int64_t *offse
     }
     int64_t rows = 1;
     for (int64_t s = 0; s < n_systems; ++s) rows = std::max(rows, (offsets[s + 1] - offsets[s] + B - 1) / B);
-    if (rows > 65535 || rows * 3 * static_cast<int64_t>(sizeof(double)) * offsets[n_systems] > kSymRowLimit)
+    if (rows > 65535 || rows * 3 * static_cast<int64_t>(sizeof(double)) * offsets[n_systems] > nb::kSymRowLimit)
       return fail(nullptr, NBODY_EINVAL, "pair_once_block %d: the partial rows would exceed %lld bytes", B,
-                  static_cast<long long>(kSymRowLimit));
+                  static_cast<long long>(nb::kSymRowLimit));
   }
 
   nbody_ctx *c = new (std::nothrow) nbody_ctx;

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pair_once_plan.h"
 #include "work_plan.h"
 
 namespace nb {
@@ -139,15 +140,7 @@ struct PrepArgs {
 };
 
 // FP64 force kernel with each pair once (sym.cu): work items are block
-// pairs (I, J), I <= J, of kSymBlock bodies of one system.
-constexpr int kSymBlock = 64;
-constexpr int kSymThreads = 64;        // two warps: one 32-body tile of block I each
-constexpr int kSymMaxBodies = 65536;   // per system, by default (the partial rows are [blocks][3][N])
-// Wide blocks of 32 T bodies (force_sym_wide_kernel) above that: T tiles.
-constexpr int kSymWideWarps = 4;
-constexpr int kSymWideThreads = 32 * kSymWideWarps;
-constexpr int kSymWideMinTiles = 8;    // 256 bodies
-constexpr int kSymWideMaxTiles = 128;  // 4,096 bodies (96 KB of shared sums)
+// pairs (I, J), I <= J, of one system; block sizes in pair_once_plan.h.
 struct SymArgs {
   const double4_32a *cur;  // staged sources (x, y, z, G m) per body
   double *partial;         // [blocks][3][N]: row J of a body of block I holds block J's pull
@@ -160,10 +153,7 @@ struct SymArgs {
 
 // Mixed force kernel with each pair once (sym_mixed.cu): block pairs (I, J),
 // I <= J, of 32 T stage entries of one system; a CTA of W = T / 4 warps per
-// item.
-constexpr int kMsymMinTiles = 4;   // 128 entries: one warp's four target tiles
-constexpr int kMsymMaxTiles = 64;  // 2,048 entries
-constexpr int kMsymMaxWarps = kMsymMaxTiles / 4;
+// item (pair_once_plan.h).
 struct MsymArgs {
   const float *cur;        // mixed stage (pair blocks of two entries)
   const float4 *boxes;     // [groups][2] widened boxes of the stage groups (box_kernel)
