@@ -22,7 +22,10 @@ an off-diagonal item meets every (target, source) pair exactly once; a
 diagonal item counts every unordered pair of distinct entries exactly once,
 for the target and for the reaction, and never an entry with itself; the
 reaction sums of a pair block sit, after 16 steps, in the lane the kernel
-folds them from.  A planted error in the schedule fails the checks.
+folds them from; and the item list gives every body exactly one value in
+each of its system's rows 0 .. blocks - 1 (ragged and exact block counts),
+which the per-body kernel adds in order.  A planted error in the schedule
+fails the checks.
 """
 from collections import Counter
 
@@ -147,3 +150,27 @@ def test_planted_schedule_errors_fail():
     _, seen = wide_fp64_item(8, diag=False)
     with pytest.raises(AssertionError):
         _check_diagonal(seen, 256)
+
+
+def item_rows(ns, B):
+    """The partial rows each body of one system receives from the items of
+    the pair-once kernels: the block pairs (I, J), I <= J, of blocks of B
+    bodies; block I's sums go to row J of its bodies, block J's to row I, a
+    diagonal item's (both sides) to row I."""
+    nb = (ns + B - 1) // B
+    got = Counter()
+    for I in range(nb):
+        for J in range(I, nb):
+            for body in range(I * B, min(ns, (I + 1) * B)):
+                got[(body, J)] += 1  # block I's sums (on a diagonal item, with block J's)
+            if I != J:
+                for body in range(J * B, min(ns, (J + 1) * B)):
+                    got[(body, I)] += 1
+    return nb, got
+
+
+@pytest.mark.parametrize("ns,B", [(1283, 64), (1536, 64), (10425, 256), (4096, 4096), (5003, 128), (129, 128)])
+def test_every_body_has_one_value_per_row(ns, B):
+    nb, got = item_rows(ns, B)
+    assert set(got) == {(body, row) for body in range(ns) for row in range(nb)}
+    assert set(got.values()) == {1}
