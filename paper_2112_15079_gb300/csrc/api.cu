@@ -1623,7 +1623,7 @@ nbody_status nbody_autotune(nbody_ctx *c, int32_t probe_steps, nbody_tiles *best
     if ((st = restore()) != NBODY_OK) return -1.0;
     return static_cast<double>(ms) / steps;
   };
-  // Round 1: every candidate once.  Round 2: the fastest few again, three
+  // First pass: every candidate once.  Second pass: the fastest few again, three
   // times each over 4x the steps, keeping each one's best: single short
   // probes of candidates a few percent apart pick the wrong one too often.
   std::vector<std::pair<double, size_t>> r1;
